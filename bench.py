@@ -1,0 +1,395 @@
+"""Benchmark of the 2DGRT secondary-ray hot path on synthetic workloads.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grt|reference]
+                    [--mode shade|train|serve] [--no-cpu-baseline]
+
+Default workload (mode "shade"): 300,000 SH surfels on 3 spheres, 2 tori, a box and a
+ground plane; an 800x800 G-buffer; 32 secondary rays per pixel by MIS (16 cosine / 8 GGX /
+8 environment) under a 512x256 log-normal HDR map with a sun; metallic GGX BRDF.  One
+step = in-place LBVH rebuild + traced primary G-buffer + fused sample/trace/shade of every
+pixel.  The metric is secondary rays per second (valid pixels x 32 / step time).
+
+Mode "train": 400x400, 16 rays/pixel (8/4/4) on the same scene, forward + adjoint of an
+L2 loss against a seeded target (shade_pixels + shade_backward).
+Mode "serve": the relight request loop (see paper_2607_22780_b300.serve).
+
+Under torchrun every rank renders its own frame (weak scaling, no data-path collective);
+ranks meet only at the barriers around the timed region and in the final max/sum.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SEED = 2607
+N_SURFELS = 300_000
+W_IMG = H_IMG = 800
+ALLOC = (16, 8, 8)
+ENV_W, ENV_H = 512, 256
+TRAIN_IMG = 400
+TRAIN_ALLOC = (8, 4, 4)
+REC_BYTES = 64      # packed surfel record
+NODE_BYTES = 64     # LBVH internal node
+SH_BYTES = 192      # 48 SH coefficients read per composited hit
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"grt_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_inputs(rank: int):
+    from paper_2607_22780_b300 import workloads as wl
+    sc = wl.scene_objects(N_SURFELS, seed=SEED)
+    cam = wl.camera_orbit(SEED + rank, W_IMG, H_IMG, 3.0)
+    env = wl.envmap_hdr(SEED + rank, ENV_W, ENV_H)
+    return sc, cam, env
+
+
+def cpu_oracle_sample(sc, cam, env, gb32, n_valid_pixels, budget_s=12.0):
+    """Time the FP64 oracle on a bounded pixel sample of the same frame (all host cores)."""
+    import oracle
+    valid = np.nonzero(gb32["valid"])[0]
+    rng = np.random.default_rng(0)
+    Nr = sum(ALLOC)
+    t0 = time.perf_counter()
+    pix = rng.choice(valid, size=4, replace=False).astype(np.int32)
+    oracle.shade_pixels(sc, gb32, env, *ALLOC, seed=SEED, pixels=pix)
+    t1 = time.perf_counter() - t0
+    n = int(max(4, min(len(valid), budget_s / max(t1 / 4, 1e-6))))
+    pix = rng.choice(valid, size=n, replace=False).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.shade_pixels(sc, gb32, env, *ALLOC, seed=SEED, pixels=pix)
+    dt = time.perf_counter() - t0
+    return {"value": n * Nr / dt, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} random valid pixels x {Nr} MIS rays of the 800x800 frame, 300k surfels, "
+                      f"FP64 brute force (every ray against every surfel), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2607_22780_b300 import workloads as wl
+    sc, cam, env = make_inputs(0)
+    # the oracle's own G-buffer of the same camera (only the sampled pixels matter)
+    gcam = wl.Camera(cam.eye, cam.target, cam.up, cam.tan_half_fovy, W_IMG, H_IMG)
+    t0 = time.perf_counter()
+    small = wl.Camera(cam.eye, cam.target, cam.up, cam.tan_half_fovy, 80, 80)
+    gb = oracle.gbuffer_f32(oracle.gbuffer(sc, small))
+    t_gb = time.perf_counter() - t0
+    steps = []
+    cb = None
+    for s in range(args.warmup + args.steps):
+        cb = cpu_oracle_sample(sc, small, env, gb, int(gb["valid"].sum()), budget_s=max(2.0, 60.0 / (args.steps + args.warmup)))
+        if s >= args.warmup:
+            steps.append(cb["value"])
+    value = float(np.median(steps))
+    cb["value"] = value
+    out = {"impl": "reference", "metric": "secondary_rays_per_s", "value": value, "unit": "rays/s",
+           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "mis_shade_300k_800x800_32spp (sampled pixels of an 80x80 view, same scene/map)",
+                      "surfels": N_SURFELS, "rays_per_pixel": sum(ALLOC), "alloc": list(ALLOC)},
+           "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "note": f"G-buffer of the sampled view took {t_gb:.1f} s"}
+    print(json.dumps(out), flush=True)
+
+
+def run_grt(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2607_22780_b300 import api, build as gbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if gbuild.stale():
+        raise RuntimeError("libgrt.so is missing or stale: run __graft_entry__.build() first")
+
+    sc, cam, env = make_inputs(rank)
+    # ---- device-resident inputs
+    S = api.Scene.from_workload(sc, device=dev)
+    E = api.Environment(torch.from_numpy(env).to(dev))
+    G = api.GBuffer.empty(W_IMG, H_IMG, cam.eye, device=dev)
+    P = W_IMG * H_IMG
+    outs = (torch.empty((P, 3), device=dev), torch.empty((P,), device=dev), torch.empty((P, 3), device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        S.rebuild()
+        api.gbuffer_primary(S, cam, out=G)
+        api.shade_pixels(S, G, E, *ALLOC, seed=SEED, outputs=outs)
+
+    step()
+    torch.cuda.synchronize()
+    n_valid = int(G.valid.sum().item())
+    R = n_valid * sum(ALLOC)
+    # kernel launches per step: rebuild 2 + 4 x 3 sort + hierarchy + records + refit; gbuffer 1; shade 1
+    launches_per_step = 2 + 12 + 3 + 1 + 1
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: per-step events, L2 flushed between steps (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        S.rebuild()
+        api.gbuffer_primary(S, cam, out=G)
+        kev[i][0].record(stream)
+        api.shade_pixels(S, G, E, *ALLOC, seed=SEED, outputs=outs)
+        kev[i][1].record(stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    shade_ms = [a.elapsed_time(b) for a, b in kev]
+    ms = float(np.mean(step_ms))
+    t_max = ms
+    rays_total = R
+    if world > 1:
+        tt = torch.tensor([ms, float(R)], device=dev, dtype=torch.float64)
+        mx = tt.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        t_max, rays_total = float(mx[0]), float(sm[1])
+    value = rays_total / (t_max * 1e-3)
+
+    # ---- algorithmic bytes of the dominant kernel (k_shade), from traversal counters
+    cnt = api.shade_count(S, G, E, *ALLOC, seed=SEED).cpu().numpy().astype(np.float64)
+    n_env = n_valid * ALLOC[2]
+    io = n_valid * (9 * 4 + 2 * 4 + 4 + 28) + n_env * (16 + 4 * (math.log2(ENV_H) + math.log2(ENV_W))) + \
+        (n_valid * sum(ALLOC)) * 16
+    alg_bytes = NODE_BYTES * cnt[0] + REC_BYTES * cnt[1] + SH_BYTES * cnt[2] + io
+    shade_s = float(np.mean(shade_ms)) * 1e-3
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / shade_s / 1e9
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        host = {k: pin(v) for k, v in sc.arrays().items()}
+        henv = pin(env)
+        hout = torch.empty((P, 7), dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * 4 for v in host.values()) + henv.numel() * 4
+        d2h = hout.numel() * 4
+        dev_in = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()}
+        denv = torch.empty(henv.shape, device=dev)
+        S2 = api.Scene(**dev_in)
+        E2 = api.Environment(denv)
+        G2 = api.GBuffer.empty(W_IMG, H_IMG, cam.eye, device=dev)
+        oc, ov, oi = torch.empty((P, 3), device=dev), torch.empty((P,), device=dev), torch.empty((P, 3), device=dev)
+
+        def e2e_step():
+            for k in host:
+                dev_in[k].copy_(host[k], non_blocking=True)
+            denv.copy_(henv, non_blocking=True)
+            S2.rebuild()
+            E2.update(denv)
+            api.gbuffer_primary(S2, cam, out=G2)
+            api.shade_pixels(S2, G2, E2, *ALLOC, seed=SEED, outputs=(oc, ov, oi))
+            hout[:, 0:3].copy_(oc, non_blocking=True)
+            hout[:, 3].copy_(ov, non_blocking=True)
+            hout[:, 4:7].copy_(oi, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b) / args.steps
+        e2e = {"value": R / (e_ms * 1e-3), "unit": "rays/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms}
+
+    # ---- fwd+bwd (training form) on the 400x400 / 16-ray configuration
+    fb = None
+    if not args.no_train:
+        fb = time_train(api, S, cam, E, dev, args)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gb32 = dict(pos=G.pos.cpu().numpy(), normal=G.normal.cpu().numpy(), albedo=G.albedo.cpu().numpy(),
+                    rough=G.rough.cpu().numpy(), metal=G.metal.cpu().numpy(), valid=G.valid.cpu().numpy(),
+                    eye=np.asarray(cam.eye, np.float32), W=W_IMG, H=H_IMG)
+        cpu = cpu_oracle_sample(sc, cam, env, gb32, n_valid)
+
+    if rank == 0:
+        out = {"metric": "secondary_rays_per_s", "value": value, "unit": "rays/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": "mis_shade_300k_800x800_32spp", "surfels": N_SURFELS,
+                          "image": [W_IMG, H_IMG], "rays_per_pixel": sum(ALLOC), "alloc_cos_ggx_env": list(ALLOC),
+                          "env": [ENV_W, ENV_H], "valid_pixels": n_valid, "rays_per_step": R,
+                          "step": "rebuild LBVH + primary G-buffer + MIS shade", "k": 16,
+                          "l2": "flushed between steps (256 MB write outside the timed events)",
+                          "parallelism": f"replicas x{world}"},
+               "gpu_launches": launches_per_step * args.steps,
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None, "kernel": "k_shade",
+                            "peak_kind": peak_kind,
+                            "alg_bytes_per_launch": alg_bytes, "kernel_ms": shade_s * 1e3,
+                            "per_ray": {"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R}},
+               "clocks": clk, "e2e": e2e, "fwd_bwd": fb, "cpu_baseline": cpu,
+               "wall_s_timed": t_wall}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def time_train(api, S, cam, E, dev, args):
+    import torch
+    from paper_2607_22780_b300 import workloads as wl
+    c = wl.Camera(cam.eye, cam.target, cam.up, cam.tan_half_fovy, TRAIN_IMG, TRAIN_IMG)
+    G = api.gbuffer_primary(S, c)
+    tgt = torch.from_numpy(wl.target_image(SEED, TRAIN_IMG, TRAIN_IMG).reshape(-1, 3)).to(dev)
+    grads = api.SurfelGrads.zeros(S)
+    P = TRAIN_IMG * TRAIN_IMG
+
+    def step():
+        col, vis, ind = api.shade_pixels(S, G, E, *TRAIN_ALLOC, seed=SEED)
+        dl = (col - tgt) * G.valid.unsqueeze(1).float()
+        for t_ in (grads.mu, grads.quat, grads.scale, grads.opacity, grads.color):
+            t_.zero_()
+        api.shade_backward(S, G, E, *TRAIN_ALLOC, SEED, dl.contiguous(), grads=grads)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fa, fb_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(1, args.steps)
+    a.record()
+    for _ in range(n):
+        step()
+    b.record()
+    fa.record()
+    for _ in range(n):
+        api.shade_pixels(S, G, E, *TRAIN_ALLOC, seed=SEED)
+    fb_.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / n
+    fms = fa.elapsed_time(fb_) / n
+    nv = int(G.valid.sum().item())
+    R = nv * sum(TRAIN_ALLOC)
+    return {"workload": "train_300k_400x400_16spp", "rays": R, "fwd_ms": fms, "fwd_bwd_ms": ms,
+            "fwd_rays_per_s": R / (fms * 1e-3), "fwd_bwd_rays_per_s": R / (ms * 1e-3)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="grt", choices=["grt", "reference"])
+    ap.add_argument("--mode", default="shade", choices=["shade", "serve"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.mode == "serve":
+        from paper_2607_22780_b300 import serve
+        serve.bench_main(args)
+    else:
+        run_grt(args)
+
+
+if __name__ == "__main__":
+    main()

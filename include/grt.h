@@ -1,0 +1,253 @@
+/*
+ * grt.h -- C ABI of libgrt: differentiable 2D Gaussian ray tracing (2DGRT) of secondary
+ * rays against 2D Gaussian surfels, with multiple-importance-sampled shading, for
+ * NVIDIA B300 (sm_103a).
+ *
+ * Paper: "IRGS++" (arXiv 2607.22780).  The operations below are the paper's
+ *   Trace(r_o, r_d) -> (c_rt, o_rt)                      Sec. III-B, Eq. 7-8
+ *   G-buffer {D, N, A, R, M} with normalised weights      Sec. III-C, Eq. 9
+ *   L_i = V L_dir + L_ind, (L_ind, 1-V) = Trace(x, w)     Eq. 10-11
+ *   c_pbr = (1/N_r) sum g(w)/q(w), MIS mixture q           Eq. 12-13, Sec. III-D
+ *   metallic microfacet BRDF                               Eq. 4-5
+ *   gradients through Trace                                Sec. III-B ("Trace operator")
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller, contiguous, row-major,
+ *     FP32 unless stated.  Host-side structs (grt_surfels, grt_trace_params, ...) are
+ *     read during the call only.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every call is
+ *     asynchronous on that stream unless stated.
+ *   - Return value: GRT_OK (0) or a GRT_ERR_* code; grt_last_error() gives the message
+ *     of the calling thread's last failure.  No call throws or aborts.
+ *   - Device-side anomalies (traversal stack overflow, non-finite inputs) set a status
+ *     word in the BVH that grt_bvh_status() reads back.
+ *   - Gradient outputs accumulate (+=) into caller-zeroed arrays.
+ */
+#ifndef GRT_H
+#define GRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRT_OK 0
+#define GRT_ERR_ARG 1         /* invalid argument (null pointer, bad size, bad enum) */
+#define GRT_ERR_OOM 2         /* device allocation failed                            */
+#define GRT_ERR_CUDA 3        /* a CUDA runtime call or kernel launch failed         */
+#define GRT_ERR_OVERFLOW 4    /* device status: traversal stack overflow             */
+#define GRT_ERR_TIMEOUT 5     /* a bounded device wait gave up                       */
+#define GRT_ERR_UNSUPPORTED 6 /* option not built in (e.g. k not in {4,8,16,32})     */
+
+/* Device status bits reported by grt_bvh_status(). */
+#define GRT_STATUS_STACK_OVERFLOW 1
+#define GRT_STATUS_NONFINITE 2
+#define GRT_STATUS_BAD_TREE 4   /* node reference out of range or walk longer than the tree */
+#define GRT_STATUS_BAD_INDEX 8  /* a pixel index outside the G-buffer was skipped            */
+
+/* Surfels (Sec. III-A "2D Gaussian splatting"; Sec. III-B "Bounding proxy").
+ * mu[n][3] centre; quat[n][4] rotation (w,x,y,z), any non-zero norm, normalised inside:
+ * the columns of R(q/|q|) are (t_u, t_v, n); scale[n][2] = (s_u, s_v) > 0;
+ * opacity[n] = o in (0,1]; color[n][color_dim]: color_dim 3 = RGB outgoing radiance,
+ * 48 = real SH degree 3 laid out [16 basis][3 channels], evaluated at the ray direction
+ * as max(0, SH + 0.5); albedo[n][3], rough[n], metal[n] feed only the primary G-buffer
+ * and may be NULL otherwise. */
+typedef struct {
+    int32_t n;
+    int32_t color_dim;
+    const float* mu;
+    const float* quat;
+    const float* scale;
+    const float* opacity;
+    const float* color;
+    const float* albedo;
+    const float* rough;
+    const float* metal;
+} grt_surfels;
+
+/* Trace parameters (Eq. 7-8).  A hit is admitted iff |n.d| >= eps_nd, tau in
+ * (t_min, t_max) and o*G >= alpha_min; alpha = min(o*G, alpha_max).  Hits are
+ * composited in ascending (tau, surfel id) and a ray stops after the hit that drops its
+ * transmittance below T_min.  k is the per-ray k-buffer size (4, 8, 16 or 32); results
+ * do not depend on k, only speed does.  Typical: 1/255, 0.99, 0.01, 3e38, 1e-4, 1e-6, 16. */
+typedef struct {
+    float alpha_min, alpha_max, t_min, t_max, T_min, eps_nd;
+    int32_t k;
+} grt_trace_params;
+
+typedef struct grt_bvh grt_bvh; /* opaque: LBVH nodes + packed surfel records (device) */
+
+typedef struct {
+    int32_t n_surfels;
+    int32_t n_nodes;        /* internal nodes, n_surfels - 1 */
+    size_t device_bytes;    /* bytes the BVH holds on the device */
+    float bounds[6];        /* scene AABB of the surfel bounds (lo xyz, hi xyz); valid after sync */
+} grt_bvh_info_t;
+
+/* Build a linear BVH (Morton codes of the cut-off-ellipse AABB centres, LSD radix
+ * sort, hierarchy from the sorted codes, bottom-up box refit) over the surfels.  Each
+ * surfel is bounded by the exact box of its alpha_min ellipse u^2+v^2 <= 2 ln(o/alpha_min)
+ * (the same region the icosahedron proxy of Eq. 6 encloses), padded for FP32.  Only
+ * params->alpha_min is read.  Allocates device memory; asynchronous on `stream`.
+ * *out stays valid until grt_bvh_destroy().  n == 0 is allowed (every ray misses). */
+int grt_build_bvh(const grt_surfels* surfels, const grt_trace_params* params, grt_bvh** out,
+                  void* stream);
+
+/* Recompute boxes and packed records after the surfel parameters changed, keeping the
+ * topology (the caller keeps n and color_dim).  Asynchronous on `stream`. */
+int grt_refit_bvh(grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                  void* stream);
+
+/* Full rebuild (Morton codes, sort, hierarchy, refit) into the existing BVH after the
+ * surfels moved; same n.  Sort scratch comes from the stream-ordered pool. */
+int grt_rebuild_bvh(grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                    void* stream);
+
+/* Synchronises the device, then frees the BVH.  NULL is ignored. */
+void grt_bvh_destroy(grt_bvh* bvh);
+
+int grt_bvh_info(const grt_bvh* bvh, grt_bvh_info_t* info);
+
+/* Synchronises `stream`, returns the device status bits accumulated since the last call
+ * in *status and clears them. */
+int grt_bvh_status(grt_bvh* bvh, int32_t* status, void* stream);
+
+/* Trace operator of Eq. 8 for R rays: ray_o[R][3], ray_d[R][3] (unit length) ->
+ * out_rgb[R][3] = c_rt, out_opacity[R] = o_rt.  Optional (may be NULL): out_hits
+ * [R][max_hits] ids of the composited surfels in order (-1 padded), out_nhits[R] number
+ * composited.  Uses the surfels the BVH was built or refit from (mu, quat, scale,
+ * opacity baked into the BVH; color read from `surfels` at composite time). */
+int grt_trace_forward(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                      const float* ray_o, const float* ray_d, int32_t R, float* out_rgb,
+                      float* out_opacity, int32_t* out_hits, int32_t max_hits, int32_t* out_nhits,
+                      void* stream);
+
+/* Gradient buffers, each accumulated (+=): mu[n][3], quat[n][4] (w.r.t. the
+ * unnormalised quaternion), scale[n][2], opacity[n], color[n][color_dim].  Any pointer
+ * may be NULL to skip that parameter. */
+typedef struct {
+    float* mu;
+    float* quat;
+    float* scale;
+    float* opacity;
+    float* color;
+} grt_grads;
+
+/* Adjoint of Eq. 8 for R rays given dL/dc_rt (dL_drgb[R][3]) and dL/do_rt
+ * (dL_dopacity[R]; may be NULL).  Hit lists are recomputed, never stored. */
+int grt_trace_backward(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                       const float* ray_o, const float* ray_d, int32_t R, const float* dL_drgb,
+                       const float* dL_dopacity, const grt_grads* grads, void* stream);
+
+/* Primary G-buffer (Eq. 9, traced along camera rays instead of rasterised): camera =
+ * host array {eye xyz, target xyz, up xyz, tan(fovy/2)}, pinhole, pixel centres, row 0
+ * at the top.  Per pixel p = y*W + x: pos[p][3] = eye + D d, normal[p][3] = normalised
+ * blend of camera-facing surfel normals, albedo[p][3], rough[p], metal[p], alpha[p] =
+ * o_rt, depth[p] = D, valid[p] = alpha >= 0.5.  Invalid pixels hold zeros.  Needs
+ * albedo/rough/metal in `surfels`. */
+int grt_gbuffer_primary(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                        const float camera[10], int32_t W, int32_t H, float* pos, float* normal,
+                        float* albedo, float* rough, float* metal, float* alpha, float* depth,
+                        int32_t* valid, void* stream);
+
+/* Environment map (Eq. 10, L_dir): equirectangular rgb[H][W][3]; texel (row, col)
+ * spans theta in [pi row/H, pi (row+1)/H] from +y and phi in [2 pi col/W, 2 pi (col+1)/W]
+ * about +y, direction (sin t sin p, cos t, sin t cos p); nearest-texel lookup.
+ * `tables` is a device buffer of grt_env_tables_bytes(W, H) bytes filled by
+ * grt_env_prepare(): texel radiance with its selection probability and the FP32
+ * marginal/conditional CDFs of the luminance distribution (environment proposal p_e of
+ * Sec. III-D). */
+typedef struct {
+    int32_t W, H;
+    const void* tables;
+} grt_envmap;
+
+size_t grt_env_tables_bytes(int32_t W, int32_t H);
+int grt_env_prepare(const float* rgb, int32_t W, int32_t H, void* tables, void* stream);
+
+/* G-buffer consumed by shading (Sec. III-C "Shading state"): device arrays over W*H
+ * pixels as written by grt_gbuffer_primary(); eye = camera position (host values). */
+typedef struct {
+    const float* pos;
+    const float* normal;
+    const float* albedo;
+    const float* rough;
+    const float* metal;
+    const int32_t* valid;
+    float eye[3];
+    int32_t W, H;
+} grt_gbuffer;
+
+/* MIS allocation (Sec. III-D, Eq. 13): sample j of a pixel is cosine for j < n_cos,
+ * GGX visible-normal for j < n_cos + n_ggx, environment otherwise; N_r = n_cos + n_ggx +
+ * n_env <= 1024.  brdf: 0 = Lambert a/pi, 1 = metallic microfacet (Eq. 4-5).  Random
+ * numbers: Philox4x32-10 with key (seed lo, seed hi) and counter (pixel index, j, 0, 0). */
+typedef struct {
+    int32_t n_cos, n_ggx, n_env;
+    int32_t brdf;
+    uint64_t seed;
+} grt_sampling;
+
+/* Shade pixels (Eq. 13): out_color[i][3] = (1/N_r) sum g/q, out_vis[i] = (1/N_r) sum V,
+ * out_ind[i][3] = (1/N_r) sum L_ind for i < n_pixels, pixel index pixel_list[i]
+ * (NULL = all W*H pixels in order).  Samples below the horizon count V = L_ind = 0.
+ * out_vis / out_ind may be NULL. */
+int grt_shade_pixels(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                     const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
+                     const int32_t* pixel_list, int32_t n_pixels, float* out_color, float* out_vis,
+                     float* out_ind, void* stream);
+
+/* Adjoint of grt_shade_pixels with respect to the surfels, given dL_dcolor[n_pixels][3]
+ * and optional dL_dvis[n_pixels], dL_dind[n_pixels][3] (NULL = 0).  Regenerates the same
+ * samples and recomputes every hit list. */
+int grt_shade_backward(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                       const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
+                       const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
+                       const float* dL_dvis, const float* dL_dind, const grt_grads* grads,
+                       void* stream);
+
+/* One shading request of a batch (same meaning as the grt_shade_pixels arguments). */
+typedef struct {
+    const grt_bvh* bvh;
+    const grt_surfels* surfels;
+    grt_gbuffer gbuffer;
+    grt_envmap env;
+    grt_sampling sampling;
+    const int32_t* pixel_list;
+    int32_t n_pixels;
+    float* out_color;
+    float* out_vis;
+    float* out_ind;
+} grt_shade_request;
+
+#define GRT_MAX_BATCH 48
+
+/* Shade up to GRT_MAX_BATCH requests (possibly on different scenes, environment maps,
+ * resolutions and sample counts) in ONE persistent launch whose warps pull pixel groups
+ * of all requests from a shared work counter.  Each request's outputs are bit-identical
+ * to shading it alone with grt_shade_pixels.  `work_counter` is a caller-owned device
+ * int32 that the call resets on `stream`. */
+int grt_shade_batch(const grt_shade_request* requests, int32_t n_requests,
+                    const grt_trace_params* params, int32_t* work_counter, void* stream);
+
+/* Performance counters of one grt_trace_forward-style pass (for roofline accounting):
+ * counts of internal nodes visited, surfel records tested and hits composited, summed
+ * over all rays, written to counters[3] (device, int64, accumulated). */
+int grt_trace_count(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                    const float* ray_o, const float* ray_d, int32_t R, long long* counters,
+                    void* stream);
+
+/* Same counters for one grt_shade_pixels pass over the given pixels (no image output). */
+int grt_shade_count(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                    const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
+                    const int32_t* pixel_list, int32_t n_pixels, long long* counters, void* stream);
+
+const char* grt_last_error(void);
+const char* grt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRT_H */

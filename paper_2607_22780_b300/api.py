@@ -1,0 +1,354 @@
+"""Python API over libgrt: torch tensors in, torch tensors out, every step in CUDA.
+
+PyTorch provides device memory and streams only; each function below marshals its
+arguments and makes exactly one libgrt call (include/grt.h) on the current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional
+
+import torch
+
+from . import _lib as L
+
+DEFAULT_PARAMS = dict(alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=0.01, t_max=3.0e38, T_min=1e-4,
+                      eps_nd=1e-6, k=16)
+
+
+def trace_params(**kw) -> L.TraceParams:
+    p = dict(DEFAULT_PARAMS)
+    p.update({k: v for k, v in kw.items() if v is not None})
+    return L.TraceParams(*[float(p[k]) for k in ("alpha_min", "alpha_max", "t_min", "t_max", "T_min", "eps_nd")],
+                         int(p["k"]))
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else t.data_ptr()
+
+
+def _dev(t, dtype=torch.float32, name="tensor", shape=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+class Scene:
+    """Surfels resident on the device plus their LBVH (grt_build_bvh).
+
+    Tensors: mu[N,3], quat[N,4] (w,x,y,z), scale[N,2], opacity[N], color[N,3|48],
+    albedo[N,3], rough[N], metal[N]; float32, contiguous, on one CUDA device.
+    """
+
+    def __init__(self, mu, quat, scale, opacity, color, albedo=None, rough=None, metal=None, params=None,
+                 stream=None):
+        n = int(mu.shape[0])
+        self.n = n
+        self.mu = _dev(mu, name="mu", shape=(n, 3))
+        self.quat = _dev(quat, name="quat", shape=(n, 4))
+        self.scale = _dev(scale, name="scale", shape=(n, 2))
+        self.opacity = _dev(opacity, name="opacity", shape=(n,))
+        self.color = _dev(color, name="color")
+        if self.color.shape[0] != n or self.color.shape[1] not in (3, 48):
+            raise ValueError("color must be [N,3] or [N,48]")
+        self.albedo = _dev(albedo, name="albedo", shape=(n, 3))
+        self.rough = _dev(rough, name="rough", shape=(n,))
+        self.metal = _dev(metal, name="metal", shape=(n,))
+        self.params = params if params is not None else trace_params()
+        self._bvh = C.c_void_p(None)
+        self._lib = L.load()
+        L.check(self._lib.grt_build_bvh(C.byref(self.surfels()), C.byref(self.params), C.byref(self._bvh),
+                                        _stream(stream)))
+
+    @staticmethod
+    def from_workload(sc, device="cuda", params=None) -> "Scene":
+        t = lambda a: torch.from_numpy(a).to(device).contiguous()
+        return Scene(t(sc.mu), t(sc.quat), t(sc.scale), t(sc.opacity), t(sc.color), t(sc.albedo), t(sc.rough),
+                     t(sc.metal), params=params)
+
+    @property
+    def color_dim(self) -> int:
+        return int(self.color.shape[1])
+
+    @property
+    def handle(self):
+        return self._bvh
+
+    def surfels(self) -> L.Surfels:
+        return L.Surfels(self.n, self.color_dim, _ptr(self.mu), _ptr(self.quat), _ptr(self.scale),
+                         _ptr(self.opacity), _ptr(self.color), _ptr(self.albedo), _ptr(self.rough),
+                         _ptr(self.metal))
+
+    def refit(self, stream=None):
+        L.check(self._lib.grt_refit_bvh(self._bvh, C.byref(self.surfels()), C.byref(self.params),
+                                        _stream(stream)))
+
+    def rebuild(self, stream=None):
+        """Full LBVH rebuild in place (same surfel count)."""
+        L.check(self._lib.grt_rebuild_bvh(self._bvh, C.byref(self.surfels()), C.byref(self.params),
+                                          _stream(stream)))
+
+    def info(self) -> dict:
+        i = L.BvhInfo()
+        L.check(self._lib.grt_bvh_info(self._bvh, C.byref(i)))
+        return dict(n_surfels=i.n_surfels, n_nodes=i.n_nodes, device_bytes=i.device_bytes, bounds=list(i.bounds))
+
+    def status(self, stream=None) -> int:
+        s = C.c_int32(0)
+        L.check(self._lib.grt_bvh_status(self._bvh, C.byref(s), _stream(stream)))
+        return s.value
+
+    def close(self):
+        if self._bvh:
+            self._lib.grt_bvh_destroy(self._bvh)
+            self._bvh = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trace_forward(scene: Scene, ray_o, ray_d, params=None, max_hits: int = 0, stream=None):
+    """c_rt[R,3], o_rt[R] (Eq. 8); with max_hits > 0 also hits[R,max_hits], nhits[R]."""
+    R = int(ray_o.shape[0])
+    _dev(ray_o, name="ray_o", shape=(R, 3))
+    _dev(ray_d, name="ray_d", shape=(R, 3))
+    dev = ray_o.device
+    rgb = torch.empty((R, 3), device=dev)
+    op = torch.empty((R,), device=dev)
+    hits = torch.empty((R, max_hits), device=dev, dtype=torch.int32) if max_hits > 0 else None
+    nh = torch.empty((R,), device=dev, dtype=torch.int32) if max_hits > 0 else None
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_trace_forward(scene.handle, C.byref(scene.surfels()), C.byref(p), _ptr(ray_o),
+                                       _ptr(ray_d), R, _ptr(rgb), _ptr(op), _ptr(hits), max_hits, _ptr(nh),
+                                       _stream(stream)))
+    return (rgb, op, hits, nh) if max_hits > 0 else (rgb, op)
+
+
+@dataclasses.dataclass
+class SurfelGrads:
+    mu: torch.Tensor
+    quat: torch.Tensor
+    scale: torch.Tensor
+    opacity: torch.Tensor
+    color: torch.Tensor
+
+    @staticmethod
+    def zeros(scene: Scene) -> "SurfelGrads":
+        z = lambda t: torch.zeros_like(t)
+        return SurfelGrads(z(scene.mu), z(scene.quat), z(scene.scale), z(scene.opacity), z(scene.color))
+
+    def struct(self) -> L.Grads:
+        return L.Grads(_ptr(self.mu), _ptr(self.quat), _ptr(self.scale), _ptr(self.opacity), _ptr(self.color))
+
+
+def trace_backward(scene: Scene, ray_o, ray_d, dL_drgb, dL_dopacity=None, grads: Optional[SurfelGrads] = None,
+                   params=None, stream=None) -> SurfelGrads:
+    R = int(ray_o.shape[0])
+    _dev(ray_o, name="ray_o", shape=(R, 3))
+    _dev(ray_d, name="ray_d", shape=(R, 3))
+    _dev(dL_drgb, name="dL_drgb", shape=(R, 3))
+    _dev(dL_dopacity, name="dL_dopacity", shape=(R,))
+    g = grads if grads is not None else SurfelGrads.zeros(scene)
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_trace_backward(scene.handle, C.byref(scene.surfels()), C.byref(p), _ptr(ray_o),
+                                        _ptr(ray_d), R, _ptr(dL_drgb), _ptr(dL_dopacity), C.byref(g.struct()),
+                                        _stream(stream)))
+    return g
+
+
+def trace_count(scene: Scene, ray_o, ray_d, params=None, stream=None):
+    """(internal nodes visited, surfel records tested, hits composited) summed over rays."""
+    R = int(ray_o.shape[0])
+    c = torch.zeros(3, dtype=torch.int64, device=ray_o.device)
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_trace_count(scene.handle, C.byref(scene.surfels()), C.byref(p), _ptr(ray_o), _ptr(ray_d),
+                                     R, _ptr(c), _stream(stream)))
+    return c
+
+
+# ----------------------------------------------------------------------------- G-buffer
+
+class GBuffer:
+    """Per-pixel shading state (Eq. 9): pos, normal, albedo, rough, metal, valid (+alpha, depth)."""
+
+    def __init__(self, W, H, eye, pos, normal, albedo, rough, metal, valid, alpha=None, depth=None):
+        self.W, self.H = int(W), int(H)
+        self.eye = tuple(float(x) for x in eye)
+        self.pos, self.normal, self.albedo = pos, normal, albedo
+        self.rough, self.metal, self.valid = rough, metal, valid
+        self.alpha, self.depth = alpha, depth
+
+    @staticmethod
+    def empty(W, H, eye, device="cuda") -> "GBuffer":
+        P = W * H
+        f = lambda *s: torch.empty(s, device=device)
+        return GBuffer(W, H, eye, f(P, 3), f(P, 3), f(P, 3), f(P), f(P),
+                       torch.empty(P, dtype=torch.int32, device=device), f(P), f(P))
+
+    @staticmethod
+    def from_arrays(d: dict, device="cuda") -> "GBuffer":
+        t = lambda a, dt=torch.float32: torch.as_tensor(a, dtype=dt).to(device).contiguous()
+        return GBuffer(d["W"], d["H"], d["eye"], t(d["pos"]), t(d["normal"]), t(d["albedo"]), t(d["rough"]),
+                       t(d["metal"]), t(d["valid"], torch.int32))
+
+    def struct(self) -> L.GBuffer:
+        P = self.W * self.H
+        for name, t, shp in (("pos", self.pos, (P, 3)), ("normal", self.normal, (P, 3)),
+                             ("albedo", self.albedo, (P, 3)), ("rough", self.rough, (P,)),
+                             ("metal", self.metal, (P,))):
+            _dev(t, name=name, shape=shp)
+        _dev(self.valid, dtype=torch.int32, name="valid", shape=(P,))
+        return L.GBuffer(_ptr(self.pos), _ptr(self.normal), _ptr(self.albedo), _ptr(self.rough),
+                         _ptr(self.metal), _ptr(self.valid), (C.c_float * 3)(*self.eye), self.W, self.H)
+
+
+def gbuffer_primary(scene: Scene, camera, params=None, out: Optional[GBuffer] = None, stream=None) -> GBuffer:
+    """Traced primary G-buffer for a workloads.Camera (eye, target, up, tan_half_fovy, width, height)."""
+    W, H = camera.width, camera.height
+    g = out if out is not None else GBuffer.empty(W, H, camera.eye, device=scene.mu.device)
+    cam = (C.c_float * 10)(*[float(x) for x in camera.as_array()])
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_gbuffer_primary(scene.handle, C.byref(scene.surfels()), C.byref(p), cam, W, H,
+                                         _ptr(g.pos), _ptr(g.normal), _ptr(g.albedo), _ptr(g.rough),
+                                         _ptr(g.metal), _ptr(g.alpha), _ptr(g.depth), _ptr(g.valid),
+                                         _stream(stream)))
+    return g
+
+
+# ----------------------------------------------------------------------------- environment
+
+class Environment:
+    """Equirectangular HDR map rgb[H,W,3] with its proposal tables (grt_env_prepare)."""
+
+    def __init__(self, rgb: torch.Tensor, stream=None):
+        H, W = int(rgb.shape[0]), int(rgb.shape[1])
+        _dev(rgb, name="rgb", shape=(H, W, 3))
+        self.rgb, self.W, self.H = rgb, W, H
+        lib = L.load()
+        nbytes = lib.grt_env_tables_bytes(W, H)
+        self.tables = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device=rgb.device)
+        L.check(lib.grt_env_prepare(_ptr(rgb), W, H, _ptr(self.tables), _stream(stream)))
+
+    def update(self, rgb: torch.Tensor, stream=None):
+        if tuple(rgb.shape) != (self.H, self.W, 3):
+            raise ValueError("update needs the same map size")
+        self.rgb = _dev(rgb, name="rgb")
+        L.check(L.load().grt_env_prepare(_ptr(rgb), self.W, self.H, _ptr(self.tables), _stream(stream)))
+
+    def struct(self) -> L.EnvMap:
+        return L.EnvMap(self.W, self.H, _ptr(self.tables))
+
+
+def sampling(n_cos, n_ggx, n_env, seed, brdf=1) -> L.Sampling:
+    return L.Sampling(int(n_cos), int(n_ggx), int(n_env), int(brdf), int(seed) & 0xFFFFFFFFFFFFFFFF)
+
+
+def shade_pixels(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
+                 params=None, outputs=None, stream=None):
+    """MIS shading (Eq. 13): colour[P,3], visibility[P], indirect[P,3] for the pixel list."""
+    n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
+    if pixels is not None:
+        _dev(pixels, dtype=torch.int32, name="pixels", shape=(n,))
+    dev = gb.pos.device
+    if outputs is None:
+        outputs = (torch.empty((n, 3), device=dev), torch.empty((n,), device=dev), torch.empty((n, 3), device=dev))
+    col, vis, ind = outputs
+    s = sampling(n_cos, n_ggx, n_env, seed, brdf)
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_shade_pixels(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
+                                      C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(col), _ptr(vis),
+                                      _ptr(ind), _stream(stream)))
+    return col, vis, ind
+
+
+def shade_count(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
+                params=None, stream=None):
+    n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
+    c = torch.zeros(3, dtype=torch.int64, device=gb.pos.device)
+    s = sampling(n_cos, n_ggx, n_env, seed, brdf)
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_shade_count(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
+                                     C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(c), _stream(stream)))
+    return c
+
+
+def shade_backward(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, dL_dcolor, dL_dvis=None,
+                   dL_dind=None, brdf=1, pixels=None, grads: Optional[SurfelGrads] = None, params=None,
+                   stream=None) -> SurfelGrads:
+    n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
+    _dev(dL_dcolor, name="dL_dcolor", shape=(n, 3))
+    _dev(dL_dvis, name="dL_dvis", shape=(n,))
+    _dev(dL_dind, name="dL_dind", shape=(n, 3))
+    g = grads if grads is not None else SurfelGrads.zeros(scene)
+    s = sampling(n_cos, n_ggx, n_env, seed, brdf)
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_shade_backward(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
+                                        C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(dL_dcolor),
+                                        _ptr(dL_dvis), _ptr(dL_dind), C.byref(g.struct()), _stream(stream)))
+    return g
+
+
+@dataclasses.dataclass
+class ShadeRequest:
+    """One request of a batched shading launch (grt_shade_batch)."""
+    scene: Scene
+    gbuffer: GBuffer
+    env: Environment
+    n_cos: int
+    n_ggx: int
+    n_env: int
+    seed: int
+    brdf: int = 1
+    pixels: Optional[torch.Tensor] = None
+    color: Optional[torch.Tensor] = None
+    vis: Optional[torch.Tensor] = None
+    ind: Optional[torch.Tensor] = None
+
+    @property
+    def n_pixels(self) -> int:
+        return int(self.pixels.shape[0]) if self.pixels is not None else self.gbuffer.W * self.gbuffer.H
+
+
+def shade_batch(requests, params=None, work_counter=None, stream=None):
+    """Shade several requests in one persistent launch; fills each request's outputs."""
+    if not requests:
+        return
+    if len(requests) > L.GRT_MAX_BATCH:
+        raise ValueError(f"at most {L.GRT_MAX_BATCH} requests per launch")
+    keep = []
+    arr = (L.ShadeRequest * len(requests))()
+    for i, r in enumerate(requests):
+        n = r.n_pixels
+        dev = r.gbuffer.pos.device
+        if r.color is None:
+            r.color = torch.empty((n, 3), device=dev)
+        sf = r.scene.surfels()
+        keep.append(sf)
+        arr[i] = L.ShadeRequest(r.scene.handle, C.pointer(sf), r.gbuffer.struct(), r.env.struct(),
+                                sampling(r.n_cos, r.n_ggx, r.n_env, r.seed, r.brdf), _ptr(r.pixels), n,
+                                _ptr(r.color), _ptr(r.vis), _ptr(r.ind))
+    if work_counter is None:
+        work_counter = torch.zeros(1, dtype=torch.int32, device=requests[0].gbuffer.pos.device)
+    p = params if params is not None else requests[0].scene.params
+    L.check(L.load().grt_shade_batch(arr, len(requests), C.byref(p), _ptr(work_counter), _stream(stream)))
+
+
+def version() -> str:
+    return L.load().grt_version().decode()

@@ -1,0 +1,319 @@
+// backward.cu -- grt_trace_backward / grt_shade_backward: adjoint of the Trace operator
+// (Eq. 8) and of the MIS estimate (Eq. 13) with respect to the surfels.
+//
+// Per ray, with adjoints Gc = dL/dc_rt and Go = dL/do_rt, composited hits k = 1..K,
+// T_k the transmittance before hit k, T_f after the last one:
+//   dL/dc_k     = Gc T_k a_k
+//   dL/da_k     = Gc . (T_k c_k - S_k / (1 - a_k)) + Go T_f / (1 - a_k),
+//                 S_k = sum_{j>k} T_j a_j c_j = c_rt - sum_{j<=k} T_j a_j c_j
+// then a = o G (zero when clamped at alpha_max), G = exp(-(u^2+v^2)/2),
+// u = (p - mu).t_u / s_u, v = (p - mu).t_v / s_v, p = o_ray + tau d,
+// tau = n.(mu - o_ray)/(n.d), into mu, the quaternion through R(q/|q|), s_u, s_v, o and
+// the colour (RGB or SH coefficients, zero where max(0, .) clamps).
+//
+// The hit list is never stored: a first traversal gives c_rt and T_f, a second replays
+// the same (tau, id) sequence and scatters gradients with vector atomics.
+#include "common_args.cuh"
+#include "shade.cuh"
+
+namespace grt {
+namespace {
+
+struct GradPtrs {
+    float *mu, *quat, *scale, *opacity, *color;
+};
+
+struct AdjointVisitor {
+    const float *mu, *quat, *scale, *opacity, *color;
+    int cdim;
+    f3 o, d;
+    float Gc[3], Go, Tf;
+    float crt[3];    // total c_rt from the first pass
+    float Cacc[3];   // running sum_{j<=k} T_j a_j c_j
+    float alpha_max;
+    GradPtrs g;
+
+    __device__ __forceinline__ void composite(int, int id, float tau, float alpha, float Tb) {
+        // colour of the hit and, for SH, which channels are live
+        float Y[16];
+        float c[3];
+        bool live[3] = {true, true, true};
+        if (cdim == 3) {
+            c[0] = __ldg(color + 3 * (size_t)id);
+            c[1] = __ldg(color + 3 * (size_t)id + 1);
+            c[2] = __ldg(color + 3 * (size_t)id + 2);
+        } else {
+            sh_basis(d.x, d.y, d.z, Y);
+            const float4* s = reinterpret_cast<const float4*>(color + 48 * (size_t)id);
+            float acc[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                float4 v = __ldg(s + q);
+                float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) acc[(4 * q + t) % 3] = fmaf(e[t], Y[(4 * q + t) / 3], acc[(4 * q + t) % 3]);
+            }
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                live[ch] = acc[ch] > 0.f;
+                c[ch] = fmaxf(acc[ch], 0.f);
+            }
+        }
+        float w = Tb * alpha;
+        float inv1a = 1.f / (1.f - alpha);
+        float dLda = Go * Tf * inv1a;
+        float dLdc[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            Cacc[ch] = fmaf(w, c[ch], Cacc[ch]);
+            float S = crt[ch] - Cacc[ch];
+            dLda = fmaf(Gc[ch], fmaf(Tb, c[ch], -S * inv1a), dLda);
+            dLdc[ch] = Gc[ch] * w;
+        }
+        if (g.color) {
+            if (cdim == 3) {
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) atomicAdd(g.color + 3 * (size_t)id + ch, dLdc[ch]);
+            } else {
+                float4* gs = reinterpret_cast<float4*>(g.color + 48 * (size_t)id);
+                float m0 = live[0] ? dLdc[0] : 0.f, m1 = live[1] ? dLdc[1] : 0.f, m2 = live[2] ? dLdc[2] : 0.f;
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    float e[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        int idx = 4 * q + t, ch = idx % 3;
+                        e[t] = (ch == 0 ? m0 : (ch == 1 ? m1 : m2)) * Y[idx / 3];
+                    }
+                    atomicAdd(gs + q, make_float4(e[0], e[1], e[2], e[3]));
+                }
+            }
+        }
+        // geometry of the hit
+        float op = __ldg(opacity + id);
+        float4 q = make_float4(__ldg(quat + 4 * (size_t)id), __ldg(quat + 4 * (size_t)id + 1),
+                               __ldg(quat + 4 * (size_t)id + 2), __ldg(quat + 4 * (size_t)id + 3));
+        float ql = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+        float iql = 1.f / ql;
+        float qw = q.x * iql, qx = q.y * iql, qy = q.z * iql, qz = q.w * iql;
+        f3 tu = mk3(1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy + qw * qz), 2.f * (qx * qz - qw * qy));
+        f3 tv = mk3(2.f * (qx * qy - qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz + qw * qx));
+        f3 n = mk3(2.f * (qx * qz + qw * qy), 2.f * (qy * qz - qw * qx), 1.f - 2.f * (qx * qx + qy * qy));
+        float su = __ldg(scale + 2 * (size_t)id), sv = __ldg(scale + 2 * (size_t)id + 1);
+        f3 m = mk3(__ldg(mu + 3 * (size_t)id), __ldg(mu + 3 * (size_t)id + 1), __ldg(mu + 3 * (size_t)id + 2));
+        f3 dp = mk3(fmaf(tau, d.x, o.x) - m.x, fmaf(tau, d.y, o.y) - m.y, fmaf(tau, d.z, o.z) - m.z);
+        float u = dot3(dp, tu) / su, v = dot3(dp, tv) / sv;
+        float G = __expf(-0.5f * fmaf(u, u, v * v));
+        if (op * G > alpha_max) return;  // clamped: alpha does not depend on the geometry
+        if (g.opacity) atomicAdd(g.opacity + id, dLda * G);
+        float dLdu = -dLda * alpha * u, dLdv = -dLda * alpha * v;
+        if (g.scale)
+            atomicAdd(reinterpret_cast<float2*>(g.scale + 2 * (size_t)id), make_float2(-dLdu * u / su, -dLdv * v / sv));
+        float nd = dot3(n, d), tud = dot3(tu, d), tvd = dot3(tv, d);
+        float au = dLdu / su, av = dLdv / sv;
+        float kn = (au * tud + av * tvd) / nd;
+        if (g.mu) {
+            atomicAdd(g.mu + 3 * (size_t)id, kn * n.x - au * tu.x - av * tv.x);
+            atomicAdd(g.mu + 3 * (size_t)id + 1, kn * n.y - au * tu.y - av * tv.y);
+            atomicAdd(g.mu + 3 * (size_t)id + 2, kn * n.z - au * tu.z - av * tv.z);
+        }
+        if (g.quat) {
+            // dL/dR columns: t_u -> dp au, t_v -> dp av, n -> -dp kn
+            float G00 = dp.x * au, G10 = dp.y * au, G20 = dp.z * au;
+            float G01 = dp.x * av, G11 = dp.y * av, G21 = dp.z * av;
+            float G02 = -dp.x * kn, G12 = -dp.y * kn, G22 = -dp.z * kn;
+            float gw = 2.f * (-qz * G01 + qy * G02 + qz * G10 - qx * G12 - qy * G20 + qx * G21);
+            float gx = 2.f * (qy * G01 + qz * G02 + qy * G10 - 2.f * qx * G11 - qw * G12 + qz * G20 + qw * G21 -
+                              2.f * qx * G22);
+            float gy = 2.f * (-2.f * qy * G00 + qx * G01 + qw * G02 + qx * G10 + qz * G12 - qw * G20 + qz * G21 -
+                              2.f * qy * G22);
+            float gz = 2.f * (-2.f * qz * G00 - qw * G01 + qx * G02 + qw * G10 - 2.f * qz * G11 + qy * G12 + qx * G20 +
+                              qy * G21);
+            float qd = qw * gw + qx * gx + qy * gy + qz * gz;
+            atomicAdd(reinterpret_cast<float4*>(g.quat + 4 * (size_t)id),
+                      make_float4((gw - qw * qd) * iql, (gx - qx * qd) * iql, (gy - qy * qd) * iql, (gz - qz * qd) * iql));
+        }
+    }
+    __device__ __forceinline__ void finish(float) {}
+};
+
+template <int K>
+__device__ __forceinline__ void ray_adjoint(const DevBvh& bvh, const TraceParams& P, const grt_surfels& s, f3 o, f3 d,
+                                            const float Gc[3], float Go, const GradPtrs& g) {
+    if (Gc[0] == 0.f && Gc[1] == 0.f && Gc[2] == 0.f && Go == 0.f) return;
+    RayState r = make_ray(o, d);
+    Counters cnt{0, 0, 0};
+    ColourVisitor fwd(s.color, s.color_dim, d, nullptr, 0);
+    trace_ray<K, false>(bvh, r, P, fwd, cnt);
+    if (fwd.nh == 0) return;
+    AdjointVisitor adj;
+    adj.mu = s.mu;
+    adj.quat = s.quat;
+    adj.scale = s.scale;
+    adj.opacity = s.opacity;
+    adj.color = s.color;
+    adj.cdim = s.color_dim;
+    adj.o = o;
+    adj.d = d;
+    adj.Go = Go;
+    adj.Tf = fwd.T;
+    adj.alpha_max = P.alpha_max;
+    adj.g = g;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        adj.Gc[c] = Gc[c];
+        adj.crt[c] = fwd.c[c];
+        adj.Cacc[c] = 0.f;
+    }
+    trace_ray<K, false>(bvh, r, P, adj, cnt);
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_trace_backward(DevBvh bvh, TraceParams P, grt_surfels s,
+                                                        const float* __restrict__ ro, const float* __restrict__ rd, int R,
+                                                        const float* __restrict__ dc, const float* __restrict__ dop,
+                                                        GradPtrs g) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R) return;
+    f3 o = mk3(ro[3 * (size_t)i], ro[3 * (size_t)i + 1], ro[3 * (size_t)i + 2]);
+    f3 d = mk3(rd[3 * (size_t)i], rd[3 * (size_t)i + 1], rd[3 * (size_t)i + 2]);
+    float Gc[3] = {dc[3 * (size_t)i], dc[3 * (size_t)i + 1], dc[3 * (size_t)i + 2]};
+    float Go = dop ? dop[i] : 0.f;
+    ray_adjoint<K>(bvh, P, s, o, d, Gc, Go, g);
+}
+
+struct ShadeBwd {
+    DevBvh bvh;
+    grt_surfels s;
+    GbufDev gb;
+    EnvDev env;
+    Sampling S;
+    const int* pixel_list;
+    int n_pixels;
+    const float *dcol, *dvis, *dind;
+    int G, spl;
+};
+
+template <int K>
+__global__ void __launch_bounds__(128) k_shade_backward(const __grid_constant__ ShadeBwd J, TraceParams P, GradPtrs g) {
+    const int lane = threadIdx.x & 31;
+    const int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int G = J.G;
+    const int slot = lane / G, sub = lane - slot * G;
+    const int li = u * (32 / G) + slot;
+    if (li >= J.n_pixels) return;
+    const int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+    if ((unsigned)pix >= (unsigned)(J.gb.W * J.gb.H)) {
+        atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
+        return;
+    }
+    if (!__ldg(J.gb.valid + pix)) return;
+    const int Nr = J.S.n_cos + J.S.n_ggx + J.S.n_env;
+    const float inv = 1.f / (float)Nr;
+    float dc[3] = {J.dcol[3 * (size_t)li] * inv, J.dcol[3 * (size_t)li + 1] * inv, J.dcol[3 * (size_t)li + 2] * inv};
+    float dv = J.dvis ? J.dvis[li] * inv : 0.f;
+    float di[3] = {0.f, 0.f, 0.f};
+    if (J.dind) {
+        di[0] = J.dind[3 * (size_t)li] * inv;
+        di[1] = J.dind[3 * (size_t)li + 1] * inv;
+        di[2] = J.dind[3 * (size_t)li + 2] * inv;
+    }
+    PixelState ps = load_pixel(J.gb, pix);
+    for (int m = 0; m < J.spl; ++m) {
+        int j = sub + m * G;
+        if (j >= Nr) break;
+        f3 w;
+        if (!draw_direction(J.S, J.env, ps, pix, j, &w)) continue;
+        SampleWeight sw = sample_weight(J.S, J.env, ps, w);
+        float Gc[3], Go = -dv;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Gc[c] = fmaf(dc[c], sw.g[c], di[c]);
+            Go = fmaf(-dc[c] * sw.g[c], sw.L[c], Go);
+        }
+        ray_adjoint<K>(J.bvh, P, J.s, ps.x, w, Gc, Go, g);
+    }
+}
+
+}  // namespace
+}  // namespace grt
+
+using namespace grt;
+
+static int check_grads(const grt_grads* g, const grt_surfels* s) {
+    if (!g) return set_error(GRT_ERR_ARG, "grads is NULL");
+    if (g->quat && ((uintptr_t)g->quat & 15)) return set_error(GRT_ERR_ARG, "grads->quat must be 16-byte aligned");
+    if (g->scale && ((uintptr_t)g->scale & 7)) return set_error(GRT_ERR_ARG, "grads->scale must be 8-byte aligned");
+    if (g->color && s->color_dim == 48 && ((uintptr_t)g->color & 15))
+        return set_error(GRT_ERR_ARG, "grads->color must be 16-byte aligned for SH");
+    if (s->n > 0 && (!s->mu || !s->quat || !s->scale || !s->opacity))
+        return set_error(GRT_ERR_ARG, "surfels need mu, quat, scale and opacity for gradients");
+    return GRT_OK;
+}
+
+extern "C" int grt_trace_backward(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p, const float* ray_o,
+                                  const float* ray_d, int32_t R, const float* dL_drgb, const float* dL_dopacity,
+                                  const grt_grads* grads, void* stream) {
+    int rc = check_trace_inputs(b, s, p);
+    if (rc) return rc;
+    rc = check_grads(grads, s);
+    if (rc) return rc;
+    if (R < 0 || (R > 0 && (!ray_o || !ray_d || !dL_drgb))) return set_error(GRT_ERR_ARG, "bad rays or dL_drgb");
+    if (R == 0) return GRT_OK;
+    DevBvh bvh = dev_bvh(b);
+    TraceParams P = to_params(*p);
+    GradPtrs g{grads->mu, grads->quat, grads->scale, grads->opacity, grads->color};
+    grt_surfels sc = *s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int grid = (R + 127) / 128;
+    dispatch_k(p->k, [&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        k_trace_backward<K><<<grid, 128, 0, st>>>(bvh, P, sc, ray_o, ray_d, R, dL_drgb, dL_dopacity, g);
+    });
+    return launch_error("k_trace_backward");
+}
+
+extern "C" int grt_shade_backward(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
+                                  const grt_gbuffer* gb, const grt_envmap* e, const grt_sampling* smp,
+                                  const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
+                                  const float* dL_dvis, const float* dL_dind, const grt_grads* grads, void* stream) {
+    int rc = check_trace_inputs(b, s, p);
+    if (rc) return rc;
+    rc = check_grads(grads, s);
+    if (rc) return rc;
+    if (!gb || !e || !smp || !e->tables) return set_error(GRT_ERR_ARG, "gbuffer, env or sampling is NULL");
+    if (n_pixels < 0 || (n_pixels > 0 && !dL_dcolor)) return set_error(GRT_ERR_ARG, "bad n_pixels or dL_dcolor");
+    if (!pixel_list && n_pixels > gb->W * gb->H) return set_error(GRT_ERR_ARG, "n_pixels exceeds W*H");
+    int Nr = smp->n_cos + smp->n_ggx + smp->n_env;
+    if (smp->n_cos < 0 || smp->n_ggx < 0 || smp->n_env < 0 || Nr > 1024 || (smp->brdf != 0 && smp->brdf != 1))
+        return set_error(GRT_ERR_ARG, "bad sampling");
+    if (n_pixels == 0 || Nr == 0) return GRT_OK;
+    ShadeBwd J;
+    J.bvh = dev_bvh(b);
+    J.s = *s;
+    J.gb = GbufDev{gb->pos, gb->normal, gb->albedo, gb->rough, gb->metal, gb->valid, gb->eye[0], gb->eye[1], gb->eye[2],
+                   gb->W, gb->H};
+    EnvLayout l = env_layout(e->W, e->H);
+    const char* tb = (const char*)e->tables;
+    J.env = EnvDev{(const float4*)(tb + l.texel), (const float*)(tb + l.marg), (const float*)(tb + l.cond), e->W, e->H,
+                   (float)e->W * (float)e->H / (2.f * kPi * kPi)};
+    J.S = Sampling{smp->n_cos, smp->n_ggx, smp->n_env, smp->brdf, (uint32_t)(smp->seed & 0xFFFFFFFFu),
+                   (uint32_t)(smp->seed >> 32)};
+    J.pixel_list = pixel_list;
+    J.n_pixels = n_pixels;
+    J.dcol = dL_dcolor;
+    J.dvis = dL_dvis;
+    J.dind = dL_dind;
+    J.G = group_lanes(Nr);
+    J.spl = (Nr + J.G - 1) / J.G;
+    int units = (n_pixels + (32 / J.G) - 1) / (32 / J.G);
+    int grid = (int)(((long long)units * 32 + 127) / 128);
+    TraceParams P = to_params(*p);
+    GradPtrs g{grads->mu, grads->quat, grads->scale, grads->opacity, grads->color};
+    cudaStream_t st = (cudaStream_t)stream;
+    dispatch_k(p->k, [&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        k_shade_backward<K><<<grid, 128, 0, st>>>(J, P, g);
+    });
+    return launch_error("k_shade_backward");
+}

@@ -1,0 +1,501 @@
+// bvh.cu -- linear BVH over 2D Gaussian surfels, built on the device.
+//
+// The paper bounds each surfel by an icosahedron proxy scaled by sqrt(2 log(o/alpha_min))
+// (Eq. 6) and hands the triangles to OptiX's hardware BVH (Sec. III-B).  B300 has no RT
+// cores, so the surfels are bounded directly by the axis-aligned box of the same
+// alpha_min ellipse and indexed by a software LBVH:
+//   1. prep      per surfel: decision normal, scaled tangents, ellipse box, box centre
+//   2. bounds    scene box of the centres (one block-reduced pass, atomics on ordered ints)
+//   3. morton    30-bit Morton code of each centre in the scene box
+//   4. sort      LSD radix sort of (code, id), 8-bit digits, stable block-local ranking
+//   5. records   packed 64-byte records in sorted order (coalesced traversal reads)
+//   6. hierarchy binary radix tree over the sorted codes (Karras, HPG 2012), duplicate
+//                codes split by position, so the depth is at most 30 + log2(n)
+//   7. refit     bottom-up box union, second arriving thread continues (atomic flags)
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+
+#include "grt_internal.cuh"
+
+namespace grt {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ unsigned int float_to_ordered(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// Per-surfel frame from the quaternion (ordinary FP32): columns of R(q/|q|).
+__device__ __forceinline__ void frame_fast(float4 q, f3* tu, f3* tv) {
+    float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+    *tu = mk3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
+    *tv = mk3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
+}
+
+struct SurfelIn {
+    const float* mu;
+    const float* quat;
+    const float* scale;
+    const float* opacity;
+    int n;
+    float alpha_min;
+};
+
+// Ellipse box: rho = sqrt(2 ln(o/alpha_min)); half extent along axis x is
+// rho * sqrt((s_u t_u.x)^2 + (s_v t_v.x)^2).  Padded by 1e-5 of the extent plus 4e-7 of
+// the coordinate magnitude so FP32 rounding of later tests never escapes the box.
+__device__ __forceinline__ void surfel_box(const SurfelIn& s, int i, float lo[3], float hi[3], f3* tu, f3* tv,
+                                           float* r2cut) {
+    float4 q = make_float4(s.quat[4 * i], s.quat[4 * i + 1], s.quat[4 * i + 2], s.quat[4 * i + 3]);
+    frame_fast(q, tu, tv);
+    float su = s.scale[2 * i], sv = s.scale[2 * i + 1];
+    float o = s.opacity[i];
+    float c = o > s.alpha_min ? 2.f * logf(o / s.alpha_min) : 0.f;
+    *r2cut = o >= s.alpha_min ? c : -1.f;
+    float rho = sqrtf(fmaxf(c, 0.f)) * (1.f + 1e-5f);
+    float m[3] = {s.mu[3 * i], s.mu[3 * i + 1], s.mu[3 * i + 2]};
+    float a[3] = {su * tu->x, su * tu->y, su * tu->z};
+    float b[3] = {sv * tv->x, sv * tv->y, sv * tv->z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float e = rho * sqrtf(a[k] * a[k] + b[k] * b[k]);
+        float pad = 1e-5f * e + 4e-7f * (fabsf(m[k]) + e) + 1e-9f;
+        lo[k] = m[k] - e - pad;
+        hi[k] = m[k] + e + pad;
+    }
+}
+
+__global__ void k_prep_bounds(SurfelIn s, float* __restrict__ centre, unsigned int* __restrict__ bounds_u) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    float cl[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, ch[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    if (i < s.n) {
+        f3 tu, tv;
+        float r2;
+        surfel_box(s, i, lo, hi, &tu, &tv, &r2);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float c = 0.5f * (lo[k] + hi[k]);
+            centre[3 * i + k] = c;
+            cl[k] = c;
+            ch[k] = c;
+        }
+    }
+    // warp then block reduction of centre bounds and box bounds
+    __shared__ float red[12][kThreads / 32];
+    float v[12] = {cl[0], cl[1], cl[2], -ch[0], -ch[1], -ch[2], lo[0], lo[1], lo[2], -hi[0], -hi[1], -hi[2]};
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        float x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        float x = red[threadIdx.x][0];
+        for (int w = 1; w < kThreads / 32; ++w) x = fminf(x, red[threadIdx.x][w]);
+        atomicMin(bounds_u + threadIdx.x, float_to_ordered(x));
+    }
+}
+
+__device__ __forceinline__ unsigned int expand_bits10(unsigned int v) {
+    v = (v * 0x00010001u) & 0xFF0000FFu;
+    v = (v * 0x00000101u) & 0x0F00F00Fu;
+    v = (v * 0x00000011u) & 0xC30C30C3u;
+    v = (v * 0x00000005u) & 0x49249249u;
+    return v;
+}
+
+__global__ void k_morton(const float* __restrict__ centre, const unsigned int* __restrict__ bounds_u, int n,
+                         unsigned int* __restrict__ keys, int* __restrict__ vals, float* __restrict__ bounds_out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[3], ext[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = ordered_to_float(bounds_u[k]);
+        float hi = -ordered_to_float(bounds_u[3 + k]);
+        ext[k] = fmaxf(hi - lo[k], 1e-30f);
+    }
+    if (i == 0 && bounds_out) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            bounds_out[k] = ordered_to_float(bounds_u[6 + k]);
+            bounds_out[3 + k] = -ordered_to_float(bounds_u[9 + k]);
+        }
+    }
+    if (i >= n) return;
+    unsigned int q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float t = (centre[3 * i + k] - lo[k]) / ext[k];
+        t = fminf(fmaxf(t * 1024.f, 0.f), 1023.f);
+        q[k] = (unsigned int)t;
+    }
+    keys[i] = (expand_bits10(q[0]) << 2) | (expand_bits10(q[1]) << 1) | expand_bits10(q[2]);
+    vals[i] = i;
+}
+
+// ---------------------------------------------------------------- radix sort (LSD, 8-bit digits)
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__global__ void k_sort_hist(const unsigned int* __restrict__ keys, int n, int shift, int nblocks,
+                            unsigned int* __restrict__ hist) {
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kSortTile;
+    for (int k = 0; k < kSortItems; ++k) {
+        int i = base + k * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of m counts in one block of 1024 threads (digit-major layout).
+__global__ void k_sort_scan(unsigned int* __restrict__ hist, int m) {
+    __shared__ unsigned int part[1024];
+    int per = (m + 1023) / 1024;
+    int b = threadIdx.x * per;
+    unsigned int s = 0;
+    for (int k = 0; k < per; ++k)
+        if (b + k < m) s += hist[b + k];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        unsigned int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned int run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (int k = 0; k < per; ++k) {
+        if (b + k < m) {
+            unsigned int c = hist[b + k];
+            hist[b + k] = run;
+            run += c;
+        }
+    }
+}
+
+// Stable scatter: keys of a tile are ranked in rounds of 256 in index order; within a
+// warp by __match_any_sync, across warps by a prefix over per-warp digit counts.
+__global__ void k_sort_scatter(const unsigned int* __restrict__ keys_in, const int* __restrict__ vals_in, int n,
+                               int shift, int nblocks, const unsigned int* __restrict__ offs,
+                               unsigned int* __restrict__ keys_out, int* __restrict__ vals_out) {
+    constexpr int W = kSortThreads / 32;
+    __shared__ unsigned int run[256];
+    __shared__ unsigned int wcnt[W][256];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    run[threadIdx.x] = offs[threadIdx.x * nblocks + blockIdx.x];
+    for (int w = 0; w < W; ++w) wcnt[w][threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kSortTile;
+    unsigned int lt = (1u << lane) - 1u;
+    for (int k = 0; k < kSortItems; ++k) {
+        int i = base + k * kSortThreads + threadIdx.x;
+        bool ok = i < n;
+        unsigned int key = ok ? keys_in[i] : 0u;
+        int val = ok ? vals_in[i] : 0;
+        unsigned int d = ok ? ((key >> shift) & 0xFF) : 256u + (unsigned)lane;  // unique dummies
+        unsigned int peers = __match_any_sync(0xffffffffu, d);
+        unsigned int rank = __popc(peers & lt);
+        if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        // prefix over warps per digit (thread = digit)
+        {
+            unsigned int s = run[threadIdx.x];
+            for (int w = 0; w < W; ++w) {
+                unsigned int c = wcnt[w][threadIdx.x];
+                wcnt[w][threadIdx.x] = s;
+                s += c;
+            }
+            run[threadIdx.x] = s;
+        }
+        __syncthreads();
+        if (ok) {
+            unsigned int pos = wcnt[warp][d] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+        for (int w = 0; w < W; ++w) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- records
+struct RecordIn {
+    SurfelIn s;
+    const int* sorted;
+    float4* records;
+    float* leaf_box;
+};
+
+__global__ void k_records(RecordIn r) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= r.s.n) return;
+    int i = r.sorted[j];
+    float lo[3], hi[3], r2cut;
+    f3 tu, tv;
+    surfel_box(r.s, i, lo, hi, &tu, &tv, &r2cut);
+    const float* q = r.s.quat + 4 * i;
+    f3 nd = normal_from_quat_d(q[0], q[1], q[2], q[3]);
+    float su = r.s.scale[2 * i], sv = r.s.scale[2 * i + 1];
+    float4* rec = r.records + 4 * (size_t)j;
+    rec[0] = make_float4(r.s.mu[3 * i], r.s.mu[3 * i + 1], r.s.mu[3 * i + 2], r.s.opacity[i]);
+    rec[1] = make_float4(nd.x, nd.y, nd.z, __int_as_float(i));
+    rec[2] = make_float4(tu.x / su, tu.y / su, tu.z / su, r2cut);
+    rec[3] = make_float4(tv.x / sv, tv.y / sv, tv.z / sv, 0.f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r.leaf_box[6 * (size_t)j + k] = lo[k];
+        r.leaf_box[6 * (size_t)j + 3 + k] = hi[k];
+    }
+}
+
+// ---------------------------------------------------------------- hierarchy (Karras 2012)
+__device__ __forceinline__ int delta(const unsigned int* __restrict__ k, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    unsigned int a = k[i], b = k[j];
+    if (a != b) return __clz(a ^ b);
+    return 32 + __clz((unsigned int)(i ^ j));
+}
+
+__global__ void k_hierarchy(const unsigned int* __restrict__ keys, int n, float4* __restrict__ nodes,
+                            int* __restrict__ parent) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(keys, n, i, i - d);
+    int lmax = 2;
+    while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta(keys, n, i, j);
+    int s = 0;
+    for (int div = 2;; div <<= 1) {
+        int t = (l + div - 1) / div;
+        if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+    }
+    int gamma = i + s * d + (d < 0 ? -1 : 0);
+    int lo = min(i, j), hi = max(i, j);
+    int left = (lo == gamma) ? ~gamma : gamma;
+    int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    float* f = reinterpret_cast<float*>(nodes + 4 * (size_t)i);
+    f[12] = __int_as_float(left);
+    f[13] = __int_as_float(right);
+    f[14] = 0.f;
+    f[15] = 0.f;
+    // parent table: leaves at [0, n), internal nodes at n + index
+    parent[left < 0 ? ~left : n + left] = (i << 1) | 0;
+    parent[right < 0 ? ~right : n + right] = (i << 1) | 1;
+    if (i == 0) parent[n] = -1;
+}
+
+__global__ void k_refit(const float* __restrict__ leaf_box, const int* __restrict__ parent, int n,
+                        float4* __restrict__ nodes, int* __restrict__ flags, int* status) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float b[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) b[k] = leaf_box[6 * (size_t)j + k];
+    int p = parent[j];
+    for (int level = 0; p >= 0; ++level) {
+        if (level > 96 || (p >> 1) >= n - 1) {  // deeper than any radix tree over 30+34 bits
+            atomicOr(status, GRT_STATUS_BAD_TREE);
+            return;
+        }
+        int node = p >> 1, slot = p & 1;
+        volatile float* f = reinterpret_cast<volatile float*>(nodes + 4 * (size_t)node);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) f[6 * slot + k] = b[k];
+        __threadfence();
+        if (atomicAdd(flags + node, 1) == 0) return;  // first arrival: the sibling finishes
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            b[k] = fminf(f[k], f[6 + k]);
+            b[3 + k] = fmaxf(f[3 + k], f[9 + k]);
+        }
+        p = parent[n + node];
+    }
+}
+
+}  // namespace
+
+static int launch_build(grt_bvh* b, const grt_surfels* s, float alpha_min, bool rebuild_topology,
+                        cudaStream_t st) {
+    const int n = b->n;
+    if (n == 0) return GRT_OK;
+    SurfelIn in{s->mu, s->quat, s->scale, s->opacity, n, alpha_min};
+    int g = (n + kThreads - 1) / kThreads;
+    if (rebuild_topology) {
+        const int nblocks = (n + kSortTile - 1) / kSortTile;
+        // scratch: centre[3n] | bounds_u[12] | keys[2][n] | vals[2][n] | hist[256*nblocks]
+        size_t bytes = sizeof(float) * 3 * (size_t)n + 64 + 2 * sizeof(unsigned int) * (size_t)n +
+                       2 * sizeof(int) * (size_t)n + sizeof(unsigned int) * 256 * (size_t)nblocks + 256;
+        char* scratch = nullptr;
+        GRT_CUDA(cudaMallocAsync((void**)&scratch, bytes, st));
+        char* p = scratch;
+        float* centre = (float*)p; p += sizeof(float) * 3 * (size_t)n;
+        p = (char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+        unsigned int* bounds_u = (unsigned int*)p; p += 64;
+        unsigned int* keys0 = (unsigned int*)p; p += sizeof(unsigned int) * (size_t)n;
+        unsigned int* keys1 = (unsigned int*)p; p += sizeof(unsigned int) * (size_t)n;
+        int* vals0 = (int*)p; p += sizeof(int) * (size_t)n;
+        int* vals1 = (int*)p; p += sizeof(int) * (size_t)n;
+        unsigned int* hist = (unsigned int*)p;
+        GRT_CUDA(cudaMemsetAsync(bounds_u, 0xFF, 64, st));
+        k_prep_bounds<<<g, kThreads, 0, st>>>(in, centre, bounds_u);
+        k_morton<<<g, kThreads, 0, st>>>(centre, bounds_u, n, keys0, vals0, b->bounds);
+        unsigned int* kin = keys0; unsigned int* kout = keys1;
+        int* vin = vals0; int* vout = vals1;
+        for (int shift = 0; shift < 32; shift += 8) {
+            k_sort_hist<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, nblocks, hist);
+            k_sort_scan<<<1, 1024, 0, st>>>(hist, 256 * nblocks);
+            k_sort_scatter<<<nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, nblocks, hist, kout, vout);
+            unsigned int* tk = kin; kin = kout; kout = tk;
+            int* tv = vin; vin = vout; vout = tv;
+        }
+        GRT_CUDA(cudaMemcpyAsync(b->sorted_ids, vin, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        if (n > 1) {
+            int gi = (n - 1 + kThreads - 1) / kThreads;
+            k_hierarchy<<<gi, kThreads, 0, st>>>(kin, n, b->nodes, b->parent);
+        }
+        GRT_CUDA(cudaGetLastError());
+        GRT_CUDA(cudaFreeAsync(scratch, st));
+    }
+    RecordIn r{in, b->sorted_ids, b->records, b->leaf_box};
+    k_records<<<g, kThreads, 0, st>>>(r);
+    if (n > 1) {
+        GRT_CUDA(cudaMemsetAsync(b->refit_flags, 0, sizeof(int) * (size_t)b->n_int, st));
+        k_refit<<<g, kThreads, 0, st>>>(b->leaf_box, b->parent, n, b->nodes, b->refit_flags, b->status);
+    }
+    GRT_CUDA(cudaGetLastError());
+    return GRT_OK;
+}
+
+static int check_surfels(const grt_surfels* s) {
+    if (!s) return set_error(GRT_ERR_ARG, "surfels is NULL");
+    if (s->n < 0) return set_error(GRT_ERR_ARG, "surfels->n = %d < 0", s->n);
+    if (s->n > (1 << 28)) return set_error(GRT_ERR_ARG, "surfels->n = %d exceeds 2^28", s->n);
+    if (s->n > 0 && (!s->mu || !s->quat || !s->scale || !s->opacity))
+        return set_error(GRT_ERR_ARG, "surfels: mu/quat/scale/opacity must be non-NULL");
+    return GRT_OK;
+}
+
+}  // namespace grt
+
+using namespace grt;
+
+extern "C" int grt_build_bvh(const grt_surfels* s, const grt_trace_params* params, grt_bvh** out, void* stream) {
+    if (!out) return set_error(GRT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_surfels(s);
+    if (rc) return rc;
+    if (!params) return set_error(GRT_ERR_ARG, "params is NULL");
+    if (!(params->alpha_min > 0.f && params->alpha_min < 1.f))
+        return set_error(GRT_ERR_ARG, "alpha_min must be in (0,1)");
+    cudaStream_t st = (cudaStream_t)stream;
+    grt_bvh* b = new grt_bvh();
+    b->n = s->n;
+    b->n_int = s->n > 1 ? s->n - 1 : 0;
+    cudaGetDevice(&b->device);
+    size_t n = (size_t)s->n, ni = (size_t)b->n_int;
+    size_t bytes = sizeof(float4) * 4 * (ni + n) + sizeof(int) * (n + ni + 1) + sizeof(int) * (ni + 1) +
+                   sizeof(float) * 6 * n + sizeof(int) * n + 64 + 64;
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc((void**)&base, bytes);
+    if (e != cudaSuccess) {
+        delete b;
+        return set_error(GRT_ERR_OOM, "cudaMalloc(%zu) for the BVH failed: %s", bytes, cudaGetErrorString(e));
+    }
+    char* p = base;
+    b->base = base;
+    b->nodes = (float4*)p; p += sizeof(float4) * 4 * ni;
+    b->records = (float4*)p; p += sizeof(float4) * 4 * n;
+    b->leaf_box = (float*)p; p += sizeof(float) * 6 * n;
+    b->parent = (int*)p; p += sizeof(int) * (n + ni + 1);
+    b->refit_flags = (int*)p; p += sizeof(int) * (ni + 1);
+    b->sorted_ids = (int*)p; p += sizeof(int) * n;
+    p = (char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    b->status = (int*)p; p += 16;
+    b->bounds = (float*)p; p += 32;
+    b->bytes = bytes;
+    e = cudaMemsetAsync(b->status, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->bounds, 0, 32, st);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        delete b;
+        return check_cuda(e, "cudaMemsetAsync");
+    }
+    rc = launch_build(b, s, params->alpha_min, true, st);
+    if (rc) {
+        cudaStreamSynchronize(st);
+        cudaFree(base);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return GRT_OK;
+}
+
+extern "C" int grt_refit_bvh(grt_bvh* b, const grt_surfels* s, const grt_trace_params* params, void* stream) {
+    if (!b) return set_error(GRT_ERR_ARG, "bvh is NULL");
+    int rc = check_surfels(s);
+    if (rc) return rc;
+    if (!params) return set_error(GRT_ERR_ARG, "params is NULL");
+    if (s->n != b->n) return set_error(GRT_ERR_ARG, "refit with n=%d but the BVH holds %d surfels", s->n, b->n);
+    return launch_build(b, s, params->alpha_min, false, (cudaStream_t)stream);
+}
+
+extern "C" int grt_rebuild_bvh(grt_bvh* b, const grt_surfels* s, const grt_trace_params* params, void* stream) {
+    if (!b) return set_error(GRT_ERR_ARG, "bvh is NULL");
+    int rc = check_surfels(s);
+    if (rc) return rc;
+    if (!params) return set_error(GRT_ERR_ARG, "params is NULL");
+    if (s->n != b->n) return set_error(GRT_ERR_ARG, "rebuild with n=%d but the BVH holds %d surfels", s->n, b->n);
+    return launch_build(b, s, params->alpha_min, true, (cudaStream_t)stream);
+}
+
+extern "C" void grt_bvh_destroy(grt_bvh* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    cudaFree(b->base);
+    delete b;
+}
+
+extern "C" int grt_bvh_info(const grt_bvh* b, grt_bvh_info_t* info) {
+    if (!b || !info) return set_error(GRT_ERR_ARG, "bvh or info is NULL");
+    info->n_surfels = b->n;
+    info->n_nodes = b->n_int;
+    info->device_bytes = b->bytes;
+    cudaError_t e = cudaMemcpy(info->bounds, b->bounds, sizeof(float) * 6, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return check_cuda(e, "cudaMemcpy(bounds)");
+    return GRT_OK;
+}
+
+extern "C" int grt_bvh_status(grt_bvh* b, int32_t* status, void* stream) {
+    if (!b || !status) return set_error(GRT_ERR_ARG, "bvh or status is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    GRT_CUDA(cudaMemcpyAsync(status, b->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GRT_CUDA(cudaMemsetAsync(b->status, 0, sizeof(int), st));
+    GRT_CUDA(cudaStreamSynchronize(st));
+    return GRT_OK;
+}
