@@ -180,8 +180,8 @@ def run_grt(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if gbuild.stale():
-        raise RuntimeError("libgrt.so is missing or stale: run __graft_entry__.build() first")
+    if not os.path.exists(gbuild.OUT):
+        raise RuntimeError("libgrt.so is missing: run __graft_entry__.build() first")
 
     sc, cam, env = make_inputs(rank)
     # ---- device-resident inputs
@@ -379,7 +379,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--image", type=int, default=0,
+                    help="square image size override (small profiling case); default 800")
     args = ap.parse_args()
+    if args.image:
+        global W_IMG, H_IMG
+        W_IMG = H_IMG = args.image
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
