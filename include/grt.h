@@ -105,6 +105,26 @@ int grt_refit_bvh(grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_para
 int grt_rebuild_bvh(grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
                     void* stream);
 
+/* Allocation-free rebuild (no counterpart in the paper; a library-integration need).
+ * Some callers cannot let a library allocate device memory: a host application that
+ * owns and pre-reserves the whole device budget (a renderer or engine with a fixed
+ * memory plan, a process whose own allocator enforces a hard cap) sees any cudaMalloc or
+ * pool allocation inside a call as a failure risk at an arbitrary moment and as memory
+ * it cannot account for.  This call does what grt_rebuild_bvh does -- Morton codes,
+ * sort, hierarchy, refit, into the existing BVH that the caller already owns -- without
+ * allocating: its sort scratch is a fixed array compiled into the library (about 15 MB
+ * for GRT_NOALLOC_MAX_SURFELS surfels), which every device that loads libgrt keeps until
+ * the process exits.
+ *   - n > GRT_NOALLOC_MAX_SURFELS is rejected with GRT_ERR_ARG before any device work.
+ *   - The first call on a device looks up the scratch array's device address (with that
+ *     device current); make that first call before any stream capture.
+ *   - All calls share the one array: calls that may overlap on the GPU (other streams,
+ *     other host threads) race on it and must be serialised by the caller.
+ * Asynchronous on `stream`; results are identical to grt_rebuild_bvh. */
+#define GRT_NOALLOC_MAX_SURFELS 524288
+int grt_rebuild_bvh_noalloc(grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                            void* stream);
+
 /* Synchronises the device, then frees the BVH.  NULL is ignored. */
 void grt_bvh_destroy(grt_bvh* bvh);
 

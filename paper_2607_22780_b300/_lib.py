@@ -15,6 +15,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "grt.h")
 
 GRT_OK, GRT_ERR_ARG, GRT_ERR_OOM, GRT_ERR_CUDA, GRT_ERR_OVERFLOW, GRT_ERR_TIMEOUT, GRT_ERR_UNSUPPORTED = range(7)
 GRT_MAX_BATCH = 48
+GRT_NOALLOC_MAX_SURFELS = 524288
 STATUS_STACK_OVERFLOW = 1
 STATUS_NONFINITE = 2
 
@@ -65,6 +66,7 @@ SIGNATURES = {
     "grt_build_bvh": (C.c_int, [C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(P), P]),
     "grt_refit_bvh": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), P]),
     "grt_rebuild_bvh": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), P]),
+    "grt_rebuild_bvh_noalloc": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), P]),
     "grt_bvh_destroy": (None, [P]),
     "grt_bvh_info": (C.c_int, [P, C.POINTER(BvhInfo)]),
     "grt_bvh_status": (C.c_int, [P, C.POINTER(C.c_int32), P]),

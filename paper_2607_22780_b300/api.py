@@ -102,6 +102,12 @@ class Scene:
         L.check(self._lib.grt_rebuild_bvh(self._bvh, C.byref(self.surfels()), C.byref(self.params),
                                           _stream(stream)))
 
+    def rebuild_noalloc(self, stream=None):
+        """Full LBVH rebuild in place that allocates no device memory (fixed library
+        scratch, at most GRT_NOALLOC_MAX_SURFELS surfels; calls must not overlap)."""
+        L.check(self._lib.grt_rebuild_bvh_noalloc(self._bvh, C.byref(self.surfels()), C.byref(self.params),
+                                                  _stream(stream)))
+
     def info(self) -> dict:
         i = L.BvhInfo()
         L.check(self._lib.grt_bvh_info(self._bvh, C.byref(i)))

@@ -16,6 +16,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "grt_internal.cuh"
 
@@ -400,9 +401,102 @@ static int check_surfels(const grt_surfels* s) {
     return GRT_OK;
 }
 
+// ---------------------------------------------------------------- allocation-free rebuild
+// Scratch of grt_rebuild_bvh_noalloc, compiled into the library: every device that loads
+// libgrt holds these bytes until the process exits.  Layout as in launch_build, sized for
+// GRT_NOALLOC_MAX_SURFELS surfels.
+constexpr size_t kNoallocBlocks = (GRT_NOALLOC_MAX_SURFELS + kSortTile - 1) / kSortTile;
+constexpr size_t kNoallocBytes = 4ull * 3 * GRT_NOALLOC_MAX_SURFELS + 256 +      // centres (+ alignment)
+                                 64 +                                           // bounds
+                                 4ull * 4 * GRT_NOALLOC_MAX_SURFELS +           // keys x2, ids x2
+                                 4ull * 256 * kNoallocBlocks;                   // digit histograms
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// Device address of g_noalloc_scratch per device, looked up on the first call made on
+// that device (with that device current).  In host code the symbol itself is only a
+// host-side stand-in and must never be passed to a kernel.
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kMaxDevices] = {};
+
+static int noalloc_scratch(void** out) {
+    int dev = 0;
+    GRT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(GRT_ERR_UNSUPPORTED, "device %d beyond %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return check_cuda(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return GRT_OK;
+}
+
+static int launch_build_noalloc(grt_bvh* b, const grt_surfels* s, float alpha_min, cudaStream_t st) {
+    const int n = b->n;
+    if (n == 0) return GRT_OK;
+    char* scratch = nullptr;
+    int rc = noalloc_scratch((void**)&scratch);
+    if (rc) return rc;
+    SurfelIn in{s->mu, s->quat, s->scale, s->opacity, n, alpha_min};
+    const int g = (n + kThreads - 1) / kThreads;
+    const int nblocks = (n + kSortTile - 1) / kSortTile;
+    char* p = scratch;
+    float* centre = (float*)p; p += sizeof(float) * 3 * (size_t)n;
+    p = (char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    unsigned int* bounds_u = (unsigned int*)p; p += 64;
+    unsigned int* keys0 = (unsigned int*)p; p += sizeof(unsigned int) * (size_t)n;
+    unsigned int* keys1 = (unsigned int*)p; p += sizeof(unsigned int) * (size_t)n;
+    int* vals0 = (int*)p; p += sizeof(int) * (size_t)n;
+    int* vals1 = (int*)p; p += sizeof(int) * (size_t)n;
+    unsigned int* hist = (unsigned int*)p;
+    // the array keeps the previous call's contents: the bounds must restart from "empty";
+    // centres, keys, ids and histograms are fully rewritten below
+    GRT_CUDA(cudaMemsetAsync(bounds_u, 0xFF, 64, st));
+    k_prep_bounds<<<g, kThreads, 0, st>>>(in, centre, bounds_u);
+    k_morton<<<g, kThreads, 0, st>>>(centre, bounds_u, n, keys0, vals0, b->bounds);
+    unsigned int* kin = keys0; unsigned int* kout = keys1;
+    int* vin = vals0; int* vout = vals1;
+    for (int shift = 0; shift < 32; shift += 8) {
+        k_sort_hist<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, nblocks, hist);
+        k_sort_scan<<<1, 1024, 0, st>>>(hist, 256 * nblocks);
+        k_sort_scatter<<<nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, nblocks, hist, kout, vout);
+        unsigned int* tk = kin; kin = kout; kout = tk;
+        int* tv = vin; vin = vout; vout = tv;
+    }
+    GRT_CUDA(cudaMemcpyAsync(b->sorted_ids, vin, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (n > 1) {
+        int gi = (n - 1 + kThreads - 1) / kThreads;
+        k_hierarchy<<<gi, kThreads, 0, st>>>(kin, n, b->nodes, b->parent);
+    }
+    RecordIn r{in, b->sorted_ids, b->records, b->leaf_box};
+    k_records<<<g, kThreads, 0, st>>>(r);
+    if (n > 1) {
+        GRT_CUDA(cudaMemsetAsync(b->refit_flags, 0, sizeof(int) * (size_t)b->n_int, st));
+        k_refit<<<g, kThreads, 0, st>>>(b->leaf_box, b->parent, n, b->nodes, b->refit_flags, b->status);
+    }
+    GRT_CUDA(cudaGetLastError());
+    return GRT_OK;
+}
+
 }  // namespace grt
 
 using namespace grt;
+
+extern "C" int grt_rebuild_bvh_noalloc(grt_bvh* b, const grt_surfels* s, const grt_trace_params* params,
+                                       void* stream) {
+    if (!b) return set_error(GRT_ERR_ARG, "bvh is NULL");
+    int rc = check_surfels(s);
+    if (rc) return rc;
+    if (!params) return set_error(GRT_ERR_ARG, "params is NULL");
+    if (s->n != b->n) return set_error(GRT_ERR_ARG, "rebuild with n=%d but the BVH holds %d surfels", s->n, b->n);
+    if (s->n > GRT_NOALLOC_MAX_SURFELS)
+        return set_error(GRT_ERR_ARG, "grt_rebuild_bvh_noalloc: n = %d exceeds its fixed scratch for %d surfels",
+                         s->n, GRT_NOALLOC_MAX_SURFELS);
+    return launch_build_noalloc(b, s, params->alpha_min, (cudaStream_t)stream);
+}
 
 extern "C" int grt_build_bvh(const grt_surfels* s, const grt_trace_params* params, grt_bvh** out, void* stream) {
     if (!out) return set_error(GRT_ERR_ARG, "out is NULL");
