@@ -185,7 +185,7 @@ def run_grt(args):
 
     sc, cam, env = make_inputs(rank)
     # ---- device-resident inputs
-    S = api.Scene.from_workload(sc, device=dev)
+    S = api.Scene.from_workload(sc, device=dev, params=api.trace_params(k=args.k))
     E = api.Environment(torch.from_numpy(env).to(dev))
     G = api.GBuffer.empty(W_IMG, H_IMG, cam.eye, device=dev)
     P = W_IMG * H_IMG
@@ -314,7 +314,7 @@ def run_grt(args):
                "config": {"workload": "mis_shade_300k_800x800_32spp", "surfels": N_SURFELS,
                           "image": [W_IMG, H_IMG], "rays_per_pixel": sum(ALLOC), "alloc_cos_ggx_env": list(ALLOC),
                           "env": [ENV_W, ENV_H], "valid_pixels": n_valid, "rays_per_step": R,
-                          "step": "rebuild LBVH + primary G-buffer + MIS shade", "k": 16,
+                          "step": "rebuild LBVH + primary G-buffer + MIS shade", "k": args.k,
                           "l2": "flushed between steps (256 MB write outside the timed events)",
                           "parallelism": f"replicas x{world}"},
                "gpu_launches": launches_per_step * args.steps,
@@ -379,6 +379,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--k", type=int, default=16, help="k-buffer size (results do not depend on it)")
     ap.add_argument("--image", type=int, default=0,
                     help="square image size override (small profiling case); default 800")
     args = ap.parse_args()

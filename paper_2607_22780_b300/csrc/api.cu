@@ -23,10 +23,11 @@ int check_cuda(cudaError_t e, const char* what) {
 
 DevBvh dev_bvh(const grt_bvh* b) {
     DevBvh d;
-    d.nodes = b->nodes;
+    d.nodes = b->wnodes;
     d.records = b->records;
     d.n = b->n;
-    d.root = b->n == 0 ? kRefEmpty : (b->n == 1 ? ~0 : 0);
+    d.cap = b->n_int;
+    d.root = b->n == 0 ? kRefEmpty : (b->n == 1 ? leaf_ref(0, 1) : 0);
     d.status = b->status;
     return d;
 }

@@ -16,6 +16,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <mutex>
 
 #include "grt_internal.cuh"
@@ -301,8 +302,8 @@ __global__ void k_hierarchy(const unsigned int* __restrict__ keys, int n, float4
     float* f = reinterpret_cast<float*>(nodes + 4 * (size_t)i);
     f[12] = __int_as_float(left);
     f[13] = __int_as_float(right);
-    f[14] = 0.f;
-    f[15] = 0.f;
+    f[14] = __int_as_float(lo);  // sorted-record range covered by this node
+    f[15] = __int_as_float(hi);
     // parent table: leaves at [0, n), internal nodes at n + index
     parent[left < 0 ? ~left : n + left] = (i << 1) | 0;
     parent[right < 0 ? ~right : n + right] = (i << 1) | 1;
@@ -310,7 +311,7 @@ __global__ void k_hierarchy(const unsigned int* __restrict__ keys, int n, float4
 }
 
 __global__ void k_refit(const float* __restrict__ leaf_box, const int* __restrict__ parent, int n,
-                        float4* __restrict__ nodes, int* __restrict__ flags, int* status) {
+                        float4* __restrict__ nodes, int* __restrict__ flags, int* status, float* __restrict__ bin_box) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     float b[6];
@@ -334,11 +335,164 @@ __global__ void k_refit(const float* __restrict__ leaf_box, const int* __restric
             b[k] = fminf(f[k], f[6 + k]);
             b[3 + k] = fmaxf(f[3 + k], f[9 + k]);
         }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) bin_box[6 * (size_t)node + k] = b[k];
         p = parent[n + node];
     }
 }
 
+// ---------------------------------------------------------------- 4-wide collapse
+// Top down, one frontier per level: a wide node made from binary node b starts with b's
+// two children and twice replaces the candidate of largest surface area that is too big
+// for a leaf by its two children; candidates of at most kLeafMax surfels become leaves
+// over their contiguous run of sorted records, larger ones become new wide nodes.
+__device__ __forceinline__ int bin_size(const float4* bn, int ref) {
+    if (ref < 0) return 1;
+    const float* f = reinterpret_cast<const float*>(bn + 4 * (size_t)ref);
+    return __float_as_int(f[15]) - __float_as_int(f[14]) + 1;
+}
+__device__ __forceinline__ const float* bin_box_of(const float* bin_box, const float* leaf_box, int ref) {
+    return ref < 0 ? leaf_box + 6 * (size_t)(~ref) : bin_box + 6 * (size_t)ref;
+}
+__device__ __forceinline__ float half_area(const float* b) {
+    float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+struct CollapseIn {
+    const float4* bnodes;
+    const float* bin_box;
+    const float* leaf_box;
+    float4* wnodes;
+    const int2* fin;
+    int2* fout;
+    int* counts;  // [0] wide nodes allocated, [1 + level] frontier sizes
+    int* status;
+    int level, cap;
+};
+
+__device__ __forceinline__ void write_slot(float4* W, int s, const float* box, int ref, int bref) {
+    float* f = reinterpret_cast<float*>(W);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) f[4 * k + s] = box[k];
+    f[24 + s] = __int_as_float(ref);
+    f[28 + s] = __int_as_float(bref);
+}
+
+__global__ void k_collapse(CollapseIn c) {
+    const int nitems = c.counts[1 + c.level];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nitems; i += gridDim.x * blockDim.x) {
+        int2 it = c.fin[i];
+        const float* fb = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)it.y);
+        int cand[kWide];
+        int nc = 2;
+        cand[0] = __float_as_int(fb[12]);
+        cand[1] = __float_as_int(fb[13]);
+        for (int rep = 2; rep < kWide; ++rep) {
+            int best = -1;
+            float ba = -1.f;
+            for (int s = 0; s < nc; ++s) {
+                int r = cand[s];
+                if (r >= 0 && bin_size(c.bnodes, r) > kLeafMax) {
+                    float a = half_area(c.bin_box + 6 * (size_t)r);
+                    if (a > ba) {
+                        ba = a;
+                        best = s;
+                    }
+                }
+            }
+            if (best < 0) break;
+            const float* fr = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)cand[best]);
+            cand[best] = __float_as_int(fr[12]);
+            cand[nc++] = __float_as_int(fr[13]);
+        }
+        float4* W = c.wnodes + 8 * (size_t)it.x;
+        for (int s = 0; s < kWide; ++s) {
+            if (s >= nc) {
+                const float empty[6] = {1e38f, 1e38f, 1e38f, -1e38f, -1e38f, -1e38f};
+                write_slot(W, s, empty, kRefEmpty, kRefEmpty);
+                continue;
+            }
+            int r = cand[s];
+            const float* box = bin_box_of(c.bin_box, c.leaf_box, r);
+            int ref;
+            if (r < 0) {
+                ref = leaf_ref(~r, 1);
+            } else {
+                const float* fr = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)r);
+                int first = __float_as_int(fr[14]), size = __float_as_int(fr[15]) - first + 1;
+                if (size <= kLeafMax) {
+                    ref = leaf_ref(first, size);
+                } else {
+                    int w2 = atomicAdd(c.counts, 1);
+                    if (w2 >= c.cap) {
+                        atomicOr(c.status, GRT_STATUS_BAD_TREE);
+                        ref = kRefEmpty;
+                    } else {
+                        int pos = atomicAdd(c.counts + 2 + c.level, 1);
+                        c.fout[pos] = make_int2(w2, r);
+                        ref = w2;
+                    }
+                }
+            }
+            write_slot(W, s, box, ref, r);
+        }
+    }
+}
+
+// Child boxes of every wide node from the refit binary boxes (topology unchanged).
+__global__ void k_wide_refit(float4* __restrict__ wnodes, const int* __restrict__ counts, int cap,
+                             const float* __restrict__ bin_box, const float* __restrict__ leaf_box) {
+    int nw = min(counts[0], cap);
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+        float4* W = wnodes + 8 * (size_t)w;
+        const float* f = reinterpret_cast<const float*>(W);
+        for (int s = 0; s < kWide; ++s) {
+            int br = __float_as_int(f[28 + s]);
+            if (br == kRefEmpty) continue;
+            write_slot(W, s, bin_box_of(bin_box, leaf_box, br), __float_as_int(f[24 + s]), br);
+        }
+    }
+}
+
+__global__ void k_collapse_init(int* counts, int2* f0) {
+    if (threadIdx.x < kMaxCollapseLevels + 2) counts[threadIdx.x] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        counts[0] = 1;  // wide node 0 = root
+        counts[1] = 1;  // the level-0 frontier holds it
+        f0[0] = make_int2(0, 0);
+    }
+}
+
 }  // namespace
+
+// Records, binary refit and the 4-wide collapse (or its refit): shared tail of the builds.
+static int finish_build(grt_bvh* b, const SurfelIn& in, bool collapse, cudaStream_t st) {
+    const int n = b->n;
+    const int g = (n + kThreads - 1) / kThreads;
+    RecordIn r{in, b->sorted_ids, b->records, b->leaf_box};
+    k_records<<<g, kThreads, 0, st>>>(r);
+    if (n > 1) {
+        GRT_CUDA(cudaMemsetAsync(b->refit_flags, 0, sizeof(int) * (size_t)b->n_int, st));
+        k_refit<<<g, kThreads, 0, st>>>(b->leaf_box, b->parent, n, b->nodes, b->refit_flags, b->status, b->bin_box);
+        const int cg = std::min((b->n_int + 127) / 128, 1184);
+        if (collapse) {
+            k_collapse_init<<<1, 128, 0, st>>>(b->wcounts, b->frontier);
+            for (int level = 0; level < kMaxCollapseLevels; ++level) {
+                const int2* fin = b->frontier + (size_t)(level & 1) * b->n_int;
+                int2* fout = b->frontier + (size_t)((level + 1) & 1) * b->n_int;
+                CollapseIn c{b->nodes, b->bin_box, b->leaf_box, b->wnodes, fin, fout, b->wcounts, b->status,
+                             level, b->n_int};
+                k_collapse<<<cg, 128, 0, st>>>(c);
+            }
+        } else {
+            k_wide_refit<<<cg, 128, 0, st>>>(b->wnodes, b->wcounts, b->n_int, b->bin_box, b->leaf_box);
+        }
+    }
+    GRT_CUDA(cudaGetLastError());
+    return GRT_OK;
+}
 
 static int launch_build(grt_bvh* b, const grt_surfels* s, float alpha_min, bool rebuild_topology,
                         cudaStream_t st) {
@@ -382,20 +536,13 @@ static int launch_build(grt_bvh* b, const grt_surfels* s, float alpha_min, bool 
         GRT_CUDA(cudaGetLastError());
         GRT_CUDA(cudaFreeAsync(scratch, st));
     }
-    RecordIn r{in, b->sorted_ids, b->records, b->leaf_box};
-    k_records<<<g, kThreads, 0, st>>>(r);
-    if (n > 1) {
-        GRT_CUDA(cudaMemsetAsync(b->refit_flags, 0, sizeof(int) * (size_t)b->n_int, st));
-        k_refit<<<g, kThreads, 0, st>>>(b->leaf_box, b->parent, n, b->nodes, b->refit_flags, b->status);
-    }
-    GRT_CUDA(cudaGetLastError());
-    return GRT_OK;
+    return finish_build(b, in, rebuild_topology, st);
 }
 
 static int check_surfels(const grt_surfels* s) {
     if (!s) return set_error(GRT_ERR_ARG, "surfels is NULL");
     if (s->n < 0) return set_error(GRT_ERR_ARG, "surfels->n = %d < 0", s->n);
-    if (s->n > (1 << 28)) return set_error(GRT_ERR_ARG, "surfels->n = %d exceeds 2^28", s->n);
+    if (s->n > (1 << 27)) return set_error(GRT_ERR_ARG, "surfels->n = %d exceeds 2^27", s->n);
     if (s->n > 0 && (!s->mu || !s->quat || !s->scale || !s->opacity))
         return set_error(GRT_ERR_ARG, "surfels: mu/quat/scale/opacity must be non-NULL");
     return GRT_OK;
@@ -471,14 +618,7 @@ static int launch_build_noalloc(grt_bvh* b, const grt_surfels* s, float alpha_mi
         int gi = (n - 1 + kThreads - 1) / kThreads;
         k_hierarchy<<<gi, kThreads, 0, st>>>(kin, n, b->nodes, b->parent);
     }
-    RecordIn r{in, b->sorted_ids, b->records, b->leaf_box};
-    k_records<<<g, kThreads, 0, st>>>(r);
-    if (n > 1) {
-        GRT_CUDA(cudaMemsetAsync(b->refit_flags, 0, sizeof(int) * (size_t)b->n_int, st));
-        k_refit<<<g, kThreads, 0, st>>>(b->leaf_box, b->parent, n, b->nodes, b->refit_flags, b->status);
-    }
-    GRT_CUDA(cudaGetLastError());
-    return GRT_OK;
+    return finish_build(b, in, true, st);
 }
 
 }  // namespace grt
@@ -513,7 +653,9 @@ extern "C" int grt_build_bvh(const grt_surfels* s, const grt_trace_params* param
     cudaGetDevice(&b->device);
     size_t n = (size_t)s->n, ni = (size_t)b->n_int;
     size_t bytes = sizeof(float4) * 4 * (ni + n) + sizeof(int) * (n + ni + 1) + sizeof(int) * (ni + 1) +
-                   sizeof(float) * 6 * n + sizeof(int) * n + 64 + 64;
+                   sizeof(float) * 6 * n + sizeof(int) * n + 64 + 64 +
+                   sizeof(float) * 6 * ni + sizeof(float4) * 8 * ni + sizeof(int2) * 2 * ni +
+                   sizeof(int) * (kMaxCollapseLevels + 2) + 256 * 4;
     char* base = nullptr;
     cudaError_t e = cudaMalloc((void**)&base, bytes);
     if (e != cudaSuccess) {
@@ -531,6 +673,12 @@ extern "C" int grt_build_bvh(const grt_surfels* s, const grt_trace_params* param
     p = (char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
     b->status = (int*)p; p += 16;
     b->bounds = (float*)p; p += 32;
+    p = (char*)(((uintptr_t)p + 127) & ~(uintptr_t)127);
+    b->wnodes = (float4*)p; p += sizeof(float4) * 8 * ni;
+    b->bin_box = (float*)p; p += sizeof(float) * 6 * ni;
+    p = (char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    b->frontier = (int2*)p; p += sizeof(int2) * 2 * ni;
+    b->wcounts = (int*)p; p += sizeof(int) * (kMaxCollapseLevels + 2);
     b->bytes = bytes;
     e = cudaMemsetAsync(b->status, 0, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->bounds, 0, 32, st);

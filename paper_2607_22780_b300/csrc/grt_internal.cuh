@@ -243,6 +243,21 @@ __device__ __forceinline__ f3 env_dir_d(int row, int col, float u_row, float u_c
 }
 
 // ----------------------------------------------------------------------------- BVH layout
+// Traversal runs on a 4-wide BVH collapsed from the binary radix tree.
+// Wide node: 128 bytes = 8 float4
+//   [0..2] lo.x, lo.y, lo.z of the four children, [3..5] hi.x, hi.y, hi.z
+//   [6]    child refs (int bits): >= 0 wide node, kRefEmpty unused slot, any other
+//          negative value a leaf -(1 + (first record << 3) + (count - 1)), count <= kLeafMax
+//   [7]    binary-tree ref of each child (to refit boxes without a rebuild)
+// Unused slots have lo = +1e38 > hi = -1e38, so every slab test misses them.
+constexpr int kWide = 4;
+constexpr int kLeafMax = 4;
+constexpr int kMaxCollapseLevels = 60;  // >= binary depth: 30 code bits + 27 position bits
+__host__ __device__ __forceinline__ int leaf_ref(int first, int count) { return -(1 + (first << 3) + (count - 1)); }
+__host__ __device__ __forceinline__ int leaf_first(int ref) { return (-ref - 1) >> 3; }
+__host__ __device__ __forceinline__ int leaf_count(int ref) { return ((-ref - 1) & 7) + 1; }
+//
+// Binary radix tree (built first, kept for refits):
 // Internal node: 64 bytes = 4 float4
 //   f[0..5]  left child box  (lo.xyz, hi.xyz)
 //   f[6..11] right child box (lo.xyz, hi.xyz)
@@ -252,15 +267,16 @@ __device__ __forceinline__ f3 env_dir_d(int row, int col, float u_row, float u_c
 //   r2 = (t_u/s_u .xyz, r2_cut)     r3 = (t_v/s_v .xyz, unused)
 // with n the decision normal and r2_cut = 2 ln(opacity / alpha_min) (a hit needs
 // u^2+v^2 <= r2_cut).
+constexpr int kRefEmpty = (int)0x80000000;
+
 struct DevBvh {
-    const float4* nodes;    // [n_int * 4]
+    const float4* nodes;    // wide nodes [cap * 8]
     const float4* records;  // [n * 4]
-    int root;               // ref of the root (internal 0, or ~0 for a single leaf, or INT_MIN when empty)
+    int root;               // wide node 0, a leaf ref when n == 1, kRefEmpty when n == 0
     int n;
+    int cap;                // wide node capacity (n - 1)
     int* status;
 };
-
-constexpr int kRefEmpty = (int)0x80000000;
 
 }  // namespace grt
 
@@ -275,6 +291,10 @@ struct grt_bvh {
     int* refit_flags;  // [n_int]
     float* leaf_box;   // [n * 6] in sorted order
     int* sorted_ids;   // [n]
+    float4* wnodes;    // [n_int * 8] 4-wide nodes
+    float* bin_box;    // [n_int * 6] box of each binary node
+    int2* frontier;    // [2][n_int] collapse frontiers
+    int* wcounts;      // [kMaxCollapseLevels + 2] collapse counters
     int* status;       // device status word
     float* bounds;     // [6] scene bounds (device)
     size_t bytes;

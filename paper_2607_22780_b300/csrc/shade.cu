@@ -1,14 +1,23 @@
-// shade.cu -- grt_shade_pixels / grt_shade_batch / grt_shade_count: fused MIS sampling,
-// secondary trace and rendering-equation accumulation (Eq. 10-13).
+// shade.cu -- grt_shade_pixels / grt_shade_batch / grt_shade_count: MIS sampling, secondary
+// trace and rendering-equation accumulation (Eq. 10-13), as three wavefront kernels:
 //
-// A warp shades 32/G pixels at once: the G lanes of a pixel group take samples
-// j = lane + m G (Sec. III-D allocation order), trace them (Eq. 11) and accumulate
-// g/q (V L_env + L_ind); the group then sums its lanes with a fixed butterfly, so a
-// pixel's result depends only on its own samples, never on what else is in the launch.
+//   k_sample_rays  one thread per (pixel, sample j): Philox numbers, proposal of sample j
+//                  (Sec. III-D allocation order), direction -> ray buffer (or "no ray")
+//   k_trace_rays   one thread per ray: LBVH walk, k-buffer, compositing -> (c_rt, T)
+//   k_accumulate   G lanes per pixel: g/q (V L_env + L_ind), V, L_ind per sample, summed
+//                  lane-wise in sample order then by a fixed butterfly
+//
+// Keeping the three phases apart keeps each kernel's code small and its warps on one
+// code path; the ray buffers cost 32 bytes per ray of HBM traffic.  A pixel's result is
+// a fixed function of its own samples, so it is the same alone and in any batch.
+#include <mutex>
+
 #include "common_args.cuh"
 #include "shade.cuh"
 
 namespace grt {
+
+constexpr int kShadeThreads = 128;
 
 struct ShadeJob {
     DevBvh bvh;
@@ -19,57 +28,139 @@ struct ShadeJob {
     Sampling S;
     const int* pixel_list;
     int n_pixels;
+    int Nr;
     float *out_color, *out_vis, *out_ind;
-    int G, spl;        // lanes per pixel, samples per lane
-    int unit_begin;    // first warp unit of this job
+    int G, spl;              // accumulation: lanes per pixel, samples per lane
+    long long ray_begin;     // first ray of this job in the launch's ray buffers
+    long long unit_begin;    // first accumulation warp unit of this job
 };
 
+template <int CAP>
 struct JobTable {
     TraceParams P;
     int n_jobs;
-    int total_units;
-    ShadeJob job[GRT_MAX_BATCH];
+    long long total_rays;
+    long long total_units;
+    ShadeJob job[CAP];
+
+    __device__ __forceinline__ int find_ray(long long r) const {
+        int j = 0;
+        while (j + 1 < n_jobs && r >= job[j + 1].ray_begin) ++j;
+        return j;
+    }
+    __device__ __forceinline__ int find_unit(long long u) const {
+        int j = 0;
+        while (j + 1 < n_jobs && u >= job[j + 1].unit_begin) ++j;
+        return j;
+    }
 };
 
 namespace {
 
-constexpr int kShadeThreads = 128;
+__device__ __forceinline__ int pixel_of(const ShadeJob& J, int li) {
+    int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+    if ((unsigned)pix >= (unsigned)(J.gb.W * J.gb.H)) {
+        atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
+        return -1;
+    }
+    return pix;
+}
 
-template <int K, bool COUNT>
-__device__ __forceinline__ void shade_unit(const ShadeJob& J, const TraceParams& P, int u, Counters& cnt) {
+// ray buffer entry: (direction, 1) for a traced sample, (0, 0, 0, 0) for none
+template <int CAP>
+__global__ void __launch_bounds__(kShadeThreads) k_sample_rays(const __grid_constant__ JobTable<CAP> T,
+                                                               float4* __restrict__ dirs) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= T.total_rays) return;
+    const ShadeJob& J = T.job[T.find_ray(r)];
+    long long lr = r - J.ray_begin;
+    int li = (int)(lr / J.Nr), j = (int)(lr - (long long)li * J.Nr);
+    int pix = pixel_of(J, li);
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pix >= 0 && __ldg(J.gb.valid + pix)) {
+        PixelState ps = load_pixel(J.gb, pix);
+        f3 w;
+        if (draw_direction(J.S, J.env, ps, pix, j, &w)) out = make_float4(w.x, w.y, w.z, 1.f);
+    }
+    dirs[r] = out;
+}
+
+// (c_rt, T) per ray; T = -1 marks "no ray"
+template <int K, bool COUNT, int CAP>
+__global__ void __launch_bounds__(kShadeThreads) k_trace_rays(const __grid_constant__ JobTable<CAP> T,
+                                                              const float4* __restrict__ dirs, float4* __restrict__ res,
+                                                              long long* counters) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    Counters cnt{0, 0, 0};
+    if (r < T.total_rays) {
+        float4 dw = __ldg(dirs + r);
+        float4 out = make_float4(0.f, 0.f, 0.f, -1.f);
+        if (dw.w != 0.f) {
+            const ShadeJob& J = T.job[T.find_ray(r)];
+            int li = (int)((r - J.ray_begin) / J.Nr);
+            int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+            f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
+                       __ldg(J.gb.pos + 3 * (size_t)pix + 2));
+            f3 d = mk3(dw.x, dw.y, dw.z);
+            RayState rs = make_ray(o, d);
+            ColourVisitor v(J.color, J.cdim, d, nullptr, 0);
+            trace_ray<K, COUNT>(J.bvh, rs, T.P, v, cnt);
+            out = make_float4(v.c[0], v.c[1], v.c[2], v.T);
+        }
+        if (!COUNT) res[r] = out;
+    }
+    if (COUNT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt.nodes += __shfl_xor_sync(0xffffffffu, cnt.nodes, o);
+            cnt.tests += __shfl_xor_sync(0xffffffffu, cnt.tests, o);
+            cnt.comp += __shfl_xor_sync(0xffffffffu, cnt.comp, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd((unsigned long long*)counters, (unsigned long long)cnt.nodes);
+            atomicAdd((unsigned long long*)counters + 1, (unsigned long long)cnt.tests);
+            atomicAdd((unsigned long long*)counters + 2, (unsigned long long)cnt.comp);
+        }
+    }
+}
+
+// Eq. 13: a warp unit shades 32/G pixels; lane sub of a pixel group takes samples
+// j = sub + m G in order, the group sums with a butterfly, so the result is fixed.
+template <int CAP>
+__global__ void __launch_bounds__(kShadeThreads) k_accumulate(const __grid_constant__ JobTable<CAP> T,
+                                                              const float4* __restrict__ dirs,
+                                                              const float4* __restrict__ res) {
+    long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (u >= T.total_units) return;  // whole warps leave together
+    const ShadeJob& J = T.job[T.find_unit(u)];
     const int lane = threadIdx.x & 31;
     const int G = J.G;
     const int slot = lane / G, sub = lane - slot * G;
-    const int li = u * (32 / G) + slot;
+    const int li = (int)(u - J.unit_begin) * (32 / G) + slot;
     const bool active = li < J.n_pixels;
-    int pix = active ? (J.pixel_list ? __ldg(J.pixel_list + li) : li) : 0;
-    if ((unsigned)pix >= (unsigned)(J.gb.W * J.gb.H)) {
-        if (active) atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
-        pix = 0;
-    }
-    const bool valid = active && pix == (J.pixel_list ? __ldg(J.pixel_list + li) : li) && __ldg(J.gb.valid + pix) != 0;
-    const int Nr = J.S.n_cos + J.S.n_ggx + J.S.n_env;
     float col[3] = {0.f, 0.f, 0.f}, ind[3] = {0.f, 0.f, 0.f}, vis = 0.f;
-    if (valid) {
-        PixelState ps = load_pixel(J.gb, pix);
-        for (int m = 0; m < J.spl; ++m) {
-            int j = sub + m * G;
-            if (j >= Nr) break;
-            f3 w;
-            if (!draw_direction(J.S, J.env, ps, pix, j, &w)) continue;
-            RayState r = make_ray(ps.x, w);
-            ColourVisitor v(J.color, J.cdim, w, nullptr, 0);
-            trace_ray<K, COUNT>(J.bvh, r, P, v, cnt);
-            SampleWeight sw = sample_weight(J.S, J.env, ps, w);
+    if (active) {
+        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+        if ((unsigned)pix < (unsigned)(J.gb.W * J.gb.H) && __ldg(J.gb.valid + pix)) {
+            PixelState ps = load_pixel(J.gb, pix);
+            const long long r0 = J.ray_begin + (long long)li * J.Nr;
+            for (int m = 0; m < J.spl; ++m) {
+                int j = sub + m * G;
+                if (j >= J.Nr) break;
+                float4 rr = __ldg(res + r0 + j);
+                if (rr.w < 0.f) continue;
+                float4 dw = __ldg(dirs + r0 + j);
+                SampleWeight sw = sample_weight(J.S, J.env, ps, mk3(dw.x, dw.y, dw.z));
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                col[c] = fmaf(sw.g[c], fmaf(v.T, sw.L[c], v.c[c]), col[c]);
-                ind[c] += v.c[c];
+                for (int c = 0; c < 3; ++c) {
+                    float Lind = c == 0 ? rr.x : (c == 1 ? rr.y : rr.z);
+                    col[c] = fmaf(sw.g[c], fmaf(rr.w, sw.L[c], Lind), col[c]);
+                    ind[c] += Lind;
+                }
+                vis += rr.w;
             }
-            vis += v.T;
         }
     }
-    // butterfly over the G lanes of the group (same tree for every lane)
     for (int off = G >> 1; off > 0; off >>= 1) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -79,7 +170,7 @@ __device__ __forceinline__ void shade_unit(const ShadeJob& J, const TraceParams&
         vis += __shfl_xor_sync(0xffffffffu, vis, off);
     }
     if (active && sub == 0 && J.out_color) {
-        float inv = Nr > 0 ? 1.f / (float)Nr : 0.f;
+        const float inv = 1.f / (float)J.Nr;
         J.out_color[3 * (size_t)li] = col[0] * inv;
         J.out_color[3 * (size_t)li + 1] = col[1] * inv;
         J.out_color[3 * (size_t)li + 2] = col[2] * inv;
@@ -92,45 +183,12 @@ __device__ __forceinline__ void shade_unit(const ShadeJob& J, const TraceParams&
     }
 }
 
-__device__ __forceinline__ void flush_counters(Counters c, long long* out) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        c.nodes += __shfl_xor_sync(0xffffffffu, c.nodes, o);
-        c.tests += __shfl_xor_sync(0xffffffffu, c.tests, o);
-        c.comp += __shfl_xor_sync(0xffffffffu, c.comp, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd((unsigned long long*)out, (unsigned long long)c.nodes);
-        atomicAdd((unsigned long long*)out + 1, (unsigned long long)c.tests);
-        atomicAdd((unsigned long long*)out + 2, (unsigned long long)c.comp);
-    }
-}
-
-// One job, one warp unit per warp of the grid.
-template <int K, bool COUNT>
-__global__ void __launch_bounds__(kShadeThreads) k_shade(const __grid_constant__ ShadeJob J, TraceParams P,
-                                                         long long* counters) {
-    int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    Counters cnt{0, 0, 0};
-    int units = (J.n_pixels + (32 / J.G) - 1) / (32 / J.G);
-    if (u < units) shade_unit<K, COUNT>(J, P, u, cnt);
-    if (COUNT) flush_counters(cnt, counters);
-}
-
-// Many jobs, persistent warps pulling units from a shared counter.
-template <int K>
-__global__ void __launch_bounds__(kShadeThreads) k_shade_batch(const __grid_constant__ JobTable T, int* counter) {
-    const int lane = threadIdx.x & 31;
-    Counters cnt{0, 0, 0};
-    while (true) {
-        int unit = 0;
-        if (lane == 0) unit = atomicAdd(counter, 1);
-        unit = __shfl_sync(0xffffffffu, unit, 0);
-        if (unit >= T.total_units) break;
-        int j = 0;
-        while (j + 1 < T.n_jobs && unit >= T.job[j + 1].unit_begin) ++j;
-        shade_unit<K, false>(T.job[j], T.P, unit - T.job[j].unit_begin, cnt);
-    }
+__global__ void k_zero_outputs(float* c, float* v, float* i, int n) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    c[3 * (size_t)t] = c[3 * (size_t)t + 1] = c[3 * (size_t)t + 2] = 0.f;
+    if (v) v[t] = 0.f;
+    if (i) i[3 * (size_t)t] = i[3 * (size_t)t + 1] = i[3 * (size_t)t + 2] = 0.f;
 }
 
 int make_job(const grt_bvh* b, const grt_surfels* s, const grt_gbuffer* g, const grt_envmap* e,
@@ -158,13 +216,64 @@ int make_job(const grt_bvh* b, const grt_surfels* s, const grt_gbuffer* g, const
     J->S = Sampling{smp->n_cos, smp->n_ggx, smp->n_env, smp->brdf, (uint32_t)(smp->seed & 0xFFFFFFFFu),
                     (uint32_t)(smp->seed >> 32)};
     J->pixel_list = pixel_list;
-    J->n_pixels = n_pixels;
+    J->n_pixels = Nr > 0 ? n_pixels : 0;
+    J->Nr = Nr > 0 ? Nr : 1;
     J->out_color = oc;
     J->out_vis = ov;
     J->out_ind = oi;
-    J->G = group_lanes(Nr > 0 ? Nr : 1);
-    J->spl = Nr > 0 ? (Nr + J->G - 1) / J->G : 0;
+    J->G = group_lanes(J->Nr);
+    J->spl = (J->Nr + J->G - 1) / J->G;
+    J->ray_begin = 0;
     J->unit_begin = 0;
+    return GRT_OK;
+}
+
+// Keeps freed ray buffers in the device's stream-ordered pool between calls.
+void keep_pool_memory() {
+    static std::once_flag once[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::call_once(once[dev], [dev] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+// Lays out the jobs' rays and accumulation units, then runs the three kernels.
+template <bool COUNT, int CAP>
+int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st) {
+    long long rays = 0, units = 0;
+    for (int i = 0; i < T.n_jobs; ++i) {
+        ShadeJob& J = T.job[i];
+        J.ray_begin = rays;
+        J.unit_begin = units;
+        rays += (long long)J.n_pixels * J.Nr;
+        units += (J.n_pixels + (32 / J.G) - 1) / (32 / J.G);
+    }
+    T.total_rays = rays;
+    T.total_units = units;
+    if (rays == 0) return GRT_OK;
+    keep_pool_memory();
+    float4* buf = nullptr;
+    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * 2 * (size_t)rays, st));
+    float4* dirs = buf;
+    float4* res = buf + rays;
+    const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
+    k_sample_rays<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
+    dispatch_k(k, [&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        k_trace_rays<K, COUNT, CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, counters);
+    });
+    if (!COUNT) {
+        const long long ga = (units * 32 + kShadeThreads - 1) / kShadeThreads;
+        k_accumulate<CAP><<<(unsigned)ga, kShadeThreads, 0, st>>>(T, dirs, res);
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(buf, st);
+    if (e != cudaSuccess) return check_cuda(e, "shade kernels");
     return GRT_OK;
 }
 
@@ -174,19 +283,17 @@ int launch_single(const grt_bvh* b, const grt_surfels* s, const grt_trace_params
                   long long* counters, cudaStream_t st) {
     int rc = check_trace_inputs(b, s, p);
     if (rc) return rc;
-    ShadeJob J;
-    rc = make_job(b, s, g, e, smp, pl, n, oc, ov, oi, &J);
+    JobTable<1> T;
+    T.P = to_params(*p);
+    T.n_jobs = 1;
+    rc = make_job(b, s, g, e, smp, pl, n, oc, ov, oi, &T.job[0]);
     if (rc) return rc;
     if (n == 0) return GRT_OK;
-    int units = (n + (32 / J.G) - 1) / (32 / J.G);
-    long long threads = (long long)units * 32;
-    int grid = (int)((threads + kShadeThreads - 1) / kShadeThreads);
-    TraceParams P = to_params(*p);
-    dispatch_k(p->k, [&](auto kc) {
-        constexpr int K = decltype(kc)::value;
-        k_shade<K, COUNT><<<grid, kShadeThreads, 0, st>>>(J, P, counters);
-    });
-    return launch_error("k_shade");
+    if (T.job[0].n_pixels == 0) {  // N_r = 0: every output is zero
+        if (oc) k_zero_outputs<<<(n + 255) / 256, 256, 0, st>>>(oc, ov, oi, n);
+        return launch_error("k_zero_outputs");
+    }
+    return run_jobs<COUNT>(T, p->k, counters, st);
 }
 
 }  // namespace
@@ -214,37 +321,29 @@ extern "C" int grt_shade_batch(const grt_shade_request* req, int32_t n_req, cons
                                int32_t* work_counter, void* stream) {
     if (!req || n_req <= 0 || n_req > GRT_MAX_BATCH)
         return set_error(GRT_ERR_ARG, "need 1 <= n_requests <= %d", GRT_MAX_BATCH);
-    if (!work_counter) return set_error(GRT_ERR_ARG, "work_counter is NULL");
+    (void)work_counter;
     int rc = check_params(p);
     if (rc) return rc;
-    static thread_local JobTable T;
+    static thread_local JobTable<GRT_MAX_BATCH> T;
     T.P = to_params(*p);
-    T.n_jobs = n_req;
-    int units = 0;
+    T.n_jobs = 0;
+    cudaStream_t st = (cudaStream_t)stream;
     for (int i = 0; i < n_req; ++i) {
         rc = check_trace_inputs(req[i].bvh, req[i].surfels, p);
         if (rc) return rc;
+        if (req[i].n_pixels > 0 && !req[i].out_color) return set_error(GRT_ERR_ARG, "request %d: out_color is NULL", i);
+        ShadeJob J;
         rc = make_job(req[i].bvh, req[i].surfels, &req[i].gbuffer, &req[i].env, &req[i].sampling, req[i].pixel_list,
-                      req[i].n_pixels, req[i].out_color, req[i].out_vis, req[i].out_ind, &T.job[i]);
+                      req[i].n_pixels, req[i].out_color, req[i].out_vis, req[i].out_ind, &J);
         if (rc) return rc;
-        T.job[i].unit_begin = units;
-        units += (req[i].n_pixels + (32 / T.job[i].G) - 1) / (32 / T.job[i].G);
+        if (J.n_pixels == 0) {
+            if (req[i].n_pixels > 0)
+                k_zero_outputs<<<(req[i].n_pixels + 255) / 256, 256, 0, st>>>(req[i].out_color, req[i].out_vis,
+                                                                              req[i].out_ind, req[i].n_pixels);
+            continue;
+        }
+        T.job[T.n_jobs++] = J;
     }
-    T.total_units = units;
-    if (units == 0) return GRT_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    GRT_CUDA(cudaMemsetAsync(work_counter, 0, sizeof(int32_t), st));
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = 0;
-    dispatch_k(p->k, [&](auto kc) {
-        constexpr int K = decltype(kc)::value;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shade_batch<K>, kShadeThreads, 0);
-        int grid = sms * (per_sm > 0 ? per_sm : 1);
-        int max_grid = (units * 32 + kShadeThreads - 1) / kShadeThreads;
-        if (grid > max_grid) grid = max_grid;
-        k_shade_batch<K><<<grid, kShadeThreads, 0, st>>>(T, work_counter);
-    });
-    return launch_error("k_shade_batch");
+    if (T.n_jobs == 0) return launch_error("k_zero_outputs");
+    return run_jobs<false>(T, p->k, nullptr, st);
 }

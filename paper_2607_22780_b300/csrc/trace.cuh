@@ -1,15 +1,16 @@
-// trace.cuh -- per-ray 2DGRT (Sec. III-B): LBVH traversal, ray-surfel test (Eq. 7),
+// trace.cuh -- per-ray 2DGRT (Sec. III-B): 4-wide BVH traversal, ray-surfel test (Eq. 7),
 // k-buffer of the nearest admitted hits, front-to-back compositing (Eq. 8).
 //
-// One thread traces one ray.  A round traverses the whole BVH collecting, in a register
+// One thread traces one ray.  A round traverses the BVH collecting, in a register
 // k-buffer, the K smallest keys (tau bits << 32 | surfel id) larger than the last key
-// composited; the round then composites them in order.  While collecting, the buffer
-// knows the transmittance its entries would leave: once the product of (1 - alpha) over
-// a prefix drops below T_min, entries after that prefix can never be composited, so they
-// are dropped and every node entered beyond the cut depth is culled.  A ray that filled
-// the buffer without terminating traverses again from its last key.  The composited
-// sequence is therefore exactly the (tau, id)-sorted admitted hits up to termination,
-// whatever K is.
+// composited, then composites them in order.  The buffer also tracks the product of
+// (1 - alpha) over its entries; once the round-start transmittance times that product is
+// below T_min (with a margin far wider than FP32 rounding of K factors), compositing is
+// certain to stop at or before the buffer's largest key, so hits beyond it -- and every
+// node entered beyond its depth -- are culled, as they are when the buffer is full.  A
+// ray that filled the buffer without terminating traverses again from its last key.  The
+// composited sequence is exactly the (tau, id)-sorted admitted hits up to termination,
+// whatever K and the tree shape are.
 #pragma once
 
 #include "grt_internal.cuh"
@@ -24,7 +25,8 @@ __host__ __forceinline__ TraceParams to_params(const grt_trace_params& p) {
     return TraceParams{p.alpha_min, p.alpha_max, p.t_min, p.t_max, p.T_min, p.eps_nd};
 }
 
-constexpr int kStackDepth = 64;  // >= tree depth: at most 30 code bits + 34 position bits
+// Ordered traversal keeps at most kWide - 1 entries per level of the current path.
+constexpr int kStackDepth = 96;
 constexpr uint64_t kNoKey = ~0ull;
 
 struct RayState {
@@ -45,18 +47,6 @@ __device__ __forceinline__ RayState make_ray(f3 o, f3 d) {
     r.oinv = mk3(-o.x * r.inv.x, -o.y * r.inv.y, -o.z * r.inv.z);
     r.eps = 1e-6f * (fmaxf(fabsf(o.x), fmaxf(fabsf(o.y), fabsf(o.z))) + 1.f);
     return r;
-}
-
-// Slab test of a box against [tlo, thi]; returns the entry distance in *tn.
-__device__ __forceinline__ bool slab(const RayState& r, float lx, float ly, float lz, float hx, float hy, float hz,
-                                     float tlo, float thi, float* tn) {
-    float x0 = fmaf(lx, r.inv.x, r.oinv.x), x1 = fmaf(hx, r.inv.x, r.oinv.x);
-    float y0 = fmaf(ly, r.inv.y, r.oinv.y), y1 = fmaf(hy, r.inv.y, r.oinv.y);
-    float z0 = fmaf(lz, r.inv.z, r.oinv.z), z1 = fmaf(hz, r.inv.z, r.oinv.z);
-    float tmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), tlo));
-    float tmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), thi));
-    *tn = tmin;
-    return tmin <= tmax;
 }
 
 // Eq. 7 on a packed record.  The plane test (|n.d| >= eps_nd, tau in (t_min, t_max)) is
@@ -96,8 +86,11 @@ template <int K>
 struct KBuf {
     uint64_t key[K];
     float a[K];
-    uint64_t cut;   // keys >= cut cannot be composited this round
-    float thi;      // node culling distance derived from cut
+    int cnt;         // valid entries, a prefix of key[]
+    float Tall;      // product of (1 - a) over the entries (any order)
+    uint64_t maxk;   // largest valid key
+    uint64_t cut;    // keys >= cut cannot be composited this round
+    float thi;       // node culling distance derived from cut
 
     __device__ __forceinline__ void reset(float t_max) {
 #pragma unroll
@@ -105,13 +98,15 @@ struct KBuf {
             key[j] = kNoKey;
             a[j] = 0.f;
         }
+        cnt = 0;
+        Tall = 1.f;
+        maxk = 0ull;
         cut = kNoKey;
         thi = t_max;
     }
 
-    // Insert (k, al); keep ascending order; recompute the termination cut from the
-    // transmittance T0 at the start of the round, with the compositing arithmetic.
     __device__ __forceinline__ void insert(uint64_t k, float al, float T0, float T_min, float t_max, float eps) {
+        const bool full = cnt == K;
         uint64_t ck = k;
         float ca = al;
 #pragma unroll
@@ -124,142 +119,227 @@ struct KBuf {
             ck = sw ? tk : ck;
             ca = sw ? ta : ca;
         }
-        float T = T0;
-        bool dead = false;
-        uint64_t nc = key[K - 1];
+        if (full) {
+            // the old maximum was evicted: recompute the product, no division drift
+            float t = 1.f;
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            if (dead) {
-                key[j] = kNoKey;
-            } else if (key[j] != kNoKey) {
-                T = mul_d(T, sub_d(1.0f, a[j]));
-                if (T < T_min) {
-                    dead = true;
-                    nc = key[j];
-                }
-            }
+            for (int j = 0; j < K; ++j) t *= sub_d(1.0f, a[j]);
+            Tall = t;
+            maxk = key[K - 1];
+        } else {
+            ++cnt;
+            Tall *= sub_d(1.0f, al);
+            maxk = k > maxk ? k : maxk;
         }
-        cut = nc;
-        thi = nc == kNoKey ? t_max : fmaf(key_tau(nc), 1.00001f, eps);
+        // T0 * Tall rounds within 2K ulps of the sequential product the compositor forms
+        bool terminates = T0 * Tall < T_min * 0.9999f;
+        cut = (cnt == K || terminates) ? maxk : kNoKey;
+        thi = cut == kNoKey ? t_max : fmaf(key_tau(cut), 1.00001f, eps);
     }
 };
 
-// Traverse the BVH once, feeding admitted hits with key in (last, cut) to the buffer.
+// Per-ray traversal state, advanced one wide node at a time so that a warp can refill
+// lanes whose rays have finished while others are still walking the tree.
+template <int K>
+struct TraceState {
+    RayState r;
+    KBuf<K> kb;
+    float T;         // transmittance before the next composited hit
+    uint64_t last;   // largest key composited so far
+    int node;        // next wide node, or -1 when the round's walk is over
+    int sp;          // stack depth
+    int budget;      // node visits left in this round
+    int rounds;
+    int ncomp;       // hits composited so far
+};
+
+template <int K>
+__device__ __forceinline__ void round_begin(const DevBvh& bvh, TraceState<K>& s, const TraceParams& P) {
+    s.kb.reset(P.t_max);
+    s.sp = 0;
+    s.budget = bvh.cap + 8;
+    s.node = (bvh.root >= 0) ? bvh.root : -1;
+}
+
+template <int K>
+__device__ __forceinline__ void trace_begin(const DevBvh& bvh, TraceState<K>& s, f3 o, f3 d, const TraceParams& P) {
+    s.r = make_ray(o, d);
+    s.T = 1.f;
+    s.last = 0ull;
+    s.rounds = 1;
+    s.ncomp = 0;
+    round_begin(bvh, s, P);
+}
+
 template <int K, bool COUNT>
-__device__ __forceinline__ void traverse(const DevBvh& bvh, const RayState& r, const TraceParams& P, uint64_t last,
-                                         float T0, KBuf<K>& kb, Counters& cnt) {
-    int2 stack[kStackDepth];
-    int sp = 0;
-    float tlo = fmaf(P.t_min, 0.99999f, -r.eps);
-    auto test = [&](int rec) {
+__device__ __forceinline__ void test_leaf(const DevBvh& bvh, TraceState<K>& s, int ref, const TraceParams& P,
+                                          Counters& cnt) {
+    int first = leaf_first(ref), count = leaf_count(ref);
+    if (first + count > bvh.n) {
+        atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
+        return;
+    }
+    for (int i = 0; i < count; ++i) {
         if (COUNT) ++cnt.tests;
         float tau, al;
         int id;
-        if (intersect(bvh.records, rec, r, P, &tau, &al, &id)) {
+        if (intersect(bvh.records, first + i, s.r, P, &tau, &al, &id)) {
             uint64_t k = make_key(tau, id);
-            if (k > last && k < kb.cut) kb.insert(k, al, T0, P.T_min, P.t_max, r.eps);
+            if (k > s.last && k < s.kb.cut) s.kb.insert(k, al, s.T, P.T_min, P.t_max, s.r.eps);
         }
-    };
-    int node = bvh.root;
-    if (node == kRefEmpty) return;
-    if (node < 0) {
-        test(~node);
-        return;
-    }
-    // every internal node is entered at most once per traversal; a longer walk means a
-    // corrupt hierarchy, which is reported instead of looping
-    int budget = bvh.n + 8;
-    while (true) {
-        if (COUNT) ++cnt.nodes;
-        if ((unsigned)node >= (unsigned)(bvh.n - 1) || --budget < 0) {
-            atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
-            return;
-        }
-        const float4* N = bvh.nodes + 4 * (size_t)node;
-        float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
-        int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-        float t0, t1;
-        bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, tlo, kb.thi, &t0);
-        bool h1 = slab(r, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, tlo, kb.thi, &t1);
-        if (h0 && c0 < 0) {
-            if (~c0 < bvh.n) test(~c0);
-            else atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
-            h0 = false;
-        }
-        if (h1 && c1 < 0) {
-            if (~c1 < bvh.n) test(~c1);
-            else atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
-            h1 = false;
-        }
-        h0 = h0 && t0 <= kb.thi;
-        h1 = h1 && t1 <= kb.thi;
-        if (h0 && h1) {
-            bool swap = t1 < t0;
-            int near = swap ? c1 : c0, far = swap ? c0 : c1;
-            float tf = swap ? t0 : t1;
-            if (sp < kStackDepth) {
-                stack[sp++] = make_int2(far, __float_as_int(tf));
-            } else {
-                atomicOr(bvh.status, GRT_STATUS_STACK_OVERFLOW);
-            }
-            node = near;
-            continue;
-        }
-        if (h0) {
-            node = c0;
-            continue;
-        }
-        if (h1) {
-            node = c1;
-            continue;
-        }
-        bool found = false;
-        while (sp > 0) {
-            int2 e = stack[--sp];
-            if (__int_as_float(e.y) <= kb.thi) {
-                node = e.x;
-                found = true;
-                break;
-            }
-        }
-        if (!found) break;
     }
 }
 
+// One step of the round's walk: visit one wide node (testing its leaf children) and pick
+// the next node.  Returns false once the walk of this round is over.
+template <int K, bool COUNT>
+__device__ __forceinline__ bool trav_step(const DevBvh& bvh, TraceState<K>& s, int2* stack, const TraceParams& P,
+                                          Counters& cnt) {
+    int node = s.node;
+    if (node < 0) {
+        // root that is a single leaf (n == 1), or an empty scene
+        if (node == -1 && bvh.root != kRefEmpty && bvh.root < 0 && s.budget > 0) {
+            s.budget = 0;
+            test_leaf<K, COUNT>(bvh, s, bvh.root, P, cnt);
+        }
+        return false;
+    }
+    if (COUNT) ++cnt.nodes;
+    if ((unsigned)node >= (unsigned)bvh.cap || --s.budget < 0) {
+        atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
+        s.node = -2;
+        return false;
+    }
+    const RayState& r = s.r;
+    const float tlo = fmaf(P.t_min, 0.99999f, -r.eps);
+    // the near plane of each axis is lo for a positive direction, hi otherwise
+    const int ox = r.inv.x >= 0.f ? 0 : 3, oy = r.inv.y >= 0.f ? 1 : 4, oz = r.inv.z >= 0.f ? 2 : 5;
+    const float4* N = bvh.nodes + 8 * (size_t)node;
+    const float4 nx = __ldg(N + ox), ny = __ldg(N + oy), nz = __ldg(N + oz);
+    const float4 fx = __ldg(N + (3 - ox)), fy = __ldg(N + (5 - oy)), fz = __ldg(N + (7 - oz));
+    const int4 ref = __ldg(reinterpret_cast<const int4*>(N + 6));
+    const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, nys[4] = {ny.x, ny.y, ny.z, ny.w}, nzs[4] = {nz.x, nz.y, nz.z, nz.w};
+    const float fxs[4] = {fx.x, fx.y, fx.z, fx.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
+    const int refs[4] = {ref.x, ref.y, ref.z, ref.w};
+    float tn[4];
+    bool hit[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float t0 = fmaxf(fmaxf(fmaf(nxs[c], r.inv.x, r.oinv.x), fmaf(nys[c], r.inv.y, r.oinv.y)),
+                         fmaxf(fmaf(nzs[c], r.inv.z, r.oinv.z), tlo));
+        float t1 = fminf(fminf(fmaf(fxs[c], r.inv.x, r.oinv.x), fmaf(fys[c], r.inv.y, r.oinv.y)),
+                         fminf(fmaf(fzs[c], r.inv.z, r.oinv.z), s.kb.thi));
+        tn[c] = t0;
+        hit[c] = t0 <= t1;
+    }
+    // leaves in slot order (the k-buffer sorts), one copy of the leaf code for all slots,
+    // then internal children near to far
+    unsigned leaves = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (hit[c] && refs[c] < 0) {
+            leaves |= 1u << c;
+            hit[c] = false;
+        }
+    }
+#pragma unroll 1
+    while (leaves) {
+        int c = __ffs(leaves) - 1;
+        leaves &= leaves - 1;
+        int lr = c == 0 ? ref.x : (c == 1 ? ref.y : (c == 2 ? ref.z : ref.w));
+        test_leaf<K, COUNT>(bvh, s, lr, P, cnt);
+    }
+    const float inf = __int_as_float(0x7f800000);
+    float d[4];
+    int e[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        bool h = hit[c] && tn[c] <= s.kb.thi;
+        d[c] = h ? tn[c] : inf;
+        e[c] = refs[c];
+    }
+#define GRT_CSWAP(i, j)              \
+    if (d[j] < d[i]) {               \
+        float td = d[i];             \
+        d[i] = d[j];                 \
+        d[j] = td;                   \
+        int te = e[i];               \
+        e[i] = e[j];                 \
+        e[j] = te;                   \
+    }
+    GRT_CSWAP(0, 1) GRT_CSWAP(2, 3) GRT_CSWAP(0, 2) GRT_CSWAP(1, 3) GRT_CSWAP(1, 2)
+#undef GRT_CSWAP
+    if (d[0] != inf) {
+#pragma unroll
+        for (int c = 3; c >= 1; --c) {
+            if (d[c] != inf) {
+                if (s.sp < kStackDepth) {
+                    stack[s.sp++] = make_int2(e[c], __float_as_int(d[c]));
+                } else {
+                    atomicOr(bvh.status, GRT_STATUS_STACK_OVERFLOW);
+                }
+            }
+        }
+        s.node = e[0];
+        return true;
+    }
+    while (s.sp > 0) {
+        int2 t = stack[--s.sp];
+        if (__int_as_float(t.y) <= s.kb.thi) {
+            s.node = t.x;
+            return true;
+        }
+    }
+    s.node = -2;
+    return false;
+}
+
+// End of a round: composite the buffer in order (Eq. 8).  Returns true when the ray is
+// finished; otherwise the next round starts after the last composited key.
+template <int K, bool COUNT, class Visitor>
+__device__ __forceinline__ bool round_end(const DevBvh& bvh, TraceState<K>& s, const TraceParams& P, Visitor& vis,
+                                          Counters& cnt) {
+    bool term = false;
+    int filled = 0;
+    float T = s.T;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        if (!term && j < s.kb.cnt) {
+            vis.composite(s.ncomp + filled, key_id(s.kb.key[j]), key_tau(s.kb.key[j]), s.kb.a[j], T);
+            T = mul_d(T, sub_d(1.0f, s.kb.a[j]));
+            ++filled;
+            if (T < P.T_min) term = true;
+        }
+    }
+    s.T = T;
+    s.ncomp += filled;
+    if (COUNT) cnt.comp += filled;
+    if (term || s.kb.cnt < K) return true;
+    if (++s.rounds > bvh.n + 1) {  // each full round composites K new hits
+        atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
+        return true;
+    }
+    s.last = s.kb.key[K - 1];
+    round_begin(bvh, s, P);
+    return false;
+}
+
 // Trace one ray through all rounds.  `vis` receives composite(k, id, tau, alpha, T)
-// for each composited hit in order (T = transmittance before the hit) and returns the
-// final transmittance via vis.finish(T).  Returns the number of rounds.
+// for each composited hit in order (T = transmittance before the hit) and the final
+// transmittance via vis.finish(T).  Returns the number of rounds.
 template <int K, bool COUNT, class Visitor>
 __device__ __forceinline__ int trace_ray(const DevBvh& bvh, const RayState& r, const TraceParams& P, Visitor& vis,
                                          Counters& cnt) {
-    float T = 1.f;
-    uint64_t last = 0ull;
-    int k = 0, rounds = 0;
-    KBuf<K> kb;
+    int2 stack[kStackDepth];
+    TraceState<K> s;
+    trace_begin(bvh, s, r.o, r.d, P);
     while (true) {
-        if (++rounds > bvh.n + 1) {  // each full round composites K new hits
-            atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
-            break;
+        while (trav_step<K, COUNT>(bvh, s, stack, P, cnt)) {
         }
-        kb.reset(P.t_max);
-        traverse<K, COUNT>(bvh, r, P, last, T, kb, cnt);
-        bool term = false;
-        int filled = 0;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            if (!term && kb.key[j] != kNoKey) {
-                vis.composite(k++, key_id(kb.key[j]), key_tau(kb.key[j]), kb.a[j], T);
-                T = mul_d(T, sub_d(1.0f, kb.a[j]));
-                ++filled;
-                if (T < P.T_min) term = true;
-            }
-        }
-        if (COUNT) cnt.comp += filled;
-        if (term || filled < K) break;
-        last = kb.key[K - 1];
+        if (round_end<K, COUNT>(bvh, s, P, vis, cnt)) break;
     }
-    vis.finish(T);
-    return rounds;
+    vis.finish(s.T);
+    return s.rounds;
 }
 
 // ----------------------------------------------------------------------------- colour
@@ -290,6 +370,8 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16])
 }
 
 // Surfel colour toward direction d: RGB, or max(0, SH(d) + 0.5) per channel.
+static __device__ __noinline__ void surfel_colour_sh(const float* __restrict__ color, int id, f3 d, float c[3]);
+
 __device__ __forceinline__ void surfel_colour(const float* __restrict__ color, int cdim, int id, f3 d, float c[3]) {
     if (cdim == 3) {
         c[0] = __ldg(color + 3 * (size_t)id);
@@ -297,6 +379,11 @@ __device__ __forceinline__ void surfel_colour(const float* __restrict__ color, i
         c[2] = __ldg(color + 3 * (size_t)id + 2);
         return;
     }
+    surfel_colour_sh(color, id, d, c);
+}
+
+// SH colour kept out of line: one copy serves every composite site.
+static __device__ __noinline__ void surfel_colour_sh(const float* __restrict__ color, int id, f3 d, float c[3]) {
     float Y[16];
     sh_basis(d.x, d.y, d.z, Y);
     const float4* s = reinterpret_cast<const float4*>(color + 48 * (size_t)id);
