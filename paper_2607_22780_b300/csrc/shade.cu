@@ -124,6 +124,71 @@ __global__ void __launch_bounds__(kShadeThreads) k_trace_rays(const __grid_const
     }
 }
 
+// Persistent variant of k_trace_rays: warps stay resident and walk their rays one wide
+// node per step; once kRefillLanes lanes have finished, the warp claims that many new
+// rays from a global counter, so a long ray holds one lane instead of a whole warp.
+constexpr int kRefillLanes = 16;
+
+template <int K, int CAP>
+__global__ void __launch_bounds__(kShadeThreads) k_trace_rays_dyn(const __grid_constant__ JobTable<CAP> T,
+                                                                  const float4* __restrict__ dirs,
+                                                                  float4* __restrict__ res,
+                                                                  unsigned long long* __restrict__ next_ray) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int2 stack[kStackDepth];
+    TraceState<K> ts;
+    ColourVisitor cv(nullptr, 3, mk3(0.f, 0.f, 0.f), nullptr, 0);
+    const ShadeJob* J = &T.job[0];
+    long long ray = -1;
+    bool act = false, drained = false;
+    Counters cnt{0, 0, 0};
+    while (true) {
+        unsigned idle = __ballot_sync(0xffffffffu, !act);
+        int nidle = __popc(idle);
+        if (!drained && (nidle >= kRefillLanes || nidle == 32)) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(next_ray, (unsigned long long)nidle);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + nidle >= (unsigned long long)T.total_rays) drained = true;
+            if (!act) {
+                long long r = (long long)base + __popc(idle & lt);
+                if (r < T.total_rays) {
+                    ray = r;
+                    float4 dw = __ldg(dirs + r);
+                    if (dw.w == 0.f) {
+                        res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
+                    } else {
+                        J = &T.job[T.find_ray(r)];
+                        int li = (int)((r - J->ray_begin) / J->Nr);
+                        int pix = J->pixel_list ? __ldg(J->pixel_list + li) : li;
+                        f3 o = mk3(__ldg(J->gb.pos + 3 * (size_t)pix), __ldg(J->gb.pos + 3 * (size_t)pix + 1),
+                                   __ldg(J->gb.pos + 3 * (size_t)pix + 2));
+                        f3 d = mk3(dw.x, dw.y, dw.z);
+                        trace_begin(J->bvh, ts, o, d, T.P);
+                        cv.color = J->color;
+                        cv.cdim = J->cdim;
+                        cv.d = d;
+                        cv.c[0] = cv.c[1] = cv.c[2] = 0.f;
+                        cv.nh = 0;
+                        act = true;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, act)) {
+            if (drained) break;
+            continue;
+        }
+        if (act && !trav_step<K, false>(J->bvh, ts, stack, T.P, cnt)) {
+            if (round_end<K, false>(J->bvh, ts, T.P, cv, cnt)) {
+                res[ray] = make_float4(cv.c[0], cv.c[1], cv.c[2], ts.T);
+                act = false;
+            }
+        }
+    }
+}
+
 // Eq. 13: a warp unit shades 32/G pixels; lane sub of a pixel group takes samples
 // j = sub + m G in order, the group sums with a butterfly, so the result is fixed.
 template <int CAP>
@@ -258,14 +323,26 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st) {
     if (rays == 0) return GRT_OK;
     keep_pool_memory();
     float4* buf = nullptr;
-    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * 2 * (size_t)rays, st));
+    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1), st));
     float4* dirs = buf;
     float4* res = buf + rays;
+    unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + 2 * rays);
     const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
     k_sample_rays<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
     dispatch_k(k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
-        k_trace_rays<K, COUNT, CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, counters);
+        if (COUNT) {  // counting pass: one ray per thread, same traversal
+            k_trace_rays<K, COUNT, CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, counters);
+        } else {
+            cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_rays_dyn<K, CAP>, kShadeThreads, 0);
+            long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+            if (grid > gr) grid = gr;
+            k_trace_rays_dyn<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, next_ray);
+        }
     });
     if (!COUNT) {
         const long long ga = (units * 32 + kShadeThreads - 1) / kShadeThreads;
