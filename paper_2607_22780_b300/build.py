@@ -38,10 +38,11 @@ def stale() -> bool:
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and not stale():
+def build(force: bool = False, verbose: bool = False, extra=(), out: str = None) -> str:
+    out = out or OUT
+    if out == OUT and not force and not stale():
         return OUT
-    bdir = os.path.join(CSRC, "_build")
+    bdir = os.path.join(CSRC, "_build" if out == OUT else "_build_" + os.path.basename(out).replace('.', '_'))
     os.makedirs(bdir, exist_ok=True)
 
     def compile_one(src):
@@ -58,13 +59,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = OUT + f".tmp{os.getpid()}"
+    tmp = out + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

@@ -127,10 +127,13 @@ __global__ void __launch_bounds__(kShadeThreads) k_trace_rays(const __grid_const
 // Persistent variant of k_trace_rays: warps stay resident and walk their rays one wide
 // node per step; once kRefillLanes lanes have finished, the warp claims that many new
 // rays from a global counter, so a long ray holds one lane instead of a whole warp.
-constexpr int kRefillLanes = 16;
+constexpr int kRefillLanes = 8;
+#ifndef GRT_TRACE_MIN_BLOCKS
+#define GRT_TRACE_MIN_BLOCKS 4  // 128 threads x 4 blocks: at most 128 registers per thread
+#endif
 
 template <int K, int CAP>
-__global__ void __launch_bounds__(kShadeThreads) k_trace_rays_dyn(const __grid_constant__ JobTable<CAP> T,
+__global__ void __launch_bounds__(kShadeThreads, GRT_TRACE_MIN_BLOCKS) k_trace_rays_dyn(const __grid_constant__ JobTable<CAP> T,
                                                                   const float4* __restrict__ dirs,
                                                                   float4* __restrict__ res,
                                                                   unsigned long long* __restrict__ next_ray) {
