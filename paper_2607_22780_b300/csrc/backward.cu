@@ -13,8 +13,7 @@
 //
 // The hit list is never stored: a first traversal gives c_rt and T_f, a second replays
 // the same (tau, id) sequence and scatters gradients with vector atomics.
-#include "common_args.cuh"
-#include "shade.cuh"
+#include "wavefront.cuh"
 
 namespace grt {
 namespace {
@@ -182,56 +181,110 @@ __global__ void __launch_bounds__(128) k_trace_backward(DevBvh bvh, TraceParams 
     ray_adjoint<K>(bvh, P, s, o, d, Gc, Go, g);
 }
 
-struct ShadeBwd {
-    DevBvh bvh;
-    grt_surfels s;
-    GbufDev gb;
-    EnvDev env;
-    Sampling S;
-    const int* pixel_list;
-    int n_pixels;
+// Per-ray adjoint of the shaded outputs (Eq. 13): for a traced sample with weight
+// g = f cos / q and environment radiance L,
+//   dL/dc_rt = (dL/dcolor * g + dL/dind) / N_r,  dL/do_rt = -(sum_c dL/dcolor_c g_c L_c + dL/dvis) / N_r.
+// (0, 0, 0, 0) marks a ray without hits or without a sample.
+struct AdjIn {
     const float *dcol, *dvis, *dind;
-    int G, spl;
 };
 
-template <int K>
-__global__ void __launch_bounds__(128) k_shade_backward(const __grid_constant__ ShadeBwd J, TraceParams P, GradPtrs g) {
-    const int lane = threadIdx.x & 31;
-    const int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int G = J.G;
-    const int slot = lane / G, sub = lane - slot * G;
-    const int li = u * (32 / G) + slot;
-    if (li >= J.n_pixels) return;
-    const int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
-    if ((unsigned)pix >= (unsigned)(J.gb.W * J.gb.H)) {
-        atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
-        return;
-    }
-    if (!__ldg(J.gb.valid + pix)) return;
-    const int Nr = J.S.n_cos + J.S.n_ggx + J.S.n_env;
-    const float inv = 1.f / (float)Nr;
-    float dc[3] = {J.dcol[3 * (size_t)li] * inv, J.dcol[3 * (size_t)li + 1] * inv, J.dcol[3 * (size_t)li + 2] * inv};
-    float dv = J.dvis ? J.dvis[li] * inv : 0.f;
-    float di[3] = {0.f, 0.f, 0.f};
-    if (J.dind) {
-        di[0] = J.dind[3 * (size_t)li] * inv;
-        di[1] = J.dind[3 * (size_t)li + 1] * inv;
-        di[2] = J.dind[3 * (size_t)li + 2] * inv;
-    }
-    PixelState ps = load_pixel(J.gb, pix);
-    for (int m = 0; m < J.spl; ++m) {
-        int j = sub + m * G;
-        if (j >= Nr) break;
-        f3 w;
-        if (!draw_direction(J.S, J.env, ps, pix, j, &w)) continue;
-        SampleWeight sw = sample_weight(J.S, J.env, ps, w);
-        float Gc[3], Go = -dv;
+__global__ void __launch_bounds__(kShadeThreads) k_adjoint_weights(const __grid_constant__ JobTable<1> T,
+                                                                   const float4* __restrict__ dirs,
+                                                                   const float4* __restrict__ res, AdjIn in,
+                                                                   float4* __restrict__ adj) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= T.total_rays) return;
+    float4 rr = __ldg(res + r);
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rr.w >= 0.f && !(rr.w == 1.f && rr.x == 0.f && rr.y == 0.f && rr.z == 0.f)) {
+        const ShadeJob& J = T.job[0];
+        int li = (int)(r / J.Nr);
+        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+        PixelState ps = load_pixel(J.gb, pix);
+        float4 dw = __ldg(dirs + r);
+        SampleWeight sw = sample_weight(J.S, J.env, ps, mk3(dw.x, dw.y, dw.z));
+        const float inv = 1.f / (float)J.Nr;
+        float Gc[3], Go = in.dvis ? -__ldg(in.dvis + li) * inv : 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            Gc[c] = fmaf(dc[c], sw.g[c], di[c]);
-            Go = fmaf(-dc[c] * sw.g[c], sw.L[c], Go);
+            float dc = __ldg(in.dcol + 3 * (size_t)li + c) * inv;
+            float di = in.dind ? __ldg(in.dind + 3 * (size_t)li + c) * inv : 0.f;
+            Gc[c] = fmaf(dc, sw.g[c], di);
+            Go = fmaf(-dc * sw.g[c], sw.L[c], Go);
         }
-        ray_adjoint<K>(J.bvh, P, J.s, ps.x, w, Gc, Go, g);
+        out = make_float4(Gc[0], Gc[1], Gc[2], Go);
+    }
+    adj[r] = out;
+}
+
+// Persistent adjoint replay: one traversal per ray, totals (c_rt, T_f) from the forward
+// pass; lanes refill from a global counter like the forward trace.
+template <int K>
+__global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : 4) k_adjoint_dyn(const __grid_constant__ JobTable<1> T,
+                                                                  const float4* __restrict__ dirs,
+                                                                  const float4* __restrict__ res,
+                                                                  const float4* __restrict__ adj, GradPtrs g,
+                                                                  unsigned long long* __restrict__ next_ray) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const ShadeJob& J = T.job[0];
+    int2 stack[kStackDepth];
+    TraceState<K> ts;
+    AdjointVisitor av;
+    av.mu = J.mu;
+    av.quat = J.quat;
+    av.scale = J.scale;
+    av.opacity = J.opacity;
+    av.color = J.color;
+    av.cdim = J.cdim;
+    av.alpha_max = T.P.alpha_max;
+    av.g = g;
+    bool act = false, drained = false;
+    Counters cnt{0, 0, 0};
+    while (true) {
+        unsigned idle = __ballot_sync(0xffffffffu, !act);
+        int nidle = __popc(idle);
+        if (!drained && (nidle >= 8 || nidle == 32)) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(next_ray, (unsigned long long)nidle);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + nidle >= (unsigned long long)T.total_rays) drained = true;
+            if (!act) {
+                long long r = (long long)base + __popc(idle & lt);
+                if (r < T.total_rays) {
+                    float4 a = __ldg(adj + r);
+                    if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f) {
+                        float4 rr = __ldg(res + r), dw = __ldg(dirs + r);
+                        int li = (int)(r / J.Nr);
+                        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+                        f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
+                                   __ldg(J.gb.pos + 3 * (size_t)pix + 2));
+                        f3 d = mk3(dw.x, dw.y, dw.z);
+                        trace_begin(J.bvh, ts, o, d, T.P);
+                        av.o = o;
+                        av.d = d;
+                        av.Gc[0] = a.x;
+                        av.Gc[1] = a.y;
+                        av.Gc[2] = a.z;
+                        av.Go = a.w;
+                        av.Tf = rr.w;
+                        av.crt[0] = rr.x;
+                        av.crt[1] = rr.y;
+                        av.crt[2] = rr.z;
+                        av.Cacc[0] = av.Cacc[1] = av.Cacc[2] = 0.f;
+                        act = true;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, act)) {
+            if (drained) break;
+            continue;
+        }
+        if (act && !trav_step<K, false>(J.bvh, ts, stack, T.P, cnt)) {
+            if (round_end<K, false>(J.bvh, ts, T.P, av, cnt)) act = false;
+        }
     }
 }
 
@@ -281,39 +334,44 @@ extern "C" int grt_shade_backward(const grt_bvh* b, const grt_surfels* s, const 
     if (rc) return rc;
     rc = check_grads(grads, s);
     if (rc) return rc;
-    if (!gb || !e || !smp || !e->tables) return set_error(GRT_ERR_ARG, "gbuffer, env or sampling is NULL");
     if (n_pixels < 0 || (n_pixels > 0 && !dL_dcolor)) return set_error(GRT_ERR_ARG, "bad n_pixels or dL_dcolor");
-    if (!pixel_list && n_pixels > gb->W * gb->H) return set_error(GRT_ERR_ARG, "n_pixels exceeds W*H");
-    int Nr = smp->n_cos + smp->n_ggx + smp->n_env;
-    if (smp->n_cos < 0 || smp->n_ggx < 0 || smp->n_env < 0 || Nr > 1024 || (smp->brdf != 0 && smp->brdf != 1))
-        return set_error(GRT_ERR_ARG, "bad sampling");
-    if (n_pixels == 0 || Nr == 0) return GRT_OK;
-    ShadeBwd J;
-    J.bvh = dev_bvh(b);
-    J.s = *s;
-    J.gb = GbufDev{gb->pos, gb->normal, gb->albedo, gb->rough, gb->metal, gb->valid, gb->eye[0], gb->eye[1], gb->eye[2],
-                   gb->W, gb->H};
-    EnvLayout l = env_layout(e->W, e->H);
-    const char* tb = (const char*)e->tables;
-    J.env = EnvDev{(const float4*)(tb + l.texel), (const float*)(tb + l.marg), (const float*)(tb + l.cond), e->W, e->H,
-                   (float)e->W * (float)e->H / (2.f * kPi * kPi)};
-    J.S = Sampling{smp->n_cos, smp->n_ggx, smp->n_env, smp->brdf, (uint32_t)(smp->seed & 0xFFFFFFFFu),
-                   (uint32_t)(smp->seed >> 32)};
-    J.pixel_list = pixel_list;
-    J.n_pixels = n_pixels;
-    J.dcol = dL_dcolor;
-    J.dvis = dL_dvis;
-    J.dind = dL_dind;
-    J.G = group_lanes(Nr);
-    J.spl = (Nr + J.G - 1) / J.G;
-    int units = (n_pixels + (32 / J.G) - 1) / (32 / J.G);
-    int grid = (int)(((long long)units * 32 + 127) / 128);
-    TraceParams P = to_params(*p);
-    GradPtrs g{grads->mu, grads->quat, grads->scale, grads->opacity, grads->color};
+    JobTable<1> T;
+    T.P = to_params(*p);
+    T.n_jobs = 1;
+    rc = make_job(b, s, gb, e, smp, pixel_list, n_pixels, nullptr, nullptr, nullptr, &T.job[0]);
+    if (rc) return rc;
+    ShadeJob& J = T.job[0];
+    if (J.n_pixels == 0) return GRT_OK;
+    const long long rays = (long long)J.n_pixels * J.Nr;
+    T.total_rays = rays;
+    T.total_units = 0;
     cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_memory();
+    float4* buf = nullptr;
+    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (3 * (size_t)rays + 1), st));
+    float4* dirs = buf;
+    float4* res = buf + rays;
+    float4* adj = buf + 2 * rays;
+    unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + 3 * rays);
+    const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
+    GradPtrs g{grads->mu, grads->quat, grads->scale, grads->opacity, grads->color};
+    k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
     dispatch_k(p->k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
-        k_shade_backward<K><<<grid, 128, 0, st>>>(J, P, g);
+        launch_trace_dyn<K, 1>(T, dirs, res, next_ray, gr, st);
+        k_adjoint_weights<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, AdjIn{dL_dcolor, dL_dvis, dL_dind},
+                                                                   adj);
+        cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_dyn<K>, kShadeThreads, 0);
+        long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+        if (grid > gr) grid = gr;
+        k_adjoint_dyn<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, next_ray);
     });
-    return launch_error("k_shade_backward");
+    cudaError_t err = cudaGetLastError();
+    cudaFreeAsync(buf, st);
+    if (err != cudaSuccess) return check_cuda(err, "shade backward kernels");
+    return GRT_OK;
 }

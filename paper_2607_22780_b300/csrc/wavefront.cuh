@@ -1,0 +1,268 @@
+// wavefront.cuh -- pieces shared by the wavefront shading and shading-adjoint passes:
+// the job table (one or many shading requests laid out as one flat list of rays), the
+// ray-sampling kernel and the persistent per-ray trace kernel.
+#pragma once
+
+#include <mutex>
+
+#include "common_args.cuh"
+#include "shade.cuh"
+
+namespace grt {
+
+constexpr int kShadeThreads = 128;
+
+struct ShadeJob {
+    DevBvh bvh;
+    const float* color;
+    const float *mu, *quat, *scale, *opacity;  // surfel parameters (adjoint pass)
+    int cdim;
+    GbufDev gb;
+    EnvDev env;
+    Sampling S;
+    const int* pixel_list;
+    int n_pixels;
+    int Nr;
+    float *out_color, *out_vis, *out_ind;
+    int G, spl;              // accumulation: lanes per pixel, samples per lane
+    long long ray_begin;     // first ray of this job in the launch's ray buffers
+    long long unit_begin;    // first accumulation warp unit of this job
+};
+
+template <int CAP>
+struct JobTable {
+    TraceParams P;
+    int n_jobs;
+    long long total_rays;
+    long long total_units;
+    ShadeJob job[CAP];
+
+    __device__ __forceinline__ int find_ray(long long r) const {
+        int j = 0;
+        while (j + 1 < n_jobs && r >= job[j + 1].ray_begin) ++j;
+        return j;
+    }
+    __device__ __forceinline__ int find_unit(long long u) const {
+        int j = 0;
+        while (j + 1 < n_jobs && u >= job[j + 1].unit_begin) ++j;
+        return j;
+    }
+};
+
+namespace {
+
+__device__ __forceinline__ int pixel_of(const ShadeJob& J, int li) {
+    int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+    if ((unsigned)pix >= (unsigned)(J.gb.W * J.gb.H)) {
+        atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
+        return -1;
+    }
+    return pix;
+}
+
+// ray buffer entry: (direction, 1) for a traced sample, (0, 0, 0, 0) for none
+template <int CAP>
+__global__ void __launch_bounds__(kShadeThreads) k_sample_rays(const __grid_constant__ JobTable<CAP> T,
+                                                               float4* __restrict__ dirs) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= T.total_rays) return;
+    const ShadeJob& J = T.job[T.find_ray(r)];
+    long long lr = r - J.ray_begin;
+    int li = (int)(lr / J.Nr), j = (int)(lr - (long long)li * J.Nr);
+    int pix = pixel_of(J, li);
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pix >= 0 && __ldg(J.gb.valid + pix)) {
+        PixelState ps = load_pixel(J.gb, pix);
+        f3 w;
+        if (draw_direction(J.S, J.env, ps, pix, j, &w)) out = make_float4(w.x, w.y, w.z, 1.f);
+    }
+    dirs[r] = out;
+}
+
+// (c_rt, T) per ray; T = -1 marks "no ray"
+template <int K, bool COUNT, int CAP>
+__global__ void __launch_bounds__(kShadeThreads) k_trace_rays(const __grid_constant__ JobTable<CAP> T,
+                                                              const float4* __restrict__ dirs, float4* __restrict__ res,
+                                                              long long* counters) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    Counters cnt{0, 0, 0};
+    if (r < T.total_rays) {
+        float4 dw = __ldg(dirs + r);
+        float4 out = make_float4(0.f, 0.f, 0.f, -1.f);
+        if (dw.w != 0.f) {
+            const ShadeJob& J = T.job[T.find_ray(r)];
+            int li = (int)((r - J.ray_begin) / J.Nr);
+            int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+            f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
+                       __ldg(J.gb.pos + 3 * (size_t)pix + 2));
+            f3 d = mk3(dw.x, dw.y, dw.z);
+            RayState rs = make_ray(o, d);
+            ColourVisitor v(J.color, J.cdim, d, nullptr, 0);
+            trace_ray<K, COUNT>(J.bvh, rs, T.P, v, cnt);
+            out = make_float4(v.c[0], v.c[1], v.c[2], v.T);
+        }
+        if (!COUNT) res[r] = out;
+    }
+    if (COUNT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt.nodes += __shfl_xor_sync(0xffffffffu, cnt.nodes, o);
+            cnt.tests += __shfl_xor_sync(0xffffffffu, cnt.tests, o);
+            cnt.comp += __shfl_xor_sync(0xffffffffu, cnt.comp, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd((unsigned long long*)counters, (unsigned long long)cnt.nodes);
+            atomicAdd((unsigned long long*)counters + 1, (unsigned long long)cnt.tests);
+            atomicAdd((unsigned long long*)counters + 2, (unsigned long long)cnt.comp);
+        }
+    }
+}
+
+// Persistent variant of k_trace_rays: warps stay resident and walk their rays one wide
+// node per step; once kRefillLanes lanes have finished, the warp claims that many new
+// rays from a global counter, so a long ray holds one lane instead of a whole warp.
+constexpr int kRefillLanes = 8;
+#ifndef GRT_TRACE_MIN_BLOCKS
+#define GRT_TRACE_MIN_BLOCKS 4  // 128 threads x 4 blocks: at most 128 registers per thread
+#endif
+
+template <int K, int CAP>
+__global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : GRT_TRACE_MIN_BLOCKS) k_trace_rays_dyn(const __grid_constant__ JobTable<CAP> T,
+                                                                  const float4* __restrict__ dirs,
+                                                                  float4* __restrict__ res,
+                                                                  unsigned long long* __restrict__ next_ray) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int2 stack[kStackDepth];
+    TraceState<K> ts;
+    ColourVisitor cv(nullptr, 3, mk3(0.f, 0.f, 0.f), nullptr, 0);
+    const ShadeJob* J = &T.job[0];
+    long long ray = -1;
+    bool act = false, drained = false;
+    Counters cnt{0, 0, 0};
+    while (true) {
+        unsigned idle = __ballot_sync(0xffffffffu, !act);
+        int nidle = __popc(idle);
+        if (!drained && (nidle >= kRefillLanes || nidle == 32)) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(next_ray, (unsigned long long)nidle);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + nidle >= (unsigned long long)T.total_rays) drained = true;
+            if (!act) {
+                long long r = (long long)base + __popc(idle & lt);
+                if (r < T.total_rays) {
+                    ray = r;
+                    float4 dw = __ldg(dirs + r);
+                    if (dw.w == 0.f) {
+                        res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
+                    } else {
+                        J = &T.job[T.find_ray(r)];
+                        int li = (int)((r - J->ray_begin) / J->Nr);
+                        int pix = J->pixel_list ? __ldg(J->pixel_list + li) : li;
+                        f3 o = mk3(__ldg(J->gb.pos + 3 * (size_t)pix), __ldg(J->gb.pos + 3 * (size_t)pix + 1),
+                                   __ldg(J->gb.pos + 3 * (size_t)pix + 2));
+                        f3 d = mk3(dw.x, dw.y, dw.z);
+                        trace_begin(J->bvh, ts, o, d, T.P);
+                        cv.color = J->color;
+                        cv.cdim = J->cdim;
+                        cv.d = d;
+                        cv.c[0] = cv.c[1] = cv.c[2] = 0.f;
+                        cv.nh = 0;
+                        act = true;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, act)) {
+            if (drained) break;
+            continue;
+        }
+        if (act && !trav_step<K, false>(J->bvh, ts, stack, T.P, cnt)) {
+            if (round_end<K, false>(J->bvh, ts, T.P, cv, cnt)) {
+                res[ray] = make_float4(cv.c[0], cv.c[1], cv.c[2], ts.T);
+                act = false;
+            }
+        }
+    }
+}
+
+__global__ void k_zero_outputs(float* c, float* v, float* i, int n) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    c[3 * (size_t)t] = c[3 * (size_t)t + 1] = c[3 * (size_t)t + 2] = 0.f;
+    if (v) v[t] = 0.f;
+    if (i) i[3 * (size_t)t] = i[3 * (size_t)t + 1] = i[3 * (size_t)t + 2] = 0.f;
+}
+
+inline int make_job(const grt_bvh* b, const grt_surfels* s, const grt_gbuffer* g, const grt_envmap* e,
+             const grt_sampling* smp, const int* pixel_list, int n_pixels, float* oc, float* ov, float* oi,
+             ShadeJob* J) {
+    if (!g || !e || !smp) return set_error(GRT_ERR_ARG, "gbuffer, env or sampling is NULL");
+    if (!g->pos || !g->normal || !g->albedo || !g->rough || !g->metal || !g->valid)
+        return set_error(GRT_ERR_ARG, "gbuffer arrays must be non-NULL");
+    if (g->W <= 0 || g->H <= 0) return set_error(GRT_ERR_ARG, "gbuffer size %dx%d", g->W, g->H);
+    if (n_pixels < 0) return set_error(GRT_ERR_ARG, "n_pixels < 0");
+    if (!pixel_list && n_pixels > g->W * g->H) return set_error(GRT_ERR_ARG, "n_pixels exceeds W*H");
+    if (!e->tables || e->W <= 0 || e->H <= 0) return set_error(GRT_ERR_ARG, "environment tables missing");
+    if (smp->n_cos < 0 || smp->n_ggx < 0 || smp->n_env < 0) return set_error(GRT_ERR_ARG, "negative sample count");
+    int Nr = smp->n_cos + smp->n_ggx + smp->n_env;
+    if (Nr > 1024) return set_error(GRT_ERR_ARG, "N_r = %d exceeds 1024", Nr);
+    if (smp->brdf != 0 && smp->brdf != 1) return set_error(GRT_ERR_ARG, "brdf must be 0 or 1");
+    J->bvh = dev_bvh(b);
+    J->color = s->color;
+    J->mu = s->mu;
+    J->quat = s->quat;
+    J->scale = s->scale;
+    J->opacity = s->opacity;
+    J->cdim = s->color_dim;
+    J->gb = GbufDev{g->pos, g->normal, g->albedo, g->rough, g->metal, g->valid, g->eye[0], g->eye[1], g->eye[2], g->W, g->H};
+    EnvLayout l = env_layout(e->W, e->H);
+    const char* tb = (const char*)e->tables;
+    J->env = EnvDev{(const float4*)(tb + l.texel), (const float*)(tb + l.marg), (const float*)(tb + l.cond), e->W, e->H,
+                    (float)e->W * (float)e->H / (2.f * kPi * kPi)};
+    J->S = Sampling{smp->n_cos, smp->n_ggx, smp->n_env, smp->brdf, (uint32_t)(smp->seed & 0xFFFFFFFFu),
+                    (uint32_t)(smp->seed >> 32)};
+    J->pixel_list = pixel_list;
+    J->n_pixels = Nr > 0 ? n_pixels : 0;
+    J->Nr = Nr > 0 ? Nr : 1;
+    J->out_color = oc;
+    J->out_vis = ov;
+    J->out_ind = oi;
+    J->G = group_lanes(J->Nr);
+    J->spl = (J->Nr + J->G - 1) / J->G;
+    J->ray_begin = 0;
+    J->unit_begin = 0;
+    return GRT_OK;
+}
+
+// Keeps freed ray buffers in the device's stream-ordered pool between calls.
+inline void keep_pool_memory() {
+    static std::once_flag once[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::call_once(once[dev], [dev] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+
+// Persistent forward trace of every ray of the table (per-ray (c_rt, T) into res).
+template <int K, int CAP>
+inline void launch_trace_dyn(const JobTable<CAP>& T, const float4* dirs, float4* res, unsigned long long* next_ray,
+                             long long blocks_max, cudaStream_t st) {
+    cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_rays_dyn<K, CAP>, kShadeThreads, 0);
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > blocks_max) grid = blocks_max;
+    k_trace_rays_dyn<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, next_ray);
+}
+
+}  // namespace
+}  // namespace grt
