@@ -380,6 +380,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--k", type=int, default=16, help="k-buffer size (results do not depend on it)")
+    ap.add_argument("--serve-requests", type=int, default=120, help="requests of the 80%%-load serving trace")
     ap.add_argument("--image", type=int, default=0,
                     help="square image size override (small profiling case); default 800")
     args = ap.parse_args()

@@ -228,7 +228,9 @@ int grt_shade_backward(const grt_bvh* bvh, const grt_surfels* surfels, const grt
                        const float* dL_dvis, const float* dL_dind, const grt_grads* grads,
                        void* stream);
 
-/* One shading request of a batch (same meaning as the grt_shade_pixels arguments). */
+/* One shading request of a batch (same meaning as the grt_shade_pixels arguments).
+ * With pixel_list NULL, output i shades pixel pixel_offset + i (a contiguous slice of
+ * the image, so a long request can be split over several launches). */
 typedef struct {
     const grt_bvh* bvh;
     const grt_surfels* surfels;
@@ -237,6 +239,7 @@ typedef struct {
     grt_sampling sampling;
     const int32_t* pixel_list;
     int32_t n_pixels;
+    int32_t pixel_offset;
     float* out_color;
     float* out_vis;
     float* out_ind;
@@ -245,12 +248,12 @@ typedef struct {
 #define GRT_MAX_BATCH 48
 
 /* Shade up to GRT_MAX_BATCH requests (possibly on different scenes, environment maps,
- * resolutions and sample counts) in ONE persistent launch whose warps pull pixel groups
- * of all requests from a shared work counter.  Each request's outputs are bit-identical
- * to shading it alone with grt_shade_pixels.  `work_counter` is a caller-owned device
- * int32 that the call resets on `stream`. */
+ * resolutions and sample counts) in one wavefront pass: every request's samples go into
+ * one ray list, one persistent trace launch serves them all, and each pixel is summed in
+ * a fixed order.  Each request's outputs are bit-identical to shading it alone with
+ * grt_shade_pixels.  Ray buffers (32 bytes per ray) come from the stream-ordered pool. */
 int grt_shade_batch(const grt_shade_request* requests, int32_t n_requests,
-                    const grt_trace_params* params, int32_t* work_counter, void* stream);
+                    const grt_trace_params* params, void* stream);
 
 /* Performance counters of one grt_trace_forward-style pass (for roofline accounting):
  * counts of internal nodes visited, surfel records tested and hits composited, summed

@@ -58,7 +58,7 @@ class Sampling(C.Structure):
 class ShadeRequest(C.Structure):
     _fields_ = [("bvh", P), ("surfels", C.POINTER(Surfels)), ("gbuffer", GBuffer), ("env", EnvMap),
                 ("sampling", Sampling), ("pixel_list", P), ("n_pixels", C.c_int32),
-                ("out_color", P), ("out_vis", P), ("out_ind", P)]
+                ("pixel_offset", C.c_int32), ("out_color", P), ("out_vis", P), ("out_ind", P)]
 
 
 # name -> (restype, argtypes)
@@ -83,7 +83,7 @@ SIGNATURES = {
     "grt_shade_backward": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                      C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P,
                                      C.POINTER(Grads), P]),
-    "grt_shade_batch": (C.c_int, [C.POINTER(ShadeRequest), C.c_int32, C.POINTER(TraceParams), P, P]),
+    "grt_shade_batch": (C.c_int, [C.POINTER(ShadeRequest), C.c_int32, C.POINTER(TraceParams), P]),
     "grt_trace_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), P, P, C.c_int32, P, P]),
     "grt_shade_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                   C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P]),

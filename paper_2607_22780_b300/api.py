@@ -326,13 +326,17 @@ class ShadeRequest:
     color: Optional[torch.Tensor] = None
     vis: Optional[torch.Tensor] = None
     ind: Optional[torch.Tensor] = None
+    pixel_offset: int = 0          # with pixels None: shade pixels [offset, offset + count)
+    count: Optional[int] = None
 
     @property
     def n_pixels(self) -> int:
-        return int(self.pixels.shape[0]) if self.pixels is not None else self.gbuffer.W * self.gbuffer.H
+        if self.pixels is not None:
+            return int(self.pixels.shape[0])
+        return self.count if self.count is not None else self.gbuffer.W * self.gbuffer.H - self.pixel_offset
 
 
-def shade_batch(requests, params=None, work_counter=None, stream=None):
+def shade_batch(requests, params=None, stream=None):
     """Shade several requests in one persistent launch; fills each request's outputs."""
     if not requests:
         return
@@ -349,11 +353,10 @@ def shade_batch(requests, params=None, work_counter=None, stream=None):
         keep.append(sf)
         arr[i] = L.ShadeRequest(r.scene.handle, C.pointer(sf), r.gbuffer.struct(), r.env.struct(),
                                 sampling(r.n_cos, r.n_ggx, r.n_env, r.seed, r.brdf), _ptr(r.pixels), n,
+                                0 if r.pixels is not None else int(r.pixel_offset),
                                 _ptr(r.color), _ptr(r.vis), _ptr(r.ind))
-    if work_counter is None:
-        work_counter = torch.zeros(1, dtype=torch.int32, device=requests[0].gbuffer.pos.device)
     p = params if params is not None else requests[0].scene.params
-    L.check(L.load().grt_shade_batch(arr, len(requests), C.byref(p), _ptr(work_counter), _stream(stream)))
+    L.check(L.load().grt_shade_batch(arr, len(requests), C.byref(p), _stream(stream)))
 
 
 def version() -> str:

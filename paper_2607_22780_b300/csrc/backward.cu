@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_weights(const __grid_
     if (rr.w >= 0.f && !(rr.w == 1.f && rr.x == 0.f && rr.y == 0.f && rr.z == 0.f)) {
         const ShadeJob& J = T.job[0];
         int li = (int)(r / J.Nr);
-        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
         PixelState ps = load_pixel(J.gb, pix);
         float4 dw = __ldg(dirs + r);
         SampleWeight sw = sample_weight(J.S, J.env, ps, mk3(dw.x, dw.y, dw.z));
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : 4) k_adjoint_dyn(
                     if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f) {
                         float4 rr = __ldg(res + r), dw = __ldg(dirs + r);
                         int li = (int)(r / J.Nr);
-                        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+                        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
                         f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
                                    __ldg(J.gb.pos + 3 * (size_t)pix + 2));
                         f3 d = mk3(dw.x, dw.y, dw.z);

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kShadeThreads) k_accumulate(const __grid_const
     const bool active = li < J.n_pixels;
     float col[3] = {0.f, 0.f, 0.f}, ind[3] = {0.f, 0.f, 0.f}, vis = 0.f;
     if (active) {
-        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
         if ((unsigned)pix < (unsigned)(J.gb.W * J.gb.H) && __ldg(J.gb.valid + pix)) {
             PixelState ps = load_pixel(J.gb, pix);
             const long long r0 = J.ray_begin + (long long)li * J.Nr;
@@ -155,10 +155,9 @@ extern "C" int grt_shade_count(const grt_bvh* b, const grt_surfels* s, const grt
 }
 
 extern "C" int grt_shade_batch(const grt_shade_request* req, int32_t n_req, const grt_trace_params* p,
-                               int32_t* work_counter, void* stream) {
+                               void* stream) {
     if (!req || n_req <= 0 || n_req > GRT_MAX_BATCH)
         return set_error(GRT_ERR_ARG, "need 1 <= n_requests <= %d", GRT_MAX_BATCH);
-    (void)work_counter;
     int rc = check_params(p);
     if (rc) return rc;
     static thread_local JobTable<GRT_MAX_BATCH> T;
@@ -173,6 +172,12 @@ extern "C" int grt_shade_batch(const grt_shade_request* req, int32_t n_req, cons
         rc = make_job(req[i].bvh, req[i].surfels, &req[i].gbuffer, &req[i].env, &req[i].sampling, req[i].pixel_list,
                       req[i].n_pixels, req[i].out_color, req[i].out_vis, req[i].out_ind, &J);
         if (rc) return rc;
+        if (!req[i].pixel_list) {
+            if (req[i].pixel_offset < 0 ||
+                (long long)req[i].pixel_offset + req[i].n_pixels > (long long)req[i].gbuffer.W * req[i].gbuffer.H)
+                return set_error(GRT_ERR_ARG, "request %d: pixel slice outside the G-buffer", i);
+            J.pixel_offset = req[i].pixel_offset;
+        }
         if (J.n_pixels == 0) {
             if (req[i].n_pixels > 0)
                 k_zero_outputs<<<(req[i].n_pixels + 255) / 256, 256, 0, st>>>(req[i].out_color, req[i].out_vis,

@@ -22,6 +22,7 @@ struct ShadeJob {
     Sampling S;
     const int* pixel_list;
     int n_pixels;
+    int pixel_offset;        // with no pixel list: pixel = pixel_offset + list index
     int Nr;
     float *out_color, *out_vis, *out_ind;
     int G, spl;              // accumulation: lanes per pixel, samples per lane
@@ -52,7 +53,7 @@ struct JobTable {
 namespace {
 
 __device__ __forceinline__ int pixel_of(const ShadeJob& J, int li) {
-    int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+    int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
     if ((unsigned)pix >= (unsigned)(J.gb.W * J.gb.H)) {
         atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
         return -1;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(kShadeThreads) k_trace_rays(const __grid_const
         if (dw.w != 0.f) {
             const ShadeJob& J = T.job[T.find_ray(r)];
             int li = (int)((r - J.ray_begin) / J.Nr);
-            int pix = J.pixel_list ? __ldg(J.pixel_list + li) : li;
+            int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
             f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
                        __ldg(J.gb.pos + 3 * (size_t)pix + 2));
             f3 d = mk3(dw.x, dw.y, dw.z);
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : GRT_TRACE_MIN_BLO
                     } else {
                         J = &T.job[T.find_ray(r)];
                         int li = (int)((r - J->ray_begin) / J->Nr);
-                        int pix = J->pixel_list ? __ldg(J->pixel_list + li) : li;
+                        int pix = J->pixel_list ? __ldg(J->pixel_list + li) : J->pixel_offset + li;
                         f3 o = mk3(__ldg(J->gb.pos + 3 * (size_t)pix), __ldg(J->gb.pos + 3 * (size_t)pix + 1),
                                    __ldg(J->gb.pos + 3 * (size_t)pix + 2));
                         f3 d = mk3(dw.x, dw.y, dw.z);
@@ -223,6 +224,7 @@ inline int make_job(const grt_bvh* b, const grt_surfels* s, const grt_gbuffer* g
     J->S = Sampling{smp->n_cos, smp->n_ggx, smp->n_env, smp->brdf, (uint32_t)(smp->seed & 0xFFFFFFFFu),
                     (uint32_t)(smp->seed >> 32)};
     J->pixel_list = pixel_list;
+    J->pixel_offset = 0;
     J->n_pixels = Nr > 0 ? n_pixels : 0;
     J->Nr = Nr > 0 ? Nr : 1;
     J->out_color = oc;

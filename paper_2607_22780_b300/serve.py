@@ -1,0 +1,284 @@
+"""Relight serving: resident scenes, continuous batching of shading requests.
+
+Each request names a resident scene and carries a camera, an HDR environment map, a
+resolution and a sample count (N_r/2 cosine, N_r/4 GGX, N_r/4 environment samples).
+Serving a request = upload its map, build its proposal tables and traced G-buffer, then
+shade every pixel with the MIS estimator against the scene's 2D Gaussian surfels.
+
+Continuous batching (iteration-level scheduling): the loop runs "iterations"; each takes
+pixel slices from the admitted requests in arrival order until a ray budget is filled and
+shades them all in ONE grt_shade_batch launch.  Requests that arrive while launches are on
+the GPU are admitted at the next iteration as long as their device memory fits the HBM
+budget; their map upload, tables and G-buffer run on a second stream and overlap the
+shading of the others.  A request completes when the launch holding its last slice ends
+(CUDA event on the GPU timeline); latency = completion - arrival.
+
+The comparator serves the same arrival trace one request at a time (each request's
+G-buffer and a whole-image grt_shade_pixels launch, back to back).  Results are
+bit-identical either way: a pixel's value depends only on its own samples.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+from typing import Dict, List, Optional
+
+import numpy as np
+import torch
+
+from . import api
+from . import workloads as wl
+
+
+@dataclasses.dataclass
+class RelightRequest:
+    rid: int
+    arrival: float          # seconds after the start of the trace
+    scene: str
+    camera: wl.Camera
+    env: np.ndarray         # [H, W, 3] float32 HDR map
+    res: int
+    rays: int               # N_r
+    seed: int
+
+    @property
+    def alloc(self):
+        return (self.rays // 2, self.rays // 4, self.rays - self.rays // 2 - self.rays // 4)
+
+
+def make_trace(n: int, rate: float, scenes: Dict[str, float], seed: int, res_choices=(256, 512, 1024),
+               rpp_choices=(8, 16, 32, 64), env_size=(512, 256), start: float = 0.0) -> List[RelightRequest]:
+    """Poisson arrivals at `rate` per second; scenes maps name -> camera distance."""
+    rng = np.random.default_rng(seed)
+    t = start
+    names = sorted(scenes)
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        name = names[int(rng.integers(len(names)))]
+        res = int(rng.choice(res_choices))
+        rpp = int(rng.choice(rpp_choices))
+        s = int(rng.integers(1 << 31))
+        cam = wl.camera_orbit(s, res, res, scenes[name])
+        env = wl.envmap_hdr(s, env_size[0], env_size[1])
+        out.append(RelightRequest(i, t, name, cam, env, res, rpp, s))
+    return out
+
+
+class _State:
+    """Device-side state of an admitted request."""
+
+    def __init__(self, req: RelightRequest, scene: api.Scene, dev, stream):
+        self.req = req
+        self.scene = scene
+        P = req.res * req.res
+        self.P = P
+        with torch.cuda.stream(stream):
+            henv = torch.from_numpy(req.env).pin_memory()
+            self.env_rgb = torch.empty(henv.shape, dtype=torch.float32, device=dev)
+            self.env_rgb.copy_(henv, non_blocking=True)
+            self.env = api.Environment(self.env_rgb, stream=stream)
+            self.gb = api.gbuffer_primary(scene, req.camera, stream=stream)
+            self.color = torch.empty((P, 3), device=dev)
+            self.vis = torch.empty((P,), device=dev)
+            self.ind = torch.empty((P, 3), device=dev)
+        self.ready = torch.cuda.Event()
+        self.ready.record(stream)
+        self._henv = henv
+        self.next = 0
+        self.done_ms: Optional[float] = None
+        self.start_ms: Optional[float] = None
+
+    @staticmethod
+    def bytes_needed(req: RelightRequest) -> int:
+        P = req.res * req.res
+        H, W = req.env.shape[:2]
+        return P * (56 + 28) + W * H * (12 + 16 + 4) + H * 4 + 4096
+
+
+class RelightServer:
+    """Resident scenes + continuous batching of relight requests on one GPU."""
+
+    def __init__(self, scenes: Dict[str, api.Scene], device="cuda", hbm_budget: int = 8 << 30,
+                 ray_budget: int = 8 << 20, max_batch: int = 16, inflight: int = 2):
+        self.scenes = scenes
+        self.device = torch.device(device)
+        self.hbm_budget = int(hbm_budget)
+        self.ray_budget = int(ray_budget)
+        self.max_batch = int(max_batch)
+        self.inflight = int(inflight)
+        self.cancelled = set()
+        self.peak_active = 0
+
+    def cancel(self, rid: int):
+        """Drop a request: pending requests are skipped, admitted ones stop getting slices."""
+        self.cancelled.add(rid)
+
+    # ------------------------------------------------------------------ batched
+    def run_batched(self, trace: List[RelightRequest], realtime: bool = True) -> dict:
+        dev = self.device
+        compute = torch.cuda.Stream(dev)
+        prep = torch.cuda.Stream(dev)
+        ref = torch.cuda.Event(enable_timing=True)
+        pending = collections.deque(sorted(trace, key=lambda r: r.arrival))
+        active: List[_State] = []
+        finished: List[_State] = []
+        inflight = collections.deque()
+        mem = 0
+        launches = 0
+        torch.cuda.synchronize(dev)
+        ref.record(compute)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        while pending or active or inflight:
+            now = (time.perf_counter() - t0) if realtime else math.inf
+            # admit arrivals while their memory fits the budget
+            while pending and pending[0].arrival <= now:
+                req = pending[0]
+                if req.rid in self.cancelled:
+                    pending.popleft()
+                    continue
+                need = _State.bytes_needed(req)
+                if active and mem + need > self.hbm_budget:
+                    break
+                pending.popleft()
+                st = _State(req, self.scenes[req.scene], dev, prep)
+                st.bytes = need
+                mem += need
+                active.append(st)
+            self.peak_active = max(self.peak_active, len(active))
+            # retire launches that have finished on the GPU
+            while inflight and inflight[0][0].query():
+                ev, ending = inflight.popleft()
+                for st in ending:
+                    st.done_ms = ref.elapsed_time(ev)
+                    mem -= st.bytes
+                    finished.append(st)
+            for st in [s for s in active if s.req.rid in self.cancelled]:
+                active.remove(st)
+                mem -= st.bytes
+            # at most `inflight` launches queued on the GPU before building the next one
+            if len(inflight) >= self.inflight:
+                inflight[0][0].synchronize()
+                continue
+            # next iteration: FIFO slices up to the ray budget
+            batch, budget = [], self.ray_budget
+            for st in active:
+                if len(batch) >= self.max_batch or budget <= 0:
+                    break
+                left = st.P - st.next
+                if left <= 0:
+                    continue
+                npx = min(left, max(32, budget // st.req.rays))
+                batch.append((st, st.next, npx))
+                st.next += npx
+                budget -= npx * st.req.rays
+            if batch:
+                reqs = []
+                for st, off, npx in batch:
+                    compute.wait_event(st.ready)
+                    a = st.req.alloc
+                    reqs.append(api.ShadeRequest(st.scene, st.gb, st.env, a[0], a[1], a[2], st.req.seed, brdf=1,
+                                                 pixel_offset=off, count=npx, color=st.color[off:off + npx],
+                                                 vis=st.vis[off:off + npx], ind=st.ind[off:off + npx]))
+                api.shade_batch(reqs, stream=compute)
+                launches += 1
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(compute)
+                ending = [st for st, _, _ in batch if st.next >= st.P]
+                for st in ending:
+                    active.remove(st)
+                inflight.append((ev, ending))
+                continue
+            if inflight:
+                inflight[0][0].synchronize()
+            elif active and not any(st.next < st.P for st in active):
+                raise RuntimeError("scheduler stalled: admitted requests without work or launch")
+            elif pending:
+                wait = pending[0].arrival - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.05))
+        torch.cuda.synchronize(dev)
+        return self._stats(finished, launches, "batched")
+
+    # ------------------------------------------------------------------ one at a time
+    def run_serial(self, trace: List[RelightRequest], realtime: bool = True) -> dict:
+        dev = self.device
+        s = torch.cuda.Stream(dev)
+        ref = torch.cuda.Event(enable_timing=True)
+        finished = []
+        torch.cuda.synchronize(dev)
+        ref.record(s)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for req in sorted(trace, key=lambda r: r.arrival):
+            if req.rid in self.cancelled:
+                continue
+            if realtime:
+                wait = req.arrival - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+            st = _State(req, self.scenes[req.scene], dev, s)
+            a = req.alloc
+            with torch.cuda.stream(s):
+                api.shade_pixels(st.scene, st.gb, st.env, a[0], a[1], a[2], req.seed, brdf=1,
+                                 outputs=(st.color, st.vis, st.ind), stream=s)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(s)
+            ev.synchronize()
+            st.done_ms = ref.elapsed_time(ev)
+            finished.append(st)
+        return self._stats(finished, len(finished), "serial")
+
+    # ------------------------------------------------------------------ stats
+    @staticmethod
+    def _stats(states: List[_State], launches: int, mode: str) -> dict:
+        if not states:
+            return {"mode": mode, "requests": 0}
+        lat = np.array([st.done_ms - 1e3 * st.req.arrival for st in states])
+        rays = sum(int(st.gb.valid.sum().item()) * st.req.rays for st in states)
+        first = min(st.req.arrival for st in states) * 1e3
+        last = max(st.done_ms for st in states)
+        span_s = max(last - first, 1e-6) * 1e-3
+        return {"mode": mode, "requests": len(states), "launches": launches, "rays": rays,
+                "rays_per_s": rays / span_s, "span_s": span_s,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+                "outputs": {st.req.rid: st for st in states}}
+
+
+def default_scenes(device="cuda", sizes=(300_000, 1_000_000, 2_000_000)) -> Dict[str, api.Scene]:
+    """The three resident scenes of the serving workload (object scene + two large scenes)."""
+    out = {}
+    for n in sizes:
+        sc = wl.scene_objects(n, seed=2607) if n <= 300_000 else wl.scene_large(n, seed=2607 + n)
+        out[f"s{n // 1000}k"] = api.Scene.from_workload(sc, device=device)
+    return out
+
+
+def scene_distances(scenes: Dict[str, api.Scene]) -> Dict[str, float]:
+    return {k: (3.0 if v.n <= 300_000 else 30.0) for k, v in scenes.items()}
+
+
+def bench_main(args):
+    """bench.py --mode serve: p50/p99 and rays/s, batched vs one at a time."""
+    import json
+    torch.cuda.set_device(0)
+    scenes = default_scenes()
+    dist = scene_distances(scenes)
+    srv = RelightServer(scenes)
+    # capacity: one at a time, back to back
+    probe = make_trace(12, 0.0, dist, seed=1)
+    cap = srv.run_serial(probe, realtime=False)
+    req_per_s = cap["requests"] / cap["span_s"]
+    out = {"metric": "relight_serving", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+           "capacity_serial": {k: v for k, v in cap.items() if k != "outputs"}}
+    for name, rate, n in (("load80", 0.8 * req_per_s, args.serve_requests), ("rate200", 200.0, args.serve_requests // 2)):
+        trace = make_trace(n, rate, dist, seed=7 if name == "load80" else 8)
+        b = srv.run_batched(trace)
+        s = srv.run_serial(trace)
+        out[name] = {"rate_per_s": rate, "batched": {k: v for k, v in b.items() if k != "outputs"},
+                     "serial": {k: v for k, v in s.items() if k != "outputs"}}
+    print(json.dumps(out), flush=True)
