@@ -267,6 +267,13 @@ int grt_shade_count(const grt_bvh* bvh, const grt_surfels* surfels, const grt_tr
                     const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
                     const int32_t* pixel_list, int32_t n_pixels, long long* counters, void* stream);
 
+/* Phase timing of grt_shade_pixels / grt_shade_batch (for roofline accounting).  With
+ * enable = 1 the following shading calls of the calling thread record CUDA events on their
+ * stream around the three kernels (ray sampling, trace, per-pixel accumulation); enable = 0
+ * stops, enable = -1 leaves the setting unchanged.  With ms_out non-NULL the call waits for
+ * the most recent timed shading call and writes its three durations in milliseconds. */
+int grt_phase_timing(int32_t enable, float* ms_out);
+
 const char* grt_last_error(void);
 const char* grt_version(void);
 

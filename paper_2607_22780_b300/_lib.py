@@ -87,6 +87,7 @@ SIGNATURES = {
     "grt_trace_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), P, P, C.c_int32, P, P]),
     "grt_shade_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                   C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P]),
+    "grt_phase_timing": (C.c_int, [C.c_int32, C.POINTER(C.c_float)]),
     "grt_last_error": (C.c_char_p, []),
     "grt_version": (C.c_char_p, []),
 }

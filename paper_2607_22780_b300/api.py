@@ -359,5 +359,13 @@ def shade_batch(requests, params=None, stream=None):
     L.check(L.load().grt_shade_batch(arr, len(requests), C.byref(p), _stream(stream)))
 
 
+def phase_timing(enable: Optional[bool] = None, read: bool = False):
+    """Turn per-kernel timing of shading calls on/off; with read=True return the last
+    call's (sample_ms, trace_ms, accumulate_ms)."""
+    ms = (C.c_float * 3)() if read else None
+    L.check(L.load().grt_phase_timing(-1 if enable is None else int(bool(enable)), ms))
+    return tuple(ms) if read else None
+
+
 def version() -> str:
     return L.load().grt_version().decode()

@@ -75,6 +75,20 @@ __global__ void __launch_bounds__(kShadeThreads) k_accumulate(const __grid_const
 }
 
 // Lays out the jobs' rays and accumulation units, then runs the three kernels.
+// Optional phase timing (grt_phase_timing): events on the call's stream around the
+// sample, trace and accumulate kernels of the most recent shading call of this thread.
+struct PhaseTiming {
+    bool on = false;
+    bool have = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    void mark(int i, cudaStream_t st) {
+        if (!on) return;
+        if (!ev[i]) cudaEventCreate(&ev[i]);
+        cudaEventRecord(ev[i], st);
+    }
+};
+thread_local PhaseTiming g_timing;
+
 template <bool COUNT, int CAP>
 int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st) {
     long long rays = 0, units = 0;
@@ -95,7 +109,9 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st) {
     float4* res = buf + rays;
     unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + 2 * rays);
     const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
+    g_timing.mark(0, st);
     k_sample_rays<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
+    g_timing.mark(1, st);
     dispatch_k(k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
         if (COUNT) {  // counting pass: one ray per thread, same traversal
@@ -106,7 +122,10 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st) {
     });
     if (!COUNT) {
         const long long ga = (units * 32 + kShadeThreads - 1) / kShadeThreads;
+        g_timing.mark(2, st);
         k_accumulate<CAP><<<(unsigned)ga, kShadeThreads, 0, st>>>(T, dirs, res);
+        g_timing.mark(3, st);
+        g_timing.have = g_timing.on;
     }
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(buf, st);
@@ -188,4 +207,16 @@ extern "C" int grt_shade_batch(const grt_shade_request* req, int32_t n_req, cons
     }
     if (T.n_jobs == 0) return launch_error("k_zero_outputs");
     return run_jobs<false>(T, p->k, nullptr, st);
+}
+
+extern "C" int grt_phase_timing(int32_t enable, float* ms_out) {
+    if (enable >= 0) {
+        g_timing.on = enable != 0;
+        g_timing.have = false;
+    }
+    if (!ms_out) return GRT_OK;
+    if (!g_timing.have) return set_error(GRT_ERR_ARG, "no timed shading call on this thread");
+    GRT_CUDA(cudaEventSynchronize(g_timing.ev[3]));
+    for (int i = 0; i < 3; ++i) GRT_CUDA(cudaEventElapsedTime(ms_out + i, g_timing.ev[i], g_timing.ev[i + 1]));
+    return GRT_OK;
 }
