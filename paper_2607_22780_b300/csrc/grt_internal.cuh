@@ -251,7 +251,10 @@ __device__ __forceinline__ f3 env_dir_d(int row, int col, float u_row, float u_c
 //   [7]    binary-tree ref of each child (to refit boxes without a rebuild)
 // Unused slots have lo = +1e38 > hi = -1e38, so every slab test misses them.
 constexpr int kWide = 4;
-constexpr int kLeafMax = 4;
+#ifndef GRT_LEAF_MAX
+#define GRT_LEAF_MAX 1
+#endif
+constexpr int kLeafMax = GRT_LEAF_MAX;  // surfels per wide-tree leaf (at most 8)
 constexpr int kMaxCollapseLevels = 60;  // >= binary depth: 30 code bits + 27 position bits
 __host__ __device__ __forceinline__ int leaf_ref(int first, int count) { return -(1 + (first << 3) + (count - 1)); }
 __host__ __device__ __forceinline__ int leaf_first(int ref) { return (-ref - 1) >> 3; }
