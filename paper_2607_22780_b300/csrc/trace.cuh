@@ -294,6 +294,87 @@ __device__ __forceinline__ bool trav_step(const DevBvh& bvh, TraceState<K>& s, i
     return false;
 }
 
+// Node visit of the two-phase walk: hit leaf children are queued (tested later by the
+// whole warp together) instead of being tested here; hit internal children go near to far
+// on the stack as in trav_step.  The queue lives in shared memory, q[slot * stride].
+template <int K, bool COUNT>
+__device__ __forceinline__ void node_step_q(const DevBvh& bvh, TraceState<K>& s, int2* stack, const TraceParams& P,
+                                            int* q, int stride, int& nq, Counters& cnt) {
+    int node = s.node;
+    if (node < 0) {
+        if (node == -1 && bvh.root != kRefEmpty && bvh.root < 0) q[stride * nq++] = bvh.root;
+        s.node = -2;
+        return;
+    }
+    if (COUNT) ++cnt.nodes;
+    if ((unsigned)node >= (unsigned)bvh.cap || --s.budget < 0) {
+        atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
+        s.node = -2;
+        s.sp = 0;
+        return;
+    }
+    const RayState& r = s.r;
+    const float tlo = fmaf(P.t_min, 0.99999f, -r.eps);
+    const int ox = r.inv.x >= 0.f ? 0 : 3, oy = r.inv.y >= 0.f ? 1 : 4, oz = r.inv.z >= 0.f ? 2 : 5;
+    const float4* N = bvh.nodes + 8 * (size_t)node;
+    const float4 nx = __ldg(N + ox), ny = __ldg(N + oy), nz = __ldg(N + oz);
+    const float4 fx = __ldg(N + (3 - ox)), fy = __ldg(N + (5 - oy)), fz = __ldg(N + (7 - oz));
+    const int4 ref = __ldg(reinterpret_cast<const int4*>(N + 6));
+    const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, nys[4] = {ny.x, ny.y, ny.z, ny.w}, nzs[4] = {nz.x, nz.y, nz.z, nz.w};
+    const float fxs[4] = {fx.x, fx.y, fx.z, fx.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
+    const int refs[4] = {ref.x, ref.y, ref.z, ref.w};
+    const float inf = __int_as_float(0x7f800000);
+    float d[4];
+    int e[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float t0 = fmaxf(fmaxf(fmaf(nxs[c], r.inv.x, r.oinv.x), fmaf(nys[c], r.inv.y, r.oinv.y)),
+                         fmaxf(fmaf(nzs[c], r.inv.z, r.oinv.z), tlo));
+        float t1 = fminf(fminf(fmaf(fxs[c], r.inv.x, r.oinv.x), fmaf(fys[c], r.inv.y, r.oinv.y)),
+                         fminf(fmaf(fzs[c], r.inv.z, r.oinv.z), s.kb.thi));
+        bool h = t0 <= t1;
+        if (h && refs[c] < 0) {
+            q[stride * nq++] = refs[c];
+            h = false;
+        }
+        d[c] = h ? t0 : inf;
+        e[c] = refs[c];
+    }
+#define GRT_CSWAP(i, j)              \
+    if (d[j] < d[i]) {               \
+        float td = d[i];             \
+        d[i] = d[j];                 \
+        d[j] = td;                   \
+        int te = e[i];               \
+        e[i] = e[j];                 \
+        e[j] = te;                   \
+    }
+    GRT_CSWAP(0, 1) GRT_CSWAP(2, 3) GRT_CSWAP(0, 2) GRT_CSWAP(1, 3) GRT_CSWAP(1, 2)
+#undef GRT_CSWAP
+    if (d[0] != inf) {
+#pragma unroll
+        for (int c = 3; c >= 1; --c) {
+            if (d[c] != inf) {
+                if (s.sp < kStackDepth) {
+                    stack[s.sp++] = make_int2(e[c], __float_as_int(d[c]));
+                } else {
+                    atomicOr(bvh.status, GRT_STATUS_STACK_OVERFLOW);
+                }
+            }
+        }
+        s.node = e[0];
+        return;
+    }
+    while (s.sp > 0) {
+        int2 t = stack[--s.sp];
+        if (__int_as_float(t.y) <= s.kb.thi) {
+            s.node = t.x;
+            return;
+        }
+    }
+    s.node = -2;
+}
+
 // End of a round: composite the buffer in order (Eq. 8).  Returns true when the ray is
 // finished; otherwise the next round starts after the last composited key.
 template <int K, bool COUNT, class Visitor>
