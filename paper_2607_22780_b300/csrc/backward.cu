@@ -218,74 +218,60 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_weights(const __grid_
     adj[r] = out;
 }
 
-// Persistent adjoint replay: one traversal per ray, totals (c_rt, T_f) from the forward
-// pass; lanes refill from a global counter like the forward trace.
+// Adjoint rays: same origin/direction as the forward shading rays, totals (c_rt, T_f)
+// from the forward pass, adjoints (dL/dc_rt, dL/do_rt) from k_adjoint_weights; one
+// traversal per ray in the persistent two-phase walk.
 template <int K>
-__global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : 4) k_adjoint_dyn(const __grid_constant__ JobTable<1> T,
-                                                                  const float4* __restrict__ dirs,
-                                                                  const float4* __restrict__ res,
-                                                                  const float4* __restrict__ adj, GradPtrs g,
-                                                                  unsigned long long* __restrict__ next_ray) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const ShadeJob& J = T.job[0];
-    int2 stack[kStackDepth];
-    TraceState<K> ts;
-    AdjointVisitor av;
-    av.mu = J.mu;
-    av.quat = J.quat;
-    av.scale = J.scale;
-    av.opacity = J.opacity;
-    av.color = J.color;
-    av.cdim = J.cdim;
-    av.alpha_max = T.P.alpha_max;
-    av.g = g;
-    bool act = false, drained = false;
-    Counters cnt{0, 0, 0};
-    while (true) {
-        unsigned idle = __ballot_sync(0xffffffffu, !act);
-        int nidle = __popc(idle);
-        if (!drained && (nidle >= 8 || nidle == 32)) {
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(next_ray, (unsigned long long)nidle);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (base + nidle >= (unsigned long long)T.total_rays) drained = true;
-            if (!act) {
-                long long r = (long long)base + __popc(idle & lt);
-                if (r < T.total_rays) {
-                    float4 a = __ldg(adj + r);
-                    if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f) {
-                        float4 rr = __ldg(res + r), dw = __ldg(dirs + r);
-                        int li = (int)(r / J.Nr);
-                        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
-                        f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
-                                   __ldg(J.gb.pos + 3 * (size_t)pix + 2));
-                        f3 d = mk3(dw.x, dw.y, dw.z);
-                        trace_begin(J.bvh, ts, o, d, T.P);
-                        av.o = o;
-                        av.d = d;
-                        av.Gc[0] = a.x;
-                        av.Gc[1] = a.y;
-                        av.Gc[2] = a.z;
-                        av.Go = a.w;
-                        av.Tf = rr.w;
-                        av.crt[0] = rr.x;
-                        av.crt[1] = rr.y;
-                        av.crt[2] = rr.z;
-                        av.Cacc[0] = av.Cacc[1] = av.Cacc[2] = 0.f;
-                        act = true;
-                    }
-                }
-            }
-        }
-        if (!__any_sync(0xffffffffu, act)) {
-            if (drained) break;
-            continue;
-        }
-        if (act && !trav_step<K, false>(J.bvh, ts, stack, T.P, cnt)) {
-            if (round_end<K, false>(J.bvh, ts, T.P, av, cnt)) act = false;
-        }
+struct AdjointTask {
+    using Visitor = AdjointVisitor;
+    const JobTable<1>* T;
+    const float4 *dirs, *res, *adj;
+    GradPtrs g;
+    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& av, const DevBvh*& bvh) {
+        float4 a = __ldg(adj + r);
+        if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f) return false;
+        const ShadeJob& J = T->job[0];
+        float4 rr = __ldg(res + r), dw = __ldg(dirs + r);
+        int li = (int)(r / J.Nr);
+        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
+        f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
+                   __ldg(J.gb.pos + 3 * (size_t)pix + 2));
+        f3 d = mk3(dw.x, dw.y, dw.z);
+        bvh = &J.bvh;
+        trace_begin(J.bvh, ts, o, d, T->P);
+        av.mu = J.mu;
+        av.quat = J.quat;
+        av.scale = J.scale;
+        av.opacity = J.opacity;
+        av.color = J.color;
+        av.cdim = J.cdim;
+        av.alpha_max = T->P.alpha_max;
+        av.g = g;
+        av.o = o;
+        av.d = d;
+        av.Gc[0] = a.x;
+        av.Gc[1] = a.y;
+        av.Gc[2] = a.z;
+        av.Go = a.w;
+        av.Tf = rr.w;
+        av.crt[0] = rr.x;
+        av.crt[1] = rr.y;
+        av.crt[2] = rr.z;
+        av.Cacc[0] = av.Cacc[1] = av.Cacc[2] = 0.f;
+        return true;
     }
+    __device__ __forceinline__ void end(long long, const TraceState<K>&, Visitor&) {}
+};
+
+template <int K>
+__global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : 4) k_adjoint_ww(const __grid_constant__ JobTable<1> T,
+                                                                               const float4* __restrict__ dirs,
+                                                                               const float4* __restrict__ res,
+                                                                               const float4* __restrict__ adj, GradPtrs g,
+                                                                               unsigned long long* __restrict__ next_ray) {
+    __shared__ int q[kQueue * kShadeThreads];
+    AdjointTask<K> task{&T, dirs, res, adj, g};
+    persistent_trace<K>(task, T.P, next_ray, T.total_rays, q + threadIdx.x, kShadeThreads);
 }
 
 }  // namespace
@@ -365,10 +351,10 @@ extern "C" int grt_shade_backward(const grt_bvh* b, const grt_surfels* s, const 
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_dyn<K>, kShadeThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_ww<K>, kShadeThreads, 0);
         long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
         if (grid > gr) grid = gr;
-        k_adjoint_dyn<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, next_ray);
+        k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, next_ray);
     });
     cudaError_t err = cudaGetLastError();
     cudaFreeAsync(buf, st);

@@ -38,6 +38,7 @@ struct GbufVisitor {
     const float *quat, *albedo, *rough, *metal;
     f3 d;
     float D, wsum, nx, ny, nz, ar, ag, ab, ro, me, T;
+    __device__ __forceinline__ GbufVisitor() {}
     __device__ __forceinline__ GbufVisitor(const grt_surfels& s, f3 dir)
         : quat(s.quat), albedo(s.albedo), rough(s.rough), metal(s.metal), d(dir), D(0), wsum(0), nx(0), ny(0), nz(0),
           ar(0), ag(0), ab(0), ro(0), me(0), T(1) {}
@@ -65,37 +66,57 @@ struct GbufOut {
     int* valid;
 };
 
+// Primary rays in the persistent two-phase walk: ray index = pixel y*W + x.
 template <int K>
-__global__ void __launch_bounds__(128) k_gbuffer(DevBvh bvh, TraceParams P, grt_surfels s, Camera cam, int W, int H,
-                                                 GbufOut out) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= W * H) return;
-    f3 o, d;
-    camera_ray_d(cam, W, H, p % W, p / W, &o, &d);
-    RayState r = make_ray(o, d);
-    GbufVisitor v(s, d);
-    Counters cnt{0, 0, 0};
-    trace_ray<K, false>(bvh, r, P, v, cnt);
-    float a = 1.f - v.T;
-    float nl = sqrtf(v.nx * v.nx + v.ny * v.ny + v.nz * v.nz);
-    bool ok = a >= 0.5f && nl > 1e-12f;
-    out.valid[p] = ok;
-    if (out.alpha) out.alpha[p] = a;
-    float iw = ok ? 1.f / v.wsum : 0.f;
-    float D = v.D * iw;
-    if (out.depth) out.depth[p] = D;
-    out.pos[3 * (size_t)p] = ok ? fmaf(D, d.x, o.x) : 0.f;
-    out.pos[3 * (size_t)p + 1] = ok ? fmaf(D, d.y, o.y) : 0.f;
-    out.pos[3 * (size_t)p + 2] = ok ? fmaf(D, d.z, o.z) : 0.f;
-    float in = ok ? 1.f / nl : 0.f;
-    out.normal[3 * (size_t)p] = v.nx * in;
-    out.normal[3 * (size_t)p + 1] = v.ny * in;
-    out.normal[3 * (size_t)p + 2] = v.nz * in;
-    out.albedo[3 * (size_t)p] = v.ar * iw;
-    out.albedo[3 * (size_t)p + 1] = v.ag * iw;
-    out.albedo[3 * (size_t)p + 2] = v.ab * iw;
-    out.rough[p] = v.ro * iw;
-    out.metal[p] = v.me * iw;
+struct GbufTask {
+    using Visitor = GbufVisitor;
+    const DevBvh* bvh;
+    const grt_surfels* s;
+    const Camera* cam;
+    const TraceParams* P;
+    int W, H;
+    GbufOut out;
+    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& v, const DevBvh*& b) {
+        f3 o, d;
+        camera_ray_d(*cam, W, H, (int)(r % W), (int)(r / W), &o, &d);
+        trace_begin(*bvh, ts, o, d, *P);
+        v = GbufVisitor(*s, d);
+        b = bvh;
+        return true;
+    }
+    __device__ __forceinline__ void end(long long r, const TraceState<K>& ts, Visitor& v) {
+        const size_t p = (size_t)r;
+        const f3 o = ts.r.o, d = ts.r.d;
+        float a = 1.f - v.T;
+        float nl = sqrtf(v.nx * v.nx + v.ny * v.ny + v.nz * v.nz);
+        bool ok = a >= 0.5f && nl > 1e-12f;
+        out.valid[p] = ok;
+        if (out.alpha) out.alpha[p] = a;
+        float iw = ok ? 1.f / v.wsum : 0.f;
+        float D = v.D * iw;
+        if (out.depth) out.depth[p] = D;
+        out.pos[3 * p] = ok ? fmaf(D, d.x, o.x) : 0.f;
+        out.pos[3 * p + 1] = ok ? fmaf(D, d.y, o.y) : 0.f;
+        out.pos[3 * p + 2] = ok ? fmaf(D, d.z, o.z) : 0.f;
+        float in = ok ? 1.f / nl : 0.f;
+        out.normal[3 * p] = v.nx * in;
+        out.normal[3 * p + 1] = v.ny * in;
+        out.normal[3 * p + 2] = v.nz * in;
+        out.albedo[3 * p] = v.ar * iw;
+        out.albedo[3 * p + 1] = v.ag * iw;
+        out.albedo[3 * p + 2] = v.ab * iw;
+        out.rough[p] = v.ro * iw;
+        out.metal[p] = v.me * iw;
+    }
+};
+
+template <int K>
+__global__ void __launch_bounds__(128, K >= 32 ? 3 : 4) k_gbuffer(DevBvh bvh, TraceParams P, grt_surfels s, Camera cam,
+                                                                  int W, int H, GbufOut out,
+                                                                  unsigned long long* next) {
+    __shared__ int q[kQueue * 128];
+    GbufTask<K> task{&bvh, &s, &cam, &P, W, H, out};
+    persistent_trace<K>(task, P, next, (long long)W * H, q + threadIdx.x, 128);
 }
 
 }  // namespace
@@ -122,12 +143,25 @@ extern "C" int grt_gbuffer_primary(const grt_bvh* b, const grt_surfels* s, const
     DevBvh bvh = dev_bvh(b);
     TraceParams P = to_params(*p);
     GbufOut out{pos, normal, albedo, rough, metal, alpha, depth, valid};
-    int n = W * H, grid = (n + 127) / 128;
+    int n = W * H, gmax = (n + 127) / 128;
     cudaStream_t st = (cudaStream_t)stream;
     grt_surfels sc = *s;
+    unsigned long long* next = nullptr;
+    GRT_CUDA(cudaMallocAsync((void**)&next, sizeof(unsigned long long), st));
+    GRT_CUDA(cudaMemsetAsync(next, 0, sizeof(unsigned long long), st));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     dispatch_k(p->k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
-        k_gbuffer<K><<<grid, 128, 0, st>>>(bvh, P, sc, cam, W, H, out);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gbuffer<K>, 128, 0);
+        int grid = sms * (per_sm > 0 ? per_sm : 1);
+        if (grid > gmax) grid = gmax;
+        k_gbuffer<K><<<grid, 128, 0, st>>>(bvh, P, sc, cam, W, H, out, next);
     });
-    return launch_error("k_gbuffer");
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(next, st);
+    if (e != cudaSuccess) return check_cuda(e, "k_gbuffer");
+    return GRT_OK;
 }

@@ -484,6 +484,27 @@ static __device__ __noinline__ void surfel_colour_sh(const float* __restrict__ c
     c[2] = fmaxf(acc[2], 0.f);
 }
 
+// Lean forward visitor of the shading rays: c_rt only (T comes from the trace state).
+struct RadianceVisitor {
+    const float* color;
+    int cdim;
+    f3 d;
+    float c[3];
+    __device__ __forceinline__ RadianceVisitor() {}
+    __device__ __forceinline__ RadianceVisitor(const float* col, int cd, f3 dir) : color(col), cdim(cd), d(dir) {
+        c[0] = c[1] = c[2] = 0.f;
+    }
+    __device__ __forceinline__ void composite(int, int id, float, float alpha, float Tb) {
+        float ck[3];
+        surfel_colour(color, cdim, id, d, ck);
+        float w = Tb * alpha;
+        c[0] = fmaf(w, ck[0], c[0]);
+        c[1] = fmaf(w, ck[1], c[1]);
+        c[2] = fmaf(w, ck[2], c[2]);
+    }
+    __device__ __forceinline__ void finish(float) {}
+};
+
 // Forward visitor: c_rt, o_rt = 1 - T (Eq. 8), optional hit list.
 struct ColourVisitor {
     const float* color;
@@ -494,6 +515,10 @@ struct ColourVisitor {
     int* hits;
     int max_hits;
     int nh;
+    __device__ __forceinline__ ColourVisitor() : color(nullptr), cdim(3), d(mk3(0.f, 0.f, 0.f)), T(1.f),
+                                                  hits(nullptr), max_hits(0), nh(0) {
+        c[0] = c[1] = c[2] = 0.f;
+    }
     __device__ __forceinline__ ColourVisitor(const float* col, int cd, f3 dir, int* h, int mh)
         : color(col), cdim(cd), d(dir), T(1.f), hits(h), max_hits(mh), nh(0) {
         c[0] = c[1] = c[2] = 0.f;
@@ -510,5 +535,71 @@ struct ColourVisitor {
     }
     __device__ __forceinline__ void finish(float Tf) { T = Tf; }
 };
+
+
+// ----------------------------------------------------------------------------- persistent walk
+// Generic persistent two-phase walk over a flat list of `total` rays.  Warps stay resident;
+// once kRefill lanes are idle they claim that many rays from *next (a global counter);
+// then the warp alternates (A) internal-node visits with hit leaves queued in shared memory,
+// until every active lane has a leaf queued or has finished its walk, (B) the queued surfel
+// tests of all lanes, (C) compositing of finished walks.  Task supplies
+//   bool begin(long long ray, TraceState<K>&, Visitor&, const DevBvh*&)  -- false: no ray
+//   void end(long long ray, const TraceState<K>&, Visitor&)              -- ray finished
+// and the Visitor type receiving composite() calls.
+constexpr int kRefill = 8;
+constexpr int kQueue = 8;
+
+template <int K, class Task>
+__device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& P, unsigned long long* next,
+                                                 long long total, int* q, int qstride) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int2 stack[kStackDepth];
+    TraceState<K> ts;
+    ts.node = -2;
+    typename Task::Visitor vis;
+    const DevBvh* bvh = nullptr;
+    long long ray = -1;
+    bool act = false, drained = false;
+    int nq = 0;
+    Counters cnt{0, 0, 0};
+    while (true) {
+        unsigned idle = __ballot_sync(0xffffffffu, !act);
+        int nidle = __popc(idle);
+        if (!drained && (nidle >= kRefill || nidle == 32)) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(next, (unsigned long long)nidle);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + nidle >= (unsigned long long)total) drained = true;
+            if (!act) {
+                long long r = (long long)base + __popc(idle & lt);
+                if (r < total) {
+                    ray = r;
+                    act = task.begin(r, ts, vis, bvh);
+                    nq = 0;
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, act)) {
+            if (drained) break;
+            continue;
+        }
+        while (true) {
+            bool walking = act && ts.node != -2 && nq <= kQueue - kWide;
+            if (!__any_sync(0xffffffffu, walking)) break;
+            if (walking) node_step_q<K, false>(*bvh, ts, stack, P, q, qstride, nq, cnt);
+            if (__all_sync(0xffffffffu, !act || nq > 0 || ts.node == -2)) break;
+        }
+        for (int i = 0; i < nq; ++i) test_leaf<K, false>(*bvh, ts, q[i * qstride], P, cnt);
+        nq = 0;
+        if (act && ts.node == -2) {
+            if (round_end<K, false>(*bvh, ts, P, vis, cnt)) {
+                vis.finish(ts.T);
+                task.end(ray, ts, vis);
+                act = false;
+            }
+        }
+    }
+}
 
 }  // namespace grt

@@ -255,87 +255,43 @@ inline void keep_pool_memory() {
 }
 
 
-// Two-phase variant of the persistent trace (after Aila & Laine's while-while walk): a
-// warp alternates (A) walking internal nodes, queueing hit leaves in shared memory, until
-// every active lane has a leaf queued or has finished its walk, (B) testing the queued
-// leaves of all lanes together, (C) compositing the lanes whose walk is over.  Lanes thus
-// run the same code in each phase instead of interleaving node visits, surfel tests and
-// compositing.
-constexpr int kLeafQueue = 8;
+// Shading rays: origin = G-buffer point of the ray's pixel, direction from k_sample_rays;
+// result (c_rt, T) per ray, T = -1 for "no ray".
+template <int K, int CAP>
+struct ShadeTrace {
+    using Visitor = RadianceVisitor;
+    const JobTable<CAP>* T;
+    const float4* dirs;
+    float4* res;
+    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& cv, const DevBvh*& bvh) {
+        float4 dw = __ldg(dirs + r);
+        if (dw.w == 0.f) {
+            res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
+            return false;
+        }
+        const ShadeJob& J = T->job[T->find_ray(r)];
+        int li = (int)((r - J.ray_begin) / J.Nr);
+        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
+        f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
+                   __ldg(J.gb.pos + 3 * (size_t)pix + 2));
+        f3 d = mk3(dw.x, dw.y, dw.z);
+        bvh = &J.bvh;
+        trace_begin(J.bvh, ts, o, d, T->P);
+        cv = RadianceVisitor(J.color, J.cdim, d);
+        return true;
+    }
+    __device__ __forceinline__ void end(long long r, const TraceState<K>& ts, Visitor& cv) {
+        res[r] = make_float4(cv.c[0], cv.c[1], cv.c[2], ts.T);
+    }
+};
 
 template <int K, int CAP>
 __global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : GRT_TRACE_MIN_BLOCKS) k_trace_rays_ww(
     const __grid_constant__ JobTable<CAP> T, const float4* __restrict__ dirs, float4* __restrict__ res,
     unsigned long long* __restrict__ next_ray) {
-    __shared__ int lq[kLeafQueue * kShadeThreads];
-    int* q = lq + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int2 stack[kStackDepth];
-    TraceState<K> ts;
-    ts.node = -2;
-    ColourVisitor cv(nullptr, 3, mk3(0.f, 0.f, 0.f), nullptr, 0);
-    const ShadeJob* J = &T.job[0];
-    long long ray = -1;
-    bool act = false, drained = false;
-    int nq = 0;
-    Counters cnt{0, 0, 0};
-    while (true) {
-        unsigned idle = __ballot_sync(0xffffffffu, !act);
-        int nidle = __popc(idle);
-        if (!drained && (nidle >= kRefillLanes || nidle == 32)) {
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(next_ray, (unsigned long long)nidle);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (base + nidle >= (unsigned long long)T.total_rays) drained = true;
-            if (!act) {
-                long long r = (long long)base + __popc(idle & lt);
-                if (r < T.total_rays) {
-                    ray = r;
-                    float4 dw = __ldg(dirs + r);
-                    if (dw.w == 0.f) {
-                        res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
-                    } else {
-                        J = &T.job[T.find_ray(r)];
-                        int li = (int)((r - J->ray_begin) / J->Nr);
-                        int pix = J->pixel_list ? __ldg(J->pixel_list + li) : J->pixel_offset + li;
-                        f3 o = mk3(__ldg(J->gb.pos + 3 * (size_t)pix), __ldg(J->gb.pos + 3 * (size_t)pix + 1),
-                                   __ldg(J->gb.pos + 3 * (size_t)pix + 2));
-                        f3 d = mk3(dw.x, dw.y, dw.z);
-                        trace_begin(J->bvh, ts, o, d, T.P);
-                        cv.color = J->color;
-                        cv.cdim = J->cdim;
-                        cv.d = d;
-                        cv.c[0] = cv.c[1] = cv.c[2] = 0.f;
-                        cv.nh = 0;
-                        nq = 0;
-                        act = true;
-                    }
-                }
-            }
-        }
-        if (!__any_sync(0xffffffffu, act)) {
-            if (drained) break;
-            continue;
-        }
-        // (A) internal nodes; leaves queued
-        while (true) {
-            bool walking = act && ts.node != -2 && nq <= kLeafQueue - 4;
-            if (!__any_sync(0xffffffffu, walking)) break;
-            if (walking) node_step_q<K, false>(J->bvh, ts, stack, T.P, q, kShadeThreads, nq, cnt);
-            if (__all_sync(0xffffffffu, !act || nq > 0 || ts.node == -2)) break;
-        }
-        // (B) queued leaves of every lane
-        for (int i = 0; i < nq; ++i) test_leaf<K, false>(J->bvh, ts, q[i * kShadeThreads], T.P, cnt);
-        nq = 0;
-        // (C) walks that are over: composite, then finish or start the next round
-        if (act && ts.node == -2) {
-            if (round_end<K, false>(J->bvh, ts, T.P, cv, cnt)) {
-                res[ray] = make_float4(cv.c[0], cv.c[1], cv.c[2], ts.T);
-                act = false;
-            }
-        }
-    }
+    __shared__ int q[kQueue * kShadeThreads];
+    ShadeTrace<K, CAP> task{&T, dirs, res};
+    persistent_trace<K>(task, T.P, next_ray, T.total_rays, q + threadIdx.x, kShadeThreads);
 }
 
 // Persistent forward trace of every ray of the table (per-ray (c_rt, T) into res).
