@@ -361,12 +361,24 @@ def serve_summary(args):
             "batched": {k: b[k] for k in keep}, "one_at_a_time": {k: o[k] for k in keep}}
 
 
+def run_train_only(args):
+    """Forward + adjoint of the training configuration only (profiling entry)."""
+    import torch
+    from paper_2607_22780_b300 import api
+    torch.cuda.set_device(0)
+    sc, cam, env = make_inputs(0)
+    S = api.Scene.from_workload(sc, params=api.trace_params(k=args.k))
+    E = api.Environment(torch.from_numpy(env).cuda())
+    print(json.dumps(time_train(api, S, cam, E, torch.device("cuda"), args)), flush=True)
+
+
 def time_train(api, S, cam, E, dev, args):
     import torch
     from paper_2607_22780_b300 import workloads as wl
-    c = wl.Camera(cam.eye, cam.target, cam.up, cam.tan_half_fovy, TRAIN_IMG, TRAIN_IMG)
+    img = args.image or TRAIN_IMG if args.mode == "train" else TRAIN_IMG
+    c = wl.Camera(cam.eye, cam.target, cam.up, cam.tan_half_fovy, img, img)
     G = api.gbuffer_primary(S, c)
-    tgt = torch.from_numpy(wl.target_image(SEED, TRAIN_IMG, TRAIN_IMG).reshape(-1, 3)).to(dev)
+    tgt = torch.from_numpy(wl.target_image(SEED, img, img).reshape(-1, 3)).to(dev)
     grads = api.SurfelGrads.zeros(S)
     P = TRAIN_IMG * TRAIN_IMG
 
@@ -406,7 +418,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="grt", choices=["grt", "reference"])
-    ap.add_argument("--mode", default="shade", choices=["shade", "serve"])
+    ap.add_argument("--mode", default="shade", choices=["shade", "serve", "train"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
@@ -426,6 +438,8 @@ def main():
     elif args.mode == "serve":
         from paper_2607_22780_b300 import serve
         serve.bench_main(args)
+    elif args.mode == "train":
+        run_train_only(args)
     else:
         run_grt(args)
 

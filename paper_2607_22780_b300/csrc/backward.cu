@@ -32,7 +32,8 @@ struct AdjointVisitor {
     float alpha_max;
     GradPtrs g;
 
-    __device__ __forceinline__ void composite(int, int id, float tau, float alpha, float Tb) {
+    // out of line: round_end unrolls its K slots, and this body is large
+    __device__ __noinline__ void composite(int, int id, float tau, float alpha, float Tb) {
         // colour of the hit and, for SH, which channels are live
         float Y[16];
         float c[3];
