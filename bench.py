@@ -45,6 +45,18 @@ RAY_IO_BYTES = 44   # direction 16 + origin 12 read, (c_rt, T) 16 written
 COLLAPSE_LEVELS = 60
 
 
+def reduce_ranks(ms: float, rays: float, device) -> tuple:
+    """Weak scaling across ranks: (max step time over ranks, rays summed over ranks)."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms, float(rays)], device=device, dtype=torch.float64)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = tt.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -245,10 +257,7 @@ def run_grt(args):
     t_max = ms
     rays_total = R
     if world > 1:
-        tt = torch.tensor([ms, float(R)], device=dev, dtype=torch.float64)
-        mx = tt.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        t_max, rays_total = float(mx[0]), float(sm[1])
+        t_max, rays_total = reduce_ranks(ms, R, dev)
     value = rays_total / (t_max * 1e-3)
 
     # ---- algorithmic bytes of the dominant kernel (the persistent trace kernel), from the
