@@ -131,43 +131,49 @@ def make_inputs(rank: int):
     return sc, cam, env
 
 
-def cpu_oracle_sample(sc, cam, env, gb32, n_valid_pixels, budget_s=12.0):
-    """Time the FP64 oracle on a bounded pixel sample of the same frame (all host cores)."""
+def oracle_view_gbuffer(sc, cam, size=80):
+    """The oracle's own G-buffer of a size x size view from the benchmark camera (the
+    oracle's timed samples shade pixels of this view: no input comes from the GPU)."""
+    import oracle
+    from paper_2607_22780_b300 import workloads as wl
+    small = wl.Camera(cam.eye, cam.target, cam.up, cam.tan_half_fovy, size, size)
+    return oracle.gbuffer_f32(oracle.gbuffer(sc, small))
+
+
+def cpu_oracle_sample(sc, env, gb32, budget_s=12.0):
+    """Time the FP64 oracle on a bounded pixel sample of the same scene, map and camera."""
     import oracle
     valid = np.nonzero(gb32["valid"])[0]
     rng = np.random.default_rng(0)
     Nr = sum(ALLOC)
-    t0 = time.perf_counter()
-    pix = rng.choice(valid, size=4, replace=False).astype(np.int32)
-    oracle.shade_pixels(sc, gb32, env, *ALLOC, seed=SEED, pixels=pix)
-    t1 = time.perf_counter() - t0
-    n = int(max(4, min(len(valid), budget_s / max(t1 / 4, 1e-6))))
-    pix = rng.choice(valid, size=n, replace=False).astype(np.int32)
-    t0 = time.perf_counter()
-    oracle.shade_pixels(sc, gb32, env, *ALLOC, seed=SEED, pixels=pix)
-    dt = time.perf_counter() - t0
+
+    def timed(n):
+        pix = rng.choice(valid, size=min(n, len(valid)), replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.shade_pixels(sc, gb32, env, *ALLOC, seed=SEED, pixels=pix)
+        return len(pix), time.perf_counter() - t0
+
+    _, t_a = timed(4)
+    _, t_b = timed(20)
+    per_px = max((t_b - t_a) / 16, 1e-6)  # the difference removes the per-call setup
+    n, dt = timed(int(max(4, budget_s / per_px)))
     return {"value": n * Nr / dt, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} random valid pixels x {Nr} MIS rays of the 800x800 frame, 300k surfels, "
-                      f"FP64 brute force (every ray against every surfel), {dt:.1f} s"}
+            "sample": f"{n} random valid pixels x {Nr} MIS rays of an 80x80 view from the benchmark camera, "
+                      f"300k surfels, FP64 brute force (every ray against every surfel), {dt:.1f} s"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    from paper_2607_22780_b300 import workloads as wl
     sc, cam, env = make_inputs(0)
-    # the oracle's own G-buffer of the same camera (only the sampled pixels matter)
-    gcam = wl.Camera(cam.eye, cam.target, cam.up, cam.tan_half_fovy, W_IMG, H_IMG)
     t0 = time.perf_counter()
-    small = wl.Camera(cam.eye, cam.target, cam.up, cam.tan_half_fovy, 80, 80)
-    gb = oracle.gbuffer_f32(oracle.gbuffer(sc, small))
+    gb = oracle_view_gbuffer(sc, cam)
     t_gb = time.perf_counter() - t0
     steps = []
     cb = None
     for s in range(args.warmup + args.steps):
-        cb = cpu_oracle_sample(sc, small, env, gb, int(gb["valid"].sum()), budget_s=max(2.0, 60.0 / (args.steps + args.warmup)))
+        cb = cpu_oracle_sample(sc, env, gb, budget_s=max(2.0, 60.0 / (args.steps + args.warmup)))
         if s >= args.warmup:
             steps.append(cb["value"])
     value = float(np.median(steps))
@@ -175,8 +181,10 @@ def run_reference(args):
     out = {"impl": "reference", "metric": "secondary_rays_per_s", "value": value, "unit": "rays/s",
            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "mis_shade_300k_800x800_32spp (sampled pixels of an 80x80 view, same scene/map)",
-                      "surfels": N_SURFELS, "rays_per_pixel": sum(ALLOC), "alloc": list(ALLOC)},
+           "config": {"workload": "mis_shade_300k_800x800_32spp", "surfels": N_SURFELS, "image": [W_IMG, H_IMG],
+                      "rays_per_pixel": sum(ALLOC), "alloc_cos_ggx_env": list(ALLOC), "env": [ENV_W, ENV_H],
+                      "k": 16, "sample": "each step shades a bounded random sample of valid pixels of an 80x80 "
+                                         "view from the same camera (same scene, map and seeds)"},
            "cpu_baseline": cb,
            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "note": f"G-buffer of the sampled view took {t_gb:.1f} s"}
@@ -318,10 +326,7 @@ def run_grt(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        gb32 = dict(pos=G.pos.cpu().numpy(), normal=G.normal.cpu().numpy(), albedo=G.albedo.cpu().numpy(),
-                    rough=G.rough.cpu().numpy(), metal=G.metal.cpu().numpy(), valid=G.valid.cpu().numpy(),
-                    eye=np.asarray(cam.eye, np.float32), W=W_IMG, H=H_IMG)
-        cpu = cpu_oracle_sample(sc, cam, env, gb32, n_valid)
+        cpu = cpu_oracle_sample(sc, env, oracle_view_gbuffer(sc, cam))
 
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
@@ -339,7 +344,7 @@ def run_grt(args):
                           "parallelism": f"replicas x{world}"},
                "gpu_launches": launches_per_step * args.steps,
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "traffic": None, "kernel": "k_trace_rays_dyn",
+                            "frac": achieved / peak, "traffic": None, "kernel": "k_trace_rays_ww",
                             "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
                             "kernel_ms": trace_s * 1e3,
                             "phase_ms": {"sample": float(np.mean(ph[:, 0])), "trace": float(np.mean(ph[:, 1])),

@@ -42,8 +42,8 @@ extern "C" {
 #define GRT_ERR_UNSUPPORTED 6 /* option not built in (e.g. k not in {4,8,16,32})     */
 
 /* Device status bits reported by grt_bvh_status(). */
-#define GRT_STATUS_STACK_OVERFLOW 1
-#define GRT_STATUS_NONFINITE 2
+#define GRT_STATUS_STACK_OVERFLOW 1  /* a traversal stack filled; deeper nodes were dropped  */
+#define GRT_STATUS_NONFINITE 2  /* a ray with a NaN or infinite origin or direction was traced as a miss */
 #define GRT_STATUS_BAD_TREE 4   /* node reference out of range or walk longer than the tree */
 #define GRT_STATUS_BAD_INDEX 8  /* a pixel index outside the G-buffer was skipped            */
 

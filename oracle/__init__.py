@@ -81,7 +81,7 @@ class _Grads(C.Structure):
 def _declare(L):
     P = C.c_void_p
     L.or_trace_rays.argtypes = [P, P, C.c_int, P, P, P, P, P, C.c_int, P, P, P, C.c_int]
-    L.or_gbuffer.argtypes = [P, P, P, C.c_int, C.c_int] + [P] * 9 + [C.c_int]
+    L.or_gbuffer.argtypes = [P, P, P, C.c_int, C.c_int, P, C.c_int] + [P] * 9 + [C.c_int]
     L.or_shade_pixels.argtypes = [P, P, P, P, P, P, C.c_int, P, P, P, P, C.c_int]
     L.or_backward_rays.argtypes = [P, P, C.c_int, P, P, P, P, P, P, C.c_int]
     L.or_backward_pixels.argtypes = [P, P, P, P, P, P, C.c_int, P, P, P, P, P, C.c_int]
@@ -197,17 +197,27 @@ def trace_rays(scene, ray_o, ray_d, params=None, max_hits=64, nthreads=0):
     return dict(rgb=rgb, opacity=op, T=T, hits=hits, nhits=nh, flags=fl)
 
 
-def gbuffer(scene, camera, params=None, nthreads=0):
-    """Primary G-buffer of a pinhole camera (Eq. 9 along the camera ray)."""
+def gbuffer(scene, camera, params=None, pixels=None, nthreads=0):
+    """Primary G-buffer of a pinhole camera (Eq. 9 along the camera ray).
+
+    With `pixels` (raster indices y*W + x) only those pixels are traced; row i of every
+    output then belongs to pixels[i]."""
     keep = _Keep()
     W, H = camera.width, camera.height
-    P_ = W * H
+    if pixels is None:
+        pl = None
+        P_ = W * H
+    else:
+        pl = np.ascontiguousarray(pixels, np.int32)
+        if pl.size and (pl.min() < 0 or pl.max() >= W * H):
+            raise ValueError("pixel index outside the image")
+        P_ = pl.shape[0]
     out = dict(pos=np.zeros((P_, 3)), normal=np.zeros((P_, 3)), albedo=np.zeros((P_, 3)),
                rough=np.zeros(P_), metal=np.zeros(P_), alpha=np.zeros(P_), depth=np.zeros(P_),
                valid=np.zeros(P_, np.int32), flags=np.zeros(P_, np.uint32))
     s = _scene(scene, keep); P = _params(params)
     cam = _f32(camera.as_array())
-    lib().or_gbuffer(_ref(s), _ref(P), _ptr(cam), W, H, _ptr(out["pos"]), _ptr(out["normal"]),
+    lib().or_gbuffer(_ref(s), _ref(P), _ptr(cam), W, H, _ptr(pl), P_, _ptr(out["pos"]), _ptr(out["normal"]),
                      _ptr(out["albedo"]), _ptr(out["rough"]), _ptr(out["metal"]), _ptr(out["alpha"]),
                      _ptr(out["depth"]), _ptr(out["valid"]), _ptr(out["flags"]), nthreads)
     out["eye"] = np.asarray(camera.eye, np.float32)

@@ -574,8 +574,10 @@ int or_trace_rays(const or_scene* sc, const or_params* P, int R, const float* ra
 }
 
 /* Primary G-buffer (Eq. 9 with a traced camera ray): normalised blend of depth,
- * camera-facing normal, albedo, roughness, metallic; valid iff opacity >= 0.5. */
+ * camera-facing normal, albedo, roughness, metallic; valid iff opacity >= 0.5.
+ * Output row i is pixel pixels[i] (all W*H pixels in raster order when pixels is NULL). */
 int or_gbuffer(const or_scene* sc, const or_params* P, const float* cam, int W, int H,
+               const int32_t* pixels, int n_out,
                double* pos, double* normal, double* albedo, double* rough, double* metal,
                double* alpha, double* depth, int32_t* valid, uint32_t* flags, int nthreads) {
     surf_pre* pre = precompute(sc);
@@ -584,7 +586,8 @@ int or_gbuffer(const or_scene* sc, const or_params* P, const float* cam, int W, 
     {
         ray_ws ws = {0};
 #pragma omp for schedule(dynamic, 8)
-        for (int p = 0; p < W * H; ++p) {
+        for (int i = 0; i < n_out; ++i) {
+            const int p = pixels ? pixels[i] : i;
             f3 o32, d32;
             camera_ray_f(cam, W, H, p % W, p / W, &o32, &d32);
             uint32_t fl = 0;
@@ -609,23 +612,23 @@ int or_gbuffer(const or_scene* sc, const or_params* P, const float* cam, int W, 
             double nl = sqrt(dotd(N, N));
             int ok = a >= 0.5 && nl > 1e-12;
             if (fabs(a - 0.5) < 1e-5) fl |= OR_FLAG_VALID;
-            valid[p] = ok;
-            alpha[p] = a;
+            valid[i] = ok;
+            alpha[i] = a;
             if (ok) {
                 D /= a;
-                depth[p] = D;
+                depth[i] = D;
                 d3 x = addd(f2d(o32), muld(f2d(d32), D));
-                pos[3 * p] = x.x; pos[3 * p + 1] = x.y; pos[3 * p + 2] = x.z;
-                normal[3 * p] = N.x / nl; normal[3 * p + 1] = N.y / nl; normal[3 * p + 2] = N.z / nl;
-                for (int ch = 0; ch < 3; ++ch) albedo[3 * p + ch] = al[ch] / a;
-                rough[p] = ro / a;
-                metal[p] = me / a;
+                pos[3 * i] = x.x; pos[3 * i + 1] = x.y; pos[3 * i + 2] = x.z;
+                normal[3 * i] = N.x / nl; normal[3 * i + 1] = N.y / nl; normal[3 * i + 2] = N.z / nl;
+                for (int ch = 0; ch < 3; ++ch) albedo[3 * i + ch] = al[ch] / a;
+                rough[i] = ro / a;
+                metal[i] = me / a;
             } else {
-                depth[p] = 0;
-                for (int ch = 0; ch < 3; ++ch) { pos[3 * p + ch] = 0; normal[3 * p + ch] = 0; albedo[3 * p + ch] = 0; }
-                rough[p] = 0; metal[p] = 0;
+                depth[i] = 0;
+                for (int ch = 0; ch < 3; ++ch) { pos[3 * i + ch] = 0; normal[3 * i + ch] = 0; albedo[3 * i + ch] = 0; }
+                rough[i] = 0; metal[i] = 0;
             }
-            if (flags) flags[p] = fl;
+            if (flags) flags[i] = fl;
         }
         free(ws.buf);
         free(ws.Tk);

@@ -18,6 +18,8 @@ GRT_MAX_BATCH = 48
 GRT_NOALLOC_MAX_SURFELS = 524288
 STATUS_STACK_OVERFLOW = 1
 STATUS_NONFINITE = 2
+STATUS_BAD_TREE = 4
+STATUS_BAD_INDEX = 8
 
 P = C.c_void_p
 

@@ -169,6 +169,12 @@ __device__ __forceinline__ void trace_begin(const DevBvh& bvh, TraceState<K>& s,
     s.rounds = 1;
     s.ncomp = 0;
     round_begin(bvh, s, P);
+    // a NaN or infinite origin or direction is reported and traced as a miss
+    if (!(isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) && isfinite(d.z))) {
+        atomicOr(bvh.status, GRT_STATUS_NONFINITE);
+        s.node = -2;
+        s.budget = 0;
+    }
 }
 
 template <int K, bool COUNT>

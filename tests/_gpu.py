@@ -39,3 +39,51 @@ def hits_equal(gpu_hits, gpu_n, ora_hits, ora_n, mask):
 
 def hdr_tol(ref, rel=1e-4):
     return rel * np.maximum(1.0, np.abs(ref))
+
+
+def upsample_gbuffer(gb, f):
+    """Nearest-neighbour enlargement of a G-buffer by an integer factor: each pixel of the
+    source becomes an f x f block (a full-resolution input made from a small oracle view)."""
+    W, H = int(gb["W"]), int(gb["H"])
+    out = dict(eye=gb["eye"], W=W * f, H=H * f)
+    for k in ("pos", "normal", "albedo", "rough", "metal", "valid"):
+        a = np.asarray(gb[k])
+        img = a.reshape(H, W, -1)
+        img = np.repeat(np.repeat(img, f, axis=0), f, axis=1)
+        out[k] = np.ascontiguousarray(img.reshape((H * f * W * f,) + a.shape[1:]))
+    return out
+
+
+def gbuffer_to_arrays(g, eye, W, H):
+    """A device G-buffer copied to host arrays (for checks that read it, never as oracle input)."""
+    return dict(pos=g.pos.cpu().numpy(), normal=g.normal.cpu().numpy(), albedo=g.albedo.cpu().numpy(),
+                rough=g.rough.cpu().numpy(), metal=g.metal.cpu().numpy(), valid=g.valid.cpu().numpy(),
+                alpha=g.alpha.cpu().numpy() if g.alpha is not None else None,
+                depth=g.depth.cpu().numpy() if g.depth is not None else None,
+                eye=np.asarray(eye, np.float32), W=W, H=H)
+
+
+def check_gbuffer_rows(got, ref, pix, min_valid):
+    """GPU G-buffer rows at pixels `pix` against the oracle's rows for the same pixels."""
+    m = unflagged(ref["flags"])
+    assert np.array_equal(got["valid"][pix][m], ref["valid"][m])
+    v = m & (ref["valid"] == 1)
+    assert v.sum() >= min_valid, v.sum()
+    for k, tol in (("pos", 5e-4), ("normal", 5e-4), ("albedo", 1e-4), ("rough", 1e-4), ("metal", 1e-4)):
+        err = np.abs(got[k][pix][v] - ref[k][v])
+        assert err.max() < tol, (k, err.max())
+
+
+GRAD_FIELDS = ("mu", "quat", "scale", "opacity", "color")
+
+
+def check_grads(g, ref, rel=2e-3, absf=1e-5):
+    """|g - ref| <= rel |ref| + absf max|ref| per parameter block (FP32 atomics vs FP64)."""
+    for f in GRAD_FIELDS:
+        a = getattr(g, f).cpu().numpy().astype(np.float64)
+        r = ref[f]
+        scale = np.abs(r).max()
+        assert scale > 0, f
+        err = np.abs(a - r) - (rel * np.abs(r) + absf * scale)
+        assert err.max() <= 0, (f, np.unravel_index(err.argmax(), err.shape), a.ravel()[err.argmax()],
+                                r.ravel()[err.argmax()])

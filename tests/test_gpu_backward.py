@@ -7,24 +7,13 @@ import pytest
 import torch
 
 import oracle
-from tests._gpu import random_rays, scene_gpu, t
+from tests._gpu import check_grads, random_rays, scene_gpu, t
 from tests._handmade import random_gbuffer
 from paper_2607_22780_b300 import api, autograd, workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-FIELDS = ("mu", "quat", "scale", "opacity", "color")
-
-
-def _check(g, ref, rel=2e-3, absf=1e-5):
-    for f in FIELDS:
-        a = getattr(g, f).cpu().numpy().astype(np.float64)
-        r = ref[f]
-        scale = np.abs(r).max()
-        assert scale > 0, f
-        err = np.abs(a - r) - (rel * np.abs(r) + absf * scale)
-        assert err.max() <= 0, (f, np.unravel_index(err.argmax(), err.shape), a.ravel()[err.argmax()],
-                                r.ravel()[err.argmax()])
+_check = check_grads
 
 
 @pytest.mark.parametrize("color_dim", [3, 48])

@@ -1,0 +1,91 @@
+"""Device status words and determinism: anomalies are reported through grt_bvh_status and
+leave the rest of the launch intact; repeated launches give bit-identical results."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests._gpu import random_rays, scene_gpu, t
+from paper_2607_22780_b300 import api, workloads as wl
+from paper_2607_22780_b300._lib import STATUS_BAD_INDEX, STATUS_NONFINITE
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(n=20000, W=32, H=24, seed=41):
+    sc = wl.scene_objects(n, seed=seed)
+    cam = wl.camera_orbit(seed, W, H, 3.0)
+    gb32 = oracle.gbuffer_f32(oracle.gbuffer(sc, cam))
+    env = wl.envmap_hdr(seed, 128, 64)
+    return sc, gb32, env
+
+
+def test_nonfinite_rays_are_reported_and_missed():
+    sc = wl.scene_sphere_plane(8000, seed=2607)
+    rng = np.random.default_rng(3)
+    o, d = random_rays(rng, 512, -2.5, 2.5, 1.0)
+    S = scene_gpu(sc)
+    assert S.status() == 0
+    base = api.trace_forward(S, t(o), t(d), max_hits=16)
+    assert S.status() == 0
+    bad = [5, 17, 300]
+    o2, d2 = o.copy(), d.copy()
+    o2[5, 0] = np.nan
+    d2[17, 2] = np.inf
+    d2[300] = np.nan
+    got = api.trace_forward(S, t(o2), t(d2), max_hits=16)
+    assert S.status() == STATUS_NONFINITE
+    assert S.status() == 0  # reading clears the word
+    keep = np.setdiff1d(np.arange(512), bad)
+    for a, b in zip(got, base):
+        assert torch.equal(a[keep], b[keep])
+    rgb, op, hits, nh = got
+    assert float(op[bad].abs().sum()) == 0 and float(rgb[bad].abs().sum()) == 0 and int(nh[bad].sum()) == 0
+
+
+def test_pixel_index_outside_gbuffer_is_skipped_and_reported():
+    sc, gb32, env = _case()
+    S = scene_gpu(sc)
+    G = api.GBuffer.from_arrays(gb32)
+    E = api.Environment(t(env))
+    P = 32 * 24
+    good = np.array([3, 100, 101, 500, 767], np.int32)
+    pix = np.array([3, -1, 100, P, 101, 500, 1 << 30, 767], np.int32)
+    a = api.shade_pixels(S, G, E, 8, 4, 4, seed=9, pixels=t(good, torch.int32))
+    assert S.status() == 0
+    b = api.shade_pixels(S, G, E, 8, 4, 4, seed=9, pixels=t(pix, torch.int32))
+    assert S.status() == STATUS_BAD_INDEX
+    at = [0, 2, 4, 5, 7]
+    for x, y in zip(a, b):
+        assert torch.equal(x, y[at])
+        assert float(y[[1, 3, 6]].abs().sum()) == 0
+    g = api.shade_backward(S, G, E, 8, 4, 4, 9, torch.ones((len(pix), 3), device="cuda"),
+                           pixels=t(pix, torch.int32))
+    assert S.status() == STATUS_BAD_INDEX
+    g0 = api.shade_backward(S, G, E, 8, 4, 4, 9, torch.ones((len(good), 3), device="cuda"),
+                            pixels=t(good, torch.int32))
+    for f in ("mu", "quat", "scale", "opacity", "color"):
+        x, y = getattr(g, f), getattr(g0, f)
+        assert torch.allclose(x, y, rtol=1e-5, atol=1e-6 * float(y.abs().max())), f
+
+
+def test_shading_and_gradients_are_deterministic():
+    sc, gb32, env = _case(n=30000, W=40, H=30, seed=43)
+    S = scene_gpu(sc)
+    G = api.GBuffer.from_arrays(gb32)
+    E = api.Environment(t(env))
+    first = api.shade_pixels(S, G, E, 16, 8, 8, seed=5)
+    for _ in range(3):
+        again = api.shade_pixels(S, G, E, 16, 8, 8, seed=5)
+        for x, y in zip(first, again):
+            assert torch.equal(x, y)
+    other = api.shade_pixels(S, G, E, 16, 8, 8, seed=6)
+    assert not torch.equal(first[0], other[0])
+    # gradients use float atomics: repeat runs agree to rounding, not bit for bit
+    dc = torch.ones_like(first[0])
+    g1 = api.shade_backward(S, G, E, 16, 8, 8, 5, dc)
+    g2 = api.shade_backward(S, G, E, 16, 8, 8, 5, dc)
+    for f in ("mu", "quat", "scale", "opacity", "color"):
+        x, y = getattr(g1, f), getattr(g2, f)
+        assert torch.allclose(x, y, rtol=1e-4, atol=1e-6 * float(x.abs().max())), f
+    assert S.status() == 0

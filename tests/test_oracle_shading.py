@@ -144,3 +144,18 @@ def test_gbuffer_miss_is_invalid():
     sc = scene([dict(mu=(5, 5, 0), scale=(0.1, 0.1), opacity=0.9)])
     g = oracle.gbuffer(sc, _cam((0.0, 0.0, 3.0)))
     assert g["valid"].sum() == 0 and np.all(g["alpha"] == 0)
+
+
+def test_gbuffer_pixel_subset_rows():
+    # traced pixels are independent: the subset's rows are the full image's rows of those pixels
+    sc = wl.scene_objects(20000, seed=4)
+    cam = wl.camera_orbit(4, 20, 16, 3.0)
+    full = oracle.gbuffer(sc, cam)
+    v = np.nonzero(full["valid"])[0]
+    pix = np.array([319, 0, v[0], 160, v[-1], v[0], v[len(v) // 2]], np.int32)
+    sub = oracle.gbuffer(sc, cam, pixels=pix)
+    for k in ("pos", "normal", "albedo", "rough", "metal", "alpha", "depth", "valid", "flags"):
+        assert np.array_equal(sub[k], full[k][pix]), k
+    assert full["valid"][pix].sum() > 0
+    with pytest.raises(ValueError):
+        oracle.gbuffer(sc, cam, pixels=np.array([320], np.int32))
