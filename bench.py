@@ -11,6 +11,8 @@ pixel.  The metric is secondary rays per second (valid pixels x 32 / step time).
 
 Mode "train": 400x400, 16 rays/pixel (8/4/4) on the same scene, forward + adjoint of an
 L2 loss against a seeded target (shade_pixels + shade_backward).
+Mode "large": 2M surfels (ground plane, 50 primitives, background shell), 1920x1080,
+16 rays/pixel (8/4/4), forward and forward + backward with recomputed hit lists.
 Mode "serve": the relight request loop (see paper_2607_22780_b300.serve).
 
 Under torchrun every rank renders its own frame (weak scaling, no data-path collective);
@@ -43,6 +45,10 @@ NODE_BYTES = 112    # 4-wide node visit: 6 child-plane float4 + 1 child-ref floa
 SH_BYTES = 192      # 48 SH coefficients read per composited hit
 RAY_IO_BYTES = 44   # direction 16 + origin 12 read, (c_rt, T) 16 written
 COLLAPSE_LEVELS = 60
+LARGE_N = 2_000_000          # unbounded scene: ground plane, 50 primitives, r = 50 shell
+LARGE_W, LARGE_H = 1920, 1080
+LARGE_ALLOC = (8, 4, 4)
+LARGE_DISTANCE = 12.0
 
 
 def reduce_ranks(ms: float, rays: float, device) -> tuple:
@@ -323,6 +329,9 @@ def run_grt(args):
     fb = None
     if not args.no_train:
         fb = time_train(api, S, cam, E, dev, args)
+    large = None
+    if rank == 0 and world == 1 and not args.no_large:
+        large = time_large(api, dev, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -350,7 +359,7 @@ def run_grt(args):
                             "phase_ms": {"sample": float(np.mean(ph[:, 0])), "trace": float(np.mean(ph[:, 1])),
                                          "accumulate": float(np.mean(ph[:, 2])), "shade_call": shade_s * 1e3},
                             "per_ray": {"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R}},
-               "clocks": clk, "e2e": e2e, "fwd_bwd": fb, "cpu_baseline": cpu, "serving": serving,
+               "clocks": clk, "e2e": e2e, "fwd_bwd": fb, "large": large, "cpu_baseline": cpu, "serving": serving,
                "wall_s_timed": t_wall}
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -396,34 +405,97 @@ def time_train(api, S, cam, E, dev, args):
     grads = api.SurfelGrads.zeros(S)
     P = TRAIN_IMG * TRAIN_IMG
 
-    def step():
-        col, vis, ind = api.shade_pixels(S, G, E, *TRAIN_ALLOC, seed=SEED)
-        dl = (col - tgt) * G.valid.unsqueeze(1).float()
+    valid = G.valid.unsqueeze(1).float()
+
+    def zero():
         for t_ in (grads.mu, grads.quat, grads.scale, grads.opacity, grads.color):
             t_.zero_()
+
+    def step_stored():
+        # forward keeps each ray's first 16 hits, the backward replays them
+        col, vis, ind, saved = api.shade_pixels_save(S, G, E, *TRAIN_ALLOC, seed=SEED, max_hits=16)
+        dl = (col - tgt) * valid
+        zero()
+        api.shade_backward(S, G, E, *TRAIN_ALLOC, SEED, dl.contiguous(), grads=grads, saved=saved)
+
+    def step_recompute():
+        # no per-ray state between the passes: the backward samples and traces again
+        col, vis, ind = api.shade_pixels(S, G, E, *TRAIN_ALLOC, seed=SEED)
+        dl = (col - tgt) * valid
+        zero()
         api.shade_backward(S, G, E, *TRAIN_ALLOC, SEED, dl.contiguous(), grads=grads)
 
-    for _ in range(max(1, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fa, fb_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n = max(1, args.steps)
-    a.record()
-    for _ in range(n):
-        step()
-    b.record()
-    fa.record()
-    for _ in range(n):
+    def fwd():
         api.shade_pixels(S, G, E, *TRAIN_ALLOC, seed=SEED)
-    fb_.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / n
-    fms = fa.elapsed_time(fb_) / n
+
+    n = max(1, args.steps)
+    ms = {}
+    for name, fn in (("fwd_bwd", step_stored), ("fwd_bwd_recompute", step_recompute), ("fwd", fwd)):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms[name] = a.elapsed_time(b) / n
     nv = int(G.valid.sum().item())
     R = nv * sum(TRAIN_ALLOC)
-    return {"workload": "train_300k_400x400_16spp", "rays": R, "fwd_ms": fms, "fwd_bwd_ms": ms,
-            "fwd_rays_per_s": R / (fms * 1e-3), "fwd_bwd_rays_per_s": R / (ms * 1e-3)}
+    return {"workload": "train_300k_400x400_16spp", "rays": R, "fwd_ms": ms["fwd"], "fwd_bwd_ms": ms["fwd_bwd"],
+            "fwd_bwd_recompute_ms": ms["fwd_bwd_recompute"], "stored_hits": 16,
+            "fwd_rays_per_s": R / (ms["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (ms["fwd_bwd"] * 1e-3),
+            "fwd_bwd_recompute_rays_per_s": R / (ms["fwd_bwd_recompute"] * 1e-3)}
+
+
+def time_large(api, dev, args):
+    """2M-surfel unbounded scene, 1920x1080, 16 rays/pixel (8/4/4), k = 16: the forward
+    (shade_pixels) and forward + backward (shade_pixels, L2 upstream gradient against the
+    seeded target, shade_backward with recomputed hit lists) per frame.  The scene's
+    records, tree and SH coefficients (~0.7 GB) exceed L2, so no flush is needed."""
+    import torch
+    from paper_2607_22780_b300 import workloads as wl
+    sc = wl.scene_large(LARGE_N, seed=SEED)
+    cam = wl.camera_orbit(SEED, LARGE_W, LARGE_H, LARGE_DISTANCE)
+    S = api.Scene.from_workload(sc, device=dev, params=api.trace_params(k=16))
+    E = api.Environment(torch.from_numpy(wl.envmap_hdr(SEED + 1, ENV_W, ENV_H)).to(dev))
+    G = api.gbuffer_primary(S, cam)
+    tgt = torch.from_numpy(wl.target_image(SEED, LARGE_H, LARGE_W).reshape(-1, 3)).to(dev)
+    valid = G.valid.unsqueeze(1).float()
+    grads = api.SurfelGrads.zeros(S)
+    P = LARGE_W * LARGE_H
+    outs = (torch.empty((P, 3), device=dev), torch.empty((P,), device=dev), torch.empty((P, 3), device=dev))
+
+    def fwd():
+        api.shade_pixels(S, G, E, *LARGE_ALLOC, seed=SEED, outputs=outs)
+
+    def fwd_bwd():
+        fwd()
+        dl = (outs[0] - tgt) * valid
+        for t_ in (grads.mu, grads.quat, grads.scale, grads.opacity, grads.color):
+            t_.zero_()
+        api.shade_backward(S, G, E, *LARGE_ALLOC, SEED, dl.contiguous(), grads=grads)
+
+    res = {}
+    n = max(1, min(args.steps, 10))
+    for name, fn in (("fwd", fwd), ("fwd_bwd", fwd_bwd)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / n
+    R = int(G.valid.sum().item()) * sum(LARGE_ALLOC)
+    assert S.status() == 0
+    return {"workload": "large_2m_1920x1080_16spp", "surfels": LARGE_N, "rays": R, "k": 16,
+            "fwd_ms": res["fwd"], "fwd_bwd_ms": res["fwd_bwd"],
+            "fwd_rays_per_s": R / (res["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (res["fwd_bwd"] * 1e-3),
+            "steps": n, "l2": "inputs larger than L2"}
 
 
 def main():
@@ -432,10 +504,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="grt", choices=["grt", "reference"])
-    ap.add_argument("--mode", default="shade", choices=["shade", "serve", "train"])
+    ap.add_argument("--mode", default="shade", choices=["shade", "serve", "train", "large"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2M-surfel 1080p forward/backward line")
     ap.add_argument("--k", type=int, default=16, help="k-buffer size (results do not depend on it)")
     ap.add_argument("--serve-requests", type=int, default=40, help="requests of the 80%%-load serving trace")
     ap.add_argument("--no-serve", action="store_true")
@@ -454,6 +527,11 @@ def main():
         serve.bench_main(args)
     elif args.mode == "train":
         run_train_only(args)
+    elif args.mode == "large":
+        import torch
+        from paper_2607_22780_b300 import api
+        torch.cuda.set_device(0)
+        print(json.dumps(time_large(api, torch.device("cuda"), args)), flush=True)
     else:
         run_grt(args)
 

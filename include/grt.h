@@ -228,6 +228,32 @@ int grt_shade_backward(const grt_bvh* bvh, const grt_surfels* surfels, const grt
                        const float* dL_dvis, const float* dL_dind, const grt_grads* grads,
                        void* stream);
 
+/* Stored forward record for the backward pass (Sec. III-B: the loss gradient flows back
+ * through the secondary trace into the surfels).  grt_shade_pixels_save does what
+ * grt_shade_pixels does and also keeps, in the caller's device buffer `saved` (256-byte
+ * aligned, at least grt_shade_saved_bytes() bytes), every secondary ray's sampled
+ * direction, its traced (c_rt, T) and its first max_hits composited hits (surfel id,
+ * tau, alpha) in compositing order: 36 + 12 max_hits bytes per ray.
+ * grt_shade_backward_saved is grt_shade_backward without the resampling and the forward
+ * re-trace: rays with at most max_hits hits are replayed from the record, longer ones are
+ * traced again.  Gradients equal grt_shade_backward's up to the order of the float atomic
+ * additions.  The backward call must get the same bvh, surfels, params, gbuffer, env,
+ * sampling, pixel_list, n_pixels and max_hits as the save call, with the surfels unchanged
+ * in between (a replayed surfel id outside the scene is skipped and reported as
+ * GRT_STATUS_BAD_INDEX).  grt_shade_saved_bytes returns 0 (and sets the error text) for
+ * invalid arguments; max_hits is in [0, GRT_MAX_SAVED_HITS]. */
+#define GRT_MAX_SAVED_HITS 64
+size_t grt_shade_saved_bytes(int32_t n_pixels, const grt_sampling* sampling, int32_t max_hits);
+int grt_shade_pixels_save(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                          const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
+                          const int32_t* pixel_list, int32_t n_pixels, float* out_color, float* out_vis,
+                          float* out_ind, int32_t max_hits, void* saved, size_t saved_bytes, void* stream);
+int grt_shade_backward_saved(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                             const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
+                             const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
+                             const float* dL_dvis, const float* dL_dind, int32_t max_hits, const void* saved,
+                             size_t saved_bytes, const grt_grads* grads, void* stream);
+
 /* One shading request of a batch (same meaning as the grt_shade_pixels arguments).
  * With pixel_list NULL, output i shades pixel pixel_offset + i (a contiguous slice of
  * the image, so a long request can be split over several launches). */

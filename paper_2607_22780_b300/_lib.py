@@ -16,6 +16,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "grt.h")
 GRT_OK, GRT_ERR_ARG, GRT_ERR_OOM, GRT_ERR_CUDA, GRT_ERR_OVERFLOW, GRT_ERR_TIMEOUT, GRT_ERR_UNSUPPORTED = range(7)
 GRT_MAX_BATCH = 48
 GRT_NOALLOC_MAX_SURFELS = 524288
+GRT_MAX_SAVED_HITS = 64
 STATUS_STACK_OVERFLOW = 1
 STATUS_NONFINITE = 2
 STATUS_BAD_TREE = 4
@@ -85,6 +86,13 @@ SIGNATURES = {
     "grt_shade_backward": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                      C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P,
                                      C.POINTER(Grads), P]),
+    "grt_shade_saved_bytes": (C.c_size_t, [C.c_int32, C.POINTER(Sampling), C.c_int32]),
+    "grt_shade_pixels_save": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
+                                        C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P,
+                                        C.c_int32, P, C.c_size_t, P]),
+    "grt_shade_backward_saved": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
+                                           C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P,
+                                           C.c_int32, P, C.c_size_t, C.POINTER(Grads), P]),
     "grt_shade_batch": (C.c_int, [C.POINTER(ShadeRequest), C.c_int32, C.POINTER(TraceParams), P]),
     "grt_trace_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), P, P, C.c_int32, P, P]),
     "grt_shade_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),

@@ -284,6 +284,53 @@ def shade_pixels(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_en
     return col, vis, ind
 
 
+class SavedShade:
+    """Forward record of one shading pass kept for its backward (grt_shade_pixels_save):
+    per secondary ray its direction, (c_rt, T) and first `max_hits` composited hits.
+    Valid for the scene, G-buffer, map, sampling and pixel list it was made with, while the
+    surfels stay unchanged."""
+
+    def __init__(self, buf: torch.Tensor, n_pixels: int, sampling_args: tuple, max_hits: int, pixels):
+        self.buf = buf
+        self.n_pixels = n_pixels
+        self.sampling_args = sampling_args
+        self.max_hits = max_hits
+        self.pixels = pixels
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.buf.numel())
+
+
+def shade_saved_bytes(n_pixels: int, n_cos, n_ggx, n_env, max_hits: int = 16) -> int:
+    s = sampling(n_cos, n_ggx, n_env, 0, 1)
+    nb = L.load().grt_shade_saved_bytes(int(n_pixels), C.byref(s), int(max_hits))
+    if nb == 0:
+        raise L.GrtError(L.GRT_ERR_ARG, L.load().grt_last_error().decode())
+    return int(nb)
+
+
+def shade_pixels_save(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
+                      max_hits: int = 16, params=None, outputs=None, stream=None):
+    """shade_pixels that also keeps the forward record for shade_backward(saved=...).
+    Returns (colour, visibility, indirect, SavedShade)."""
+    n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
+    if pixels is not None:
+        _dev(pixels, dtype=torch.int32, name="pixels", shape=(n,))
+    dev = gb.pos.device
+    if outputs is None:
+        outputs = (torch.empty((n, 3), device=dev), torch.empty((n,), device=dev), torch.empty((n, 3), device=dev))
+    col, vis, ind = outputs
+    nb = shade_saved_bytes(n, n_cos, n_ggx, n_env, max_hits)
+    buf = torch.empty(nb, dtype=torch.uint8, device=dev)
+    s = sampling(n_cos, n_ggx, n_env, seed, brdf)
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_shade_pixels_save(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
+                                           C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(col), _ptr(vis),
+                                           _ptr(ind), int(max_hits), _ptr(buf), nb, _stream(stream)))
+    return col, vis, ind, SavedShade(buf, n, (n_cos, n_ggx, n_env, seed, brdf), int(max_hits), pixels)
+
+
 def shade_count(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
                 params=None, stream=None):
     n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
@@ -297,7 +344,10 @@ def shade_count(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env
 
 def shade_backward(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, dL_dcolor, dL_dvis=None,
                    dL_dind=None, brdf=1, pixels=None, grads: Optional[SurfelGrads] = None, params=None,
-                   stream=None) -> SurfelGrads:
+                   saved: Optional[SavedShade] = None, stream=None) -> SurfelGrads:
+    """Adjoint of shade_pixels w.r.t. the surfels (gradients accumulate into `grads`).
+    With `saved` (from shade_pixels_save with the same arguments) the forward record is
+    replayed; otherwise samples and hit lists are recomputed."""
     n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
     _dev(dL_dcolor, name="dL_dcolor", shape=(n, 3))
     _dev(dL_dvis, name="dL_dvis", shape=(n,))
@@ -305,9 +355,18 @@ def shade_backward(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_
     g = grads if grads is not None else SurfelGrads.zeros(scene)
     s = sampling(n_cos, n_ggx, n_env, seed, brdf)
     p = params if params is not None else scene.params
-    L.check(L.load().grt_shade_backward(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
-                                        C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(dL_dcolor),
-                                        _ptr(dL_dvis), _ptr(dL_dind), C.byref(g.struct()), _stream(stream)))
+    lib = L.load()
+    if saved is None:
+        L.check(lib.grt_shade_backward(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
+                                       C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(dL_dcolor),
+                                       _ptr(dL_dvis), _ptr(dL_dind), C.byref(g.struct()), _stream(stream)))
+        return g
+    if saved.n_pixels != n or saved.sampling_args != (n_cos, n_ggx, n_env, seed, brdf) or saved.pixels is not pixels:
+        raise ValueError("saved record was made with other pixels or sampling")
+    L.check(lib.grt_shade_backward_saved(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
+                                         C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(dL_dcolor),
+                                         _ptr(dL_dvis), _ptr(dL_dind), saved.max_hits, _ptr(saved.buf), saved.nbytes,
+                                         C.byref(g.struct()), _stream(stream)))
     return g
 
 

@@ -30,30 +30,40 @@ class TraceFunction(torch.autograd.Function):
 
 
 class ShadeFunction(torch.autograd.Function):
-    """(colour, visibility, indirect) = shade_pixels(...) as a function of the surfels."""
+    """(colour, visibility, indirect) = shade_pixels(...) as a function of the surfels.
+
+    With store_hits = L the forward keeps each ray's first L composited hits and the
+    backward replays them (rays with more hits are traced again); with store_hits = None
+    the backward recomputes every hit list (no per-ray memory kept between the passes)."""
 
     @staticmethod
-    def forward(ctx, scene, gb, env, alloc, seed, brdf, pixels, mu, quat, scale, opacity, color):
-        col, vis, ind = api.shade_pixels(scene, gb, env, *alloc, seed, brdf=brdf, pixels=pixels)
-        ctx.args = (scene, gb, env, alloc, seed, brdf, pixels)
+    def forward(ctx, scene, gb, env, alloc, seed, brdf, pixels, store_hits, mu, quat, scale, opacity, color):
+        if store_hits is None:
+            col, vis, ind = api.shade_pixels(scene, gb, env, *alloc, seed, brdf=brdf, pixels=pixels)
+            saved = None
+        else:
+            col, vis, ind, saved = api.shade_pixels_save(scene, gb, env, *alloc, seed, brdf=brdf, pixels=pixels,
+                                                         max_hits=store_hits)
+        ctx.args = (scene, gb, env, alloc, seed, brdf, pixels, saved)
         return col, vis, ind
 
     @staticmethod
     def backward(ctx, g_col, g_vis, g_ind):
-        scene, gb, env, alloc, seed, brdf, pixels = ctx.args
-        n = g_col.shape[0]
-        dev = g_col.device
+        scene, gb, env, alloc, seed, brdf, pixels, saved = ctx.args
+        ctx.args = None
+        n = gb.W * gb.H if pixels is None else int(pixels.shape[0])
+        dev = gb.pos.device
         g_col = g_col.contiguous() if g_col is not None else torch.zeros((n, 3), device=dev)
         g = api.shade_backward(scene, gb, env, *alloc, seed, g_col,
                                None if g_vis is None else g_vis.contiguous(),
-                               None if g_ind is None else g_ind.contiguous(), brdf=brdf, pixels=pixels)
-        return (None,) * 7 + (g.mu, g.quat, g.scale, g.opacity, g.color)
+                               None if g_ind is None else g_ind.contiguous(), brdf=brdf, pixels=pixels, saved=saved)
+        return (None,) * 8 + (g.mu, g.quat, g.scale, g.opacity, g.color)
 
 
 def trace(scene, ray_o, ray_d):
     return TraceFunction.apply(scene, ray_o, ray_d, scene.mu, scene.quat, scene.scale, scene.opacity, scene.color)
 
 
-def shade(scene, gb, env, alloc, seed, brdf=1, pixels=None):
-    return ShadeFunction.apply(scene, gb, env, tuple(alloc), seed, brdf, pixels, scene.mu, scene.quat, scene.scale,
-                               scene.opacity, scene.color)
+def shade(scene, gb, env, alloc, seed, brdf=1, pixels=None, store_hits=16):
+    return ShadeFunction.apply(scene, gb, env, tuple(alloc), seed, brdf, pixels, store_hits, scene.mu, scene.quat,
+                               scene.scale, scene.opacity, scene.color)

@@ -222,56 +222,107 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_weights(const __grid_
 // Adjoint rays: same origin/direction as the forward shading rays, totals (c_rt, T_f)
 // from the forward pass, adjoints (dL/dc_rt, dL/do_rt) from k_adjoint_weights; one
 // traversal per ray in the persistent two-phase walk.
+// Adjoint state of shading ray r: origin from the G-buffer, direction and forward totals
+// (c_rt, T_f) from the forward pass, adjoints (dL/dc_rt, dL/do_rt) from k_adjoint_weights.
+__device__ __forceinline__ void adjoint_init(AdjointVisitor& av, const ShadeJob& J, const TraceParams& P, GradPtrs g,
+                                             float4 a, float4 rr, f3 o, f3 d) {
+    av.mu = J.mu;
+    av.quat = J.quat;
+    av.scale = J.scale;
+    av.opacity = J.opacity;
+    av.color = J.color;
+    av.cdim = J.cdim;
+    av.alpha_max = P.alpha_max;
+    av.g = g;
+    av.o = o;
+    av.d = d;
+    av.Gc[0] = a.x;
+    av.Gc[1] = a.y;
+    av.Gc[2] = a.z;
+    av.Go = a.w;
+    av.Tf = rr.w;
+    av.crt[0] = rr.x;
+    av.crt[1] = rr.y;
+    av.crt[2] = rr.z;
+    av.Cacc[0] = av.Cacc[1] = av.Cacc[2] = 0.f;
+}
+
+__device__ __forceinline__ f3 ray_origin(const ShadeJob& J, long long r) {
+    int li = (int)(r / J.Nr);
+    int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
+    return mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
+               __ldg(J.gb.pos + 3 * (size_t)pix + 2));
+}
+
+// Adjoint rays in the persistent two-phase walk: the (tau, id) sequence is recomputed by
+// tracing the ray again.  With a saved record (nh non-NULL), only rays whose hit count
+// exceeds the record's L are traced here; k_adjoint_replay handles the others.
 template <int K>
 struct AdjointTask {
     using Visitor = AdjointVisitor;
     const JobTable<1>* T;
     const float4 *dirs, *res, *adj;
     GradPtrs g;
+    const int* nh;
+    int L;
     __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& av, const DevBvh*& bvh) {
+        if (nh && __ldg(nh + r) <= L) return false;
         float4 a = __ldg(adj + r);
         if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f) return false;
         const ShadeJob& J = T->job[0];
         float4 rr = __ldg(res + r), dw = __ldg(dirs + r);
-        int li = (int)(r / J.Nr);
-        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
-        f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
-                   __ldg(J.gb.pos + 3 * (size_t)pix + 2));
+        f3 o = ray_origin(J, r);
         f3 d = mk3(dw.x, dw.y, dw.z);
         bvh = &J.bvh;
         trace_begin(J.bvh, ts, o, d, T->P);
-        av.mu = J.mu;
-        av.quat = J.quat;
-        av.scale = J.scale;
-        av.opacity = J.opacity;
-        av.color = J.color;
-        av.cdim = J.cdim;
-        av.alpha_max = T->P.alpha_max;
-        av.g = g;
-        av.o = o;
-        av.d = d;
-        av.Gc[0] = a.x;
-        av.Gc[1] = a.y;
-        av.Gc[2] = a.z;
-        av.Go = a.w;
-        av.Tf = rr.w;
-        av.crt[0] = rr.x;
-        av.crt[1] = rr.y;
-        av.crt[2] = rr.z;
-        av.Cacc[0] = av.Cacc[1] = av.Cacc[2] = 0.f;
+        adjoint_init(av, J, T->P, g, a, rr, o, d);
         return true;
     }
     __device__ __forceinline__ void end(long long, const TraceState<K>&, Visitor&) {}
 };
+
+// Replay of the saved hit records: one thread per ray with at most L composited hits
+// walks its (id, tau, alpha) list in compositing order, rebuilding T_k exactly as the
+// forward compositor did.
+__global__ void __launch_bounds__(kShadeThreads) k_adjoint_replay(const __grid_constant__ JobTable<1> T,
+                                                                  const float4* __restrict__ dirs,
+                                                                  const float4* __restrict__ res,
+                                                                  const float4* __restrict__ adj,
+                                                                  const __grid_constant__ SavedHits sv, GradPtrs g) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= T.total_rays) return;
+    const int n = __ldg(sv.nh + r);
+    if (n == 0 || n > sv.L) return;
+    float4 a = __ldg(adj + r);
+    if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f) return;
+    const ShadeJob& J = T.job[0];
+    float4 rr = __ldg(res + r), dw = __ldg(dirs + r);
+    AdjointVisitor av;
+    adjoint_init(av, J, T.P, g, a, rr, ray_origin(J, r), mk3(dw.x, dw.y, dw.z));
+    const int ns = J.bvh.n;
+    float Tb = 1.f;
+    for (int k = 0; k < n; ++k) {
+        const size_t i = (size_t)k * sv.R + r;
+        const int id = __ldg(sv.ids + i);
+        const float tau = __ldg(sv.tau + i), alpha = __ldg(sv.alpha + i);
+        if ((unsigned)id >= (unsigned)ns) {
+            atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
+            return;
+        }
+        av.composite(k, id, tau, alpha, Tb);
+        Tb = mul_d(Tb, sub_d(1.0f, alpha));
+    }
+}
 
 template <int K>
 __global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : 4) k_adjoint_ww(const __grid_constant__ JobTable<1> T,
                                                                                const float4* __restrict__ dirs,
                                                                                const float4* __restrict__ res,
                                                                                const float4* __restrict__ adj, GradPtrs g,
+                                                                               const int* __restrict__ nh, int L,
                                                                                unsigned long long* __restrict__ next_ray) {
     __shared__ int q[kQueue * kShadeThreads];
-    AdjointTask<K> task{&T, dirs, res, adj, g};
+    AdjointTask<K> task{&T, dirs, res, adj, g, nh, L};
     persistent_trace<K>(task, T.P, next_ray, T.total_rays, q + threadIdx.x, kShadeThreads);
 }
 
@@ -313,10 +364,14 @@ extern "C" int grt_trace_backward(const grt_bvh* b, const grt_surfels* s, const 
     return launch_error("k_trace_backward");
 }
 
-extern "C" int grt_shade_backward(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
-                                  const grt_gbuffer* gb, const grt_envmap* e, const grt_sampling* smp,
-                                  const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
-                                  const float* dL_dvis, const float* dL_dind, const grt_grads* grads, void* stream) {
+// Shading adjoint: with save == NULL the samples are drawn and traced again (dirs, res
+// in pool scratch); with a saved record they are read from it and rays with at most L
+// hits are replayed instead of traced.
+static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
+                               const grt_gbuffer* gb, const grt_envmap* e, const grt_sampling* smp,
+                               const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
+                               const float* dL_dvis, const float* dL_dind, const grt_grads* grads,
+                               const SaveBufs* save, cudaStream_t st) {
     int rc = check_trace_inputs(b, s, p);
     if (rc) return rc;
     rc = check_grads(grads, s);
@@ -332,22 +387,24 @@ extern "C" int grt_shade_backward(const grt_bvh* b, const grt_surfels* s, const 
     const long long rays = (long long)J.n_pixels * J.Nr;
     T.total_rays = rays;
     T.total_units = 0;
-    cudaStream_t st = (cudaStream_t)stream;
     keep_pool_memory();
     float4* buf = nullptr;
-    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (3 * (size_t)rays + 1), st));
-    float4* dirs = buf;
-    float4* res = buf + rays;
-    float4* adj = buf + 2 * rays;
-    unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + 3 * rays);
+    const size_t nbuf = save ? (size_t)rays + 1 : 3 * (size_t)rays + 1;
+    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * nbuf, st));
+    float4* adj = buf;
+    unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + rays);
+    float4* dirs = save ? save->dirs : buf + rays + 1;
+    float4* res = save ? save->res : buf + 2 * rays + 1;
     const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
     GradPtrs g{grads->mu, grads->quat, grads->scale, grads->opacity, grads->color};
-    k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
+    if (!save) k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
     dispatch_k(p->k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
-        launch_trace_dyn<K, 1>(T, dirs, res, next_ray, gr, st);
+        if (!save) launch_trace_dyn<K, 1>(T, dirs, res, next_ray, gr, st);
         k_adjoint_weights<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, AdjIn{dL_dcolor, dL_dvis, dL_dind},
                                                                    adj);
+        if (save && save->hits.L > 0)
+            k_adjoint_replay<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, adj, save->hits, g);
         cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
@@ -355,10 +412,32 @@ extern "C" int grt_shade_backward(const grt_bvh* b, const grt_surfels* s, const 
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_ww<K>, kShadeThreads, 0);
         long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
         if (grid > gr) grid = gr;
-        k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, next_ray);
+        const int* nh = save && save->hits.L > 0 ? save->hits.nh : nullptr;
+        k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, nh,
+                                                                  save ? save->hits.L : 0, next_ray);
     });
     cudaError_t err = cudaGetLastError();
     cudaFreeAsync(buf, st);
     if (err != cudaSuccess) return check_cuda(err, "shade backward kernels");
     return GRT_OK;
+}
+
+extern "C" int grt_shade_backward(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
+                                  const grt_gbuffer* gb, const grt_envmap* e, const grt_sampling* smp,
+                                  const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
+                                  const float* dL_dvis, const float* dL_dind, const grt_grads* grads, void* stream) {
+    return shade_backward_impl(b, s, p, gb, e, smp, pixel_list, n_pixels, dL_dcolor, dL_dvis, dL_dind, grads, nullptr,
+                               (cudaStream_t)stream);
+}
+
+extern "C" int grt_shade_backward_saved(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
+                                        const grt_gbuffer* gb, const grt_envmap* e, const grt_sampling* smp,
+                                        const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
+                                        const float* dL_dvis, const float* dL_dind, int32_t max_hits,
+                                        const void* saved, size_t saved_bytes, const grt_grads* grads, void* stream) {
+    SaveBufs sb;
+    int rc = saved_buffers(saved, saved_bytes, n_pixels, smp, max_hits, &sb);
+    if (rc) return rc;
+    return shade_backward_impl(b, s, p, gb, e, smp, pixel_list, n_pixels, dL_dcolor, dL_dvis, dL_dind, grads, &sb,
+                               (cudaStream_t)stream);
 }

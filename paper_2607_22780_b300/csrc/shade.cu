@@ -90,7 +90,7 @@ struct PhaseTiming {
 thread_local PhaseTiming g_timing;
 
 template <bool COUNT, int CAP>
-int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st) {
+int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, const SaveBufs* save = nullptr) {
     long long rays = 0, units = 0;
     for (int i = 0; i < T.n_jobs; ++i) {
         ShadeJob& J = T.job[i];
@@ -102,12 +102,20 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st) {
     T.total_rays = rays;
     T.total_units = units;
     if (rays == 0) return GRT_OK;
-    keep_pool_memory();
     float4* buf = nullptr;
-    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1), st));
-    float4* dirs = buf;
-    float4* res = buf + rays;
-    unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + 2 * rays);
+    float4 *dirs, *res;
+    unsigned long long* next_ray;
+    if (save) {
+        dirs = save->dirs;
+        res = save->res;
+        next_ray = save->next;
+    } else {
+        keep_pool_memory();
+        GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1), st));
+        dirs = buf;
+        res = buf + rays;
+        next_ray = reinterpret_cast<unsigned long long*>(buf + 2 * rays);
+    }
     const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
     g_timing.mark(0, st);
     k_sample_rays<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
@@ -116,6 +124,8 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st) {
         constexpr int K = decltype(kc)::value;
         if (COUNT) {  // counting pass: one ray per thread, same traversal
             k_trace_rays<K, COUNT, CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, counters);
+        } else if (save) {
+            if constexpr (CAP == 1) launch_trace_save<K, CAP>(T, dirs, res, save->hits, next_ray, gr, st);
         } else {
             launch_trace_dyn<K, CAP>(T, dirs, res, next_ray, gr, st);
         }
@@ -128,7 +138,7 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st) {
         g_timing.have = g_timing.on;
     }
     cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(buf, st);
+    if (buf) cudaFreeAsync(buf, st);
     if (e != cudaSuccess) return check_cuda(e, "shade kernels");
     return GRT_OK;
 }
@@ -136,7 +146,7 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st) {
 template <bool COUNT>
 int launch_single(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p, const grt_gbuffer* g,
                   const grt_envmap* e, const grt_sampling* smp, const int* pl, int n, float* oc, float* ov, float* oi,
-                  long long* counters, cudaStream_t st) {
+                  long long* counters, cudaStream_t st, const SaveBufs* save = nullptr) {
     int rc = check_trace_inputs(b, s, p);
     if (rc) return rc;
     JobTable<1> T;
@@ -149,7 +159,7 @@ int launch_single(const grt_bvh* b, const grt_surfels* s, const grt_trace_params
         if (oc) k_zero_outputs<<<(n + 255) / 256, 256, 0, st>>>(oc, ov, oi, n);
         return launch_error("k_zero_outputs");
     }
-    return run_jobs<COUNT>(T, p->k, counters, st);
+    return run_jobs<COUNT>(T, p->k, counters, st, save);
 }
 
 }  // namespace
@@ -171,6 +181,31 @@ extern "C" int grt_shade_count(const grt_bvh* b, const grt_surfels* s, const grt
     if (!counters) return set_error(GRT_ERR_ARG, "counters is NULL");
     return launch_single<true>(b, s, p, g, e, smp, pixel_list, n_pixels, nullptr, nullptr, nullptr, counters,
                                (cudaStream_t)stream);
+}
+
+extern "C" size_t grt_shade_saved_bytes(int32_t n_pixels, const grt_sampling* smp, int32_t max_hits) {
+    if (n_pixels < 0 || !smp || smp->n_cos < 0 || smp->n_ggx < 0 || smp->n_env < 0) {
+        set_error(GRT_ERR_ARG, "bad n_pixels or sampling");
+        return 0;
+    }
+    if (max_hits < 0 || max_hits > GRT_MAX_SAVED_HITS) {
+        set_error(GRT_ERR_ARG, "max_hits = %d outside [0, %d]", max_hits, GRT_MAX_SAVED_HITS);
+        return 0;
+    }
+    const long long R = (long long)n_pixels * (smp->n_cos + smp->n_ggx + smp->n_env);
+    return saved_layout(R, max_hits).total;
+}
+
+extern "C" int grt_shade_pixels_save(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
+                                     const grt_gbuffer* g, const grt_envmap* e, const grt_sampling* smp,
+                                     const int32_t* pixel_list, int32_t n_pixels, float* out_color, float* out_vis,
+                                     float* out_ind, int32_t max_hits, void* saved, size_t saved_bytes, void* stream) {
+    if (n_pixels > 0 && !out_color) return set_error(GRT_ERR_ARG, "out_color is NULL");
+    SaveBufs sb;
+    int rc = saved_buffers(saved, saved_bytes, n_pixels, smp, max_hits, &sb);
+    if (rc) return rc;
+    return launch_single<false>(b, s, p, g, e, smp, pixel_list, n_pixels, out_color, out_vis, out_ind, nullptr,
+                                (cudaStream_t)stream, &sb);
 }
 
 extern "C" int grt_shade_batch(const grt_shade_request* req, int32_t n_req, const grt_trace_params* p,

@@ -294,6 +294,131 @@ __global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : GRT_TRACE_MIN_BLO
     persistent_trace<K>(task, T.P, next_ray, T.total_rays, q + threadIdx.x, kShadeThreads);
 }
 
+// Forward record kept for the backward pass (grt_shade_pixels_save): per ray the number
+// of composited hits and, slot-major ([slot][ray], coalesced across a warp), the surfel id,
+// tau and alpha of its first L hits in compositing order.
+struct SavedHits {
+    int* nh;
+    int* ids;
+    float* tau;
+    float* alpha;
+    long long R;
+    int L;
+};
+
+// Layout of the caller's saved-forward buffer: ray directions and traced (c_rt, T) as in
+// the shading pass, the persistent kernel's ray counter, then the hit record.
+struct SavedLayout {
+    size_t dirs, res, next, nh, ids, tau, alpha, total;
+};
+
+inline SavedLayout saved_layout(long long R, int L) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    SavedLayout o;
+    size_t off = 0;
+    o.dirs = off;
+    off = up(off + 16 * (size_t)R);
+    o.res = off;
+    off = up(off + 16 * (size_t)R);
+    o.next = off;
+    off = up(off + 8);
+    o.nh = off;
+    off = up(off + 4 * (size_t)R);
+    o.ids = off;
+    off = up(off + 4 * (size_t)L * R);
+    o.tau = off;
+    off = up(off + 4 * (size_t)L * R);
+    o.alpha = off;
+    off = up(off + 4 * (size_t)L * R);
+    o.total = off;
+    return o;
+}
+
+// Caller-owned buffers of grt_shade_pixels_save / grt_shade_backward_saved.
+struct SaveBufs {
+    float4* dirs;
+    float4* res;
+    unsigned long long* next;
+    SavedHits hits;
+};
+
+// The saved-forward buffer checked against the layout of this call's rays.
+inline int saved_buffers(const void* saved, size_t saved_bytes, int32_t n_pixels, const grt_sampling* smp,
+                         int32_t max_hits, SaveBufs* out) {
+    size_t need = grt_shade_saved_bytes(n_pixels, smp, max_hits);
+    if (need == 0) return GRT_ERR_ARG;
+    if (!saved || ((uintptr_t)saved & 255))
+        return set_error(GRT_ERR_ARG, "saved must be a 256-byte aligned device pointer");
+    if (saved_bytes < need) return set_error(GRT_ERR_ARG, "saved buffer holds %zu bytes, %zu needed", saved_bytes, need);
+    const long long R = (long long)n_pixels * (smp->n_cos + smp->n_ggx + smp->n_env);
+    SavedLayout L = saved_layout(R, max_hits);
+    char* base = (char*)saved;
+    out->dirs = reinterpret_cast<float4*>(base + L.dirs);
+    out->res = reinterpret_cast<float4*>(base + L.res);
+    out->next = reinterpret_cast<unsigned long long*>(base + L.next);
+    out->hits = SavedHits{reinterpret_cast<int*>(base + L.nh), reinterpret_cast<int*>(base + L.ids),
+                          reinterpret_cast<float*>(base + L.tau), reinterpret_cast<float*>(base + L.alpha), R, max_hits};
+    return GRT_OK;
+}
+
+// Radiance visitor that also writes the first L composited hits of its ray.
+struct SavingVisitor : RadianceVisitor {
+    const SavedHits* sv;
+    long long r;
+    __device__ __forceinline__ SavingVisitor() {}
+    __device__ __forceinline__ SavingVisitor(const float* col, int cd, f3 dir, const SavedHits* s, long long ray)
+        : RadianceVisitor(col, cd, dir), sv(s), r(ray) {}
+    __device__ __forceinline__ void composite(int k, int id, float tau, float alpha, float Tb) {
+        RadianceVisitor::composite(k, id, tau, alpha, Tb);
+        if (k < sv->L) {
+            const size_t i = (size_t)k * sv->R + r;
+            sv->ids[i] = id;
+            sv->tau[i] = tau;
+            sv->alpha[i] = alpha;
+        }
+    }
+};
+
+template <int K, int CAP>
+struct ShadeTraceSave {
+    using Visitor = SavingVisitor;
+    const JobTable<CAP>* T;
+    const float4* dirs;
+    float4* res;
+    const SavedHits* sv;
+    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& cv, const DevBvh*& bvh) {
+        float4 dw = __ldg(dirs + r);
+        if (dw.w == 0.f) {
+            res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
+            sv->nh[r] = 0;
+            return false;
+        }
+        const ShadeJob& J = T->job[T->find_ray(r)];
+        int li = (int)((r - J.ray_begin) / J.Nr);
+        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
+        f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
+                   __ldg(J.gb.pos + 3 * (size_t)pix + 2));
+        f3 d = mk3(dw.x, dw.y, dw.z);
+        bvh = &J.bvh;
+        trace_begin(J.bvh, ts, o, d, T->P);
+        cv = SavingVisitor(J.color, J.cdim, d, sv, r);
+        return true;
+    }
+    __device__ __forceinline__ void end(long long r, const TraceState<K>& ts, Visitor& cv) {
+        res[r] = make_float4(cv.c[0], cv.c[1], cv.c[2], ts.T);
+        sv->nh[r] = ts.ncomp;
+    }
+};
+
+template <int K, int CAP>
+__global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : GRT_TRACE_MIN_BLOCKS) k_trace_rays_save(
+    const __grid_constant__ JobTable<CAP> T, const float4* __restrict__ dirs, float4* __restrict__ res,
+    const __grid_constant__ SavedHits sv, unsigned long long* __restrict__ next_ray) {
+    __shared__ int q[kQueue * kShadeThreads];
+    ShadeTraceSave<K, CAP> task{&T, dirs, res, &sv};
+    persistent_trace<K>(task, T.P, next_ray, T.total_rays, q + threadIdx.x, kShadeThreads);
+}
+
 // Persistent forward trace of every ray of the table (per-ray (c_rt, T) into res).
 template <int K, int CAP>
 inline void launch_trace_dyn(const JobTable<CAP>& T, const float4* dirs, float4* res, unsigned long long* next_ray,
@@ -313,6 +438,20 @@ inline void launch_trace_dyn(const JobTable<CAP>& T, const float4* dirs, float4*
     if (grid > blocks_max) grid = blocks_max;
     k_trace_rays_dyn<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, next_ray);
 #endif
+}
+
+// Persistent forward trace that also keeps the per-ray hit record.
+template <int K, int CAP>
+inline void launch_trace_save(const JobTable<CAP>& T, const float4* dirs, float4* res, const SavedHits& sv,
+                              unsigned long long* next_ray, long long blocks_max, cudaStream_t st) {
+    cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_rays_save<K, CAP>, kShadeThreads, 0);
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > blocks_max) grid = blocks_max;
+    k_trace_rays_save<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, sv, next_ray);
 }
 
 }  // namespace

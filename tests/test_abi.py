@@ -36,3 +36,28 @@ def test_bad_params_rejected_without_gpu():
     assert rc == _lib.GRT_ERR_ARG  # bvh is NULL comes first
     assert lib.grt_env_tables_bytes(512, 256) >= 512 * 256 * 16
     assert lib.grt_env_tables_bytes(0, 256) == 0
+
+
+def test_saved_record_size_and_checks_without_gpu():
+    lib = _lib.load()
+    smp = _lib.Sampling(8, 4, 4, 1, 7)
+    R = 1000 * 16
+    nb = lib.grt_shade_saved_bytes(1000, ctypes.byref(smp), 16)
+    # directions and (c_rt, T) 32 B, hit count 4 B, (id, tau, alpha) 12 B per slot, per ray
+    assert R * (36 + 12 * 16) <= nb <= R * (36 + 12 * 16) + 7 * 256
+    assert lib.grt_shade_saved_bytes(1000, ctypes.byref(smp), 0) < nb
+    assert lib.grt_shade_saved_bytes(1000, ctypes.byref(smp), _lib.GRT_MAX_SAVED_HITS + 1) == 0
+    assert b"max_hits" in lib.grt_last_error()
+    assert lib.grt_shade_saved_bytes(-1, ctypes.byref(smp), 4) == 0
+    # a buffer that is too small (or misaligned) is rejected before any device work
+    s = _lib.Surfels(0, 3)
+    p = _lib.TraceParams(1 / 255, 0.99, 0.01, 3e38, 1e-4, 1e-6, 16)
+    g, e = _lib.GBuffer(), _lib.EnvMap()
+    rc = lib.grt_shade_pixels_save(None, ctypes.byref(s), ctypes.byref(p), ctypes.byref(g), ctypes.byref(e),
+                                   ctypes.byref(smp), None, 1000, ctypes.c_void_p(1 << 20), None, None, 16,
+                                   ctypes.c_void_p(1 << 20), nb - 1, None)
+    assert rc == _lib.GRT_ERR_ARG and b"bytes" in lib.grt_last_error()
+    rc = lib.grt_shade_backward_saved(None, ctypes.byref(s), ctypes.byref(p), ctypes.byref(g), ctypes.byref(e),
+                                      ctypes.byref(smp), None, 1000, ctypes.c_void_p(1 << 20), None, None, 16,
+                                      ctypes.c_void_p((1 << 20) + 16), nb, None, None)
+    assert rc == _lib.GRT_ERR_ARG and b"aligned" in lib.grt_last_error()

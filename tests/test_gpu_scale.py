@@ -57,10 +57,13 @@ def _fd_params(g, rng, per_field=(13, 13, 13, 13, 12), frac=0.05):
 
 
 def test_c3_gradient_vs_central_differences(objects_300k):
-    # 400x400 frame, 16 rays/pixel, L2 loss against the seeded target; each parameter is
-    # moved by +-h and +-2h (BVH refit each time).  A parameter whose two difference
-    # quotients disagree has a hit-set change (cut-off radius, alpha_min, termination)
-    # inside the step and is not differentiable there; the others must match.
+    # 400x400 frame, 16 rays/pixel, L2 loss against the seeded target, 64 random parameters.
+    # The rendered loss is piecewise smooth: a step that moves a hit across the alpha_min
+    # cut-off, or across an exact depth tie (coplanar surfels), jumps.  Each parameter walks
+    # a ladder of steps h0 / 4^k; a step is clean when the composited-hit total at +-h is
+    # unchanged and the loss change |g| 2h (>= 5e-4) stands above the FP32 rounding of the
+    # image (~2e-5); the first two consecutive clean steps whose quotients agree within 1% give
+    # the finite difference, which must match the analytic gradient within 2%.
     sc = objects_300k
     S = scene_gpu(sc)
     cam = wl.camera_orbit(SEED, 400, 400, 3.0)
@@ -73,40 +76,56 @@ def test_c3_gradient_vs_central_differences(objects_300k):
         col, _, _ = api.shade_pixels(S, G, E, *ALLOC, seed=SEED)
         return 0.5 * float((((col.double() - tgt) * valid) ** 2).sum())
 
-    L0 = loss()
+    def composited():
+        return int(api.shade_count(S, G, E, *ALLOC, seed=SEED)[2])
+
+    L0, c0 = loss(), composited()
     col, _, _ = api.shade_pixels(S, G, E, *ALLOC, seed=SEED)
     dl = ((col.double() - tgt) * valid).float().contiguous()
     g = api.shade_backward(S, G, E, *ALLOC, SEED, dl)
-    steps = dict(mu=2e-5, quat=1e-4, scale=None, opacity=1e-4, color=1e-3)
+    h0 = dict(mu=1e-4, quat=1e-3, scale=None, opacity=1e-3, color=4e-2)
 
-    def fd(f, i, h):
+    def step(f, i, h):
+        """(quotient, clean) for the central difference of step h."""
         p = getattr(S, f).view(-1)
         x = float(p[i])
         xp, xm = np.float32(x + h), np.float32(x - h)
         p[i] = float(xp)
         S.refit()
-        lp = loss()
+        lp, cp = loss(), composited()
         p[i] = float(xm)
         S.refit()
-        lm = loss()
+        lm, cm = loss(), composited()
         p[i] = x
-        return (lp - lm) / (float(xp) - float(xm))
+        return (lp - lm) / (float(xp) - float(xm)), cp == c0 and cm == c0
 
     rng = np.random.default_rng(64)
     rows = []
     for f, i in _fd_params(g, rng):
-        h = steps[f] if steps[f] is not None else 1e-3 * abs(float(getattr(S, f).view(-1)[i]))
         a = float(getattr(g, f).view(-1)[i])
-        d1, d2 = fd(f, i, h), fd(f, i, 2 * h)
-        rows.append((f, i, a, d1, d2))
+        h = h0[f] if h0[f] is not None else 1e-2 * abs(float(getattr(S, f).view(-1)[i]))
+        prev, fd = None, None
+        for k in range(6):
+            hk = h / 4 ** k
+            if abs(a) * 2 * hk < 5e-4:
+                break
+            q, clean = step(f, i, hk)
+            if not clean:
+                prev = None
+                continue
+            if prev is not None and abs(q - prev) <= 0.01 * max(abs(q), abs(prev)):
+                fd = prev
+                break
+            prev = q
+        rows.append((f, i, a, fd))
     S.refit()
     assert loss() == L0  # parameters restored exactly, forward deterministic
-    stable = [r for r in rows if abs(r[3] - r[4]) <= 0.05 * max(abs(r[3]), abs(r[4]))]
-    bad = [r for r in stable if abs(r[3] - r[2]) > 0.02 * max(abs(r[3]), abs(r[2]))]
-    fields = {r[0] for r in stable}
-    print("\n".join("%-8s %8d  g=% .6e  fd(h)=% .6e  fd(2h)=% .6e" % r for r in rows))
+    print("\n".join("%-8s %8d  g=% .6e  fd=%s" % (f, i, a, "-" if d is None else "% .6e" % d) for f, i, a, d in rows))
+    checked = [r for r in rows if r[3] is not None]
+    bad = [r for r in checked if abs(r[3] - r[2]) > 0.02 * max(abs(r[3]), abs(r[2]))]
+    per_field = {f: sum(r[0] == f for r in checked) for f in GRAD_FIELDS}
     assert len(rows) == 64
-    assert len(stable) >= 40 and fields == set(GRAD_FIELDS), (len(stable), fields)
+    assert len(checked) >= 32 and min(per_field.values()) >= 3, per_field
     assert not bad, bad
 
 
