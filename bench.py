@@ -456,15 +456,16 @@ def time_large(api, dev, args):
     records, tree and SH coefficients (~0.7 GB) exceed L2, so no flush is needed."""
     import torch
     from paper_2607_22780_b300 import workloads as wl
+    W, H = (args.image, args.image * 9 // 16) if args.mode == "large" and args.image else (LARGE_W, LARGE_H)
     sc = wl.scene_large(LARGE_N, seed=SEED)
-    cam = wl.camera_orbit(SEED, LARGE_W, LARGE_H, LARGE_DISTANCE)
+    cam = wl.camera_orbit(SEED, W, H, LARGE_DISTANCE)
     S = api.Scene.from_workload(sc, device=dev, params=api.trace_params(k=16))
     E = api.Environment(torch.from_numpy(wl.envmap_hdr(SEED + 1, ENV_W, ENV_H)).to(dev))
     G = api.gbuffer_primary(S, cam)
-    tgt = torch.from_numpy(wl.target_image(SEED, LARGE_H, LARGE_W).reshape(-1, 3)).to(dev)
+    tgt = torch.from_numpy(wl.target_image(SEED, H, W).reshape(-1, 3)).to(dev)
     valid = G.valid.unsqueeze(1).float()
     grads = api.SurfelGrads.zeros(S)
-    P = LARGE_W * LARGE_H
+    P = W * H
     outs = (torch.empty((P, 3), device=dev), torch.empty((P,), device=dev), torch.empty((P, 3), device=dev))
 
     def fwd():
@@ -491,10 +492,25 @@ def time_large(api, dev, args):
         torch.cuda.synchronize()
         res[name] = a.elapsed_time(b) / n
     R = int(G.valid.sum().item()) * sum(LARGE_ALLOC)
+    # roofline of the forward trace kernel: logical bytes from the traversal counters over
+    # its event time inside the shading call
+    api.phase_timing(True)
+    tr = []
+    for _ in range(3):
+        fwd()
+        tr.append(api.phase_timing(read=True)[1])
+    api.phase_timing(False)
+    cnt = api.shade_count(S, G, E, *LARGE_ALLOC, seed=SEED).cpu().numpy().astype(np.float64)
+    alg = NODE_BYTES * cnt[0] + REC_BYTES * cnt[1] + SH_BYTES * cnt[2] + RAY_IO_BYTES * R
+    trace_ms = float(np.median(tr))
+    peak, peak_kind = measured_peaks()
     assert S.status() == 0
-    return {"workload": "large_2m_1920x1080_16spp", "surfels": LARGE_N, "rays": R, "k": 16,
+    return {"workload": f"large_2m_{W}x{H}_16spp", "surfels": LARGE_N, "rays": R, "k": 16,
             "fwd_ms": res["fwd"], "fwd_bwd_ms": res["fwd_bwd"],
             "fwd_rays_per_s": R / (res["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (res["fwd_bwd"] * 1e-3),
+            "trace_kernel_ms": trace_ms, "per_ray": {"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R},
+            "roofline_trace": {"bound": "hbm", "achieved": alg / (trace_ms * 1e-3) / 1e9, "peak": peak,
+                               "unit": "GB/s", "frac": alg / (trace_ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind},
             "steps": n, "l2": "inputs larger than L2"}
 
 
