@@ -11,8 +11,13 @@
 // tau = n.(mu - o_ray)/(n.d), into mu, the quaternion through R(q/|q|), s_u, s_v, o and
 // the colour (RGB or SH coefficients, zero where max(0, .) clamps).
 //
-// The hit list is never stored: a first traversal gives c_rt and T_f, a second replays
-// the same (tau, id) sequence and scatters gradients with vector atomics.
+// Shading rays get their (tau, id, alpha) sequences from a per-ray hit record: the
+// caller's forward record (grt_shade_backward_saved) or a transient one that the backward
+// traces itself (grt_shade_backward, chunked to bound memory).  Recorded rays are replayed
+// by one thread each; rays with more hits than the record holds, and the rays of
+// grt_trace_backward, are traversed again in compositing order.
+#include <algorithm>
+
 #include "wavefront.cuh"
 
 namespace grt {
@@ -364,9 +369,34 @@ extern "C" int grt_trace_backward(const grt_bvh* b, const grt_surfels* s, const 
     return launch_error("k_trace_backward");
 }
 
-// Shading adjoint: with save == NULL the samples are drawn and traced again (dirs, res
-// in pool scratch); with a saved record they are read from it and rays with at most L
-// hits are replayed instead of traced.
+// Recomputing adjoint (no forward record): the backward draws the samples again and
+// traces them once, keeping a transient hit record that it then replays.  Rays are taken
+// in chunks so that the transient record (directions, totals, adjoints, hit count and
+// kRecomputeHits hits: 244 bytes per ray) stays below ~2 GB whatever the frame size.
+constexpr long long kRecomputeChunkRays = 8ll << 20;
+constexpr int kRecomputeHits = 16;
+
+// Adjoint weights, replay of the recorded rays, and a traced adjoint walk for the rays
+// the record does not hold (all rays when hits.L == 0).
+template <int K>
+static void run_adjoint(const JobTable<1>& T, const float4* dirs, const float4* res, const SavedHits& hits,
+                        float4* adj, unsigned long long* next_ray, const AdjIn& in, const GradPtrs& g,
+                        cudaStream_t st) {
+    const long long gr = (T.total_rays + kShadeThreads - 1) / kShadeThreads;
+    k_adjoint_weights<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, in, adj);
+    if (hits.L > 0) k_adjoint_replay<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, adj, hits, g);
+    cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_ww<K>, kShadeThreads, 0);
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > gr) grid = gr;
+    k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, hits.L > 0 ? hits.nh : nullptr,
+                                                              hits.L, next_ray);
+}
+
+// Shading adjoint, from a caller's forward record (save) or recomputing (save == NULL).
 static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
                                const grt_gbuffer* gb, const grt_envmap* e, const grt_sampling* smp,
                                const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
@@ -382,40 +412,53 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
     T.n_jobs = 1;
     rc = make_job(b, s, gb, e, smp, pixel_list, n_pixels, nullptr, nullptr, nullptr, &T.job[0]);
     if (rc) return rc;
-    ShadeJob& J = T.job[0];
+    const ShadeJob& J = T.job[0];
     if (J.n_pixels == 0) return GRT_OK;
     const long long rays = (long long)J.n_pixels * J.Nr;
     T.total_rays = rays;
     T.total_units = 0;
-    keep_pool_memory();
-    float4* buf = nullptr;
-    const size_t nbuf = save ? (size_t)rays + 1 : 3 * (size_t)rays + 1;
-    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * nbuf, st));
-    float4* adj = buf;
-    unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + rays);
-    float4* dirs = save ? save->dirs : buf + rays + 1;
-    float4* res = save ? save->res : buf + 2 * rays + 1;
-    const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
     GradPtrs g{grads->mu, grads->quat, grads->scale, grads->opacity, grads->color};
-    if (!save) k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
-    dispatch_k(p->k, [&](auto kc) {
-        constexpr int K = decltype(kc)::value;
-        if (!save) launch_trace_dyn<K, 1>(T, dirs, res, next_ray, gr, st);
-        k_adjoint_weights<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, AdjIn{dL_dcolor, dL_dvis, dL_dind},
-                                                                   adj);
-        if (save && save->hits.L > 0)
-            k_adjoint_replay<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, adj, save->hits, g);
-        cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_ww<K>, kShadeThreads, 0);
-        long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
-        if (grid > gr) grid = gr;
-        const int* nh = save && save->hits.L > 0 ? save->hits.nh : nullptr;
-        k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, nh,
-                                                                  save ? save->hits.L : 0, next_ray);
-    });
+    keep_pool_memory();
+    char* buf = nullptr;
+    if (save) {
+        GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * ((size_t)rays + 1), st));
+        float4* adj = reinterpret_cast<float4*>(buf);
+        unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(adj + rays);
+        dispatch_k(p->k, [&](auto kc) {
+            run_adjoint<decltype(kc)::value>(T, save->dirs, save->res, save->hits, adj, next_ray,
+                                             AdjIn{dL_dcolor, dL_dvis, dL_dind}, g, st);
+        });
+    } else {
+        const long long chunk_px = std::min<long long>(J.n_pixels, std::max<long long>(1, kRecomputeChunkRays / J.Nr));
+        const long long Rc = chunk_px * J.Nr;
+        const SavedLayout lay = saved_layout(Rc, kRecomputeHits);
+        GRT_CUDA(cudaMallocAsync((void**)&buf, lay.total + sizeof(float4) * (size_t)Rc, st));
+        float4* dirs = reinterpret_cast<float4*>(buf + lay.dirs);
+        float4* res = reinterpret_cast<float4*>(buf + lay.res);
+        unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + lay.next);
+        float4* adj = reinterpret_cast<float4*>(buf + lay.total);
+        for (long long p0 = 0; p0 < J.n_pixels; p0 += chunk_px) {
+            JobTable<1> Tc = T;
+            ShadeJob& Jc = Tc.job[0];
+            Jc.n_pixels = (int)std::min<long long>(chunk_px, J.n_pixels - p0);
+            if (Jc.pixel_list)
+                Jc.pixel_list += p0;
+            else
+                Jc.pixel_offset += (int)p0;
+            Tc.total_rays = (long long)Jc.n_pixels * Jc.Nr;
+            const SavedHits hits{reinterpret_cast<int*>(buf + lay.nh), reinterpret_cast<int*>(buf + lay.ids),
+                                 reinterpret_cast<float*>(buf + lay.tau), reinterpret_cast<float*>(buf + lay.alpha),
+                                 Tc.total_rays, kRecomputeHits};
+            const AdjIn in{dL_dcolor + 3 * p0, dL_dvis ? dL_dvis + p0 : nullptr, dL_dind ? dL_dind + 3 * p0 : nullptr};
+            const long long gr = (Tc.total_rays + kShadeThreads - 1) / kShadeThreads;
+            k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(Tc, dirs);
+            dispatch_k(p->k, [&](auto kc) {
+                constexpr int K = decltype(kc)::value;
+                launch_trace_save<K, 1>(Tc, dirs, res, hits, next_ray, gr, st);
+                run_adjoint<K>(Tc, dirs, res, hits, adj, next_ray, in, g, st);
+            });
+        }
+    }
     cudaError_t err = cudaGetLastError();
     cudaFreeAsync(buf, st);
     if (err != cudaSuccess) return check_cuda(err, "shade backward kernels");

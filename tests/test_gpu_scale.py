@@ -167,12 +167,6 @@ def test_c4_shading_and_gradients_sampled_pixels(large_2m):
         a = a.cpu().numpy()[pix]
         bad = (np.abs(a - r) > hdr_tol(r)).reshape(len(pix), -1).any(1) & m
         assert bad.sum() == 0, (a[bad], r[bad])
-    # whole-frame backward with recomputed hit lists: finite, nothing reported
-    dc = torch.ones_like(col)
-    gf = api.shade_backward(S, G, E, *ALLOC, SEED, dc)
-    for f in GRAD_FIELDS:
-        assert torch.isfinite(getattr(gf, f)).all(), f
-    assert float(gf.opacity.abs().sum()) > 0
     # gradients of the sampled, unflagged pixels against the oracle
     keep = pix[m]
     w = rng.normal(size=(len(keep), 3)).astype(np.float32)
@@ -180,4 +174,13 @@ def test_c4_shading_and_gradients_sampled_pixels(large_2m):
     assert np.all(refg["flags"] == 0)
     gs = api.shade_backward(S, G, E, *ALLOC, SEED, t(w), pixels=t(keep, torch.int32))
     check_grads(gs, refg)
+    # the whole frame (33M ray slots, recomputed in several chunks) with the same upstream
+    # gradient on those pixels and zero elsewhere gives the same gradients
+    dc = torch.zeros_like(col)
+    dc[torch.from_numpy(keep).long().cuda()] = t(w)
+    gf = api.shade_backward(S, G, E, *ALLOC, SEED, dc)
+    for f in GRAD_FIELDS:
+        x, y = getattr(gf, f), getattr(gs, f)
+        assert torch.isfinite(x).all(), f
+        assert torch.allclose(x, y, rtol=1e-4, atol=1e-6 * float(y.abs().max())), f
     assert S.status() == 0
