@@ -412,8 +412,8 @@ def time_train(api, S, cam, E, dev, args):
             t_.zero_()
 
     def step_stored():
-        # forward keeps each ray's first 16 hits, the backward replays them
-        col, vis, ind, saved = api.shade_pixels_save(S, G, E, *TRAIN_ALLOC, seed=SEED, max_hits=16)
+        # forward keeps each ray's first 64 hits, the backward replays them
+        col, vis, ind, saved = api.shade_pixels_save(S, G, E, *TRAIN_ALLOC, seed=SEED, max_hits=64)
         dl = (col - tgt) * valid
         zero()
         api.shade_backward(S, G, E, *TRAIN_ALLOC, SEED, dl.contiguous(), grads=grads, saved=saved)
@@ -444,7 +444,7 @@ def time_train(api, S, cam, E, dev, args):
     nv = int(G.valid.sum().item())
     R = nv * sum(TRAIN_ALLOC)
     return {"workload": "train_300k_400x400_16spp", "rays": R, "fwd_ms": ms["fwd"], "fwd_bwd_ms": ms["fwd_bwd"],
-            "fwd_bwd_recompute_ms": ms["fwd_bwd_recompute"], "stored_hits": 16,
+            "fwd_bwd_recompute_ms": ms["fwd_bwd_recompute"], "stored_hits": 64,
             "fwd_rays_per_s": R / (ms["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (ms["fwd_bwd"] * 1e-3),
             "fwd_bwd_recompute_rays_per_s": R / (ms["fwd_bwd_recompute"] * 1e-3)}
 

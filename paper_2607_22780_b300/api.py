@@ -302,7 +302,7 @@ class SavedShade:
         return int(self.buf.numel())
 
 
-def shade_saved_bytes(n_pixels: int, n_cos, n_ggx, n_env, max_hits: int = 16) -> int:
+def shade_saved_bytes(n_pixels: int, n_cos, n_ggx, n_env, max_hits: int = 64) -> int:
     s = sampling(n_cos, n_ggx, n_env, 0, 1)
     nb = L.load().grt_shade_saved_bytes(int(n_pixels), C.byref(s), int(max_hits))
     if nb == 0:
@@ -311,9 +311,10 @@ def shade_saved_bytes(n_pixels: int, n_cos, n_ggx, n_env, max_hits: int = 16) ->
 
 
 def shade_pixels_save(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
-                      max_hits: int = 16, params=None, outputs=None, stream=None):
-    """shade_pixels that also keeps the forward record for shade_backward(saved=...).
-    Returns (colour, visibility, indirect, SavedShade)."""
+                      max_hits: int = 64, params=None, outputs=None, stream=None):
+    """shade_pixels that also keeps the forward record for shade_backward(saved=...):
+    36 + 12 max_hits bytes per ray slot (pixels x N_r).  Returns (colour, visibility,
+    indirect, SavedShade)."""
     n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
     if pixels is not None:
         _dev(pixels, dtype=torch.int32, name="pixels", shape=(n,))

@@ -64,6 +64,6 @@ def trace(scene, ray_o, ray_d):
     return TraceFunction.apply(scene, ray_o, ray_d, scene.mu, scene.quat, scene.scale, scene.opacity, scene.color)
 
 
-def shade(scene, gb, env, alloc, seed, brdf=1, pixels=None, store_hits=16):
+def shade(scene, gb, env, alloc, seed, brdf=1, pixels=None, store_hits=64):
     return ShadeFunction.apply(scene, gb, env, tuple(alloc), seed, brdf, pixels, store_hits, scene.mu, scene.quat,
                                scene.scale, scene.opacity, scene.color)

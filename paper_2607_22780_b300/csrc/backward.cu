@@ -260,18 +260,17 @@ __device__ __forceinline__ f3 ray_origin(const ShadeJob& J, long long r) {
 }
 
 // Adjoint rays in the persistent two-phase walk: the (tau, id) sequence is recomputed by
-// tracing the ray again.  With a saved record (nh non-NULL), only rays whose hit count
-// exceeds the record's L are traced here; k_adjoint_replay handles the others.
+// tracing the ray again.  With a hit record, only the rays k_adjoint_replay listed (more
+// hits than the record holds) are walked here.
 template <int K>
 struct AdjointTask {
     using Visitor = AdjointVisitor;
     const JobTable<1>* T;
     const float4 *dirs, *res, *adj;
     GradPtrs g;
-    const int* nh;
-    int L;
-    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& av, const DevBvh*& bvh) {
-        if (nh && __ldg(nh + r) <= L) return false;
+    const long long* list;  // rays to walk (those the replay could not take), or all rays
+    __device__ __forceinline__ bool begin(long long i, TraceState<K>& ts, Visitor& av, const DevBvh*& bvh) {
+        const long long r = list ? __ldg(list + i) : i;
         float4 a = __ldg(adj + r);
         if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f) return false;
         const ShadeJob& J = T->job[0];
@@ -293,13 +292,19 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_replay(const __grid_c
                                                                   const float4* __restrict__ dirs,
                                                                   const float4* __restrict__ res,
                                                                   const float4* __restrict__ adj,
-                                                                  const __grid_constant__ SavedHits sv, GradPtrs g) {
+                                                                  const __grid_constant__ SavedHits sv, GradPtrs g,
+                                                                  unsigned long long* __restrict__ over_count,
+                                                                  long long* __restrict__ over_list) {
     long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= T.total_rays) return;
     const int n = __ldg(sv.nh + r);
-    if (n == 0 || n > sv.L) return;
+    if (n == 0) return;
     float4 a = __ldg(adj + r);
     if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f) return;
+    if (n > sv.L) {  // longer than the record: left to the traced adjoint walk
+        over_list[atomicAdd(over_count, 1ull)] = r;
+        return;
+    }
     const ShadeJob& J = T.job[0];
     float4 rr = __ldg(res + r), dw = __ldg(dirs + r);
     AdjointVisitor av;
@@ -324,11 +329,13 @@ __global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : 4) k_adjoint_ww(c
                                                                                const float4* __restrict__ dirs,
                                                                                const float4* __restrict__ res,
                                                                                const float4* __restrict__ adj, GradPtrs g,
-                                                                               const int* __restrict__ nh, int L,
+                                                                               const unsigned long long* __restrict__ n_list,
+                                                                               const long long* __restrict__ list,
                                                                                unsigned long long* __restrict__ next_ray) {
     __shared__ int q[kQueue * kShadeThreads];
-    AdjointTask<K> task{&T, dirs, res, adj, g, nh, L};
-    persistent_trace<K>(task, T.P, next_ray, T.total_rays, q + threadIdx.x, kShadeThreads);
+    AdjointTask<K> task{&T, dirs, res, adj, g, list};
+    const long long total = n_list ? (long long)*n_list : T.total_rays;
+    persistent_trace<K>(task, T.P, next_ray, total, q + threadIdx.x, kShadeThreads);
 }
 
 }  // namespace
@@ -372,28 +379,34 @@ extern "C" int grt_trace_backward(const grt_bvh* b, const grt_surfels* s, const 
 // Recomputing adjoint (no forward record): the backward draws the samples again and
 // traces them once, keeping a transient hit record that it then replays.  Rays are taken
 // in chunks so that the transient record (directions, totals, adjoints, hit count and
-// kRecomputeHits hits: 244 bytes per ray) stays below ~2 GB whatever the frame size.
-constexpr long long kRecomputeChunkRays = 8ll << 20;
-constexpr int kRecomputeHits = 16;
+// kRecomputeHits hits, overflow list: 828 bytes per ray) stays below ~1.8 GB whatever the
+// frame size.
+// 64 slots hold every hit of all but ~0.2% of the rays of the object and unbounded scenes
+// (at most 96 hits seen); the few longer rays are traversed again.
+constexpr long long kRecomputeChunkRays = 2ll << 20;
+constexpr int kRecomputeHits = 64;
 
 // Adjoint weights, replay of the recorded rays, and a traced adjoint walk for the rays
-// the record does not hold (all rays when hits.L == 0).
+// the record does not hold (all rays when hits.L == 0).  `work` holds two counters and,
+// with a record, room for a list of every ray.
 template <int K>
 static void run_adjoint(const JobTable<1>& T, const float4* dirs, const float4* res, const SavedHits& hits,
-                        float4* adj, unsigned long long* next_ray, const AdjIn& in, const GradPtrs& g,
-                        cudaStream_t st) {
+                        float4* adj, unsigned long long* work, const AdjIn& in, const GradPtrs& g, cudaStream_t st) {
     const long long gr = (T.total_rays + kShadeThreads - 1) / kShadeThreads;
+    unsigned long long* next_ray = work;
+    unsigned long long* n_over = work + 1;
+    long long* over = reinterpret_cast<long long*>(work + 2);
+    cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), st);
     k_adjoint_weights<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, in, adj);
-    if (hits.L > 0) k_adjoint_replay<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, adj, hits, g);
-    cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
+    if (hits.L > 0) k_adjoint_replay<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, adj, hits, g, n_over, over);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_ww<K>, kShadeThreads, 0);
     long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
     if (grid > gr) grid = gr;
-    k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, hits.L > 0 ? hits.nh : nullptr,
-                                                              hits.L, next_ray);
+    k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, hits.L > 0 ? n_over : nullptr,
+                                                              hits.L > 0 ? over : nullptr, next_ray);
 }
 
 // Shading adjoint, from a caller's forward record (save) or recomputing (save == NULL).
@@ -421,22 +434,23 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
     keep_pool_memory();
     char* buf = nullptr;
     if (save) {
-        GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * ((size_t)rays + 1), st));
+        GRT_CUDA(cudaMallocAsync((void**)&buf, (sizeof(float4) + sizeof(long long)) * (size_t)rays + 16, st));
         float4* adj = reinterpret_cast<float4*>(buf);
-        unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(adj + rays);
+        unsigned long long* work = reinterpret_cast<unsigned long long*>(adj + rays);
         dispatch_k(p->k, [&](auto kc) {
-            run_adjoint<decltype(kc)::value>(T, save->dirs, save->res, save->hits, adj, next_ray,
+            run_adjoint<decltype(kc)::value>(T, save->dirs, save->res, save->hits, adj, work,
                                              AdjIn{dL_dcolor, dL_dvis, dL_dind}, g, st);
         });
     } else {
         const long long chunk_px = std::min<long long>(J.n_pixels, std::max<long long>(1, kRecomputeChunkRays / J.Nr));
         const long long Rc = chunk_px * J.Nr;
         const SavedLayout lay = saved_layout(Rc, kRecomputeHits);
-        GRT_CUDA(cudaMallocAsync((void**)&buf, lay.total + sizeof(float4) * (size_t)Rc, st));
+        GRT_CUDA(cudaMallocAsync((void**)&buf, lay.total + (sizeof(float4) + sizeof(long long)) * (size_t)Rc + 16, st));
         float4* dirs = reinterpret_cast<float4*>(buf + lay.dirs);
         float4* res = reinterpret_cast<float4*>(buf + lay.res);
         unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + lay.next);
         float4* adj = reinterpret_cast<float4*>(buf + lay.total);
+        unsigned long long* work = reinterpret_cast<unsigned long long*>(adj + Rc);
         for (long long p0 = 0; p0 < J.n_pixels; p0 += chunk_px) {
             JobTable<1> Tc = T;
             ShadeJob& Jc = Tc.job[0];
@@ -455,7 +469,7 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
             dispatch_k(p->k, [&](auto kc) {
                 constexpr int K = decltype(kc)::value;
                 launch_trace_save<K, 1>(Tc, dirs, res, hits, next_ray, gr, st);
-                run_adjoint<K>(Tc, dirs, res, hits, adj, next_ray, in, g, st);
+                run_adjoint<K>(Tc, dirs, res, hits, adj, work, in, g, st);
             });
         }
     }
