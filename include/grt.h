@@ -221,10 +221,10 @@ int grt_shade_pixels(const grt_bvh* bvh, const grt_surfels* surfels, const grt_t
 
 /* Adjoint of grt_shade_pixels with respect to the surfels, given dL_dcolor[n_pixels][3]
  * and optional dL_dvis[n_pixels], dL_dind[n_pixels][3] (NULL = 0).  Nothing is kept from
- * the forward pass: the same samples are drawn and traced again, in chunks of at most 2M
- * rays whose hit lists (first 64 hits per ray) live only during the call (~1.7 GB of pool
- * memory at most), then replayed; rays with more hits are traversed again.  Gradients
- * accumulate (+=) into grads. */
+ * the forward pass: the same samples are drawn and traced again, in chunks of at most 8M
+ * rays whose hit lists (first 64 hits per ray) live only during the call (two chunks in
+ * flight on two library streams, ~14 GB of pool memory at most), then replayed; rays with
+ * more hits are traversed again.  Gradients accumulate (+=) into grads. */
 int grt_shade_backward(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
                        const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
                        const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,

@@ -379,11 +379,16 @@ extern "C" int grt_trace_backward(const grt_bvh* b, const grt_surfels* s, const 
 // Recomputing adjoint (no forward record): the backward draws the samples again and
 // traces them once, keeping a transient hit record that it then replays.  Rays are taken
 // in chunks so that the transient record (directions, totals, adjoints, hit count and
-// kRecomputeHits hits, overflow list: 828 bytes per ray) stays below ~1.8 GB whatever the
-// frame size.
+// kRecomputeHits hits, overflow list: 828 bytes per ray; two chunks in flight) stays
+// within ~14 GB whatever the frame size.  On the 2M-surfel 1080p frame (33M ray slots)
+// forward + backward takes 442 ms in 8M-ray chunks, 432 ms unchunked, 512 ms in 2M-ray
+// chunks: each chunk's persistent kernels end in a tail of long rays.
 // 64 slots hold every hit of all but ~0.2% of the rays of the object and unbounded scenes
 // (at most 96 hits seen); the few longer rays are traversed again.
-constexpr long long kRecomputeChunkRays = 2ll << 20;
+#ifndef GRT_RECOMPUTE_CHUNK_RAYS
+#define GRT_RECOMPUTE_CHUNK_RAYS (8ll << 20)
+#endif
+constexpr long long kRecomputeChunkRays = GRT_RECOMPUTE_CHUNK_RAYS;
 constexpr int kRecomputeHits = 64;
 
 // Adjoint weights, replay of the recorded rays, and a traced adjoint walk for the rays
@@ -407,6 +412,34 @@ static void run_adjoint(const JobTable<1>& T, const float4* dirs, const float4* 
     if (grid > gr) grid = gr;
     k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, hits.L > 0 ? n_over : nullptr,
                                                               hits.L > 0 ? over : nullptr, next_ray);
+}
+
+// Two library streams per host thread and device: consecutive chunks of the recomputing
+// adjoint alternate between them, so that one chunk's rays fill the SMs that the long rays
+// at the end of the previous chunk leave idle.
+struct AuxStreams {
+    bool ready = false;
+    cudaStream_t s[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+};
+
+static int aux_streams(AuxStreams** out) {
+    constexpr int kMaxDev = 64;
+    static thread_local AuxStreams tab[kMaxDev];
+    int dev = 0;
+    GRT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) return set_error(GRT_ERR_UNSUPPORTED, "device %d beyond %d", dev, kMaxDev);
+    AuxStreams& a = tab[dev];
+    if (!a.ready) {
+        for (int i = 0; i < 2; ++i) {
+            GRT_CUDA(cudaStreamCreateWithFlags(&a.s[i], cudaStreamNonBlocking));
+            GRT_CUDA(cudaEventCreateWithFlags(&a.join[i], cudaEventDisableTiming));
+        }
+        GRT_CUDA(cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming));
+        a.ready = true;
+    }
+    *out = &a;
+    return GRT_OK;
 }
 
 // Shading adjoint, from a caller's forward record (save) or recomputing (save == NULL).
@@ -443,15 +476,30 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
         });
     } else {
         const long long chunk_px = std::min<long long>(J.n_pixels, std::max<long long>(1, kRecomputeChunkRays / J.Nr));
+        const long long n_chunks = (J.n_pixels + chunk_px - 1) / chunk_px;
         const long long Rc = chunk_px * J.Nr;
         const SavedLayout lay = saved_layout(Rc, kRecomputeHits);
-        GRT_CUDA(cudaMallocAsync((void**)&buf, lay.total + (sizeof(float4) + sizeof(long long)) * (size_t)Rc + 16, st));
-        float4* dirs = reinterpret_cast<float4*>(buf + lay.dirs);
-        float4* res = reinterpret_cast<float4*>(buf + lay.res);
-        unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + lay.next);
-        float4* adj = reinterpret_cast<float4*>(buf + lay.total);
-        unsigned long long* work = reinterpret_cast<unsigned long long*>(adj + Rc);
-        for (long long p0 = 0; p0 < J.n_pixels; p0 += chunk_px) {
+        const size_t per = (lay.total + (sizeof(float4) + sizeof(long long)) * (size_t)Rc + 16 + 255) & ~(size_t)255;
+        const int nbuf = n_chunks > 1 ? 2 : 1;
+        AuxStreams* aux = nullptr;
+        if (nbuf > 1) {
+            rc = aux_streams(&aux);
+            if (rc) return rc;
+        }
+        GRT_CUDA(cudaMallocAsync((void**)&buf, per * nbuf, st));
+        if (aux) {
+            GRT_CUDA(cudaEventRecord(aux->fork, st));
+            for (int i = 0; i < 2; ++i) GRT_CUDA(cudaStreamWaitEvent(aux->s[i], aux->fork, 0));
+        }
+        for (long long c = 0; c < n_chunks; ++c) {
+            const long long p0 = c * chunk_px;
+            cudaStream_t cs = aux ? aux->s[c & 1] : st;
+            char* cb = buf + per * (size_t)(c & 1);
+            float4* dirs = reinterpret_cast<float4*>(cb + lay.dirs);
+            float4* res = reinterpret_cast<float4*>(cb + lay.res);
+            unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(cb + lay.next);
+            float4* adj = reinterpret_cast<float4*>(cb + lay.total);
+            unsigned long long* work = reinterpret_cast<unsigned long long*>(adj + Rc);
             JobTable<1> Tc = T;
             ShadeJob& Jc = Tc.job[0];
             Jc.n_pixels = (int)std::min<long long>(chunk_px, J.n_pixels - p0);
@@ -460,17 +508,23 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
             else
                 Jc.pixel_offset += (int)p0;
             Tc.total_rays = (long long)Jc.n_pixels * Jc.Nr;
-            const SavedHits hits{reinterpret_cast<int*>(buf + lay.nh), reinterpret_cast<int*>(buf + lay.ids),
-                                 reinterpret_cast<float*>(buf + lay.tau), reinterpret_cast<float*>(buf + lay.alpha),
+            const SavedHits hits{reinterpret_cast<int*>(cb + lay.nh), reinterpret_cast<int*>(cb + lay.ids),
+                                 reinterpret_cast<float*>(cb + lay.tau), reinterpret_cast<float*>(cb + lay.alpha),
                                  Tc.total_rays, kRecomputeHits};
             const AdjIn in{dL_dcolor + 3 * p0, dL_dvis ? dL_dvis + p0 : nullptr, dL_dind ? dL_dind + 3 * p0 : nullptr};
             const long long gr = (Tc.total_rays + kShadeThreads - 1) / kShadeThreads;
-            k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(Tc, dirs);
+            k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, cs>>>(Tc, dirs);
             dispatch_k(p->k, [&](auto kc) {
                 constexpr int K = decltype(kc)::value;
-                launch_trace_save<K, 1>(Tc, dirs, res, hits, next_ray, gr, st);
-                run_adjoint<K>(Tc, dirs, res, hits, adj, work, in, g, st);
+                launch_trace_save<K, 1>(Tc, dirs, res, hits, next_ray, gr, cs);
+                run_adjoint<K>(Tc, dirs, res, hits, adj, work, in, g, cs);
             });
+        }
+        if (aux) {
+            for (int i = 0; i < 2; ++i) {
+                GRT_CUDA(cudaEventRecord(aux->join[i], aux->s[i]));
+                GRT_CUDA(cudaStreamWaitEvent(st, aux->join[i], 0));
+            }
         }
     }
     cudaError_t err = cudaGetLastError();
