@@ -45,6 +45,9 @@ NODE_BYTES = 112    # 4-wide node visit: 6 child-plane float4 + 1 child-ref floa
 SH_BYTES = 192      # 48 SH coefficients read per composited hit
 RAY_IO_BYTES = 44   # direction 16 + origin 12 read, (c_rt, T) 16 written
 COLLAPSE_LEVELS = 60
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_trace_rays_ww launch of the default
+# workload (k = 16, 800x800), one ncu capture of the current kernel (761.8 MB + 326.3 MB)
+TRACE_DRAM_BYTES = 1_088_072_960
 LARGE_N = 2_000_000          # unbounded scene: ground plane, 50 primitives, r = 50 shell
 LARGE_W, LARGE_H = 1920, 1080
 LARGE_ALLOC = (8, 4, 4)
@@ -353,7 +356,9 @@ def run_grt(args):
                           "parallelism": f"replicas x{world}"},
                "gpu_launches": launches_per_step * args.steps,
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "traffic": None, "kernel": "k_trace_rays_ww",
+                            "frac": achieved / peak,
+                            "traffic": TRACE_DRAM_BYTES if (args.k == 16 and W_IMG == 800) else None,
+                            "kernel": "k_trace_rays_ww",
                             "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
                             "kernel_ms": trace_s * 1e3,
                             "phase_ms": {"sample": float(np.mean(ph[:, 0])), "trace": float(np.mean(ph[:, 1])),
