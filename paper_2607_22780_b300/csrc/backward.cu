@@ -261,7 +261,8 @@ __device__ __forceinline__ f3 ray_origin(const ShadeJob& J, long long r) {
 
 // Adjoint rays in the persistent two-phase walk: the (tau, id) sequence is recomputed by
 // tracing the ray again.  With a hit record, only the rays k_adjoint_replay listed (more
-// hits than the record holds) are walked here.
+// hits than the record holds) are walked here: their L recorded hits are replayed, and
+// the traversal resumes after the last of them.
 template <int K>
 struct AdjointTask {
     using Visitor = AdjointVisitor;
@@ -269,6 +270,7 @@ struct AdjointTask {
     const float4 *dirs, *res, *adj;
     GradPtrs g;
     const long long* list;  // rays to walk (those the replay could not take), or all rays
+    const SavedHits* sv;    // with a list: their records, replayed before the walk resumes
     __device__ __forceinline__ bool begin(long long i, TraceState<K>& ts, Visitor& av, const DevBvh*& bvh) {
         const long long r = list ? __ldg(list + i) : i;
         float4 a = __ldg(adj + r);
@@ -278,8 +280,27 @@ struct AdjointTask {
         f3 o = ray_origin(J, r);
         f3 d = mk3(dw.x, dw.y, dw.z);
         bvh = &J.bvh;
-        trace_begin(J.bvh, ts, o, d, T->P);
         adjoint_init(av, J, T->P, g, a, rr, o, d);
+        if (!list) {
+            trace_begin(J.bvh, ts, o, d, T->P);
+            return true;
+        }
+        // the recorded first L hits, then the traversal from the last recorded key on
+        float Tb = 1.f, tau = 0.f;
+        int id = 0;
+        for (int k = 0; k < sv->L; ++k) {
+            const size_t j = (size_t)k * sv->R + r;
+            id = __ldg(sv->ids + j);
+            tau = __ldg(sv->tau + j);
+            const float alpha = __ldg(sv->alpha + j);
+            if ((unsigned)id >= (unsigned)J.bvh.n) {
+                atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
+                return false;
+            }
+            av.composite(k, id, tau, alpha, Tb);
+            Tb = mul_d(Tb, sub_d(1.0f, alpha));
+        }
+        trace_resume(J.bvh, ts, o, d, T->P, make_key(tau, id), Tb, sv->L);
         return true;
     }
     __device__ __forceinline__ void end(long long, const TraceState<K>&, Visitor&) {}
@@ -331,9 +352,10 @@ __global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : 4) k_adjoint_ww(c
                                                                                const float4* __restrict__ adj, GradPtrs g,
                                                                                const unsigned long long* __restrict__ n_list,
                                                                                const long long* __restrict__ list,
+                                                                               const __grid_constant__ SavedHits sv,
                                                                                unsigned long long* __restrict__ next_ray) {
     __shared__ int q[kQueue * kShadeThreads];
-    AdjointTask<K> task{&T, dirs, res, adj, g, list};
+    AdjointTask<K> task{&T, dirs, res, adj, g, list, &sv};
     const long long total = n_list ? (long long)*n_list : T.total_rays;
     persistent_trace<K>(task, T.P, next_ray, total, q + threadIdx.x, kShadeThreads);
 }
@@ -411,7 +433,7 @@ static void run_adjoint(const JobTable<1>& T, const float4* dirs, const float4* 
     long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
     if (grid > gr) grid = gr;
     k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, hits.L > 0 ? n_over : nullptr,
-                                                              hits.L > 0 ? over : nullptr, next_ray);
+                                                              hits.L > 0 ? over : nullptr, hits, next_ray);
 }
 
 // Two library streams per host thread and device: consecutive chunks of the recomputing

@@ -177,6 +177,18 @@ __device__ __forceinline__ void trace_begin(const DevBvh& bvh, TraceState<K>& s,
     }
 }
 
+// Continue a ray after `ncomp` hits already composited (the last one with key `last`),
+// with transmittance T in front of the next hit: the next round collects keys > last.
+template <int K>
+__device__ __forceinline__ void trace_resume(const DevBvh& bvh, TraceState<K>& s, f3 o, f3 d, const TraceParams& P,
+                                             uint64_t last, float T, int ncomp) {
+    trace_begin(bvh, s, o, d, P);
+    if (s.node == -2) return;  // non-finite ray
+    s.last = last;
+    s.T = T;
+    s.ncomp = ncomp;
+}
+
 template <int K, bool COUNT>
 __device__ __forceinline__ void test_leaf(const DevBvh& bvh, TraceState<K>& s, int ref, const TraceParams& P,
                                           Counters& cnt) {
