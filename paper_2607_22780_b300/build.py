@@ -9,8 +9,10 @@ from __future__ import annotations
 
 import glob
 import os
+import shutil
 import subprocess
 import sys
+import tempfile
 from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -42,7 +44,8 @@ def build(force: bool = False, verbose: bool = False, extra=(), out: str = None)
     out = out or OUT
     if out == OUT and not force and not stale():
         return OUT
-    bdir = os.path.join(CSRC, "_build" if out == OUT else "_build_" + os.path.basename(out).replace('.', '_'))
+    tmp_objs = out != OUT
+    bdir = os.path.join(CSRC, "_build") if not tmp_objs else tempfile.mkdtemp(prefix="grt_build_")
     os.makedirs(bdir, exist_ok=True)
 
     def compile_one(src):
@@ -65,6 +68,8 @@ def build(force: bool = False, verbose: bool = False, extra=(), out: str = None)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, out)
+    if tmp_objs:
+        shutil.rmtree(bdir, ignore_errors=True)
     return out
 
 

@@ -11,6 +11,7 @@
 namespace grt {
 
 constexpr int kShadeThreads = 128;
+static_assert(kShadeThreads == kPersistentThreads, "persistent kernels index shared memory by 128 lanes");
 
 struct ShadeJob {
     DevBvh bvh;
@@ -119,76 +120,9 @@ __global__ void __launch_bounds__(kShadeThreads) k_trace_rays(const __grid_const
     }
 }
 
-// Persistent variant of k_trace_rays: warps stay resident and walk their rays one wide
-// node per step; once kRefillLanes lanes have finished, the warp claims that many new
-// rays from a global counter, so a long ray holds one lane instead of a whole warp.
-constexpr int kRefillLanes = 8;
-#ifndef GRT_TRACE_WW
-#define GRT_TRACE_WW 1
-#endif
 #ifndef GRT_TRACE_MIN_BLOCKS
 #define GRT_TRACE_MIN_BLOCKS 4  // 128 threads x 4 blocks: at most 128 registers per thread
 #endif
-
-template <int K, int CAP>
-__global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : GRT_TRACE_MIN_BLOCKS) k_trace_rays_dyn(const __grid_constant__ JobTable<CAP> T,
-                                                                  const float4* __restrict__ dirs,
-                                                                  float4* __restrict__ res,
-                                                                  unsigned long long* __restrict__ next_ray) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int2 stack[kStackDepth];
-    TraceState<K> ts;
-    ColourVisitor cv(nullptr, 3, mk3(0.f, 0.f, 0.f), nullptr, 0);
-    const ShadeJob* J = &T.job[0];
-    long long ray = -1;
-    bool act = false, drained = false;
-    Counters cnt{0, 0, 0};
-    while (true) {
-        unsigned idle = __ballot_sync(0xffffffffu, !act);
-        int nidle = __popc(idle);
-        if (!drained && (nidle >= kRefillLanes || nidle == 32)) {
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(next_ray, (unsigned long long)nidle);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (base + nidle >= (unsigned long long)T.total_rays) drained = true;
-            if (!act) {
-                long long r = (long long)base + __popc(idle & lt);
-                if (r < T.total_rays) {
-                    ray = r;
-                    float4 dw = __ldg(dirs + r);
-                    if (dw.w == 0.f) {
-                        res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
-                    } else {
-                        J = &T.job[T.find_ray(r)];
-                        int li = (int)((r - J->ray_begin) / J->Nr);
-                        int pix = J->pixel_list ? __ldg(J->pixel_list + li) : J->pixel_offset + li;
-                        f3 o = mk3(__ldg(J->gb.pos + 3 * (size_t)pix), __ldg(J->gb.pos + 3 * (size_t)pix + 1),
-                                   __ldg(J->gb.pos + 3 * (size_t)pix + 2));
-                        f3 d = mk3(dw.x, dw.y, dw.z);
-                        trace_begin(J->bvh, ts, o, d, T.P);
-                        cv.color = J->color;
-                        cv.cdim = J->cdim;
-                        cv.d = d;
-                        cv.c[0] = cv.c[1] = cv.c[2] = 0.f;
-                        cv.nh = 0;
-                        act = true;
-                    }
-                }
-            }
-        }
-        if (!__any_sync(0xffffffffu, act)) {
-            if (drained) break;
-            continue;
-        }
-        if (act && !trav_step<K, false>(J->bvh, ts, stack, T.P, cnt)) {
-            if (round_end<K, false>(J->bvh, ts, T.P, cv, cnt)) {
-                res[ray] = make_float4(cv.c[0], cv.c[1], cv.c[2], ts.T);
-                act = false;
-            }
-        }
-    }
-}
 
 __global__ void k_zero_outputs(float* c, float* v, float* i, int n) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -427,17 +361,10 @@ inline void launch_trace_dyn(const JobTable<CAP>& T, const float4* dirs, float4*
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-#if GRT_TRACE_WW
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_rays_ww<K, CAP>, kShadeThreads, 0);
     long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
     if (grid > blocks_max) grid = blocks_max;
     k_trace_rays_ww<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, next_ray);
-#else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_rays_dyn<K, CAP>, kShadeThreads, 0);
-    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    if (grid > blocks_max) grid = blocks_max;
-    k_trace_rays_dyn<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, next_ray);
-#endif
 }
 
 // Persistent forward trace that also keeps the per-ray hit record.
