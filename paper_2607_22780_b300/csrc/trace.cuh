@@ -589,12 +589,32 @@ struct ColourVisitor {
 // once kRefill lanes are idle they claim that many rays from *next (a global counter);
 // then the warp alternates (A) internal-node visits with hit leaves queued in shared memory,
 // until every active lane has a leaf queued or has finished its walk, (B) the queued surfel
-// tests of all lanes, (C) compositing of finished walks.  Task supplies
+// tests of all lanes, (C) compositing of finished walks, once kCompositeBatch of them (or
+// all active lanes) are waiting.  Task supplies
 //   bool begin(long long ray, TraceState<K>&, Visitor&, const DevBvh*&)  -- false: no ray
 //   void end(long long ray, const TraceState<K>&, Visitor&)              -- ray finished
 // and the Visitor type receiving composite() calls.
-constexpr int kRefill = 8;
-constexpr int kQueue = 8;
+#ifndef GRT_REFILL
+#define GRT_REFILL 4
+#endif
+#ifndef GRT_QUEUE
+#define GRT_QUEUE 12
+#endif
+#ifndef GRT_LEAF_BATCH
+#define GRT_LEAF_BATCH 1
+#endif
+#ifndef GRT_COMPOSITE_BATCH
+#define GRT_COMPOSITE_BATCH 8
+#endif
+// Scheduling of the walk, measured on the 300k-surfel 800x800 workload (M rays/s):
+// queue 8 / 12 / 16 / 24 leaves: 339 / 364 / 351 / 333; leaf batch 1 / 2 / 4: 339 / 328 /
+// 307; composite batch 1 / 4 / 8 / 16 / 24: 364 / 389 / 394 / 377 / 323 (compositing runs
+// the SH colour of each hit, 22 % of the trace time, at 19 % lane use when unbatched);
+// refill at 4 / 8 / 12 idle lanes: 397 / 394 / 385.
+constexpr int kRefill = GRT_REFILL;         // idle lanes that trigger a refill
+constexpr int kQueue = GRT_QUEUE;           // queued leaves per lane
+constexpr int kLeafBatch = GRT_LEAF_BATCH;  // leaves every walking lane queues before the tests
+constexpr int kCompositeBatch = GRT_COMPOSITE_BATCH;  // finished walks composited together
 constexpr int kPersistentThreads = 128;  // block size of every persistent_trace kernel
 
 template <int K, class Task>
@@ -641,11 +661,20 @@ __device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& 
             bool walking = act && ts.node != -2 && nq <= kQueue - kWide;
             if (!__any_sync(0xffffffffu, walking)) break;
             if (walking) node_step_q<K, false>(*bvh, ts, stack, P, q, qstride, nq, cnt);
-            if (__all_sync(0xffffffffu, !act || nq > 0 || ts.node == -2)) break;
+            if (__all_sync(0xffffffffu, !act || nq >= kLeafBatch || ts.node == -2)) break;
         }
         for (int i = 0; i < nq; ++i) test_leaf<K, false>(*bvh, ts, q[i * qstride], P, cnt);
         nq = 0;
-        if (act && ts.node == -2) {
+        // finished walks wait until kCompositeBatch of them (or every active lane) can
+        // composite in the same pass
+        const bool fin = act && ts.node == -2;
+        bool go = fin;
+        if (kCompositeBatch > 1) {
+            const unsigned fm = __ballot_sync(0xffffffffu, fin);
+            const unsigned am = __ballot_sync(0xffffffffu, act);
+            go = fin && (__popc(fm) >= kCompositeBatch || fm == am);
+        }
+        if (go) {
             if (round_end<K, false>(*bvh, ts, P, vis, cnt)) {
                 vis.finish(ts.T);
                 task.end(ray, ts, vis);
