@@ -101,6 +101,8 @@ def _declare(L):
     L.or_pdf_env_dir.restype = C.c_double
     L.or_camera_ray.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
     L.or_normal_from_quat.argtypes = [P, P]
+    L.or_denoise.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                             C.c_double, P, C.c_int]
 
 
 def _f32(a):
@@ -386,3 +388,18 @@ def normal_from_quat(q):
     qq = _f32(q); n = np.zeros(3, np.float32)
     lib().or_normal_from_quat(_ptr(qq), _ptr(n))
     return n
+
+
+def denoise(color, depth, normal, valid, W, H, radius=3, sigma_s=2.0, sigma_d=1.0, sigma_n=64.0, eps_d=1e-3,
+            nthreads=0):
+    """Cross-bilateral denoiser (Sec. III-D) in FP64: colour[P,3], depth[P], normal[P,3],
+    valid[P] of a W x H image -> denoised colour[P,3]."""
+    P_ = int(W) * int(H)
+    col = np.ascontiguousarray(color, np.float64).reshape(P_, 3)
+    dep = np.ascontiguousarray(depth, np.float64).reshape(P_)
+    nrm = np.ascontiguousarray(normal, np.float64).reshape(P_, 3)
+    val = np.ascontiguousarray(valid, np.int32).reshape(P_)
+    out = np.zeros((P_, 3))
+    lib().or_denoise(_ptr(col), _ptr(dep), _ptr(nrm), _ptr(val), int(W), int(H), int(radius), float(sigma_s),
+                     float(sigma_d), float(sigma_n), float(eps_d), _ptr(out), nthreads)
+    return out

@@ -1082,3 +1082,61 @@ void or_normal_from_quat(const float* q, float* n) {
     f3 r = normal_from_quat_f(q);
     n[0] = r.x; n[1] = r.y; n[2] = r.z;
 }
+
+/* ---------------------------------------------------------------- denoiser (FP64) */
+
+/* Screen-space depth derivative along one axis at pixel (x, y): central difference when
+ * both neighbours are valid, one-sided when only one is, 0 otherwise. */
+static double depth_slope(const double* D, const int32_t* valid, int W, int H, int x, int y, int ax) {
+    int xm = x - (ax == 0), ym = y - (ax == 1), xp = x + (ax == 0), yp = y + (ax == 1);
+    int has_m = xm >= 0 && ym >= 0 && valid[ym * W + xm];
+    int has_p = xp < W && yp < H && valid[yp * W + xp];
+    if (has_m && has_p) return 0.5 * (D[yp * W + xp] - D[ym * W + xm]);
+    if (has_p) return D[yp * W + xp] - D[y * W + x];
+    if (has_m) return D[y * W + x] - D[ym * W + xm];
+    return 0.0;
+}
+
+/* Cross-bilateral denoiser (Sec. III-D): c_den(p) = sum_{p' in Q(p)} B(p,p') c(p') /
+ * sum B(p,p'), B = exp(-|p-p'|^2 / (2 s_s^2)) * exp(-|D(p)-D(p')| / (s_d |grad D(p).(p-p')|
+ * + e_d)) * max(0, N(p).N(p'))^s_n, with N normalised per pixel; Q(p) = the valid pixels of
+ * the (2r+1)^2 window around p inside the image.  Invalid pixels keep their input. */
+int or_denoise(const double* color, const double* depth, const double* normal, const int32_t* valid, int W, int H,
+               int radius, double sigma_s, double sigma_d, double sigma_n, double eps_d, double* out,
+               int nthreads) {
+    int nt = nthreads_or_default(nthreads);
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
+    for (int p = 0; p < W * H; ++p) {
+        int x = p % W, y = p / W;
+        if (!valid[p]) {
+            for (int c = 0; c < 3; ++c) out[3 * p + c] = color[3 * p + c];
+            continue;
+        }
+        double gx = depth_slope(depth, valid, W, H, x, y, 0), gy = depth_slope(depth, valid, W, H, x, y, 1);
+        double nl = sqrt(normal[3 * p] * normal[3 * p] + normal[3 * p + 1] * normal[3 * p + 1] +
+                         normal[3 * p + 2] * normal[3 * p + 2]);
+        double np[3] = {normal[3 * p] / nl, normal[3 * p + 1] / nl, normal[3 * p + 2] / nl};
+        double acc[3] = {0, 0, 0}, wsum = 0;
+        for (int dy = -radius; dy <= radius; ++dy) {
+            for (int dx = -radius; dx <= radius; ++dx) {
+                int xq = x + dx, yq = y + dy;
+                if (xq < 0 || yq < 0 || xq >= W || yq >= H) continue;
+                int q = yq * W + xq;
+                if (!valid[q]) continue;
+                double nq_l = sqrt(normal[3 * q] * normal[3 * q] + normal[3 * q + 1] * normal[3 * q + 1] +
+                                   normal[3 * q + 2] * normal[3 * q + 2]);
+                double cosn = nq_l > 0 ? (np[0] * normal[3 * q] + np[1] * normal[3 * q + 1] + np[2] * normal[3 * q + 2]) / nq_l
+                                       : 0.0;
+                /* p - p' = (-dx, -dy) */
+                double ws = exp(-(double)(dx * dx + dy * dy) / (2.0 * sigma_s * sigma_s));
+                double wd = exp(-fabs(depth[p] - depth[q]) / (sigma_d * fabs(gx * (-dx) + gy * (-dy)) + eps_d));
+                double wn = pow(cosn > 0 ? cosn : 0.0, sigma_n);
+                double w = ws * wd * wn;
+                for (int c = 0; c < 3; ++c) acc[c] += w * color[3 * q + c];
+                wsum += w;
+            }
+        }
+        for (int c = 0; c < 3; ++c) out[3 * p + c] = acc[c] / wsum;
+    }
+    return 0;
+}
