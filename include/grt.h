@@ -284,6 +284,25 @@ typedef struct {
 int grt_shade_batch(const grt_shade_request* requests, int32_t n_requests,
                     const grt_trace_params* params, void* stream);
 
+/* Cross-bilateral denoiser for low-sample shading (Sec. III-D, "Denoising"):
+ *   out(p) = sum_{p' in Q(p)} B(p,p') color(p') / sum B(p,p'),
+ *   B = exp(-|p-p'|^2 / (2 sigma_s^2)) * exp(-|D(p)-D(p')| / (sigma_d |grad D(p).(p-p')| + eps_d))
+ *       * max(0, N(p).N(p'))^sigma_n,
+ * over images of W x H pixels in raster order: color[P][3], depth[P] (e.g. the G-buffer
+ * depth), normal[P][3] (normalised inside), valid[P] (0 = no surface), out[P][3].  Q(p) is
+ * the valid pixels of the (2 radius + 1)^2 window inside the image; grad D is the central
+ * difference of depth (one-sided next to an invalid or missing neighbour).  Invalid pixels,
+ * and valid ones with a zero normal, keep their colour.  out must not alias color.
+ * radius in [0, GRT_DENOISE_MAX_RADIUS]; sigma_s, sigma_d, sigma_n, eps_d > 0.  The paper
+ * leaves the window and the parameter values open (defaults in the Python binding). */
+#define GRT_DENOISE_MAX_RADIUS 8
+typedef struct {
+    int32_t radius;
+    float sigma_s, sigma_d, sigma_n, eps_d;
+} grt_denoise_params;
+int grt_denoise(const float* color, const float* depth, const float* normal, const int32_t* valid, int32_t W,
+                int32_t H, const grt_denoise_params* params, float* out, void* stream);
+
 /* Performance counters of one grt_trace_forward-style pass (for roofline accounting):
  * counts of internal nodes visited, surfel records tested and hits composited, summed
  * over all rays, written to counters[3] (device, int64, accumulated). */

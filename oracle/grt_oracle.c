@@ -1100,7 +1100,8 @@ static double depth_slope(const double* D, const int32_t* valid, int W, int H, i
 /* Cross-bilateral denoiser (Sec. III-D): c_den(p) = sum_{p' in Q(p)} B(p,p') c(p') /
  * sum B(p,p'), B = exp(-|p-p'|^2 / (2 s_s^2)) * exp(-|D(p)-D(p')| / (s_d |grad D(p).(p-p')|
  * + e_d)) * max(0, N(p).N(p'))^s_n, with N normalised per pixel; Q(p) = the valid pixels of
- * the (2r+1)^2 window around p inside the image.  Invalid pixels keep their input. */
+ * the (2r+1)^2 window around p inside the image.  Invalid pixels, and valid pixels whose
+ * normal has zero length (nothing to compare with), keep their input. */
 int or_denoise(const double* color, const double* depth, const double* normal, const int32_t* valid, int W, int H,
                int radius, double sigma_s, double sigma_d, double sigma_n, double eps_d, double* out,
                int nthreads) {
@@ -1108,13 +1109,13 @@ int or_denoise(const double* color, const double* depth, const double* normal, c
 #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
     for (int p = 0; p < W * H; ++p) {
         int x = p % W, y = p / W;
-        if (!valid[p]) {
+        double nl = sqrt(normal[3 * p] * normal[3 * p] + normal[3 * p + 1] * normal[3 * p + 1] +
+                         normal[3 * p + 2] * normal[3 * p + 2]);
+        if (!valid[p] || nl == 0.0) {  /* no surface, or no normal to compare with */
             for (int c = 0; c < 3; ++c) out[3 * p + c] = color[3 * p + c];
             continue;
         }
         double gx = depth_slope(depth, valid, W, H, x, y, 0), gy = depth_slope(depth, valid, W, H, x, y, 1);
-        double nl = sqrt(normal[3 * p] * normal[3 * p] + normal[3 * p + 1] * normal[3 * p + 1] +
-                         normal[3 * p + 2] * normal[3 * p + 2]);
         double np[3] = {normal[3 * p] / nl, normal[3 * p + 1] / nl, normal[3 * p + 2] / nl};
         double acc[3] = {0, 0, 0}, wsum = 0;
         for (int dy = -radius; dy <= radius; ++dy) {

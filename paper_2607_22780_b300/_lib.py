@@ -17,6 +17,7 @@ GRT_OK, GRT_ERR_ARG, GRT_ERR_OOM, GRT_ERR_CUDA, GRT_ERR_OVERFLOW, GRT_ERR_TIMEOU
 GRT_MAX_BATCH = 48
 GRT_NOALLOC_MAX_SURFELS = 524288
 GRT_MAX_SAVED_HITS = 64
+GRT_DENOISE_MAX_RADIUS = 8
 STATUS_STACK_OVERFLOW = 1
 STATUS_NONFINITE = 2
 STATUS_BAD_TREE = 4
@@ -56,6 +57,11 @@ class GBuffer(C.Structure):
 class Sampling(C.Structure):
     _fields_ = [("n_cos", C.c_int32), ("n_ggx", C.c_int32), ("n_env", C.c_int32), ("brdf", C.c_int32),
                 ("seed", C.c_uint64)]
+
+
+class DenoiseParams(C.Structure):
+    _fields_ = [("radius", C.c_int32), ("sigma_s", C.c_float), ("sigma_d", C.c_float), ("sigma_n", C.c_float),
+                ("eps_d", C.c_float)]
 
 
 class ShadeRequest(C.Structure):
@@ -98,6 +104,7 @@ SIGNATURES = {
     "grt_shade_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                   C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P]),
     "grt_phase_timing": (C.c_int, [C.c_int32, C.POINTER(C.c_float)]),
+    "grt_denoise": (C.c_int, [P, P, P, P, C.c_int32, C.c_int32, C.POINTER(DenoiseParams), P, P]),
     "grt_last_error": (C.c_char_p, []),
     "grt_version": (C.c_char_p, []),
 }

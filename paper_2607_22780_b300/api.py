@@ -419,6 +419,28 @@ def shade_batch(requests, params=None, stream=None):
     L.check(L.load().grt_shade_batch(arr, len(requests), C.byref(p), _stream(stream)))
 
 
+DENOISE_DEFAULTS = dict(radius=3, sigma_s=2.0, sigma_d=1.0, sigma_n=64.0, eps_d=1e-3)
+
+
+def denoise(color, depth, normal, valid, W: int, H: int, out=None, stream=None, **params):
+    """Cross-bilateral denoiser (Sec. III-D) of a W x H image: colour[P,3] guided by
+    depth[P], normal[P,3] and valid[P] (int32).  Parameters: radius, sigma_s, sigma_d,
+    sigma_n, eps_d (defaults in DENOISE_DEFAULTS)."""
+    P_ = int(W) * int(H)
+    _dev(color, name="color", shape=(P_, 3))
+    _dev(depth, name="depth", shape=(P_,))
+    _dev(normal, name="normal", shape=(P_, 3))
+    _dev(valid, dtype=torch.int32, name="valid", shape=(P_,))
+    q = dict(DENOISE_DEFAULTS)
+    q.update(params)
+    prm = L.DenoiseParams(int(q["radius"]), float(q["sigma_s"]), float(q["sigma_d"]), float(q["sigma_n"]),
+                          float(q["eps_d"]))
+    out = torch.empty_like(color) if out is None else _dev(out, name="out", shape=(P_, 3))
+    L.check(L.load().grt_denoise(_ptr(color), _ptr(depth), _ptr(normal), _ptr(valid), int(W), int(H),
+                                 C.byref(prm), _ptr(out), _stream(stream)))
+    return out
+
+
 def phase_timing(enable: Optional[bool] = None, read: bool = False):
     """Turn per-kernel timing of shading calls on/off; with read=True return the last
     call's (sample_ms, trace_ms, accumulate_ms)."""

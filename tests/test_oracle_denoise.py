@@ -89,3 +89,10 @@ def test_output_is_a_convex_combination_of_the_window():
         x, y = p % W, p // W
         win = img[max(0, y - r):y + r + 1, max(0, x - r):x + r + 1].reshape(-1, 3)
         assert np.all(out[p] >= win.min(0) - 1e-15) and np.all(out[p] <= win.max(0) + 1e-15)
+
+
+def test_zero_normal_keeps_input():
+    col, dep, nrm, val = _line([0.2, 0.7, 0.4], normals=[[0, 0, 1], [0, 0, 0], [0, 0, 1]])
+    out = oracle.denoise(col, dep, nrm, val, 3, 1, radius=2, sigma_s=1e9)
+    assert out[1, 0] == 0.7                         # no normal to compare with
+    assert out[0, 0] == pytest.approx(0.3, abs=1e-15)  # the zero-normal neighbour gets weight 0
