@@ -335,6 +335,7 @@ def run_grt(args):
     large = None
     if rank == 0 and world == 1 and not args.no_large:
         large = time_large(api, dev, args)
+    den = time_denoise(api, G, outs[0], args) if rank == 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -364,7 +365,7 @@ def run_grt(args):
                             "phase_ms": {"sample": float(np.mean(ph[:, 0])), "trace": float(np.mean(ph[:, 1])),
                                          "accumulate": float(np.mean(ph[:, 2])), "shade_call": shade_s * 1e3},
                             "per_ray": {"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R}},
-               "clocks": clk, "e2e": e2e, "fwd_bwd": fb, "large": large, "cpu_baseline": cpu, "serving": serving,
+               "clocks": clk, "e2e": e2e, "fwd_bwd": fb, "large": large, "denoise": den, "cpu_baseline": cpu, "serving": serving,
                "wall_s_timed": t_wall}
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -452,6 +453,32 @@ def time_train(api, S, cam, E, dev, args):
             "fwd_bwd_recompute_ms": ms["fwd_bwd_recompute"], "stored_hits": 64,
             "fwd_rays_per_s": R / (ms["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (ms["fwd_bwd"] * 1e-3),
             "fwd_bwd_recompute_rays_per_s": R / (ms["fwd_bwd_recompute"] * 1e-3)}
+
+
+def time_denoise(api, G, color, args):
+    """Cross-bilateral denoiser (default window 7x7) over the shaded frame, guided by the
+    G-buffer depth and normals."""
+    import torch
+    out = torch.empty_like(color)
+
+    def run():
+        api.denoise(color, G.depth, G.normal, G.valid, G.W, G.H, out=out)
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 20
+    a.record()
+    for _ in range(n):
+        run()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / n
+    P = G.W * G.H
+    return {"workload": f"denoise_{G.W}x{G.H}", "params": dict(api.DENOISE_DEFAULTS), "ms": ms,
+            "pixels_per_s": P / (ms * 1e-3), "bytes_per_launch": P * 44,
+            "achieved_GBps": P * 44 / (ms * 1e-3) / 1e9}
 
 
 def time_large(api, dev, args):
