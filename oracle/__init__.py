@@ -101,6 +101,10 @@ def _declare(L):
     L.or_pdf_env_dir.restype = C.c_double
     L.or_camera_ray.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
     L.or_normal_from_quat.argtypes = [P, P]
+    L.or_env_prefilter.argtypes = [C.c_int, C.c_int, P, P, P, P]
+    L.or_splitsum_many.argtypes = [C.c_int, P, P, P, P, P, C.c_int, C.c_int, P, P, P, P, P]
+    L.or_trace_attr.argtypes = [P, P, C.c_int, P, P, P, P, P, P, P, P, C.c_int]
+    L.or_shade_relight.argtypes = [P, P, P, P, P, P, P, P, P, C.c_int, P, P, P, P, C.c_int]
     L.or_denoise.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                              C.c_double, P, C.c_int]
 
@@ -403,3 +407,65 @@ def denoise(color, depth, normal, valid, W, H, radius=3, sigma_s=2.0, sigma_d=1.
     lib().or_denoise(_ptr(col), _ptr(dep), _ptr(nrm), _ptr(val), int(W), int(H), int(radius), float(sigma_s),
                      float(sigma_d), float(sigma_n), float(eps_d), _ptr(out), nthreads)
     return out
+
+
+# ----------------------------------------------------------------------------- relighting
+
+DIFF_W, DIFF_H, SPEC_W, SPEC_H, SPEC_LEVELS, LUT_N = 32, 16, 64, 32, 6, 32
+
+
+def env_prefilter(env):
+    """Prefiltered form E of a novel map (Sec. III-E, Eq. 15): diffuse grid [16,32,3],
+    specular levels r = 0.2..1 [5,32,64,3], split-sum BRDF table [32 (nv), 32 (r), 2]."""
+    e = _f32(env)
+    H, W = e.shape[:2]
+    diff = np.zeros((DIFF_H, DIFF_W, 3))
+    spec = np.zeros((SPEC_LEVELS - 1, SPEC_H, SPEC_W, 3))
+    lut = np.zeros((LUT_N, LUT_N, 2))
+    lib().or_env_prefilter(W, H, _ptr(e), _ptr(diff), _ptr(spec), _ptr(lut))
+    return dict(diff=diff, spec=spec, lut=lut, env=e)
+
+
+def splitsum(pre, albedo, rough, metal, normal, view):
+    """SplitSum(a, r, m, n, E) seen from direction `view`, for arrays of N surface states."""
+    a = np.ascontiguousarray(albedo, np.float64).reshape(-1, 3)
+    n_ = a.shape[0]
+    r = np.ascontiguousarray(rough, np.float64).reshape(n_)
+    m = np.ascontiguousarray(metal, np.float64).reshape(n_)
+    nr = np.ascontiguousarray(normal, np.float64).reshape(n_, 3)
+    v = np.ascontiguousarray(view, np.float64).reshape(n_, 3)
+    e = pre["env"]
+    out = np.zeros((n_, 3))
+    lib().or_splitsum_many(n_, _ptr(a), _ptr(r), _ptr(m), _ptr(nr), _ptr(v), e.shape[1], e.shape[0], _ptr(e),
+                           _ptr(pre["diff"]), _ptr(pre["spec"]), _ptr(pre["lut"]), _ptr(out))
+    return out
+
+
+def trace_attr(scene, ray_o, ray_d, params=None, nthreads=0):
+    """Trace_attr (Eq. 14), Gaussian backend: V[R], albedo[R,3], rough[R], metal[R], normal[R,3]."""
+    keep = _Keep()
+    s = _scene(scene, keep); P = _params(params)
+    ro = _f32(ray_o).reshape(-1, 3); rd = _f32(ray_d).reshape(-1, 3)
+    R = ro.shape[0]
+    out = dict(V=np.zeros(R), albedo=np.zeros((R, 3)), rough=np.zeros(R), metal=np.zeros(R),
+               normal=np.zeros((R, 3)), flags=np.zeros(R, np.uint32))
+    lib().or_trace_attr(_ref(s), _ref(P), R, _ptr(ro), _ptr(rd), _ptr(out["V"]), _ptr(out["albedo"]),
+                        _ptr(out["rough"]), _ptr(out["metal"]), _ptr(out["normal"]), _ptr(out["flags"]), nthreads)
+    return out
+
+
+def shade_relight(scene, gb, env, pre, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None, params=None, nthreads=0):
+    """MIS relighting (Eq. 15 in Eq. 13) under the novel map `env` with its prefiltered
+    form `pre` (env_prefilter).  Returns dict color[P,3], vis[P], ind[P,3], flags[P]."""
+    keep = _Keep()
+    s = _scene(scene, keep); P = _params(params); g = _gbuf(gb, keep); e = _env(env, keep)
+    S = _sampling(n_cos, n_ggx, n_env, seed, brdf)
+    if pixels is None:
+        pl = None; n = int(gb["W"]) * int(gb["H"])
+    else:
+        pl = np.ascontiguousarray(pixels, np.int32); n = pl.shape[0]
+    col = np.zeros((n, 3)); vis = np.zeros(n); ind = np.zeros((n, 3)); fl = np.zeros(n, np.uint32)
+    lib().or_shade_relight(_ref(s), _ref(P), _ref(g), _ref(e), _ptr(pre["diff"]), _ptr(pre["spec"]),
+                           _ptr(pre["lut"]), _ref(S), _ptr(pl), n, _ptr(col), _ptr(vis), _ptr(ind), _ptr(fl),
+                           nthreads)
+    return dict(color=col, vis=vis, ind=ind, flags=fl)

@@ -763,12 +763,9 @@ typedef struct {
     double rgb[3], op, T;
 } sample_eval;
 
-/* Evaluate the sample: trace, environment, pdfs, BRDF. */
-static void eval_sample(const or_scene* sc, const surf_pre* pre, const or_params* P, const or_env* env,
-                        const env_tab* et, const or_sampling* S, ray_ws* ws, f3 x32, f3 w32,
-                        d3 n, d3 wo, const double* alb, double rough, double metal,
-                        sample_eval* e, uint32_t* flags) {
-    trace_one(sc, pre, P, x32, w32, ws, e->rgb, &e->op, &e->T, 0, NULL, NULL, flags);
+/* Environment radiance along the sample, mixture pdf q and BRDF weight g = f cos / q. */
+static void sample_weights(const or_env* env, const env_tab* et, const or_sampling* S, f3 w32, d3 n, d3 wo,
+                           const double* alb, double rough, double metal, sample_eval* e) {
     d3 w = normd(f2d(w32));
     int row, col;
     or_texel_of(w32.x, w32.y, w32.z, env->W, env->H, &row, &col);
@@ -785,6 +782,15 @@ static void eval_sample(const or_scene* sc, const surf_pre* pre, const or_params
     double f[3];
     or_brdf(wo_a, w_a, n_a, alb, rough, metal, S->brdf, f);
     for (int ch = 0; ch < 3; ++ch) e->g[ch] = q > 0 ? f[ch] * cosn / q : 0.0;
+}
+
+/* Evaluate the sample: trace, environment, pdfs, BRDF. */
+static void eval_sample(const or_scene* sc, const surf_pre* pre, const or_params* P, const or_env* env,
+                        const env_tab* et, const or_sampling* S, ray_ws* ws, f3 x32, f3 w32,
+                        d3 n, d3 wo, const double* alb, double rough, double metal,
+                        sample_eval* e, uint32_t* flags) {
+    trace_one(sc, pre, P, x32, w32, ws, e->rgb, &e->op, &e->T, 0, NULL, NULL, flags);
+    sample_weights(env, et, S, w32, n, wo, alb, rough, metal, e);
 }
 
 static void pixel_setup(const or_gbuf* gb, int p, f3* x32, f3* n32, f3* b1, f3* b2, f3* wo32, d3* n,
@@ -1139,5 +1145,282 @@ int or_denoise(const double* color, const double* depth, const double* normal, c
         }
         for (int c = 0; c < 3; ++c) out[3 * p + c] = acc[c] / wsum;
     }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- relighting (FP64) */
+/* Sec. III-E: Trace_attr (Eq. 14) returns the visibility V_r of the novel environment and
+ * the material state (a_r, r_r, m_r, n_r) met along a secondary ray; the incident radiance
+ * under the novel map is L = V_r L_new(w) + (1 - V_r) SplitSum(a_r, r_r, m_r, n_r, E)
+ * (Eq. 15), substituted for L_i in the MIS estimate.  E, left open by the paper, is:
+ *   E_diff(n)    = (1/pi) sum_t L_t max(0, n.w_t) dW_t                 on a 32 x 16 grid,
+ *   E_spec(R, r) = sum_t L_t w_t / sum_t w_t, w_t = D(R.h_t) max(0, R.w_t) dW_t,
+ *                  h_t = normalize(w_t + R) (the split-sum lobe with n = v = R),
+ *                  levels r = l/5, l = 1..5 on 64 x 32 grids; level 0 is the map itself,
+ *   A, B(nv, r)  = split-sum BRDF integrals of the specular lobe of Eq. 5 (D, Smith G,
+ *                  Schlick F = F0 + (1 - F0)(1 - v.h)^5 split as F0 A + B), midpoint rule
+ *                  over 256 x 256 GGX half-vector samples, 32 x 32 cell centres,
+ * texels t of the novel map with centre directions w_t and solid angles dW_t.  All grids
+ * use the map's equirectangular layout with cell centres; lookups are bilinear (wrapping
+ * in phi, clamped in theta) and linear across roughness levels. */
+#define OR_DIFF_W 32
+#define OR_DIFF_H 16
+#define OR_SPEC_W 64
+#define OR_SPEC_H 32
+#define OR_SPEC_LEVELS 6
+#define OR_LUT_N 32
+#define OR_LUT_M 256
+
+typedef struct {
+    int W, H;                 /* novel map */
+    const float* rgb;         /* [H][W][3] */
+    const double* diff;       /* [OR_DIFF_H][OR_DIFF_W][3] */
+    const double* spec;       /* [OR_SPEC_LEVELS - 1][OR_SPEC_H][OR_SPEC_W][3] */
+    const double* lut;        /* [OR_LUT_N (nv)][OR_LUT_N (r)][2] */
+} or_prefiltered;
+
+static d3 grid_dir(int row, int col, int W, int H) {
+    double ph = 2.0 * PI_D * (col + 0.5) / W, th = PI_D * (row + 0.5) / H;
+    return md3(sin(th) * sin(ph), cos(th), sin(th) * cos(ph));
+}
+
+void or_env_prefilter(int W, int H, const float* rgb, double* diff, double* spec, double* lut) {
+    int n = W * H;
+    d3* dir = (d3*)malloc(sizeof(d3) * (size_t)n);
+    double* dw = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int r = 0; r < H; ++r)
+        for (int c = 0; c < W; ++c) {
+            dir[r * W + c] = grid_dir(r, c, W, H);
+            dw[r * W + c] = (2.0 * PI_D / W) * (cos(PI_D * r / H) - cos(PI_D * (r + 1) / H));
+        }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int g = 0; g < OR_DIFF_W * OR_DIFF_H; ++g) {
+        d3 nn = grid_dir(g / OR_DIFF_W, g % OR_DIFF_W, OR_DIFF_W, OR_DIFF_H);
+        double acc[3] = {0, 0, 0};
+        for (int t = 0; t < n; ++t) {
+            double c = dotd(nn, dir[t]);
+            if (c <= 0) continue;
+            for (int ch = 0; ch < 3; ++ch) acc[ch] += rgb[3 * (size_t)t + ch] * c * dw[t];
+        }
+        for (int ch = 0; ch < 3; ++ch) diff[3 * g + ch] = acc[ch] / PI_D;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int g = 0; g < (OR_SPEC_LEVELS - 1) * OR_SPEC_W * OR_SPEC_H; ++g) {
+        int lev = 1 + g / (OR_SPEC_W * OR_SPEC_H), cell = g % (OR_SPEC_W * OR_SPEC_H);
+        double a = ggx_alpha((double)lev / (OR_SPEC_LEVELS - 1));
+        d3 R = grid_dir(cell / OR_SPEC_W, cell % OR_SPEC_W, OR_SPEC_W, OR_SPEC_H);
+        double acc[3] = {0, 0, 0}, wsum = 0;
+        for (int t = 0; t < n; ++t) {
+            double c = dotd(R, dir[t]);
+            if (c <= 0) continue;
+            d3 h = normd(addd(dir[t], R));
+            double w = ggx_D(dotd(R, h), a) * c * dw[t];
+            for (int ch = 0; ch < 3; ++ch) acc[ch] += rgb[3 * (size_t)t + ch] * w;
+            wsum += w;
+        }
+        for (int ch = 0; ch < 3; ++ch) spec[3 * (size_t)g + ch] = wsum > 0 ? acc[ch] / wsum : 0.0;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int ij = 0; ij < OR_LUT_N * OR_LUT_N; ++ij) {
+        {
+            int i = ij / OR_LUT_N, j = ij % OR_LUT_N;
+            double nv = (i + 0.5) / OR_LUT_N, a = ggx_alpha((j + 0.5) / OR_LUT_N);
+            d3 v = md3(sqrt(1.0 - nv * nv), 0.0, nv);
+            double A = 0, B = 0;
+            for (int p = 0; p < OR_LUT_M; ++p) {
+                for (int q = 0; q < OR_LUT_M; ++q) {
+                    double u1 = (p + 0.5) / OR_LUT_M, u2 = (q + 0.5) / OR_LUT_M;
+                    double th = atan(a * sqrt(u1 / (1.0 - u1))), ph = 2.0 * PI_D * u2;
+                    d3 h = md3(sin(th) * cos(ph), sin(th) * sin(ph), cos(th));
+                    double vh = dotd(v, h);
+                    if (vh <= 0) continue;
+                    d3 l = addd(muld(h, 2.0 * vh), muld(v, -1.0));
+                    if (l.z <= 0) continue;
+                    double Gv = ggx_G1(nv, a) * ggx_G1(l.z, a) * vh / (nv * h.z);
+                    double x = 1.0 - vh, x5 = x * x * x * x * x;
+                    A += Gv * (1.0 - x5);
+                    B += Gv * x5;
+                }
+            }
+            lut[2 * (i * OR_LUT_N + j)] = A / (OR_LUT_M * OR_LUT_M);
+            lut[2 * (i * OR_LUT_N + j) + 1] = B / (OR_LUT_M * OR_LUT_M);
+        }
+    }
+    free(dir);
+    free(dw);
+}
+
+/* Bilinear lookup of an equirectangular grid (cell centres) in direction w. */
+static void grid_lookup_d(const double* g, const float* gf, int W, int H, d3 w, double out[3]) {
+    double ph = atan2(w.x, w.z);
+    if (ph < 0) ph += 2.0 * PI_D;
+    double th = atan2(sqrt(w.x * w.x + w.z * w.z), w.y);
+    double u = ph / (2.0 * PI_D) * W - 0.5, v = th / PI_D * H - 0.5;
+    double fi = floor(u), fu = u - fi;
+    int i0 = ((int)fi % W + W) % W, i1 = (i0 + 1) % W;
+    int j0, j1;
+    double fv;
+    if (v <= 0) { j0 = j1 = 0; fv = 0; }
+    else if (v >= H - 1) { j0 = j1 = H - 1; fv = 0; }
+    else { j0 = (int)floor(v); j1 = j0 + 1; fv = v - j0; }
+    for (int ch = 0; ch < 3; ++ch) {
+#define OR_G(j, i) (g ? g[3 * ((size_t)(j) * W + (i)) + ch] : (double)gf[3 * ((size_t)(j) * W + (i)) + ch])
+        out[ch] = (1 - fv) * ((1 - fu) * OR_G(j0, i0) + fu * OR_G(j0, i1)) + fv * ((1 - fu) * OR_G(j1, i0) + fu * OR_G(j1, i1));
+#undef OR_G
+    }
+}
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* SplitSum(a, r, m, n, E) seen from direction v (unit, towards the viewer of the hit). */
+static void splitsum(const or_prefiltered* E, const double a[3], double r, double m, d3 n, d3 v, double out[3]) {
+    double nv = clampd(dotd(n, v), 1e-4, 1.0);
+    d3 R = addd(muld(n, 2.0 * nv), muld(v, -1.0));
+    double ed[3], e0[3], e1[3];
+    grid_lookup_d(E->diff, NULL, OR_DIFF_W, OR_DIFF_H, n, ed);
+    double t = clampd(r, 0.0, 1.0) * (OR_SPEC_LEVELS - 1);
+    int l0 = (int)floor(t);
+    if (l0 > OR_SPEC_LEVELS - 2) l0 = OR_SPEC_LEVELS - 2;
+    double f = t - l0;
+    if (l0 == 0) grid_lookup_d(NULL, E->rgb, E->W, E->H, R, e0);
+    else grid_lookup_d(E->spec + 3 * (size_t)(l0 - 1) * OR_SPEC_W * OR_SPEC_H, NULL, OR_SPEC_W, OR_SPEC_H, R, e0);
+    grid_lookup_d(E->spec + 3 * (size_t)l0 * OR_SPEC_W * OR_SPEC_H, NULL, OR_SPEC_W, OR_SPEC_H, R, e1);
+    double x = clampd(nv * OR_LUT_N - 0.5, 0.0, OR_LUT_N - 1.0), y = clampd(clampd(r, 0.0, 1.0) * OR_LUT_N - 0.5, 0.0, OR_LUT_N - 1.0);
+    int x0 = (int)floor(x), y0 = (int)floor(y);
+    int x1 = x0 + 1 < OR_LUT_N ? x0 + 1 : x0, y1 = y0 + 1 < OR_LUT_N ? y0 + 1 : y0;
+    double fx = x - x0, fy = y - y0, AB[2];
+    for (int k = 0; k < 2; ++k)
+        AB[k] = (1 - fx) * ((1 - fy) * E->lut[2 * (x0 * OR_LUT_N + y0) + k] + fy * E->lut[2 * (x0 * OR_LUT_N + y1) + k]) +
+                fx * ((1 - fy) * E->lut[2 * (x1 * OR_LUT_N + y0) + k] + fy * E->lut[2 * (x1 * OR_LUT_N + y1) + k]);
+    for (int ch = 0; ch < 3; ++ch) {
+        double kd = a[ch] * (1.0 - m), F0 = 0.04 * (1.0 - m) + a[ch] * m;
+        double es = (1 - f) * e0[ch] + f * e1[ch];
+        out[ch] = kd * ed[ch] + es * (F0 * AB[0] + AB[1]);
+    }
+}
+
+void or_splitsum_many(int n, const double* a, const double* r, const double* m, const double* nrm, const double* v,
+                      int W, int H, const float* rgb, const double* diff, const double* spec, const double* lut,
+                      double* out) {
+    or_prefiltered E = {W, H, rgb, diff, spec, lut};
+    for (int i = 0; i < n; ++i)
+        splitsum(&E, a + 3 * i, r[i], m[i], md3(nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]),
+                 md3(v[3 * i], v[3 * i + 1], v[3 * i + 2]), out + 3 * i);
+}
+
+/* Trace_attr (Eq. 14), Gaussian backend: the hits and order of Trace (Eq. 8); V_r = the
+ * final transmittance; a_r, r_r, m_r = T_k a_k-weighted means of the surfels' albedo,
+ * roughness, metallic; n_r = normalised weighted sum of their normals turned towards the
+ * ray origin.  No hit: V_r = 1 and zero attributes. */
+static void trace_attr_one(const or_scene* sc, const surf_pre* pre, const or_params* P, f3 o32, f3 d32,
+                           ray_ws* ws, double* V, double a[3], double* r, double* m, double n[3], uint32_t* flags) {
+    int nh = collect_hits(sc, pre, P, o32, d32, &ws->buf, &ws->cap, flags);
+    ws_ensure(ws, nh + 1);
+    double T;
+    int K = composite_count(ws->buf, nh, P, ws->Tk, &T, flags);
+    double wsum = 0, acc[3] = {0, 0, 0}, ra = 0, ma = 0;
+    d3 nacc = md3(0, 0, 0);
+    for (int k = 0; k < K; ++k) {
+        const hit_t* h = &ws->buf[k];
+        double w = ws->Tk[k] * h->alpha;
+        for (int ch = 0; ch < 3; ++ch) acc[ch] += w * sc->albedo[3 * (size_t)h->id + ch];
+        ra += w * sc->rough[h->id];
+        ma += w * sc->metal[h->id];
+        d3 ni = pre[h->id].n;
+        if (h->den32 > 0.0f) ni = muld(ni, -1.0);
+        nacc = addd(nacc, muld(ni, w));
+        wsum += w;
+    }
+    *V = T;
+    double nl = sqrt(dotd(nacc, nacc));
+    for (int ch = 0; ch < 3; ++ch) a[ch] = wsum > 0 ? acc[ch] / wsum : 0.0;
+    *r = wsum > 0 ? ra / wsum : 0.0;
+    *m = wsum > 0 ? ma / wsum : 0.0;
+    n[0] = nl > 0 ? nacc.x / nl : 0.0;
+    n[1] = nl > 0 ? nacc.y / nl : 0.0;
+    n[2] = nl > 0 ? nacc.z / nl : 0.0;
+}
+
+int or_trace_attr(const or_scene* sc, const or_params* P, int R, const float* ray_o, const float* ray_d,
+                  double* out_V, double* out_a, double* out_r, double* out_m, double* out_n, uint32_t* out_flags,
+                  int nthreads) {
+    surf_pre* pre = precompute(sc);
+    int nt = nthreads_or_default(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        ray_ws ws = {0};
+#pragma omp for schedule(dynamic, 8)
+        for (int i = 0; i < R; ++i) {
+            uint32_t fl = 0;
+            f3 o = mk3(ray_o[3 * i], ray_o[3 * i + 1], ray_o[3 * i + 2]);
+            f3 d = mk3(ray_d[3 * i], ray_d[3 * i + 1], ray_d[3 * i + 2]);
+            trace_attr_one(sc, pre, P, o, d, &ws, out_V + i, out_a + 3 * (size_t)i, out_r + i, out_m + i,
+                           out_n + 3 * (size_t)i, &fl);
+            if (out_flags) out_flags[i] = fl;
+        }
+        free(ws.buf);
+        free(ws.Tk);
+    }
+    free(pre);
+    return 0;
+}
+
+/* MIS relighting (Eq. 15 in Eq. 13): as or_shade_pixels with L_i = V_r L_new(w) +
+ * (1 - V_r) SplitSum(a_r, r_r, m_r, n_r, E) seen from v = -w; indirect output = the mean
+ * of (1 - V_r) SplitSum.  `env` is the novel map (its proposal tables drive the samples). */
+int or_shade_relight(const or_scene* sc, const or_params* P, const or_gbuf* gb, const or_env* env,
+                     const double* diff, const double* spec, const double* lut, const or_sampling* S,
+                     const int32_t* pixel_list, int n_pixels, double* out_color, double* out_vis, double* out_ind,
+                     uint32_t* out_flags, int nthreads) {
+    surf_pre* pre = precompute(sc);
+    env_tab et;
+    env_tab_build(env, &et);
+    or_prefiltered E = {env->W, env->H, env->rgb, diff, spec, lut};
+    int Nr = S->n_cos + S->n_ggx + S->n_env;
+    int nt = nthreads_or_default(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        ray_ws ws = {0};
+#pragma omp for schedule(dynamic, 1)
+        for (int i = 0; i < n_pixels; ++i) {
+            int p = pixel_list ? pixel_list[i] : i;
+            double col[3] = {0, 0, 0}, vis = 0, ind[3] = {0, 0, 0};
+            uint32_t fl = 0;
+            if (gb->valid[p] && Nr > 0) {
+                f3 x32, n32, b1, b2, wo32;
+                d3 n, wo;
+                pixel_setup(gb, p, &x32, &n32, &b1, &b2, &wo32, &n, &wo);
+                double alb[3] = {gb->albedo[3 * (size_t)p], gb->albedo[3 * (size_t)p + 1], gb->albedo[3 * (size_t)p + 2]};
+                for (int j = 0; j < Nr; ++j) {
+                    sample_t s = draw_sample(S, &et, env, p, j, n32, b1, b2, wo32, gb->rough[p]);
+                    if (!s.ok) continue;
+                    double V, ar[3], rr, mr, nr[3];
+                    trace_attr_one(sc, pre, P, x32, s.w32, &ws, &V, ar, &rr, &mr, nr, &fl);
+                    sample_eval e;
+                    sample_weights(env, &et, S, s.w32, n, wo, alb, gb->rough[p], gb->metal[p], &e);
+                    double ss[3] = {0, 0, 0};
+                    if (V < 1.0) {
+                        d3 w = normd(f2d(s.w32));
+                        splitsum(&E, ar, rr, mr, md3(nr[0], nr[1], nr[2]), muld(w, -1.0), ss);
+                    }
+                    for (int ch = 0; ch < 3; ++ch) {
+                        double Lind = (1.0 - V) * ss[ch];
+                        col[ch] += e.g[ch] * (V * e.Lenv[ch] + Lind);
+                        ind[ch] += Lind;
+                    }
+                    vis += V;
+                }
+                for (int ch = 0; ch < 3; ++ch) { col[ch] /= Nr; ind[ch] /= Nr; }
+                vis /= Nr;
+            }
+            for (int ch = 0; ch < 3; ++ch) { out_color[3 * (size_t)i + ch] = col[ch]; out_ind[3 * (size_t)i + ch] = ind[ch]; }
+            out_vis[i] = vis;
+            if (out_flags) out_flags[i] = fl;
+        }
+        free(ws.buf);
+        free(ws.Tk);
+    }
+    env_tab_free(&et);
+    free(pre);
     return 0;
 }
