@@ -336,6 +336,7 @@ def run_grt(args):
     if rank == 0 and world == 1 and not args.no_large:
         large = time_large(api, dev, args)
     den = time_denoise(api, G, outs[0], args) if rank == 0 else None
+    rel = time_relight(api, S, G, E, R, args) if rank == 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -365,7 +366,7 @@ def run_grt(args):
                             "phase_ms": {"sample": float(np.mean(ph[:, 0])), "trace": float(np.mean(ph[:, 1])),
                                          "accumulate": float(np.mean(ph[:, 2])), "shade_call": shade_s * 1e3},
                             "per_ray": {"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R}},
-               "clocks": clk, "e2e": e2e, "fwd_bwd": fb, "large": large, "denoise": den, "cpu_baseline": cpu, "serving": serving,
+               "clocks": clk, "e2e": e2e, "fwd_bwd": fb, "large": large, "denoise": den, "relight": rel, "cpu_baseline": cpu, "serving": serving,
                "wall_s_timed": t_wall}
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -453,6 +454,37 @@ def time_train(api, S, cam, E, dev, args):
             "fwd_bwd_recompute_ms": ms["fwd_bwd_recompute"], "stored_hits": 64,
             "fwd_rays_per_s": R / (ms["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (ms["fwd_bwd"] * 1e-3),
             "fwd_bwd_recompute_rays_per_s": R / (ms["fwd_bwd_recompute"] * 1e-3)}
+
+
+def time_relight(api, S, G, E, R, args):
+    """Split-sum relighting (Eq. 15) of the benchmark frame under its map: prefiltering of
+    the map, then the MIS estimate with Trace_attr (Eq. 14) for every secondary ray."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        E.prefilter()
+    a.record()
+    E.prefilter()
+    b.record()
+    torch.cuda.synchronize()
+    pre_ms = a.elapsed_time(b)
+    outs = api.shade_relight(S, G, E, *ALLOC, seed=SEED)
+    for _ in range(3):
+        api.shade_relight(S, G, E, *ALLOC, seed=SEED, outputs=outs)
+    torch.cuda.synchronize()
+    n = 5
+    api.phase_timing(True)
+    tr = []
+    a.record()
+    for _ in range(n):
+        api.shade_relight(S, G, E, *ALLOC, seed=SEED, outputs=outs)
+        tr.append(api.phase_timing(read=True)[1])
+    b.record()
+    torch.cuda.synchronize()
+    api.phase_timing(False)
+    ms = a.elapsed_time(b) / n
+    return {"workload": "relight_300k_800x800_32spp", "prefilter_ms": pre_ms, "ms": ms, "trace_ms": float(np.median(tr)),
+            "rays": R, "rays_per_s": R / (ms * 1e-3)}
 
 
 def time_denoise(api, G, color, args):

@@ -284,6 +284,36 @@ typedef struct {
 int grt_shade_batch(const grt_shade_request* requests, int32_t n_requests,
                     const grt_trace_params* params, void* stream);
 
+/* Relighting under a novel map (Sec. III-E).
+ * Trace_attr (Eq. 14), Gaussian backend: the hits of Trace (Eq. 8), same order and
+ * termination, blended with w_k = T_k a_k into out_albedo[R][3], out_rough[R], out_metal[R]
+ * (weighted means) and out_normal[R][3] (normalised weighted sum of the surfel normals turned
+ * towards the ray origin); out_vis[R] = V_r = final transmittance.  No hit: V_r = 1, zeros.
+ * Surfels need quat, albedo, rough and metal. */
+int grt_trace_attr(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                   const float* ray_o, const float* ray_d, int32_t R, float* out_vis, float* out_albedo,
+                   float* out_rough, float* out_metal, float* out_normal, void* stream);
+
+/* Prefiltered form E of a novel map rgb[H][W][3] (Eq. 15 leaves it open): E_diff(n) = (1/pi)
+ * sum_t L_t max(0, n.w_t) dW_t on a 32 x 16 equirectangular grid; E_spec(R, r) = GGX-lobe
+ * (n = v = R) normalised texel average for r = 0.2, 0.4, ..., 1 on 64 x 32 grids (r = 0 is
+ * the map itself); the split-sum BRDF table A, B(n.v, r) of the specular lobe of Eq. 5 on 32 x
+ * 32 cell centres (256 x 256 midpoint rule over GGX half vectors).  out: caller-owned device
+ * buffer of grt_env_prefilter_bytes() bytes, 16-byte aligned; a pool scratch of 16 bytes per
+ * texel is used during the call. */
+size_t grt_env_prefilter_bytes(void);
+int grt_env_prefilter(const float* rgb, int32_t W, int32_t H, void* out, size_t out_bytes, void* stream);
+
+/* MIS relighting (Eq. 15 substituted into Eq. 13): as grt_shade_pixels, with env the novel
+ * map (its proposal tables drive the samples) and, per sample, L_i = V_r L_new(w) + (1 - V_r)
+ * SplitSum(a_r, r_r, m_r, n_r, E) seen from v = -w, SplitSum = a (1 - m) E_diff(n) +
+ * E_spec(R, r) (F0 A + B), R = 2 (n.v) n - v, F0 = 0.04 (1 - m) + a m.  out_ind = the mean of
+ * (1 - V_r) SplitSum.  prefiltered: the output of grt_env_prefilter for the same map. */
+int grt_shade_relight(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                      const grt_gbuffer* gbuffer, const grt_envmap* env, const void* prefiltered,
+                      const grt_sampling* sampling, const int32_t* pixel_list, int32_t n_pixels, float* out_color,
+                      float* out_vis, float* out_ind, void* stream);
+
 /* Cross-bilateral denoiser for low-sample shading (Sec. III-D, "Denoising"):
  *   out(p) = sum_{p' in Q(p)} B(p,p') color(p') / sum B(p,p'),
  *   B = exp(-|p-p'|^2 / (2 sigma_s^2)) * exp(-|D(p)-D(p')| / (sigma_d |grad D(p).(p-p')| + eps_d))

@@ -247,6 +247,7 @@ class Environment:
         H, W = int(rgb.shape[0]), int(rgb.shape[1])
         _dev(rgb, name="rgb", shape=(H, W, 3))
         self.rgb, self.W, self.H = rgb, W, H
+        self.prefiltered = None
         lib = L.load()
         nbytes = lib.grt_env_tables_bytes(W, H)
         self.tables = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device=rgb.device)
@@ -256,10 +257,21 @@ class Environment:
         if tuple(rgb.shape) != (self.H, self.W, 3):
             raise ValueError("update needs the same map size")
         self.rgb = _dev(rgb, name="rgb")
+        self.prefiltered = None
         L.check(L.load().grt_env_prepare(_ptr(rgb), self.W, self.H, _ptr(self.tables), _stream(stream)))
 
     def struct(self) -> L.EnvMap:
         return L.EnvMap(self.W, self.H, _ptr(self.tables))
+
+    def prefilter(self, stream=None) -> torch.Tensor:
+        """Prefiltered form E of this map for relighting (grt_env_prefilter), cached until
+        the next update()."""
+        lib = L.load()
+        nb = lib.grt_env_prefilter_bytes()
+        buf = torch.empty(nb // 4, dtype=torch.float32, device=self.rgb.device)
+        L.check(lib.grt_env_prefilter(_ptr(self.rgb), self.W, self.H, _ptr(buf), nb, _stream(stream)))
+        self.prefiltered = buf
+        return buf
 
 
 def sampling(n_cos, n_ggx, n_env, seed, brdf=1) -> L.Sampling:
@@ -417,6 +429,39 @@ def shade_batch(requests, params=None, stream=None):
                                 _ptr(r.color), _ptr(r.vis), _ptr(r.ind))
     p = params if params is not None else requests[0].scene.params
     L.check(L.load().grt_shade_batch(arr, len(requests), C.byref(p), _stream(stream)))
+
+
+def trace_attr(scene: Scene, ray_o, ray_d, params=None, stream=None):
+    """Trace_attr (Eq. 14): (V[R], albedo[R,3], rough[R], metal[R], normal[R,3])."""
+    R = int(ray_o.shape[0])
+    _dev(ray_o, name="ray_o", shape=(R, 3))
+    _dev(ray_d, name="ray_d", shape=(R, 3))
+    dev = ray_o.device
+    V, a, r, m, n = (torch.empty(R, device=dev), torch.empty((R, 3), device=dev), torch.empty(R, device=dev),
+                     torch.empty(R, device=dev), torch.empty((R, 3), device=dev))
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_trace_attr(scene.handle, C.byref(scene.surfels()), C.byref(p), _ptr(ray_o), _ptr(ray_d), R,
+                                    _ptr(V), _ptr(a), _ptr(r), _ptr(m), _ptr(n), _stream(stream)))
+    return V, a, r, m, n
+
+
+def shade_relight(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
+                  params=None, outputs=None, stream=None):
+    """MIS relighting under `env` (Eq. 15 in Eq. 13): colour[P,3], visibility[P], indirect[P,3]."""
+    n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
+    if pixels is not None:
+        _dev(pixels, dtype=torch.int32, name="pixels", shape=(n,))
+    dev = gb.pos.device
+    if outputs is None:
+        outputs = (torch.empty((n, 3), device=dev), torch.empty((n,), device=dev), torch.empty((n, 3), device=dev))
+    col, vis, ind = outputs
+    pre = env.prefiltered if env.prefiltered is not None else env.prefilter(stream)
+    s = sampling(n_cos, n_ggx, n_env, seed, brdf)
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_shade_relight(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
+                                       C.byref(env.struct()), _ptr(pre), C.byref(s), _ptr(pixels), n, _ptr(col),
+                                       _ptr(vis), _ptr(ind), _stream(stream)))
+    return col, vis, ind
 
 
 DENOISE_DEFAULTS = dict(radius=3, sigma_s=2.0, sigma_d=1.0, sigma_n=64.0, eps_d=1e-3)

@@ -90,7 +90,8 @@ struct PhaseTiming {
 thread_local PhaseTiming g_timing;
 
 template <bool COUNT, int CAP>
-int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, const SaveBufs* save = nullptr) {
+int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, const SaveBufs* save = nullptr,
+             const RelightDev* rel = nullptr) {
     long long rays = 0, units = 0;
     for (int i = 0; i < T.n_jobs; ++i) {
         ShadeJob& J = T.job[i];
@@ -126,6 +127,8 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
             k_trace_rays<K, COUNT, CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, counters);
         } else if (save) {
             if constexpr (CAP == 1) launch_trace_save<K, CAP>(T, dirs, res, save->hits, next_ray, gr, st);
+        } else if (rel) {
+            if constexpr (CAP == 1) launch_trace_relight<K, CAP>(T, dirs, res, *rel, next_ray, gr, st);
         } else {
             launch_trace_dyn<K, CAP>(T, dirs, res, next_ray, gr, st);
         }
@@ -146,7 +149,8 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
 template <bool COUNT>
 int launch_single(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p, const grt_gbuffer* g,
                   const grt_envmap* e, const grt_sampling* smp, const int* pl, int n, float* oc, float* ov, float* oi,
-                  long long* counters, cudaStream_t st, const SaveBufs* save = nullptr) {
+                  long long* counters, cudaStream_t st, const SaveBufs* save = nullptr,
+                  const RelightDev* rel = nullptr) {
     int rc = check_trace_inputs(b, s, p);
     if (rc) return rc;
     JobTable<1> T;
@@ -159,7 +163,7 @@ int launch_single(const grt_bvh* b, const grt_surfels* s, const grt_trace_params
         if (oc) k_zero_outputs<<<(n + 255) / 256, 256, 0, st>>>(oc, ov, oi, n);
         return launch_error("k_zero_outputs");
     }
-    return run_jobs<COUNT>(T, p->k, counters, st, save);
+    return run_jobs<COUNT>(T, p->k, counters, st, save, rel);
 }
 
 }  // namespace
@@ -206,6 +210,22 @@ extern "C" int grt_shade_pixels_save(const grt_bvh* b, const grt_surfels* s, con
     if (rc) return rc;
     return launch_single<false>(b, s, p, g, e, smp, pixel_list, n_pixels, out_color, out_vis, out_ind, nullptr,
                                 (cudaStream_t)stream, &sb);
+}
+
+extern "C" int grt_shade_relight(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
+                                 const grt_gbuffer* g, const grt_envmap* e, const void* prefiltered,
+                                 const grt_sampling* smp, const int32_t* pixel_list, int32_t n_pixels,
+                                 float* out_color, float* out_vis, float* out_ind, void* stream) {
+    if (n_pixels > 0 && !out_color) return set_error(GRT_ERR_ARG, "out_color is NULL");
+    if (!prefiltered || ((uintptr_t)prefiltered & 15))
+        return set_error(GRT_ERR_ARG, "prefiltered must be a 16-byte aligned device pointer");
+    if (s && s->n > 0 && (!s->albedo || !s->rough || !s->metal || !s->quat))
+        return set_error(GRT_ERR_ARG, "surfels need quat, albedo, rough and metal for relighting");
+    const PrefLayout L = pref_layout();
+    const float* f = static_cast<const float*>(prefiltered);
+    const RelightDev E{f + L.diff, f + L.spec, f + L.lut};
+    return launch_single<false>(b, s, p, g, e, smp, pixel_list, n_pixels, out_color, out_vis, out_ind, nullptr,
+                                (cudaStream_t)stream, nullptr, &E);
 }
 
 extern "C" int grt_shade_batch(const grt_shade_request* req, int32_t n_req, const grt_trace_params* p,

@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "common_args.cuh"
+#include "relight.cuh"
 #include "shade.cuh"
 
 namespace grt {
@@ -17,6 +18,7 @@ struct ShadeJob {
     DevBvh bvh;
     const float* color;
     const float *mu, *quat, *scale, *opacity;  // surfel parameters (adjoint pass)
+    AttrSrc attr;                              // surfel materials (relighting pass)
     int cdim;
     GbufDev gb;
     EnvDev env;
@@ -152,6 +154,7 @@ inline int make_job(const grt_bvh* b, const grt_surfels* s, const grt_gbuffer* g
     J->quat = s->quat;
     J->scale = s->scale;
     J->opacity = s->opacity;
+    J->attr = AttrSrc{s->quat, s->albedo, s->rough, s->metal};
     J->cdim = s->color_dim;
     J->gb = GbufDev{g->pos, g->normal, g->albedo, g->rough, g->metal, g->valid, g->eye[0], g->eye[1], g->eye[2], g->W, g->H};
     EnvLayout l = env_layout(e->W, e->H);
@@ -351,6 +354,68 @@ __global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : GRT_TRACE_MIN_BLO
     __shared__ int q[kQueue * kShadeThreads];
     ShadeTraceSave<K, CAP> task{&T, dirs, res, &sv};
     persistent_trace<K>(task, T.P, next_ray, T.total_rays, q + threadIdx.x, kShadeThreads);
+}
+
+// Relighting rays (Eq. 15): the same rays, but Trace_attr (Eq. 14) instead of Trace; the
+// result (( 1 - V_r) SplitSum(a_r, r_r, m_r, n_r, E), V_r) takes the place of (c_rt, T), so
+// the accumulation forms V L_new + (1 - V) SplitSum exactly as it forms V L_env + c_rt.
+template <int K, int CAP>
+struct ShadeTraceRelight {
+    using Visitor = AttrVisitor;
+    const JobTable<CAP>* T;
+    const float4* dirs;
+    float4* res;
+    const RelightDev* E;
+    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& v, const DevBvh*& bvh) {
+        float4 dw = __ldg(dirs + r);
+        if (dw.w == 0.f) {
+            res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
+            return false;
+        }
+        const ShadeJob& J = T->job[T->find_ray(r)];
+        int li = (int)((r - J.ray_begin) / J.Nr);
+        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
+        f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
+                   __ldg(J.gb.pos + 3 * (size_t)pix + 2));
+        f3 d = mk3(dw.x, dw.y, dw.z);
+        bvh = &J.bvh;
+        trace_begin(J.bvh, ts, o, d, T->P);
+        v = AttrVisitor(&J.attr, d);
+        return true;
+    }
+    __device__ __forceinline__ void end(long long r, const TraceState<K>& ts, Visitor& v) {
+        const float V = ts.T;
+        float ss[3] = {0.f, 0.f, 0.f};
+        if (V < 1.f) {
+            v.resolve();
+            const ShadeJob& J = T->job[T->find_ray(r)];
+            splitsum_d(*E, J.env, v.a, v.r, v.m, mk3(v.n[0], v.n[1], v.n[2]), mk3(-v.d.x, -v.d.y, -v.d.z), ss);
+        }
+        const float o = 1.f - V;
+        res[r] = make_float4(o * ss[0], o * ss[1], o * ss[2], V);
+    }
+};
+
+template <int K, int CAP>
+__global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : GRT_TRACE_MIN_BLOCKS) k_trace_rays_relight(
+    const __grid_constant__ JobTable<CAP> T, const float4* __restrict__ dirs, float4* __restrict__ res,
+    const __grid_constant__ RelightDev E, unsigned long long* __restrict__ next_ray) {
+    __shared__ int q[kQueue * kShadeThreads];
+    ShadeTraceRelight<K, CAP> task{&T, dirs, res, &E};
+    persistent_trace<K>(task, T.P, next_ray, T.total_rays, q + threadIdx.x, kShadeThreads);
+}
+
+template <int K, int CAP>
+inline void launch_trace_relight(const JobTable<CAP>& T, const float4* dirs, float4* res, const RelightDev& E,
+                                 unsigned long long* next_ray, long long blocks_max, cudaStream_t st) {
+    cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_rays_relight<K, CAP>, kShadeThreads, 0);
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > blocks_max) grid = blocks_max;
+    k_trace_rays_relight<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, E, next_ray);
 }
 
 // Persistent forward trace of every ray of the table (per-ray (c_rt, T) into res).
