@@ -1162,7 +1162,8 @@ int or_denoise(const double* color, const double* depth, const double* normal, c
  *                  over 256 x 256 GGX half-vector samples, 32 x 32 cell centres,
  * texels t of the novel map with centre directions w_t and solid angles dW_t.  All grids
  * use the map's equirectangular layout with cell centres; lookups are bilinear (wrapping
- * in phi, clamped in theta) and linear across roughness levels. */
+ * in phi; towards the pole-row mean inside the polar half-cell caps) and linear across
+ * roughness levels. */
 #define OR_DIFF_W 32
 #define OR_DIFF_H 16
 #define OR_SPEC_W 64
@@ -1250,7 +1251,10 @@ void or_env_prefilter(int W, int H, const float* rgb, double* diff, double* spec
     free(dw);
 }
 
-/* Bilinear lookup of an equirectangular grid (cell centres) in direction w. */
+/* Lookup of an equirectangular grid (cell centres) in direction w: bilinear between cell
+ * centres (wrapping in phi); inside the half-cell caps around the poles, where phi loses
+ * its meaning, linear in theta from the pole-row value towards the mean of that row at the
+ * pole itself, so the lookup is continuous on the whole sphere. */
 static void grid_lookup_d(const double* g, const float* gf, int W, int H, d3 w, double out[3]) {
     double ph = atan2(w.x, w.z);
     if (ph < 0) ph += 2.0 * PI_D;
@@ -1258,14 +1262,20 @@ static void grid_lookup_d(const double* g, const float* gf, int W, int H, d3 w, 
     double u = ph / (2.0 * PI_D) * W - 0.5, v = th / PI_D * H - 0.5;
     double fi = floor(u), fu = u - fi;
     int i0 = ((int)fi % W + W) % W, i1 = (i0 + 1) % W;
-    int j0, j1;
-    double fv;
-    if (v <= 0) { j0 = j1 = 0; fv = 0; }
-    else if (v >= H - 1) { j0 = j1 = H - 1; fv = 0; }
+    int j0, j1, pole = -1;
+    double fv, tp = 1.0;
+    if (v <= 0) { j0 = j1 = 0; fv = 0; pole = 0; tp = 2.0 * v + 1.0; }
+    else if (v >= H - 1) { j0 = j1 = H - 1; fv = 0; pole = H - 1; tp = 2.0 * ((H - 0.5) - v); }
     else { j0 = (int)floor(v); j1 = j0 + 1; fv = v - j0; }
     for (int ch = 0; ch < 3; ++ch) {
 #define OR_G(j, i) (g ? g[3 * ((size_t)(j) * W + (i)) + ch] : (double)gf[3 * ((size_t)(j) * W + (i)) + ch])
         out[ch] = (1 - fv) * ((1 - fu) * OR_G(j0, i0) + fu * OR_G(j0, i1)) + fv * ((1 - fu) * OR_G(j1, i0) + fu * OR_G(j1, i1));
+        if (pole >= 0) {
+            double mean = 0;
+            for (int i = 0; i < W; ++i) mean += OR_G(pole, i);
+            mean /= W;
+            out[ch] = (1 - tp) * mean + tp * out[ch];
+        }
 #undef OR_G
     }
 }

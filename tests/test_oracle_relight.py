@@ -150,3 +150,17 @@ def test_relight_behind_an_opaque_sheet():
     assert r["vis"][0] == pytest.approx(0.01 * (1 - 0), abs=1e-6) or r["flags"][0]
     # each sample's indirect is 0.99 (0.8 E_diff(-z) + E_spec (0.04 A + B)) with E ~ 1
     assert 0.99 * 0.8 < r["ind"][0, 0] < 0.99 * 1.0
+
+
+def test_lookups_are_continuous_at_the_poles():
+    # phi is meaningless at the poles: directions 1e-7 rad off +y (and -y) at different phi
+    # must read the same value (the lookups fade to the pole-row mean inside the polar caps)
+    pre = oracle.env_prefilter(wl.envmap_hdr(3, 64, 32))
+    for sgn in (1.0, -1.0):
+        phis = np.linspace(0, 2 * np.pi, 17)[:-1]
+        e = 1e-7
+        n = np.stack([e * np.sin(phis), np.full(16, sgn), e * np.cos(phis)], -1)
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        for r in (0.05, 0.3, 0.9):
+            out = oracle.splitsum(pre, np.ones((16, 3)), np.full(16, r), np.zeros(16), n, n)
+            assert np.ptp(out, axis=0).max() < 1e-5 * np.abs(out).max(), (sgn, r, np.ptp(out, axis=0))
