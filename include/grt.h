@@ -298,7 +298,9 @@ int grt_trace_attr(const grt_bvh* bvh, const grt_surfels* surfels, const grt_tra
  * sum_t L_t max(0, n.w_t) dW_t on a 32 x 16 equirectangular grid; E_spec(R, r) = GGX-lobe
  * (n = v = R) normalised texel average for r = 0.2, 0.4, ..., 1 on 64 x 32 grids (r = 0 is
  * the map itself); the split-sum BRDF table A, B(n.v, r) of the specular lobe of Eq. 5 on 32 x
- * 32 cell centres (256 x 256 midpoint rule over GGX half vectors).  out: caller-owned device
+ * 32 cell centres (256 x 256 midpoint rule over GGX half vectors); the top and bottom row
+ * means of each grid and of the map, towards which lookups fade inside the polar half-cell
+ * caps (phi has no meaning at a pole).  out: caller-owned device
  * buffer of grt_env_prefilter_bytes() bytes, 16-byte aligned; a pool scratch of 16 bytes per
  * texel is used during the call. */
 size_t grt_env_prefilter_bytes(void);

@@ -123,6 +123,19 @@ __global__ void __launch_bounds__(kPrefThreads) k_brdf_lut(float* __restrict__ l
     }
 }
 
+// Means of the top (block 0) and bottom (block 1) rows of an rgb grid [H][W][3].
+__global__ void __launch_bounds__(kPrefThreads) k_row_means(const float* __restrict__ g, int W, int H,
+                                                            float* __restrict__ out) {
+    __shared__ float sh[3][kPrefThreads / 32];
+    const float* row = g + 3 * (size_t)(blockIdx.x == 0 ? 0 : H - 1) * W;
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int i = threadIdx.x; i < W; i += kPrefThreads)
+        for (int ch = 0; ch < 3; ++ch) acc[ch] += __ldg(row + 3 * i + ch);
+    block_sum(acc, sh);
+    if (threadIdx.x == 0)
+        for (int ch = 0; ch < 3; ++ch) out[3 * blockIdx.x + ch] = acc[ch] / (float)W;
+}
+
 // Trace_attr over a flat ray list (ray mode), in the persistent two-phase walk.
 struct AttrOut {
     float *vis, *albedo, *rough, *metal, *normal;
@@ -190,6 +203,11 @@ extern "C" int grt_env_prefilter(const float* rgb, int32_t W, int32_t H, void* o
     k_pref_diff<<<kDiffW * kDiffH, kPrefThreads, 0, st>>>(rgb, td, n, f + L.diff);
     k_pref_spec<<<(kSpecLevels - 1) * kSpecW * kSpecH, kPrefThreads, 0, st>>>(rgb, td, n, f + L.spec);
     k_brdf_lut<<<kLutN * kLutN, kPrefThreads, 0, st>>>(f + L.lut);
+    k_row_means<<<2, kPrefThreads, 0, st>>>(f + L.diff, kDiffW, kDiffH, f + L.poles);
+    for (int l = 1; l < kSpecLevels; ++l)
+        k_row_means<<<2, kPrefThreads, 0, st>>>(f + L.spec + 3 * (size_t)(l - 1) * kSpecW * kSpecH, kSpecW, kSpecH,
+                                                f + L.poles + 6 * l);
+    k_row_means<<<2, kPrefThreads, 0, st>>>(rgb, W, H, f + L.poles + 6 * kSpecLevels);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(td, st);
     if (e != cudaSuccess) return check_cuda(e, "prefilter kernels");

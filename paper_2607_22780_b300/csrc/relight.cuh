@@ -13,7 +13,9 @@
 // E_spec = GGX-lobe (n = v = R) normalised average on 64 x 32 for r = 0.2, 0.4, ..., 1 (level
 // r = 0 is the map itself), and the split-sum BRDF table A, B on 32 x 32 (n.v, r) cell
 // centres by a 256 x 256 midpoint rule over GGX half vectors.  Lookups are bilinear
-// (wrapping in phi, clamped in theta), linear across roughness levels.
+// (wrapping in phi) and linear across roughness levels; inside the half-cell caps around
+// the poles, where phi has no meaning, they fade linearly in theta towards the mean of the
+// pole row (precomputed with the tables), so every lookup is continuous on the sphere.
 #pragma once
 
 #include "shade.cuh"
@@ -22,23 +24,26 @@ namespace grt {
 
 constexpr int kDiffW = 32, kDiffH = 16, kSpecW = 64, kSpecH = 32, kSpecLevels = 6, kLutN = 32, kLutM = 256;
 
-// Float offsets of the three tables in a prefiltered buffer.
+// Float offsets of the tables in a prefiltered buffer.  poles: for the diffuse grid, each
+// specular level and the map itself, the mean of the top row then of the bottom row (rgb).
 struct PrefLayout {
-    size_t diff, spec, lut, total;
+    size_t diff, spec, lut, poles, total;
 };
 __host__ __device__ __forceinline__ PrefLayout pref_layout() {
     PrefLayout l;
     l.diff = 0;
     l.spec = l.diff + 3 * kDiffW * kDiffH;
     l.lut = l.spec + 3 * (size_t)(kSpecLevels - 1) * kSpecW * kSpecH;
-    l.total = l.lut + 2 * kLutN * kLutN;
+    l.poles = l.lut + 2 * kLutN * kLutN;
+    l.total = l.poles + 6 * (kSpecLevels + 1);
     return l;
 }
 
 struct RelightDev {
-    const float* diff;  // [kDiffH][kDiffW][3]
-    const float* spec;  // [kSpecLevels - 1][kSpecH][kSpecW][3]
-    const float* lut;   // [kLutN (n.v)][kLutN (r)][2]
+    const float* diff;   // [kDiffH][kDiffW][3]
+    const float* spec;   // [kSpecLevels - 1][kSpecH][kSpecW][3]
+    const float* lut;    // [kLutN (n.v)][kLutN (r)][2]
+    const float* poles;  // [diff, spec levels 1.., map][top, bottom][3]
 };
 
 // Direction through the centre of cell (row, col) of a W x H equirectangular grid.
@@ -49,9 +54,9 @@ __device__ __forceinline__ f3 grid_dir(int row, int col, int W, int H) {
     return mk3(st * sp, ct, st * cp);
 }
 
-// Bilinear lookup in direction w: `get(row, col, ch)` reads a cell.
+// Lookup in direction w: `get(row, col, ch)` reads a cell, pole[6] = top and bottom row means.
 template <class Get>
-__device__ __forceinline__ void grid_lookup(Get get, int W, int H, f3 w, float out[3]) {
+__device__ __forceinline__ void grid_lookup(Get get, const float* pole, int W, int H, f3 w, float out[3]) {
     float ph = atan2f(w.x, w.z);
     if (ph < 0.f) ph += 2.f * kPi;
     const float th = atan2f(sqrtf(w.x * w.x + w.z * w.z), w.y);
@@ -60,23 +65,29 @@ __device__ __forceinline__ void grid_lookup(Get get, int W, int H, f3 w, float o
     int i0 = (int)fi % W;
     if (i0 < 0) i0 += W;
     const int i1 = i0 + 1 < W ? i0 + 1 : 0;
-    int j0, j1;
-    float fv;
+    int j0, j1, pole_row = -1;
+    float fv, tp = 1.f;
     if (v <= 0.f) {
         j0 = j1 = 0;
         fv = 0.f;
+        pole_row = 0;
+        tp = 2.f * v + 1.f;
     } else if (v >= (float)(H - 1)) {
         j0 = j1 = H - 1;
         fv = 0.f;
+        pole_row = 1;
+        tp = 2.f * (((float)H - 0.5f) - v);
     } else {
         j0 = (int)floorf(v);
         j1 = j0 + 1;
         fv = v - (float)j0;
     }
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch)
+    for (int ch = 0; ch < 3; ++ch) {
         out[ch] = (1.f - fv) * ((1.f - fu) * get(j0, i0, ch) + fu * get(j0, i1, ch)) +
                   fv * ((1.f - fu) * get(j1, i0, ch) + fu * get(j1, i1, ch));
+        if (pole_row >= 0) out[ch] = (1.f - tp) * __ldg(pole + 3 * pole_row + ch) + tp * out[ch];
+    }
 }
 
 __device__ __forceinline__ void splitsum_d(const RelightDev& E, const EnvDev& env, const float a[3], float r, float m,
@@ -84,8 +95,8 @@ __device__ __forceinline__ void splitsum_d(const RelightDev& E, const EnvDev& en
     const float nv = fminf(fmaxf(dot3(n, v), 1e-4f), 1.f);
     const f3 R = mk3(2.f * nv * n.x - v.x, 2.f * nv * n.y - v.y, 2.f * nv * n.z - v.z);
     float ed[3], e0[3], e1[3];
-    grid_lookup([&](int j, int i, int ch) { return __ldg(E.diff + 3 * (j * kDiffW + i) + ch); }, kDiffW, kDiffH, n,
-                ed);
+    grid_lookup([&](int j, int i, int ch) { return __ldg(E.diff + 3 * (j * kDiffW + i) + ch); }, E.poles, kDiffW,
+                kDiffH, n, ed);
     const float rc = fminf(fmaxf(r, 0.f), 1.f);
     const float t = rc * (float)(kSpecLevels - 1);
     int l0 = (int)floorf(t);
@@ -97,14 +108,15 @@ __device__ __forceinline__ void splitsum_d(const RelightDev& E, const EnvDev& en
                 const float4 x = __ldg(env.texel + (size_t)j * env.W + i);
                 return ch == 0 ? x.x : (ch == 1 ? x.y : x.z);
             },
-            env.W, env.H, R, e0);
+            E.poles + 6 * kSpecLevels, env.W, env.H, R, e0);
     } else {
         const float* s0 = E.spec + 3 * (size_t)(l0 - 1) * kSpecW * kSpecH;
-        grid_lookup([&](int j, int i, int ch) { return __ldg(s0 + 3 * (j * kSpecW + i) + ch); }, kSpecW, kSpecH, R,
-                    e0);
+        grid_lookup([&](int j, int i, int ch) { return __ldg(s0 + 3 * (j * kSpecW + i) + ch); }, E.poles + 6 * l0,
+                    kSpecW, kSpecH, R, e0);
     }
     const float* s1 = E.spec + 3 * (size_t)l0 * kSpecW * kSpecH;
-    grid_lookup([&](int j, int i, int ch) { return __ldg(s1 + 3 * (j * kSpecW + i) + ch); }, kSpecW, kSpecH, R, e1);
+    grid_lookup([&](int j, int i, int ch) { return __ldg(s1 + 3 * (j * kSpecW + i) + ch); }, E.poles + 6 * (l0 + 1),
+                kSpecW, kSpecH, R, e1);
     const float x = fminf(fmaxf(nv * (float)kLutN - 0.5f, 0.f), (float)(kLutN - 1));
     const float y = fminf(fmaxf(rc * (float)kLutN - 0.5f, 0.f), (float)(kLutN - 1));
     const int x0 = (int)floorf(x), y0 = (int)floorf(y);

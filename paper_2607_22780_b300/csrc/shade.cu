@@ -223,7 +223,7 @@ extern "C" int grt_shade_relight(const grt_bvh* b, const grt_surfels* s, const g
         return set_error(GRT_ERR_ARG, "surfels need quat, albedo, rough and metal for relighting");
     const PrefLayout L = pref_layout();
     const float* f = static_cast<const float*>(prefiltered);
-    const RelightDev E{f + L.diff, f + L.spec, f + L.lut};
+    const RelightDev E{f + L.diff, f + L.spec, f + L.lut, f + L.poles};
     return launch_single<false>(b, s, p, g, e, smp, pixel_list, n_pixels, out_color, out_vis, out_ind, nullptr,
                                 (cudaStream_t)stream, nullptr, &E);
 }

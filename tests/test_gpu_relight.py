@@ -21,9 +21,11 @@ def _tables(E):
     f = E.prefiltered.cpu().numpy()
     d = 3 * oracle.DIFF_W * oracle.DIFF_H
     s = 3 * (oracle.SPEC_LEVELS - 1) * oracle.SPEC_W * oracle.SPEC_H
+    lut = 2 * oracle.LUT_N ** 2
     return (f[:d].reshape(oracle.DIFF_H, oracle.DIFF_W, 3),
             f[d:d + s].reshape(oracle.SPEC_LEVELS - 1, oracle.SPEC_H, oracle.SPEC_W, 3),
-            f[d + s:d + s + 2 * oracle.LUT_N ** 2].reshape(oracle.LUT_N, oracle.LUT_N, 2))
+            f[d + s:d + s + lut].reshape(oracle.LUT_N, oracle.LUT_N, 2),
+            f[d + s + lut:d + s + lut + 6 * (oracle.SPEC_LEVELS + 1)].reshape(oracle.SPEC_LEVELS + 1, 2, 3))
 
 
 @pytest.mark.parametrize("size", [(64, 32), (512, 256)])
@@ -31,9 +33,12 @@ def test_prefilter_matches_oracle(size):
     env = wl.envmap_hdr(5, *size)
     E = api.Environment(t(env))
     E.prefilter()
-    diff, spec, lut = _tables(E)
+    diff, spec, lut, poles = _tables(E)
     ref = oracle.env_prefilter(env)
-    for a, r in ((diff, ref["diff"]), (spec, ref["spec"]), (lut, ref["lut"])):
+    # pole-row means of the diffuse grid, the specular levels and the map
+    grids = [ref["diff"]] + list(ref["spec"]) + [env.astype(np.float64)]
+    ref_poles = np.stack([np.stack([g[0].mean(0), g[-1].mean(0)]) for g in grids])
+    for a, r in ((diff, ref["diff"]), (spec, ref["spec"]), (lut, ref["lut"]), (poles, ref_poles)):
         err = np.abs(a - r) - 1e-4 * np.maximum(np.abs(r), 1e-2)
         assert err.max() <= 0, (np.unravel_index(err.argmax(), err.shape), a.ravel()[err.argmax()], r.ravel()[err.argmax()])
 
