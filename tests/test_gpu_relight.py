@@ -1,10 +1,6 @@
 """GPU parity of relighting (Sec. III-E, Eq. 14-15) against the FP64 oracle: the prefiltered
 map E (1e-4 relative), Trace_attr per ray (1e-4; normals 5e-4), and the relit MIS estimate
-on unflagged pixels: visibility 1e-4, colour and indirect 1e-3 max(1, |ref|).  The relit
-radiance reads the HDR map (a sun of 200 over ~0.06 rad) and its prefiltered grids
-bilinearly at reflection directions R = 2 (n.v) n - v built from FP32 blended normals; R
-differs from the FP64 one by ~2e-7 rad and the interpolant's slope reaches ~4e3 per rad,
-so radiance differences of up to ~1e-3 are FP32 rounding, not a different estimate."""
+on unflagged pixels within 1e-4 max(1, |ref|), as for shading (observed: 3e-6)."""
 import numpy as np
 import pytest
 import torch
@@ -85,7 +81,7 @@ def _objects_case(n=30000, W=48, H=40, seed=17):
 def _check_relit(got, ref, pix=None):
     m = unflagged(ref["flags"])
     assert m.mean() > 0.95
-    for a, r, rel in ((got[0], ref["color"], 1e-3), (got[1], ref["vis"], 1e-4), (got[2], ref["ind"], 1e-3)):
+    for a, r, rel in ((got[0], ref["color"], 1e-4), (got[1], ref["vis"], 1e-4), (got[2], ref["ind"], 1e-4)):
         a = a.cpu().numpy()
         if pix is not None:
             a = a[pix]
