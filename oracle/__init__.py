@@ -82,7 +82,8 @@ def _declare(L):
     P = C.c_void_p
     L.or_trace_rays.argtypes = [P, P, C.c_int, P, P, P, P, P, C.c_int, P, P, P, C.c_int]
     L.or_gbuffer.argtypes = [P, P, P, C.c_int, C.c_int, P, C.c_int] + [P] * 9 + [C.c_int]
-    L.or_shade_pixels.argtypes = [P, P, P, P, P, P, C.c_int, P, P, P, P, C.c_int]
+    L.or_shade_pixels.argtypes = [P, P, P, P, P, P, C.c_int, P, P, P, P, P, C.c_int]
+    L.or_backward_material.argtypes = [P, P, P, P, P, P, C.c_int, P, P, P, P, P, P, P, C.c_int]
     L.or_backward_rays.argtypes = [P, P, C.c_int, P, P, P, P, P, P, C.c_int]
     L.or_backward_pixels.argtypes = [P, P, P, P, P, P, C.c_int, P, P, P, P, P, C.c_int]
     L.or_philox4x32_10.argtypes = [P, P, P]
@@ -241,7 +242,8 @@ def gbuffer_f32(gb):
 
 def shade_pixels(scene, gb, env, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None, params=None,
                  nthreads=0):
-    """MIS shading (Eq. 13).  Returns dict color[P,3], vis[P], ind[P,3], flags[P]."""
+    """MIS shading (Eq. 13).  Returns dict color[P,3], vis[P], ind[P,3], light[P,3] (the
+    mean incident radiance of Eq. 16), flags[P]."""
     keep = _Keep()
     s = _scene(scene, keep); P = _params(params); g = _gbuf(gb, keep); e = _env(env, keep)
     S = _sampling(n_cos, n_ggx, n_env, seed, brdf)
@@ -250,9 +252,33 @@ def shade_pixels(scene, gb, env, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
     else:
         pl = np.ascontiguousarray(pixels, np.int32); n = pl.shape[0]
     col = np.zeros((n, 3)); vis = np.zeros(n); ind = np.zeros((n, 3)); fl = np.zeros(n, np.uint32)
+    light = np.zeros((n, 3))
     lib().or_shade_pixels(_ref(s), _ref(P), _ref(g), _ref(e), _ref(S), _ptr(pl), n, _ptr(col),
-                          _ptr(vis), _ptr(ind), _ptr(fl), nthreads)
-    return dict(color=col, vis=vis, ind=ind, flags=fl)
+                          _ptr(vis), _ptr(ind), _ptr(light), _ptr(fl), nthreads)
+    return dict(color=col, vis=vis, ind=ind, light=light, flags=fl)
+
+
+def backward_material(scene, gb, env, n_cos, n_ggx, n_env, seed, dL_dcolor, dL_dlight=None, brdf=1, pixels=None,
+                      params=None, nthreads=0):
+    """Adjoint of the MIS estimate (Eq. 13) and of the mean incident radiance (Eq. 16) with
+    respect to the map and the per-pixel materials, directions and proposal held fixed.
+    Returns dict env[H,W,3], albedo[n,3], rough[n], metal[n], flags[n]."""
+    keep = _Keep()
+    s = _scene(scene, keep); P = _params(params); g = _gbuf(gb, keep); e = _env(env, keep)
+    S = _sampling(n_cos, n_ggx, n_env, seed, brdf)
+    if pixels is None:
+        pl = None; n = int(gb["W"]) * int(gb["H"])
+    else:
+        pl = np.ascontiguousarray(pixels, np.int32); n = pl.shape[0]
+    H, W = np.asarray(env).shape[:2]
+    dc = np.ascontiguousarray(dL_dcolor, np.float64).reshape(n, 3)
+    dl = None if dL_dlight is None else np.ascontiguousarray(dL_dlight, np.float64).reshape(n, 3)
+    out = dict(env=np.zeros((H, W, 3)), albedo=np.zeros((n, 3)), rough=np.zeros(n), metal=np.zeros(n),
+               flags=np.zeros(n, np.uint32))
+    lib().or_backward_material(_ref(s), _ref(P), _ref(g), _ref(e), _ref(S), _ptr(pl), n, _ptr(dc), _ptr(dl),
+                               _ptr(out["env"]), _ptr(out["albedo"]), _ptr(out["rough"]), _ptr(out["metal"]),
+                               _ptr(out["flags"]), nthreads)
+    return out
 
 
 def _grads(scene):

@@ -759,7 +759,9 @@ static sample_t draw_sample(const or_sampling* S, const env_tab* et, const or_en
 
 typedef struct {
     double g[3];        /* f * cos / q, per channel, for this sample */
+    double cq;          /* cos / q */
     double Lenv[3];
+    int row, col;       /* environment texel of the direction */
     double rgb[3], op, T;
 } sample_eval;
 
@@ -769,6 +771,8 @@ static void sample_weights(const or_env* env, const env_tab* et, const or_sampli
     d3 w = normd(f2d(w32));
     int row, col;
     or_texel_of(w32.x, w32.y, w32.z, env->W, env->H, &row, &col);
+    e->row = row;
+    e->col = col;
     const float* L = env->rgb + ((size_t)row * env->W + col) * 3;
     for (int ch = 0; ch < 3; ++ch) e->Lenv[ch] = L[ch];
     int Nr = S->n_cos + S->n_ggx + S->n_env;
@@ -781,6 +785,7 @@ static void sample_weights(const or_env* env, const env_tab* et, const or_sampli
     double q = (S->n_cos * pc + S->n_ggx * pg + S->n_env * pe) / Nr;
     double f[3];
     or_brdf(wo_a, w_a, n_a, alb, rough, metal, S->brdf, f);
+    e->cq = q > 0 ? cosn / q : 0.0;
     for (int ch = 0; ch < 3; ++ch) e->g[ch] = q > 0 ? f[ch] * cosn / q : 0.0;
 }
 
@@ -806,11 +811,12 @@ static void pixel_setup(const or_gbuf* gb, int p, f3* x32, f3* n32, f3* b1, f3* 
 }
 
 /* MIS shading of Eq. 13 for a list of pixels (or all W*H when pixel_list is NULL):
- * colour = (1/N_r) sum g/q, visibility = (1/N_r) sum V, indirect = (1/N_r) sum L_ind.
+ * colour = (1/N_r) sum g/q, visibility = (1/N_r) sum V, indirect = (1/N_r) sum L_ind,
+ * light (optional) = (1/N_r) sum L_i, the mean incident radiance of Eq. 16.
  * Samples below the horizon contribute nothing (V = 0, L_ind = 0). */
 int or_shade_pixels(const or_scene* sc, const or_params* P, const or_gbuf* gb, const or_env* env,
                     const or_sampling* S, const int32_t* pixel_list, int n_pixels, double* out_color,
-                    double* out_vis, double* out_ind, uint32_t* out_flags, int nthreads) {
+                    double* out_vis, double* out_ind, double* out_light, uint32_t* out_flags, int nthreads) {
     surf_pre* pre = precompute(sc);
     env_tab et;
     env_tab_build(env, &et);
@@ -822,7 +828,7 @@ int or_shade_pixels(const or_scene* sc, const or_params* P, const or_gbuf* gb, c
 #pragma omp for schedule(dynamic, 1)
         for (int i = 0; i < n_pixels; ++i) {
             int p = pixel_list ? pixel_list[i] : i;
-            double col[3] = {0, 0, 0}, vis = 0, ind[3] = {0, 0, 0};
+            double col[3] = {0, 0, 0}, vis = 0, ind[3] = {0, 0, 0}, light[3] = {0, 0, 0};
             uint32_t fl = 0;
             if (gb->valid[p] && Nr > 0) {
                 f3 x32, n32, b1, b2, wo32;
@@ -840,13 +846,16 @@ int or_shade_pixels(const or_scene* sc, const or_params* P, const or_gbuf* gb, c
                         double Li = V * e.Lenv[ch] + e.rgb[ch];
                         col[ch] += e.g[ch] * Li;
                         ind[ch] += e.rgb[ch];
+                        light[ch] += Li;
                     }
                     vis += V;
                 }
-                for (int ch = 0; ch < 3; ++ch) { col[ch] /= Nr; ind[ch] /= Nr; }
+                for (int ch = 0; ch < 3; ++ch) { col[ch] /= Nr; ind[ch] /= Nr; light[ch] /= Nr; }
                 vis /= Nr;
             }
             for (int ch = 0; ch < 3; ++ch) { out_color[3 * (size_t)i + ch] = col[ch]; out_ind[3 * (size_t)i + ch] = ind[ch]; }
+            if (out_light)
+                for (int ch = 0; ch < 3; ++ch) out_light[3 * (size_t)i + ch] = light[ch];
             out_vis[i] = vis;
             if (out_flags) out_flags[i] = fl;
         }
@@ -1425,6 +1434,120 @@ int or_shade_relight(const or_scene* sc, const or_params* P, const or_gbuf* gb, 
             }
             for (int ch = 0; ch < 3; ++ch) { out_color[3 * (size_t)i + ch] = col[ch]; out_ind[3 * (size_t)i + ch] = ind[ch]; }
             out_vis[i] = vis;
+            if (out_flags) out_flags[i] = fl;
+        }
+        free(ws.buf);
+        free(ws.Tk);
+    }
+    env_tab_free(&et);
+    free(pre);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- material and map adjoint (FP64) */
+
+/* Partial derivatives of the BRDF (Eq. 4-5; Lambert for brdf = 0) per channel with respect
+ * to the albedo of that channel (dfa), the metallic weight (dfm) and the roughness (dfr),
+ * alpha = max(r^2, 1e-4) (no roughness derivative where the clamp holds). */
+static void brdf_partials(d3 wo, d3 wi, d3 n, const double* alb, double rough, double metal, int brdf,
+                          double dfa[3], double dfm[3], double dfr[3]) {
+    for (int ch = 0; ch < 3; ++ch) {
+        dfa[ch] = (brdf == 0 ? 1.0 : 1.0 - metal) / PI_D;
+        dfm[ch] = brdf == 0 ? 0.0 : -alb[ch] / PI_D;
+        dfr[ch] = 0.0;
+    }
+    if (brdf == 0) return;
+    double won = dotd(wo, n), win = dotd(wi, n);
+    if (!(won > 0.0) || !(win > 0.0)) return;
+    d3 h = normd(addd(wo, wi));
+    double hn = dotd(h, n), ih = dotd(wi, h);
+    if (!(hn > 0.0)) return;
+    double a = ggx_alpha(rough);
+    double D = ggx_D(hn, a), Gi = ggx_G1(win, a), Go = ggx_G1(won, a);
+    double DG = D * Gi * Go / (4.0 * win * won);
+    double x = 1.0 - ih;
+    if (x < 0) x = 0;
+    double x5 = x * x * x * x * x;
+    double dDG_dr = 0.0;
+    if (rough * rough > 1e-4) {
+        double t = hn * hn * (a * a - 1.0) + 1.0;
+        double dD = 2.0 * a / (PI_D * t * t) * (1.0 - 2.0 * a * a * hn * hn / t);
+        double si = sqrt(a * a + (1.0 - a * a) * win * win), so = sqrt(a * a + (1.0 - a * a) * won * won);
+        double dGi = -2.0 * win / ((win + si) * (win + si)) * a * (1.0 - win * win) / si;
+        double dGo = -2.0 * won / ((won + so) * (won + so)) * a * (1.0 - won * won) / so;
+        dDG_dr = DG * (dD / D + dGi / Gi + dGo / Go) * 2.0 * rough;
+    }
+    for (int ch = 0; ch < 3; ++ch) {
+        double F0 = 0.04 * (1.0 - metal) + metal * alb[ch];
+        double F = F0 + (1.0 - F0) * x5;
+        dfa[ch] += DG * metal * (1.0 - x5);
+        dfm[ch] += DG * (1.0 - x5) * (alb[ch] - 0.04);
+        dfr[ch] = dDG_dr * F;
+    }
+}
+
+/* Adjoint of the MIS estimate (Eq. 13) and of the mean incident radiance of Eq. 16 with
+ * respect to the environment map and the per-pixel materials, the sampled directions and
+ * the proposal density q held fixed: given dL/dcolor and dL/dlight per listed pixel,
+ *   dL/dL_env[t] += (1/N_r) sum_{j: w_j in t} (dL/dc g_j + dL/dlight) V_j,
+ *   dL/da_c      += (1/N_r) sum_j dL/dc_c (df_c/da_c) (cos/q)_j L_i,j,c   (and m, r alike),
+ * with L_i = V L_env + L_ind.  Map gradients accumulate in grad_env[H][W][3]; material
+ * gradients are written per list entry (grad_albedo[n][3], grad_rough[n], grad_metal[n]). */
+int or_backward_material(const or_scene* sc, const or_params* P, const or_gbuf* gb, const or_env* env,
+                         const or_sampling* S, const int32_t* pixel_list, int n_pixels, const double* dL_dcolor,
+                         const double* dL_dlight, double* grad_env, double* grad_albedo, double* grad_rough,
+                         double* grad_metal, uint32_t* out_flags, int nthreads) {
+    surf_pre* pre = precompute(sc);
+    env_tab et;
+    env_tab_build(env, &et);
+    int Nr = S->n_cos + S->n_ggx + S->n_env;
+    int nt = nthreads_or_default(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        ray_ws ws = {0};
+#pragma omp for schedule(dynamic, 1)
+        for (int i = 0; i < n_pixels; ++i) {
+            int p = pixel_list ? pixel_list[i] : i;
+            double ga[3] = {0, 0, 0}, gr = 0, gm = 0;
+            uint32_t fl = 0;
+            if (gb->valid[p] && Nr > 0) {
+                f3 x32, n32, b1, b2, wo32;
+                d3 n, wo;
+                pixel_setup(gb, p, &x32, &n32, &b1, &b2, &wo32, &n, &wo);
+                double alb[3] = {gb->albedo[3 * (size_t)p], gb->albedo[3 * (size_t)p + 1], gb->albedo[3 * (size_t)p + 2]};
+                const double* dc = dL_dcolor + 3 * (size_t)i;
+                double dl[3] = {0, 0, 0};
+                if (dL_dlight)
+                    for (int ch = 0; ch < 3; ++ch) dl[ch] = dL_dlight[3 * (size_t)i + ch];
+                for (int j = 0; j < Nr; ++j) {
+                    sample_t s = draw_sample(S, &et, env, p, j, n32, b1, b2, wo32, gb->rough[p]);
+                    if (!s.ok) continue;
+                    sample_eval e;
+                    eval_sample(sc, pre, P, env, &et, S, &ws, x32, s.w32, n, wo, alb, gb->rough[p], gb->metal[p],
+                                &e, &fl);
+                    double V = 1.0 - e.op;
+                    d3 w = normd(f2d(s.w32));
+                    double dfa[3], dfm[3], dfr[3];
+                    brdf_partials(wo, w, n, alb, gb->rough[p], gb->metal[p], S->brdf, dfa, dfm, dfr);
+                    for (int ch = 0; ch < 3; ++ch) {
+                        double Li = V * e.Lenv[ch] + e.rgb[ch];
+                        ga[ch] += dc[ch] * dfa[ch] * e.cq * Li;
+                        gm += dc[ch] * dfm[ch] * e.cq * Li;
+                        gr += dc[ch] * dfr[ch] * e.cq * Li;
+                        if (grad_env) {
+                            double v = (dc[ch] * e.g[ch] + dl[ch]) * V / Nr;
+                            atomic_add_d(grad_env + 3 * ((size_t)e.row * env->W + e.col) + ch, v);
+                        }
+                    }
+                }
+                for (int ch = 0; ch < 3; ++ch) ga[ch] /= Nr;
+                gr /= Nr;
+                gm /= Nr;
+            }
+            if (grad_albedo)
+                for (int ch = 0; ch < 3; ++ch) grad_albedo[3 * (size_t)i + ch] = ga[ch];
+            if (grad_rough) grad_rough[i] = gr;
+            if (grad_metal) grad_metal[i] = gm;
             if (out_flags) out_flags[i] = fl;
         }
         free(ws.buf);
