@@ -257,6 +257,29 @@ int grt_shade_backward_saved(const grt_bvh* bvh, const grt_surfels* surfels, con
                              const float* dL_dvis, const float* dL_dind, int32_t max_hits, const void* saved,
                              size_t saved_bytes, const grt_grads* grads, void* stream);
 
+/* grt_shade_pixels plus out_light[n_pixels][3] = (1/N_r) sum_j L_i(w_j), the mean incident
+ * radiance of the lighting regulariser (Eq. 16), L_i = V L_env + L_ind (samples below the
+ * horizon count 0). */
+int grt_shade_pixels_light(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                           const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
+                           const int32_t* pixel_list, int32_t n_pixels, float* out_color, float* out_vis,
+                           float* out_ind, float* out_light, void* stream);
+
+/* Adjoint of the estimate (Eq. 13) and of the mean incident radiance (Eq. 16) with respect
+ * to the environment map and the per-pixel materials of the G-buffer (the paper optimises
+ * lighting and materials jointly, Sec. III-F), the sampled directions and the proposal
+ * density q held fixed.  Given dL_dcolor[n_pixels][3] and optional dL_dlight[n_pixels][3]:
+ *   grad_env[H][W][3]    += (1/N_r) sum_j (dL/dc g_j + dL/dlight) V_j at the texel of w_j,
+ *   grad_albedo[n][3], grad_rough[n], grad_metal[n] += (1/N_r) sum_j dL/dc (df/dx) (cos/q)_j L_i,j
+ * (per list entry; no roughness gradient where max(r^2, 1e-4) clamps).  Every gradient
+ * pointer may be NULL; all accumulate.  The samples are drawn and traced again (32 bytes per
+ * ray of pool scratch during the call); map gradients are float atomics. */
+int grt_shade_backward_material(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
+                                const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
+                                const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
+                                const float* dL_dlight, float* grad_env, float* grad_albedo, float* grad_rough,
+                                float* grad_metal, void* stream);
+
 /* One shading request of a batch (same meaning as the grt_shade_pixels arguments).
  * With pixel_list NULL, output i shades pixel pixel_offset + i (a contiguous slice of
  * the image, so a long request can be split over several launches). */

@@ -99,6 +99,11 @@ SIGNATURES = {
     "grt_shade_backward_saved": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                            C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P,
                                            C.c_int32, P, C.c_size_t, C.POINTER(Grads), P]),
+    "grt_shade_pixels_light": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
+                                         C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P, P, P]),
+    "grt_shade_backward_material": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
+                                              C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P, P,
+                                              P, P, P]),
     "grt_shade_batch": (C.c_int, [C.POINTER(ShadeRequest), C.c_int32, C.POINTER(TraceParams), P]),
     "grt_trace_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), P, P, C.c_int32, P, P]),
     "grt_shade_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),

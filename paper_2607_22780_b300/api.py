@@ -279,21 +279,61 @@ def sampling(n_cos, n_ggx, n_env, seed, brdf=1) -> L.Sampling:
 
 
 def shade_pixels(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
-                 params=None, outputs=None, stream=None):
-    """MIS shading (Eq. 13): colour[P,3], visibility[P], indirect[P,3] for the pixel list."""
+                 params=None, outputs=None, light: bool = False, stream=None):
+    """MIS shading (Eq. 13): colour[P,3], visibility[P], indirect[P,3] for the pixel list,
+    and with light=True also the mean incident radiance light[P,3] of Eq. 16."""
     n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
     if pixels is not None:
         _dev(pixels, dtype=torch.int32, name="pixels", shape=(n,))
     dev = gb.pos.device
     if outputs is None:
         outputs = (torch.empty((n, 3), device=dev), torch.empty((n,), device=dev), torch.empty((n, 3), device=dev))
-    col, vis, ind = outputs
+    col, vis, ind = outputs[:3]
     s = sampling(n_cos, n_ggx, n_env, seed, brdf)
     p = params if params is not None else scene.params
+    if light:
+        lt = outputs[3] if len(outputs) > 3 else torch.empty((n, 3), device=dev)
+        L.check(L.load().grt_shade_pixels_light(scene.handle, C.byref(scene.surfels()), C.byref(p),
+                                                C.byref(gb.struct()), C.byref(env.struct()), C.byref(s),
+                                                _ptr(pixels), n, _ptr(col), _ptr(vis), _ptr(ind), _ptr(lt),
+                                                _stream(stream)))
+        return col, vis, ind, lt
     L.check(L.load().grt_shade_pixels(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
                                       C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(col), _ptr(vis),
                                       _ptr(ind), _stream(stream)))
     return col, vis, ind
+
+
+@dataclasses.dataclass
+class MaterialGrads:
+    """Gradients into the environment map [H,W,3] and the per-pixel materials."""
+    env: torch.Tensor
+    albedo: torch.Tensor
+    rough: torch.Tensor
+    metal: torch.Tensor
+
+
+def shade_backward_material(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, dL_dcolor,
+                            dL_dlight=None, brdf=1, pixels=None, grads: Optional[MaterialGrads] = None, params=None,
+                            stream=None) -> MaterialGrads:
+    """Adjoint of shade_pixels (colour and the Eq. 16 mean incident radiance) into the map
+    and the per-pixel albedo, roughness and metallic; directions and proposal held fixed.
+    Gradients accumulate into `grads` (zeros when omitted)."""
+    n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
+    _dev(dL_dcolor, name="dL_dcolor", shape=(n, 3))
+    _dev(dL_dlight, name="dL_dlight", shape=(n, 3))
+    dev = gb.pos.device
+    if grads is None:
+        grads = MaterialGrads(torch.zeros((env.H, env.W, 3), device=dev), torch.zeros((n, 3), device=dev),
+                              torch.zeros(n, device=dev), torch.zeros(n, device=dev))
+    s = sampling(n_cos, n_ggx, n_env, seed, brdf)
+    p = params if params is not None else scene.params
+    L.check(L.load().grt_shade_backward_material(scene.handle, C.byref(scene.surfels()), C.byref(p),
+                                                 C.byref(gb.struct()), C.byref(env.struct()), C.byref(s),
+                                                 _ptr(pixels), n, _ptr(dL_dcolor), _ptr(dL_dlight), _ptr(grads.env),
+                                                 _ptr(grads.albedo), _ptr(grads.rough), _ptr(grads.metal),
+                                                 _stream(stream)))
+    return grads
 
 
 class SavedShade:

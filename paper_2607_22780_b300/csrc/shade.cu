@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(kShadeThreads) k_accumulate(const __grid_const
     const int slot = lane / G, sub = lane - slot * G;
     const int li = (int)(u - J.unit_begin) * (32 / G) + slot;
     const bool active = li < J.n_pixels;
-    float col[3] = {0.f, 0.f, 0.f}, ind[3] = {0.f, 0.f, 0.f}, vis = 0.f;
+    float col[3] = {0.f, 0.f, 0.f}, ind[3] = {0.f, 0.f, 0.f}, light[3] = {0.f, 0.f, 0.f}, vis = 0.f;
+    const bool want_light = J.out_light != nullptr;  // the same for the whole warp (one job)
     if (active) {
         int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
         if ((unsigned)pix < (unsigned)(J.gb.W * J.gb.H) && __ldg(J.gb.valid + pix)) {
@@ -45,8 +46,10 @@ __global__ void __launch_bounds__(kShadeThreads) k_accumulate(const __grid_const
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     float Lind = c == 0 ? rr.x : (c == 1 ? rr.y : rr.z);
-                    col[c] = fmaf(sw.g[c], fmaf(rr.w, sw.L[c], Lind), col[c]);
+                    const float Li = fmaf(rr.w, sw.L[c], Lind);
+                    col[c] = fmaf(sw.g[c], Li, col[c]);
                     ind[c] += Lind;
+                    light[c] += Li;
                 }
                 vis += rr.w;
             }
@@ -59,6 +62,15 @@ __global__ void __launch_bounds__(kShadeThreads) k_accumulate(const __grid_const
             ind[c] += __shfl_xor_sync(0xffffffffu, ind[c], off);
         }
         vis += __shfl_xor_sync(0xffffffffu, vis, off);
+        if (want_light) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) light[c] += __shfl_xor_sync(0xffffffffu, light[c], off);
+        }
+    }
+    if (active && sub == 0 && want_light) {
+        const float inv = 1.f / (float)J.Nr;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) J.out_light[3 * (size_t)li + c] = light[c] * inv;
     }
     if (active && sub == 0 && J.out_color) {
         const float inv = 1.f / (float)J.Nr;
@@ -71,6 +83,78 @@ __global__ void __launch_bounds__(kShadeThreads) k_accumulate(const __grid_const
             J.out_ind[3 * (size_t)li + 1] = ind[1] * inv;
             J.out_ind[3 * (size_t)li + 2] = ind[2] * inv;
         }
+    }
+}
+
+// Adjoint of the estimate (Eq. 13) and of the mean incident radiance (Eq. 16) into the
+// environment map and the per-pixel materials, directions and proposal held fixed: the
+// lane layout of k_accumulate; material gradients summed in the same fixed order and added
+// to the list entry's outputs, map gradients added to the sample's texel by atomics.
+struct MaterialAdj {
+    const float *dcol, *dlight;
+    float *g_env, *g_albedo, *g_rough, *g_metal;
+};
+
+__global__ void __launch_bounds__(kShadeThreads) k_material_adjoint(const __grid_constant__ JobTable<1> T,
+                                                                    const float4* __restrict__ dirs,
+                                                                    const float4* __restrict__ res, MaterialAdj A) {
+    long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (u >= T.total_units) return;
+    const ShadeJob& J = T.job[0];
+    const int lane = threadIdx.x & 31;
+    const int G = J.G;
+    const int slot = lane / G, sub = lane - slot * G;
+    const int li = (int)(u - J.unit_begin) * (32 / G) + slot;
+    const bool active = li < J.n_pixels;
+    float ga[3] = {0.f, 0.f, 0.f}, gr = 0.f, gm = 0.f;
+    if (active) {
+        int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
+        if ((unsigned)pix < (unsigned)(J.gb.W * J.gb.H) && __ldg(J.gb.valid + pix)) {
+            PixelState ps = load_pixel(J.gb, pix);
+            float dc[3], dl[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dc[c] = __ldg(A.dcol + 3 * (size_t)li + c);
+                dl[c] = A.dlight ? __ldg(A.dlight + 3 * (size_t)li + c) : 0.f;
+            }
+            const float inv = 1.f / (float)J.Nr;
+            const long long r0 = J.ray_begin + (long long)li * J.Nr;
+            for (int m = 0; m < J.spl; ++m) {
+                int j = sub + m * G;
+                if (j >= J.Nr) break;
+                float4 rr = __ldg(res + r0 + j);
+                if (rr.w < 0.f) continue;
+                float4 dw = __ldg(dirs + r0 + j);
+                const f3 w = mk3(dw.x, dw.y, dw.z);
+                SampleWeight sw = sample_weight(J.S, J.env, ps, w);
+                float dfa[3], dfm[3], dfr[3];
+                brdf_partials(J.S.brdf, ps.wo, w, ps.n, ps.alb, ps.rough, ps.metal, dfa, dfm, dfr);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float Lind = c == 0 ? rr.x : (c == 1 ? rr.y : rr.z);
+                    const float Li = fmaf(rr.w, sw.L[c], Lind);
+                    const float k = dc[c] * sw.cq * Li;
+                    ga[c] = fmaf(k, dfa[c], ga[c]);
+                    gm = fmaf(k, dfm[c], gm);
+                    gr = fmaf(k, dfr[c], gr);
+                    if (A.g_env) atomicAdd(A.g_env + 3 * (size_t)sw.texel + c, fmaf(dc[c], sw.g[c], dl[c]) * rr.w * inv);
+                }
+            }
+        }
+    }
+    for (int off = G >> 1; off > 0; off >>= 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ga[c] += __shfl_xor_sync(0xffffffffu, ga[c], off);
+        gr += __shfl_xor_sync(0xffffffffu, gr, off);
+        gm += __shfl_xor_sync(0xffffffffu, gm, off);
+    }
+    if (active && sub == 0) {
+        const float inv = 1.f / (float)J.Nr;
+        if (A.g_albedo)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) A.g_albedo[3 * (size_t)li + c] += ga[c] * inv;
+        if (A.g_rough) A.g_rough[li] += gr * inv;
+        if (A.g_metal) A.g_metal[li] += gm * inv;
     }
 }
 
@@ -226,6 +310,67 @@ extern "C" int grt_shade_relight(const grt_bvh* b, const grt_surfels* s, const g
     const RelightDev E{f + L.diff, f + L.spec, f + L.lut, f + L.poles};
     return launch_single<false>(b, s, p, g, e, smp, pixel_list, n_pixels, out_color, out_vis, out_ind, nullptr,
                                 (cudaStream_t)stream, nullptr, &E);
+}
+
+extern "C" int grt_shade_pixels_light(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
+                                      const grt_gbuffer* g, const grt_envmap* e, const grt_sampling* smp,
+                                      const int32_t* pixel_list, int32_t n_pixels, float* out_color, float* out_vis,
+                                      float* out_ind, float* out_light, void* stream) {
+    if (n_pixels > 0 && (!out_color || !out_light)) return set_error(GRT_ERR_ARG, "out_color or out_light is NULL");
+    int rc = check_trace_inputs(b, s, p);
+    if (rc) return rc;
+    JobTable<1> T;
+    T.P = to_params(*p);
+    T.n_jobs = 1;
+    rc = make_job(b, s, g, e, smp, pixel_list, n_pixels, out_color, out_vis, out_ind, &T.job[0]);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_pixels == 0) return GRT_OK;
+    if (T.job[0].n_pixels == 0) {  // N_r = 0: every output is zero
+        k_zero_outputs<<<(n_pixels + 255) / 256, 256, 0, st>>>(out_color, out_vis, out_ind, n_pixels);
+        GRT_CUDA(cudaMemsetAsync(out_light, 0, sizeof(float) * 3 * (size_t)n_pixels, st));
+        return launch_error("k_zero_outputs");
+    }
+    T.job[0].out_light = out_light;
+    return run_jobs<false>(T, p->k, nullptr, st);
+}
+
+extern "C" int grt_shade_backward_material(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
+                                           const grt_gbuffer* g, const grt_envmap* e, const grt_sampling* smp,
+                                           const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
+                                           const float* dL_dlight, float* grad_env, float* grad_albedo,
+                                           float* grad_rough, float* grad_metal, void* stream) {
+    if (n_pixels > 0 && !dL_dcolor) return set_error(GRT_ERR_ARG, "dL_dcolor is NULL");
+    int rc = check_trace_inputs(b, s, p);
+    if (rc) return rc;
+    JobTable<1> T;
+    T.P = to_params(*p);
+    T.n_jobs = 1;
+    rc = make_job(b, s, g, e, smp, pixel_list, n_pixels, nullptr, nullptr, nullptr, &T.job[0]);
+    if (rc) return rc;
+    ShadeJob& J = T.job[0];
+    if (J.n_pixels == 0) return GRT_OK;
+    const long long rays = (long long)J.n_pixels * J.Nr;
+    const long long units = (J.n_pixels + (32 / J.G) - 1) / (32 / J.G);
+    T.total_rays = rays;
+    T.total_units = units;
+    cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_memory();
+    float4* buf = nullptr;
+    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1), st));
+    float4* dirs = buf;
+    float4* res = buf + rays;
+    unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + 2 * rays);
+    const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
+    k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
+    dispatch_k(p->k, [&](auto kc) { launch_trace_dyn<decltype(kc)::value, 1>(T, dirs, res, next_ray, gr, st); });
+    const long long ga = (units * 32 + kShadeThreads - 1) / kShadeThreads;
+    k_material_adjoint<<<(unsigned)ga, kShadeThreads, 0, st>>>(
+        T, dirs, res, MaterialAdj{dL_dcolor, dL_dlight, grad_env, grad_albedo, grad_rough, grad_metal});
+    cudaError_t err = cudaGetLastError();
+    cudaFreeAsync(buf, st);
+    if (err != cudaSuccess) return check_cuda(err, "material adjoint kernels");
+    return GRT_OK;
 }
 
 extern "C" int grt_shade_batch(const grt_shade_request* req, int32_t n_req, const grt_trace_params* p,

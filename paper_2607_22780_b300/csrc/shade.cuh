@@ -99,6 +99,50 @@ __device__ __forceinline__ void brdf_eval(int mode, f3 wo, f3 wi, f3 n, const fl
     }
 }
 
+// Partial derivatives of f (brdf_eval) per channel with respect to that channel's albedo
+// (dfa), the metallic weight (dfm) and the roughness (dfr; zero where a = max(r^2, 1e-4)
+// is clamped), written in a2 = a^2: dD/da2 = (1 - 2 a2 (h.n)^2 / t) / (pi t^2),
+// dG1/da2 = -c (1 - c^2) / ((c + s)^2 s), s = sqrt(a2 + (1 - a2) c^2), da2/dr = 4 a r.
+__device__ __forceinline__ void brdf_partials(int mode, f3 wo, f3 wi, f3 n, const float alb[3], float rough,
+                                              float metal, float dfa[3], float dfm[3], float dfr[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        dfa[c] = (mode == 0 ? 1.f : 1.f - metal) * kInvPi;
+        dfm[c] = mode == 0 ? 0.f : -alb[c] * kInvPi;
+        dfr[c] = 0.f;
+    }
+    if (mode != 1) return;
+    float won = dot3(wo, n), win = dot3(wi, n);
+    if (!(won > 0.f) || !(win > 0.f)) return;
+    f3 hs = mk3(wo.x + wi.x, wo.y + wi.y, wo.z + wi.z);
+    float il = rsqrtf(dot3(hs, hs));
+    f3 h = mk3(hs.x * il, hs.y * il, hs.z * il);
+    float hn = dot3(h, n);
+    if (!(hn > 0.f)) return;
+    const float a = fmaxf(rough * rough, 1e-4f), a2 = a * a;
+    const float D = ggx_D(h, n, hn, a2), Gi = ggx_G1(win, a2), Go = ggx_G1(won, a2);
+    const float DG = D * Gi * Go / (4.f * win * won);
+    float x = fmaxf(1.f - dot3(wi, h), 0.f);
+    float x2 = x * x, x5 = x2 * x2 * x;
+    float dDG = 0.f;
+    if (rough * rough > 1e-4f) {
+        f3 cr = mk3(h.y * n.z - h.z * n.y, h.z * n.x - h.x * n.z, h.x * n.y - h.y * n.x);
+        const float t = fmaf(hn * hn, a2, dot3(cr, cr));
+        const float dD = (1.f - 2.f * a2 * hn * hn / t) / (kPi * t * t);
+        const float si = sqrtf(fmaf(1.f - a2, win * win, a2)), so = sqrtf(fmaf(1.f - a2, won * won, a2));
+        const float dGi = -win * (1.f - win * win) / ((win + si) * (win + si) * si);
+        const float dGo = -won * (1.f - won * won) / ((won + so) * (won + so) * so);
+        dDG = DG * (dD / D + dGi / Gi + dGo / Go) * 4.f * a * rough;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float F0 = fmaf(metal, alb[c], 0.04f * (1.f - metal));
+        dfa[c] = fmaf(DG * metal, 1.f - x5, dfa[c]);
+        dfm[c] = fmaf(DG * (1.f - x5), alb[c] - 0.04f, dfm[c]);
+        dfr[c] = dDG * fmaf(1.f - F0, x5, F0);
+    }
+}
+
 // Per-pixel shading state; decision quantities (n32, wo32, frame) drive the sampler.
 struct PixelState {
     f3 x, n, wo, b1, b2;
@@ -140,16 +184,20 @@ __device__ __forceinline__ bool draw_direction(const Sampling& S, const EnvDev& 
     return ok && dot_d(*w, ps.n) > 0.f;
 }
 
-// Integrand weight of a traced sample: g = f cos / q per channel, and L_env(w).
+// Integrand weight of a traced sample: g = f cos / q per channel, cos / q, and L_env(w)
+// with its texel index.
 struct SampleWeight {
     float g[3];
     float L[3];
+    float cq;
+    int texel;
 };
 
 __device__ __forceinline__ SampleWeight sample_weight(const Sampling& S, const EnvDev& E, const PixelState& ps, f3 w) {
     SampleWeight sw;
     int row, col;
     texel_of_d(w, E.W, E.H, &row, &col);
+    sw.texel = row * E.W + col;
     float4 tx = __ldg(E.texel + (size_t)row * E.W + col);
     sw.L[0] = tx.x;
     sw.L[1] = tx.y;
@@ -166,6 +214,7 @@ __device__ __forceinline__ SampleWeight sample_weight(const Sampling& S, const E
     float f[3];
     brdf_eval(S.brdf, ps.wo, w, ps.n, ps.alb, ps.rough, ps.metal, f);
     float s = q > 0.f ? cosn / q : 0.f;
+    sw.cq = s;
     sw.g[0] = f[0] * s;
     sw.g[1] = f[1] * s;
     sw.g[2] = f[2] * s;

@@ -28,6 +28,7 @@ struct ShadeJob {
     int pixel_offset;        // with no pixel list: pixel = pixel_offset + list index
     int Nr;
     float *out_color, *out_vis, *out_ind;
+    float* out_light;        // optional mean incident radiance (Eq. 16)
     int G, spl;              // accumulation: lanes per pixel, samples per lane
     long long ray_begin;     // first ray of this job in the launch's ray buffers
     long long unit_begin;    // first accumulation warp unit of this job
@@ -170,6 +171,7 @@ inline int make_job(const grt_bvh* b, const grt_surfels* s, const grt_gbuffer* g
     J->out_color = oc;
     J->out_vis = ov;
     J->out_ind = oi;
+    J->out_light = nullptr;
     J->G = group_lanes(J->Nr);
     J->spl = (J->Nr + J->G - 1) / J->G;
     J->ray_begin = 0;
