@@ -20,7 +20,7 @@ def _blocks_close(got, ref, rel=2e-3, absf=1e-5):
     assert err.max() <= 0, (np.unravel_index(err.argmax(), err.shape), got.ravel()[err.argmax()], ref.ravel()[err.argmax()])
 
 
-def _case(seed=61, n=20000, W=40, H=32):
+def _case(seed=61, n=150000, W=48, H=40):
     sc = wl.scene_objects(n, seed=seed)
     gb32 = oracle.gbuffer_f32(oracle.gbuffer(sc, wl.camera_orbit(seed, W, H, 3.0)))
     env = wl.envmap_hdr(seed, 64, 32)
