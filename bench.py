@@ -435,9 +435,23 @@ def time_train(api, S, cam, E, dev, args):
     def fwd():
         api.shade_pixels(S, G, E, *TRAIN_ALLOC, seed=SEED)
 
+    mg = api.MaterialGrads(torch.zeros((E.H, E.W, 3), device=dev), torch.zeros((img * img, 3), device=dev),
+                           torch.zeros(img * img, device=dev), torch.zeros(img * img, device=dev))
+
+    def step_material():
+        # forward with the mean incident radiance of Eq. 16, then the adjoint into the map
+        # and the per-pixel materials (L1-style upstream gradients)
+        col, vis, ind, light = api.shade_pixels(S, G, E, *TRAIN_ALLOC, seed=SEED, light=True)
+        dl = (torch.sign(col - tgt) * valid).contiguous()
+        dlight = (torch.sign(light - light.mean(1, keepdim=True)) * valid).contiguous()
+        for t_ in (mg.env, mg.albedo, mg.rough, mg.metal):
+            t_.zero_()
+        api.shade_backward_material(S, G, E, *TRAIN_ALLOC, SEED, dl, dlight, grads=mg)
+
     n = max(1, args.steps)
     ms = {}
-    for name, fn in (("fwd_bwd", step_stored), ("fwd_bwd_recompute", step_recompute), ("fwd", fwd)):
+    for name, fn in (("fwd_bwd", step_stored), ("fwd_bwd_recompute", step_recompute), ("fwd", fwd),
+                     ("fwd_bwd_material", step_material)):
         for _ in range(max(3, args.warmup)):
             fn()
         torch.cuda.synchronize()
@@ -452,6 +466,7 @@ def time_train(api, S, cam, E, dev, args):
     R = nv * sum(TRAIN_ALLOC)
     return {"workload": "train_300k_400x400_16spp", "rays": R, "fwd_ms": ms["fwd"], "fwd_bwd_ms": ms["fwd_bwd"],
             "fwd_bwd_recompute_ms": ms["fwd_bwd_recompute"], "stored_hits": 64,
+            "fwd_bwd_material_ms": ms["fwd_bwd_material"],
             "fwd_rays_per_s": R / (ms["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (ms["fwd_bwd"] * 1e-3),
             "fwd_bwd_recompute_rays_per_s": R / (ms["fwd_bwd_recompute"] * 1e-3)}
 
