@@ -106,6 +106,8 @@ def _declare(L):
     L.or_splitsum_many.argtypes = [C.c_int, P, P, P, P, P, C.c_int, C.c_int, P, P, P, P, P]
     L.or_trace_attr.argtypes = [P, P, C.c_int, P, P, P, P, P, P, P, P, C.c_int]
     L.or_shade_relight.argtypes = [P, P, P, P, P, P, P, P, P, C.c_int, P, P, P, P, C.c_int]
+    L.or_mesh_trace_attr.argtypes = [P, P, C.c_int, P, P, P, P, P, P, P, P, C.c_int]
+    L.or_shade_relight_mesh.argtypes = [P, P, P, P, P, P, P, P, P, C.c_int, P, P, P, P, C.c_int]
     L.or_denoise.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                              C.c_double, P, C.c_int]
 
@@ -494,4 +496,53 @@ def shade_relight(scene, gb, env, pre, n_cos, n_ggx, n_env, seed, brdf=1, pixels
     lib().or_shade_relight(_ref(s), _ref(P), _ref(g), _ref(e), _ptr(pre["diff"]), _ptr(pre["spec"]),
                            _ptr(pre["lut"]), _ref(S), _ptr(pl), n, _ptr(col), _ptr(vis), _ptr(ind), _ptr(fl),
                            nthreads)
+    return dict(color=col, vis=vis, ind=ind, flags=fl)
+
+
+
+# ----------------------------------------------------------------------------- mesh backend
+
+FLAG_MESH = 16
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("nv", C.c_int), ("nt", C.c_int), ("pos", C.c_void_p), ("tri", C.c_void_p), ("normal", C.c_void_p),
+                ("albedo", C.c_void_p), ("rough", C.c_void_p), ("metal", C.c_void_p)]
+
+
+def _mesh(m, keep):
+    arrs = [_f32(m.pos), np.ascontiguousarray(m.tri, np.int32), _f32(m.normal), _f32(m.albedo), _f32(m.rough),
+            _f32(m.metal)]
+    keep.refs.extend(arrs)
+    return _Mesh(arrs[0].shape[0], arrs[1].shape[0], *[_ptr(a) for a in arrs])
+
+
+def mesh_trace_attr(mesh, ray_o, ray_d, params=None, nthreads=0):
+    """Trace_attr (Eq. 14), mesh backend: V[R] (0 hit, 1 miss), albedo[R,3], rough[R],
+    metal[R], normal[R,3], flags[R] (FLAG_MESH near an edge or a tie)."""
+    keep = _Keep()
+    m = _mesh(mesh, keep); P = _params(params)
+    ro = _f32(ray_o).reshape(-1, 3); rd = _f32(ray_d).reshape(-1, 3)
+    R = ro.shape[0]
+    out = dict(V=np.zeros(R), albedo=np.zeros((R, 3)), rough=np.zeros(R), metal=np.zeros(R),
+               normal=np.zeros((R, 3)), flags=np.zeros(R, np.uint32))
+    lib().or_mesh_trace_attr(_ref(m), _ref(P), R, _ptr(ro), _ptr(rd), _ptr(out["V"]), _ptr(out["albedo"]),
+                             _ptr(out["rough"]), _ptr(out["metal"]), _ptr(out["normal"]), _ptr(out["flags"]),
+                             nthreads)
+    return out
+
+
+def shade_relight_mesh(mesh, gb, env, pre, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None, params=None, nthreads=0):
+    """MIS relighting (Eq. 15) with the mesh backend of Eq. 14."""
+    keep = _Keep()
+    m = _mesh(mesh, keep); P = _params(params); g = _gbuf(gb, keep); e = _env(env, keep)
+    S = _sampling(n_cos, n_ggx, n_env, seed, brdf)
+    if pixels is None:
+        pl = None; n = int(gb["W"]) * int(gb["H"])
+    else:
+        pl = np.ascontiguousarray(pixels, np.int32); n = pl.shape[0]
+    col = np.zeros((n, 3)); vis = np.zeros(n); ind = np.zeros((n, 3)); fl = np.zeros(n, np.uint32)
+    lib().or_shade_relight_mesh(_ref(m), _ref(P), _ref(g), _ref(e), _ptr(pre["diff"]), _ptr(pre["spec"]),
+                                _ptr(pre["lut"]), _ref(S), _ptr(pl), n, _ptr(col), _ptr(vis), _ptr(ind), _ptr(fl),
+                                nthreads)
     return dict(color=col, vis=vis, ind=ind, flags=fl)

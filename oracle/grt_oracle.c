@@ -1387,11 +1387,20 @@ int or_trace_attr(const or_scene* sc, const or_params* P, int R, const float* ra
 /* MIS relighting (Eq. 15 in Eq. 13): as or_shade_pixels with L_i = V_r L_new(w) +
  * (1 - V_r) SplitSum(a_r, r_r, m_r, n_r, E) seen from v = -w; indirect output = the mean
  * of (1 - V_r) SplitSum.  `env` is the novel map (its proposal tables drive the samples). */
-int or_shade_relight(const or_scene* sc, const or_params* P, const or_gbuf* gb, const or_env* env,
-                     const double* diff, const double* spec, const double* lut, const or_sampling* S,
-                     const int32_t* pixel_list, int n_pixels, double* out_color, double* out_vis, double* out_ind,
-                     uint32_t* out_flags, int nthreads) {
-    surf_pre* pre = precompute(sc);
+/* Backend of the secondary query of Eq. 14: the Gaussian trace or the mesh closest hit. */
+typedef struct {
+    const or_scene* sc;
+    const surf_pre* pre;
+    const struct or_mesh_s* mesh;
+} attr_backend;
+
+static void mesh_attr_one(const struct or_mesh_s* m, const or_params* P, f3 o32, f3 d32, double* V, double a[3],
+                          double* r, double* mm, double n[3], uint32_t* flags);
+
+static void relight_pixels(const attr_backend* B, const or_params* P, const or_gbuf* gb, const or_env* env,
+                           const double* diff, const double* spec, const double* lut, const or_sampling* S,
+                           const int32_t* pixel_list, int n_pixels, double* out_color, double* out_vis,
+                           double* out_ind, uint32_t* out_flags, int nthreads) {
     env_tab et;
     env_tab_build(env, &et);
     or_prefiltered E = {env->W, env->H, env->rgb, diff, spec, lut};
@@ -1414,7 +1423,10 @@ int or_shade_relight(const or_scene* sc, const or_params* P, const or_gbuf* gb, 
                     sample_t s = draw_sample(S, &et, env, p, j, n32, b1, b2, wo32, gb->rough[p]);
                     if (!s.ok) continue;
                     double V, ar[3], rr, mr, nr[3];
-                    trace_attr_one(sc, pre, P, x32, s.w32, &ws, &V, ar, &rr, &mr, nr, &fl);
+                    if (B->mesh)
+                        mesh_attr_one(B->mesh, P, x32, s.w32, &V, ar, &rr, &mr, nr, &fl);
+                    else
+                        trace_attr_one(B->sc, B->pre, P, x32, s.w32, &ws, &V, ar, &rr, &mr, nr, &fl);
                     sample_eval e;
                     sample_weights(env, &et, S, s.w32, n, wo, alb, gb->rough[p], gb->metal[p], &e);
                     double ss[3] = {0, 0, 0};
@@ -1440,6 +1452,16 @@ int or_shade_relight(const or_scene* sc, const or_params* P, const or_gbuf* gb, 
         free(ws.Tk);
     }
     env_tab_free(&et);
+}
+
+int or_shade_relight(const or_scene* sc, const or_params* P, const or_gbuf* gb, const or_env* env,
+                     const double* diff, const double* spec, const double* lut, const or_sampling* S,
+                     const int32_t* pixel_list, int n_pixels, double* out_color, double* out_vis, double* out_ind,
+                     uint32_t* out_flags, int nthreads) {
+    surf_pre* pre = precompute(sc);
+    attr_backend B = {sc, pre, NULL};
+    relight_pixels(&B, P, gb, env, diff, spec, lut, S, pixel_list, n_pixels, out_color, out_vis, out_ind, out_flags,
+                   nthreads);
     free(pre);
     return 0;
 }
@@ -1555,5 +1577,108 @@ int or_backward_material(const or_scene* sc, const or_params* P, const or_gbuf* 
     }
     env_tab_free(&et);
     free(pre);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- mesh backend (FP64) */
+/* Sec. III-E: the mesh backend answers Eq. 14 with the closest hit of the ray against a
+ * triangle mesh: a miss gives V_r = 1 and zero attributes; a hit gives V_r = 0 and the
+ * barycentric interpolation of the hit triangle's per-vertex albedo, roughness, metallic
+ * and normal (normalised, turned towards the ray origin).  Intersection by the
+ * Moeller-Trumbore test in FP64 over every triangle; the nearest t in (t_min, t_max) wins,
+ * equal t by triangle index.  Flags: a barycentric coordinate within 1e-6 of an edge, a
+ * second hit within 1e-6 (relative) of the nearest, or t within 1e-6 of t_min. */
+typedef struct or_mesh_s {
+    int nv, nt;
+    const float *pos;
+    const int32_t* tri;
+    const float *normal, *albedo, *rough, *metal;
+} or_mesh;
+
+#define OR_FLAG_MESH 16
+
+static d3 crossd(d3 a, d3 b) { return md3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+
+static void mesh_attr_one(const or_mesh* m, const or_params* P, f3 o32, f3 d32, double* V, double a[3],
+                          double* r, double* mm, double n[3], uint32_t* flags) {
+    d3 o = f2d(o32), d = f2d(d32);
+    double best = (double)P->t_max, second = (double)P->t_max, bu = 0, bv = 0;
+    int bt = -1;
+    for (int t = 0; t < m->nt; ++t) {
+        const float* p0 = m->pos + 3 * (size_t)m->tri[3 * t];
+        const float* p1 = m->pos + 3 * (size_t)m->tri[3 * t + 1];
+        const float* p2 = m->pos + 3 * (size_t)m->tri[3 * t + 2];
+        d3 v0 = md3(p0[0], p0[1], p0[2]);
+        d3 e1 = md3(p1[0] - v0.x, p1[1] - v0.y, p1[2] - v0.z), e2 = md3(p2[0] - v0.x, p2[1] - v0.y, p2[2] - v0.z);
+        d3 pv = crossd(d, e2);
+        double det = dotd(e1, pv);
+        if (fabs(det) < 1e-12 * sqrt(dotd(e1, e1) * dotd(e2, e2))) continue;
+        double inv = 1.0 / det;
+        d3 sv = addd(o, muld(v0, -1.0));
+        double u = dotd(sv, pv) * inv;
+        if (u < -1e-6 || u > 1.0 + 1e-6) continue;
+        d3 qv = crossd(sv, e1);
+        double v = dotd(d, qv) * inv;
+        if (v < -1e-6 || u + v > 1.0 + 1e-6) continue;
+        double tt = dotd(e2, qv) * inv;
+        if (!(tt > (double)P->t_min * (1 - 1e-6) && tt < (double)P->t_max)) continue;
+        int inside = u >= 0 && v >= 0 && u + v <= 1.0 && tt > (double)P->t_min;
+        if (!inside || fmin(fmin(u, v), 1.0 - u - v) < 1e-6 || fabs(tt - (double)P->t_min) < 1e-6 * (double)P->t_min)
+            *flags |= OR_FLAG_MESH;  /* near an edge or t_min: a decision FP32 may take the other way */
+        if (!inside) continue;
+        if (tt < best) {
+            second = best;
+            best = tt; bu = u; bv = v; bt = t;
+        } else if (tt < second) {
+            second = tt;
+        }
+    }
+    if (bt >= 0 && second < (double)P->t_max && fabs(second - best) <= 1e-6 * best) *flags |= OR_FLAG_MESH;
+    if (bt < 0) {
+        *V = 1.0;
+        a[0] = a[1] = a[2] = 0; *r = 0; *mm = 0; n[0] = n[1] = n[2] = 0;
+        return;
+    }
+    *V = 0.0;
+    const int32_t* tv = m->tri + 3 * bt;
+    double w[3] = {1.0 - bu - bv, bu, bv};
+    double na[3] = {0, 0, 0};
+    a[0] = a[1] = a[2] = 0; *r = 0; *mm = 0;
+    for (int k = 0; k < 3; ++k) {
+        int vi = tv[k];
+        for (int ch = 0; ch < 3; ++ch) {
+            a[ch] += w[k] * m->albedo[3 * (size_t)vi + ch];
+            na[ch] += w[k] * m->normal[3 * (size_t)vi + ch];
+        }
+        *r += w[k] * m->rough[vi];
+        *mm += w[k] * m->metal[vi];
+    }
+    double nl = sqrt(na[0] * na[0] + na[1] * na[1] + na[2] * na[2]);
+    double sgn = (na[0] * d.x + na[1] * d.y + na[2] * d.z) > 0 ? -1.0 : 1.0;
+    for (int ch = 0; ch < 3; ++ch) n[ch] = nl > 0 ? sgn * na[ch] / nl : 0.0;
+}
+
+int or_mesh_trace_attr(const or_mesh* m, const or_params* P, int R, const float* ray_o, const float* ray_d,
+                       double* out_V, double* out_a, double* out_r, double* out_m, double* out_n, uint32_t* out_flags,
+                       int nthreads) {
+    int nt = nthreads_or_default(nthreads);
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 8)
+    for (int i = 0; i < R; ++i) {
+        uint32_t fl = 0;
+        f3 o = mk3(ray_o[3 * i], ray_o[3 * i + 1], ray_o[3 * i + 2]);
+        f3 d = mk3(ray_d[3 * i], ray_d[3 * i + 1], ray_d[3 * i + 2]);
+        mesh_attr_one(m, P, o, d, out_V + i, out_a + 3 * (size_t)i, out_r + i, out_m + i, out_n + 3 * (size_t)i, &fl);
+        if (out_flags) out_flags[i] = fl;
+    }
+    return 0;
+}
+
+int or_shade_relight_mesh(const or_mesh* m, const or_params* P, const or_gbuf* gb, const or_env* env,
+                          const double* diff, const double* spec, const double* lut, const or_sampling* S,
+                          const int32_t* pixel_list, int n_pixels, double* out_color, double* out_vis,
+                          double* out_ind, uint32_t* out_flags, int nthreads) {
+    attr_backend B = {NULL, NULL, m};
+    relight_pixels(&B, P, gb, env, diff, spec, lut, S, pixel_list, n_pixels, out_color, out_vis, out_ind, out_flags,
+                   nthreads);
     return 0;
 }

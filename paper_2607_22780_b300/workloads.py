@@ -13,6 +13,8 @@ albedo/roughness/metallic) with the sizes of the synthetic workloads:
 * ``scene_sphere_plane``  -- 8k surfels on a unit sphere plus a 4x4 ground plane.
 * ``scene_objects``       -- 300k surfels on 3 spheres, 2 tori, a box and a plane.
 * ``scene_large``         -- 1M/2M surfels: 40x40 plane, 50 primitives, r=50 shell.
+* ``mesh_objects``        -- the objects scene's layout as a triangle mesh with per-vertex
+                             normals and materials (for the mesh relighting backend).
 
 Every surfel stores: centre mu[3], rotation quaternion (w,x,y,z) whose matrix
 columns are (t_u, t_v, n) with n the surface normal, scales (s_u, s_v),
@@ -29,7 +31,7 @@ import numpy as np
 __all__ = [
     "Scene", "Camera", "scene_sphere_plane", "scene_objects", "scene_large",
     "scene_random_soup", "envmap_constant", "envmap_hdr", "camera_orbit",
-    "camera_c1", "quat_from_frames",
+    "camera_c1", "quat_from_frames", "Mesh", "mesh_objects",
 ]
 
 
@@ -273,6 +275,110 @@ def scene_objects(n: int = 300_000, seed: int = 2607, color_dim: int = 48) -> Sc
     parts.append(_plane_y(rng, cnt[6], -1.0, 4.0, 4.0))
     pos = np.concatenate([p for p, _ in parts]); nrm = np.concatenate([q for _, q in parts])
     return _finish(rng, pos, nrm, 0.002, 0.02, color_dim)
+
+
+@dataclasses.dataclass
+class Mesh:
+    """Triangle mesh with per-vertex attributes (float32 / int32, contiguous)."""
+    pos: np.ndarray      # [V, 3]
+    tri: np.ndarray      # [T, 3] vertex indices
+    normal: np.ndarray   # [V, 3] unit
+    albedo: np.ndarray   # [V, 3]
+    rough: np.ndarray    # [V]
+    metal: np.ndarray    # [V]
+
+
+def _rot_y_to(axis):
+    ax = np.asarray(axis, np.float64); ax = ax / np.linalg.norm(ax)
+    y = np.array([0.0, 1.0, 0.0])
+    c = float(np.dot(y, ax)); w = np.cross(y, ax); s = np.linalg.norm(w)
+    if s < 1e-12:
+        return np.eye(3) if c > 0 else np.diag([1.0, -1.0, -1.0])
+    w /= s
+    K = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+    return np.eye(3) + s * K + (1 - c) * K @ K
+
+
+def _grid_tris(nu, nv, wrap_u, wrap_v, base):
+    """Two triangles per cell of an nu x nv vertex grid (index u * nv + v)."""
+    cu = nu if wrap_u else nu - 1
+    cv = nv if wrap_v else nv - 1
+    u, v = np.meshgrid(np.arange(cu), np.arange(cv), indexing="ij")
+    u1 = (u + 1) % nu; v1 = (v + 1) % nv
+    a = u * nv + v; b = u1 * nv + v; c = u1 * nv + v1; d = u * nv + v1
+    return np.concatenate([np.stack([a, b, c], -1).reshape(-1, 3), np.stack([a, c, d], -1).reshape(-1, 3)]) + base
+
+
+def mesh_objects(seed: int = 2607, res: int = 64) -> Mesh:
+    """The layout of ``scene_objects`` (same seed: same radii, positions and torus axes) as a
+    triangle mesh: UV spheres and tori of res x 2 res vertices, cube faces and the 8x8 ground
+    plane as res x res grids.  Per vertex: analytic normal, albedo U[0,1]^3, roughness
+    U[0.05,1], metallic Bernoulli(0.3)."""
+    rng = np.random.default_rng(seed)
+    radii = rng.uniform(0.3, 0.6, 3)
+    Rt, rt = 0.5, 0.15
+    half = 0.3
+    foot = list(radii) + [Rt + rt, Rt + rt, half * np.sqrt(2)]
+    centres = _place_objects(rng, foot, 2.0, -1.0)
+    axes = [rng.normal(size=3) for _ in range(2)]
+    P, N, T = [], [], []
+    nv_ = 0
+
+    def add(pos, nrm, tris):
+        nonlocal nv_
+        P.append(pos); N.append(nrm); T.append(tris + nv_)
+        nv_ += pos.shape[0]
+
+    nl, nlon = res, 2 * res
+    for i in range(3):
+        th = np.pi * (np.arange(nl) + 0.5) / nl
+        ph = 2 * np.pi * np.arange(nlon) / nlon
+        TH, PH = np.meshgrid(th, ph, indexing="ij")
+        d = np.stack([np.sin(TH) * np.sin(PH), np.cos(TH), np.sin(TH) * np.cos(PH)], -1).reshape(-1, 3)
+        c = centres[i] + [0, radii[i], 0]
+        # poles closed by the first and last rings' fans
+        top = c + [0, radii[i], 0]; bot = c - [0, radii[i], 0]
+        pos = np.concatenate([c + radii[i] * d, [top, bot]])
+        nrm = np.concatenate([d, [[0, 1.0, 0], [0, -1.0, 0]]])
+        tris = _grid_tris(nl, nlon, False, True, 0)
+        k = np.arange(nlon)
+        ti, bi = nl * nlon, nl * nlon + 1
+        fan_t = np.stack([np.full(nlon, ti), k, (k + 1) % nlon], -1)
+        fan_b = np.stack([np.full(nlon, bi), (nl - 1) * nlon + (k + 1) % nlon, (nl - 1) * nlon + k], -1)
+        add(pos, nrm, np.concatenate([tris, fan_t, fan_b]))
+    for j in range(2):
+        u = 2 * np.pi * np.arange(2 * res) / (2 * res)
+        v = 2 * np.pi * np.arange(res) / res
+        U, Vv = np.meshgrid(u, v, indexing="ij")
+        loc = np.stack([(Rt + rt * np.cos(Vv)) * np.cos(U), rt * np.sin(Vv), (Rt + rt * np.cos(Vv)) * np.sin(U)], -1)
+        nn = np.stack([np.cos(Vv) * np.cos(U), np.sin(Vv), np.cos(Vv) * np.sin(U)], -1)
+        Rm = _rot_y_to(axes[j])
+        c = centres[3 + j] + [0, Rt + rt, 0]
+        add(loc.reshape(-1, 3) @ Rm.T + c, nn.reshape(-1, 3) @ Rm.T, _grid_tris(2 * res, res, True, True, 0))
+    g = np.linspace(-1.0, 1.0, res)
+    A, B = np.meshgrid(g, g, indexing="ij")
+    cb = centres[5] + [0, half, 0]
+    for d in range(3):
+        o1, o2 = [e for e in range(3) if e != d]
+        for sgn in (1.0, -1.0):
+            pos = np.zeros((res * res, 3))
+            pos[:, d] = sgn * half
+            pos[:, o1] = half * A.reshape(-1)
+            pos[:, o2] = half * B.reshape(-1)
+            nrm = np.zeros((res * res, 3)); nrm[:, d] = sgn
+            add(pos + cb, nrm, _grid_tris(res, res, False, False, 0))
+    pos = np.zeros((res * res, 3))
+    pos[:, 0] = 4.0 * A.reshape(-1); pos[:, 1] = -1.0; pos[:, 2] = 4.0 * B.reshape(-1)
+    nrm = np.tile([0.0, 1.0, 0.0], (res * res, 1))
+    add(pos, nrm, _grid_tris(res, res, False, False, 0))
+    pos = np.concatenate(P); nrm = np.concatenate(N); tri = np.concatenate(T)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    V = pos.shape[0]
+    return Mesh(pos=np.ascontiguousarray(pos, np.float32), tri=np.ascontiguousarray(tri, np.int32),
+                normal=np.ascontiguousarray(nrm, np.float32),
+                albedo=rng.uniform(0.0, 1.0, (V, 3)).astype(np.float32),
+                rough=rng.uniform(0.05, 1.0, V).astype(np.float32),
+                metal=(rng.uniform(size=V) < 0.3).astype(np.float32))
 
 
 def scene_large(n: int = 2_000_000, seed: int = 2607, color_dim: int = 48) -> Scene:
