@@ -339,6 +339,40 @@ int grt_shade_relight(const grt_bvh* bvh, const grt_surfels* surfels, const grt_
                       const grt_sampling* sampling, const int32_t* pixel_list, int32_t n_pixels, float* out_color,
                       float* out_vis, float* out_ind, void* stream);
 
+/* Mesh backend of the relighting query (Sec. III-E): a triangle mesh with per-vertex
+ * attributes (all device pointers, float32 / int32): pos[V][3], tri[T][3] (vertex indices),
+ * normal[V][3], albedo[V][3], rough[V], metal[V]. */
+typedef struct {
+    int32_t n_vertices, n_triangles;
+    const float* pos;
+    const int32_t* tri;
+    const float* normal;
+    const float* albedo;
+    const float* rough;
+    const float* metal;
+} grt_mesh;
+
+/* Builds the 4-wide LBVH of a mesh's triangles (the same build as grt_build_bvh with one
+ * triangle per leaf; the tree keeps its own copy of the geometry, the attributes are read
+ * from the mesh at query time).  A vertex index outside [0, n_vertices) is reported as
+ * GRT_STATUS_BAD_INDEX (grt_bvh_status) and read as vertex 0.  Free with grt_bvh_destroy. */
+int grt_build_mesh_bvh(const grt_mesh* mesh, grt_bvh** out, void* stream);
+
+/* Trace_attr (Eq. 14), mesh backend: the closest triangle hit with t in (t_min, t_max)
+ * (Moeller-Trumbore; equal t by triangle index): a miss gives out_vis = 1 and zeros; a hit
+ * gives out_vis = 0 and the barycentric interpolation of the triangle's per-vertex albedo,
+ * roughness, metallic and normal (normalised, turned towards the ray origin).  Only
+ * params->t_min / t_max are used. */
+int grt_mesh_trace_attr(const grt_bvh* mesh_bvh, const grt_mesh* mesh, const grt_trace_params* params,
+                        const float* ray_o, const float* ray_d, int32_t R, float* out_vis, float* out_albedo,
+                        float* out_rough, float* out_metal, float* out_normal, void* stream);
+
+/* grt_shade_relight with the mesh backend answering Eq. 14 (V_r in {0, 1}). */
+int grt_shade_relight_mesh(const grt_bvh* mesh_bvh, const grt_mesh* mesh, const grt_trace_params* params,
+                           const grt_gbuffer* gbuffer, const grt_envmap* env, const void* prefiltered,
+                           const grt_sampling* sampling, const int32_t* pixel_list, int32_t n_pixels,
+                           float* out_color, float* out_vis, float* out_ind, void* stream);
+
 /* Cross-bilateral denoiser for low-sample shading (Sec. III-D, "Denoising"):
  *   out(p) = sum_{p' in Q(p)} B(p,p') color(p') / sum B(p,p'),
  *   B = exp(-|p-p'|^2 / (2 sigma_s^2)) * exp(-|D(p)-D(p')| / (sigma_d |grad D(p).(p-p')| + eps_d))

@@ -45,6 +45,11 @@ class Grads(C.Structure):
     _fields_ = [(k, P) for k in ("mu", "quat", "scale", "opacity", "color")]
 
 
+class Mesh(C.Structure):
+    _fields_ = [("n_vertices", C.c_int32), ("n_triangles", C.c_int32)] + \
+        [(k, P) for k in ("pos", "tri", "normal", "albedo", "rough", "metal")]
+
+
 class EnvMap(C.Structure):
     _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("tables", P)]
 
@@ -115,6 +120,11 @@ SIGNATURES = {
     "grt_env_prefilter": (C.c_int, [P, C.c_int32, C.c_int32, P, C.c_size_t, P]),
     "grt_shade_relight": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                     C.POINTER(EnvMap), P, C.POINTER(Sampling), P, C.c_int32, P, P, P, P]),
+    "grt_build_mesh_bvh": (C.c_int, [C.POINTER(Mesh), C.POINTER(P), P]),
+    "grt_mesh_trace_attr": (C.c_int, [P, C.POINTER(Mesh), C.POINTER(TraceParams), P, P, C.c_int32, P, P, P, P, P,
+                                      P]),
+    "grt_shade_relight_mesh": (C.c_int, [P, C.POINTER(Mesh), C.POINTER(TraceParams), C.POINTER(GBuffer),
+                                         C.POINTER(EnvMap), P, C.POINTER(Sampling), P, C.c_int32, P, P, P, P]),
     "grt_last_error": (C.c_char_p, []),
     "grt_version": (C.c_char_p, []),
 }

@@ -504,6 +504,95 @@ def shade_relight(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_e
     return col, vis, ind
 
 
+class MeshScene:
+    """Triangle mesh resident on the device plus its LBVH (grt_build_mesh_bvh): the mesh
+    backend of the relighting query.  Tensors: pos[V,3], tri[T,3] (int32), normal[V,3],
+    albedo[V,3], rough[V], metal[V]; float32 unless stated, contiguous, on one CUDA device."""
+
+    def __init__(self, pos, tri, normal, albedo, rough, metal, params=None, stream=None):
+        nv, nt = int(pos.shape[0]), int(tri.shape[0])
+        self.n_vertices, self.n_triangles = nv, nt
+        self.pos = _dev(pos, name="pos", shape=(nv, 3))
+        self.tri = _dev(tri, dtype=torch.int32, name="tri", shape=(nt, 3))
+        self.normal = _dev(normal, name="normal", shape=(nv, 3))
+        self.albedo = _dev(albedo, name="albedo", shape=(nv, 3))
+        self.rough = _dev(rough, name="rough", shape=(nv,))
+        self.metal = _dev(metal, name="metal", shape=(nv,))
+        self.params = params if params is not None else trace_params()
+        self._bvh = C.c_void_p(None)
+        self._lib = L.load()
+        L.check(self._lib.grt_build_mesh_bvh(C.byref(self.mesh()), C.byref(self._bvh), _stream(stream)))
+
+    @staticmethod
+    def from_workload(m, device="cuda", params=None) -> "MeshScene":
+        t = lambda a: torch.from_numpy(a).to(device).contiguous()
+        return MeshScene(t(m.pos), t(m.tri.astype("int32")), t(m.normal), t(m.albedo), t(m.rough), t(m.metal),
+                         params=params)
+
+    @property
+    def handle(self):
+        return self._bvh
+
+    def mesh(self) -> L.Mesh:
+        return L.Mesh(self.n_vertices, self.n_triangles, _ptr(self.pos), _ptr(self.tri), _ptr(self.normal),
+                      _ptr(self.albedo), _ptr(self.rough), _ptr(self.metal))
+
+    def info(self) -> dict:
+        i = L.BvhInfo()
+        L.check(self._lib.grt_bvh_info(self._bvh, C.byref(i)))
+        return dict(n_triangles=i.n_surfels, n_nodes=i.n_nodes, device_bytes=i.device_bytes, bounds=list(i.bounds))
+
+    def status(self, stream=None) -> int:
+        s = C.c_int32(0)
+        L.check(self._lib.grt_bvh_status(self._bvh, C.byref(s), _stream(stream)))
+        return s.value
+
+    def close(self):
+        if self._bvh:
+            self._lib.grt_bvh_destroy(self._bvh)
+            self._bvh = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mesh_trace_attr(mesh: MeshScene, ray_o, ray_d, params=None, stream=None):
+    """Trace_attr (Eq. 14), mesh backend: (V[R], albedo[R,3], rough[R], metal[R], normal[R,3])."""
+    R = int(ray_o.shape[0])
+    _dev(ray_o, name="ray_o", shape=(R, 3))
+    _dev(ray_d, name="ray_d", shape=(R, 3))
+    dev = ray_o.device
+    V, a, r, m, n = (torch.empty(R, device=dev), torch.empty((R, 3), device=dev), torch.empty(R, device=dev),
+                     torch.empty(R, device=dev), torch.empty((R, 3), device=dev))
+    p = params if params is not None else mesh.params
+    L.check(L.load().grt_mesh_trace_attr(mesh.handle, C.byref(mesh.mesh()), C.byref(p), _ptr(ray_o), _ptr(ray_d),
+                                         R, _ptr(V), _ptr(a), _ptr(r), _ptr(m), _ptr(n), _stream(stream)))
+    return V, a, r, m, n
+
+
+def shade_relight_mesh(mesh: MeshScene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1,
+                       pixels=None, params=None, outputs=None, stream=None):
+    """MIS relighting under `env` (Eq. 15) with the mesh backend answering Eq. 14:
+    colour[P,3], visibility[P], indirect[P,3]."""
+    n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
+    if pixels is not None:
+        _dev(pixels, dtype=torch.int32, name="pixels", shape=(n,))
+    dev = gb.pos.device
+    if outputs is None:
+        outputs = (torch.empty((n, 3), device=dev), torch.empty((n,), device=dev), torch.empty((n, 3), device=dev))
+    col, vis, ind = outputs
+    pre = env.prefiltered if env.prefiltered is not None else env.prefilter(stream)
+    s = sampling(n_cos, n_ggx, n_env, seed, brdf)
+    p = params if params is not None else mesh.params
+    L.check(L.load().grt_shade_relight_mesh(mesh.handle, C.byref(mesh.mesh()), C.byref(p), C.byref(gb.struct()),
+                                            C.byref(env.struct()), _ptr(pre), C.byref(s), _ptr(pixels), n,
+                                            _ptr(col), _ptr(vis), _ptr(ind), _stream(stream)))
+    return col, vis, ind
+
+
 DENOISE_DEFAULTS = dict(radius=3, sigma_s=2.0, sigma_d=1.0, sigma_n=64.0, eps_d=1e-3)
 
 

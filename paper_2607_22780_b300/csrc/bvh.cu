@@ -80,6 +80,9 @@ __device__ __forceinline__ void surfel_box(const SurfelIn& s, int i, float lo[3]
     }
 }
 
+__device__ __forceinline__ void reduce_bounds(const float cl[3], const float ch[3], const float lo[3],
+                                              const float hi[3], unsigned int* __restrict__ bounds_u);
+
 __global__ void k_prep_bounds(SurfelIn s, float* __restrict__ centre, unsigned int* __restrict__ bounds_u) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
@@ -96,7 +99,13 @@ __global__ void k_prep_bounds(SurfelIn s, float* __restrict__ centre, unsigned i
             ch[k] = c;
         }
     }
-    // warp then block reduction of centre bounds and box bounds
+    reduce_bounds(cl, ch, lo, hi, bounds_u);
+}
+
+// Warp then block reduction of centre bounds and box bounds into bounds_u (ordered ints:
+// [0..2] min centre, [3..5] -max centre, [6..8] min box, [9..11] -max box).
+__device__ __forceinline__ void reduce_bounds(const float cl[3], const float ch[3], const float lo[3],
+                                              const float hi[3], unsigned int* __restrict__ bounds_u) {
     __shared__ float red[12][kThreads / 32];
     float v[12] = {cl[0], cl[1], cl[2], -ch[0], -ch[1], -ch[2], lo[0], lo[1], lo[2], -hi[0], -hi[1], -hi[2]};
 #pragma unroll
@@ -240,6 +249,72 @@ __global__ void k_sort_scatter(const MortonKey* __restrict__ keys_in, const int*
         __syncthreads();
         for (int w = 0; w < W; ++w) wcnt[w][threadIdx.x] = 0;
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- triangles (mesh backend)
+// The same tree over triangles: each leaf is one triangle, bounded by the box of its three
+// vertices; the record of leaf j is (v0, triangle id), (v1 - v0), (v2 - v0), unused.
+struct TriIn {
+    const float* pos;
+    const int* tri;
+    int n, nv;
+    int* status;
+};
+
+__device__ __forceinline__ void tri_box(const TriIn& t, int i, float lo[3], float hi[3], f3 v[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        int vi = t.tri[3 * i + c];
+        if ((unsigned)vi >= (unsigned)t.nv) {  // a vertex index outside the mesh: reported, vertex 0 used
+            atomicOr(t.status, GRT_STATUS_BAD_INDEX);
+            vi = 0;
+        }
+        v[c] = mk3(t.pos[3 * (size_t)vi], t.pos[3 * (size_t)vi + 1], t.pos[3 * (size_t)vi + 2]);
+    }
+    lo[0] = fminf(v[0].x, fminf(v[1].x, v[2].x));
+    lo[1] = fminf(v[0].y, fminf(v[1].y, v[2].y));
+    lo[2] = fminf(v[0].z, fminf(v[1].z, v[2].z));
+    hi[0] = fmaxf(v[0].x, fmaxf(v[1].x, v[2].x));
+    hi[1] = fmaxf(v[0].y, fmaxf(v[1].y, v[2].y));
+    hi[2] = fmaxf(v[0].z, fmaxf(v[1].z, v[2].z));
+}
+
+__global__ void k_tri_prep(TriIn t, float* __restrict__ centre, unsigned int* __restrict__ bounds_u) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    float cl[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, ch[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    if (i < t.n) {
+        f3 v[3];
+        tri_box(t, i, lo, hi, v);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float c = 0.5f * (lo[k] + hi[k]);
+            centre[3 * i + k] = c;
+            cl[k] = c;
+            ch[k] = c;
+        }
+    }
+    reduce_bounds(cl, ch, lo, hi, bounds_u);
+}
+
+__global__ void k_tri_records(TriIn t, const int* __restrict__ sorted, float4* __restrict__ records,
+                              float* __restrict__ leaf_box) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= t.n) return;
+    const int i = sorted[j];
+    float lo[3], hi[3];
+    f3 v[3];
+    tri_box(t, i, lo, hi, v);
+    float4* rec = records + 4 * (size_t)j;
+    rec[0] = make_float4(v[0].x, v[0].y, v[0].z, __int_as_float(i));
+    rec[1] = make_float4(v[1].x - v[0].x, v[1].y - v[0].y, v[1].z - v[0].z, 0.f);
+    rec[2] = make_float4(v[2].x - v[0].x, v[2].y - v[0].y, v[2].z - v[0].z, 0.f);
+    rec[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        leaf_box[6 * (size_t)j + k] = lo[k];
+        leaf_box[6 * (size_t)j + 3 + k] = hi[k];
     }
 }
 
@@ -472,12 +547,27 @@ __global__ void k_collapse_init(int* counts, int2* f0) {
 
 }  // namespace
 
-// Records, binary refit and the 4-wide collapse (or its refit): shared tail of the builds.
-static int finish_build(grt_bvh* b, const SurfelIn& in, bool collapse, cudaStream_t st) {
-    const int n = b->n;
-    const int g = (n + kThreads - 1) / kThreads;
+// Per-primitive steps of a build: leaf boxes and centres, and the packed records.
+static void launch_prep(const SurfelIn& in, float* centre, unsigned int* bounds_u, int g, cudaStream_t st) {
+    k_prep_bounds<<<g, kThreads, 0, st>>>(in, centre, bounds_u);
+}
+static void launch_prep(const TriIn& in, float* centre, unsigned int* bounds_u, int g, cudaStream_t st) {
+    k_tri_prep<<<g, kThreads, 0, st>>>(in, centre, bounds_u);
+}
+static void launch_records(const SurfelIn& in, grt_bvh* b, int g, cudaStream_t st) {
     RecordIn r{in, b->sorted_ids, b->records, b->leaf_box};
     k_records<<<g, kThreads, 0, st>>>(r);
+}
+static void launch_records(const TriIn& in, grt_bvh* b, int g, cudaStream_t st) {
+    k_tri_records<<<g, kThreads, 0, st>>>(in, b->sorted_ids, b->records, b->leaf_box);
+}
+
+// Records, binary refit and the 4-wide collapse (or its refit): shared tail of the builds.
+template <class In>
+static int finish_build(grt_bvh* b, const In& in, bool collapse, cudaStream_t st) {
+    const int n = b->n;
+    const int g = (n + kThreads - 1) / kThreads;
+    launch_records(in, b, g, st);
     if (n > 1) {
         GRT_CUDA(cudaMemsetAsync(b->refit_flags, 0, sizeof(int) * (size_t)b->n_int, st));
         k_refit<<<g, kThreads, 0, st>>>(b->leaf_box, b->parent, n, b->nodes, b->refit_flags, b->status, b->bin_box);
@@ -507,7 +597,8 @@ static constexpr size_t build_scratch_bytes(size_t n) {
 }
 
 // Prep, Morton codes, radix sort and radix tree into b, using `scratch` (build_scratch_bytes).
-static int build_topology(grt_bvh* b, const SurfelIn& in, char* scratch, cudaStream_t st) {
+template <class In>
+static int build_topology(grt_bvh* b, const In& in, char* scratch, cudaStream_t st) {
     const int n = b->n;
     const int g = (n + kThreads - 1) / kThreads;
     const int nblocks = (n + kSortTile - 1) / kSortTile;
@@ -522,7 +613,7 @@ static int build_topology(grt_bvh* b, const SurfelIn& in, char* scratch, cudaStr
     unsigned int* hist = (unsigned int*)p;
     // the bounds restart from "empty"; centres, keys, ids and histograms are fully rewritten
     GRT_CUDA(cudaMemsetAsync(bounds_u, 0xFF, 64, st));
-    k_prep_bounds<<<g, kThreads, 0, st>>>(in, centre, bounds_u);
+    launch_prep(in, centre, bounds_u, g, st);
     k_morton<<<g, kThreads, 0, st>>>(centre, bounds_u, n, keys0, vals0, b->bounds);
     MortonKey* kin = keys0;
     MortonKey* kout = keys1;
@@ -631,20 +722,13 @@ extern "C" int grt_rebuild_bvh_noalloc(grt_bvh* b, const grt_surfels* s, const g
     return launch_build_noalloc(b, s, params->alpha_min, (cudaStream_t)stream);
 }
 
-extern "C" int grt_build_bvh(const grt_surfels* s, const grt_trace_params* params, grt_bvh** out, void* stream) {
-    if (!out) return set_error(GRT_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    int rc = check_surfels(s);
-    if (rc) return rc;
-    if (!params) return set_error(GRT_ERR_ARG, "params is NULL");
-    if (!(params->alpha_min > 0.f && params->alpha_min < 1.f))
-        return set_error(GRT_ERR_ARG, "alpha_min must be in (0,1)");
-    cudaStream_t st = (cudaStream_t)stream;
+// Device storage of a tree over n leaves (one allocation); NULL on failure.
+static grt_bvh* alloc_bvh(int nleaf, cudaStream_t st, int* rc_out) {
     grt_bvh* b = new grt_bvh();
-    b->n = s->n;
-    b->n_int = s->n > 1 ? s->n - 1 : 0;
+    b->n = nleaf;
+    b->n_int = nleaf > 1 ? nleaf - 1 : 0;
     cudaGetDevice(&b->device);
-    size_t n = (size_t)s->n, ni = (size_t)b->n_int;
+    size_t n = (size_t)nleaf, ni = (size_t)b->n_int;
     size_t bytes = sizeof(float4) * 4 * (ni + n) + sizeof(int) * (n + ni + 1) + sizeof(int) * (ni + 1) +
                    sizeof(float) * 6 * n + sizeof(int) * n + 64 + 64 +
                    sizeof(float) * 6 * ni + sizeof(float4) * 8 * ni + sizeof(int2) * 2 * ni +
@@ -653,7 +737,8 @@ extern "C" int grt_build_bvh(const grt_surfels* s, const grt_trace_params* param
     cudaError_t e = cudaMalloc((void**)&base, bytes);
     if (e != cudaSuccess) {
         delete b;
-        return set_error(GRT_ERR_OOM, "cudaMalloc(%zu) for the BVH failed: %s", bytes, cudaGetErrorString(e));
+        *rc_out = set_error(GRT_ERR_OOM, "cudaMalloc(%zu) for the BVH failed: %s", bytes, cudaGetErrorString(e));
+        return nullptr;
     }
     char* p = base;
     b->base = base;
@@ -678,14 +763,65 @@ extern "C" int grt_build_bvh(const grt_surfels* s, const grt_trace_params* param
     if (e != cudaSuccess) {
         cudaFree(base);
         delete b;
-        return check_cuda(e, "cudaMemsetAsync");
+        *rc_out = check_cuda(e, "cudaMemsetAsync");
+        return nullptr;
     }
+    *rc_out = GRT_OK;
+    return b;
+}
+
+extern "C" int grt_build_bvh(const grt_surfels* s, const grt_trace_params* params, grt_bvh** out, void* stream) {
+    if (!out) return set_error(GRT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_surfels(s);
+    if (rc) return rc;
+    if (!params) return set_error(GRT_ERR_ARG, "params is NULL");
+    if (!(params->alpha_min > 0.f && params->alpha_min < 1.f))
+        return set_error(GRT_ERR_ARG, "alpha_min must be in (0,1)");
+    cudaStream_t st = (cudaStream_t)stream;
+    grt_bvh* b = alloc_bvh(s->n, st, &rc);
+    if (!b) return rc;
+    char* base = (char*)b->base;
     rc = launch_build(b, s, params->alpha_min, true, st);
     if (rc) {
         cudaStreamSynchronize(st);
         cudaFree(base);
         delete b;
         return rc;
+    }
+    *out = b;
+    return GRT_OK;
+}
+
+extern "C" int grt_build_mesh_bvh(const grt_mesh* m, grt_bvh** out, void* stream) {
+    if (!out) return set_error(GRT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!m) return set_error(GRT_ERR_ARG, "mesh is NULL");
+    if (m->n_triangles < 0 || m->n_triangles > (1 << 27))
+        return set_error(GRT_ERR_ARG, "n_triangles = %d outside [0, 2^27]", m->n_triangles);
+    if (m->n_triangles > 0 && (m->n_vertices <= 0 || !m->pos || !m->tri))
+        return set_error(GRT_ERR_ARG, "a mesh with triangles needs vertices, pos and tri");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = GRT_OK;
+    grt_bvh* b = alloc_bvh(m->n_triangles, st, &rc);
+    if (!b) return rc;
+    if (b->n > 0) {
+        TriIn in{m->pos, m->tri, b->n, m->n_vertices, b->status};
+        char* scratch = nullptr;
+        cudaError_t e = cudaMallocAsync((void**)&scratch, build_scratch_bytes((size_t)b->n), st);
+        if (e == cudaSuccess) {
+            rc = build_topology(b, in, scratch, st);
+            cudaFreeAsync(scratch, st);
+            if (!rc) rc = finish_build(b, in, true, st);
+        } else {
+            rc = check_cuda(e, "cudaMallocAsync");
+        }
+        if (rc) {
+            cudaStreamSynchronize(st);
+            cudaFree(b->base);
+            delete b;
+            return rc;
+        }
     }
     *out = b;
     return GRT_OK;

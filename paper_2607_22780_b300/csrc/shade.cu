@@ -175,7 +175,7 @@ thread_local PhaseTiming g_timing;
 
 template <bool COUNT, int CAP>
 int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, const SaveBufs* save = nullptr,
-             const RelightDev* rel = nullptr) {
+             const RelightDev* rel = nullptr, const MeshDev* mesh = nullptr) {
     long long rays = 0, units = 0;
     for (int i = 0; i < T.n_jobs; ++i) {
         ShadeJob& J = T.job[i];
@@ -211,6 +211,9 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
             k_trace_rays<K, COUNT, CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, counters);
         } else if (save) {
             if constexpr (CAP == 1) launch_trace_save<K, CAP>(T, dirs, res, save->hits, next_ray, gr, st);
+        } else if (rel && mesh) {
+            if constexpr (CAP == 1)
+                k_trace_rays_mesh<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, *rel, *mesh);
         } else if (rel) {
             if constexpr (CAP == 1) launch_trace_relight<K, CAP>(T, dirs, res, *rel, next_ray, gr, st);
         } else {
@@ -371,6 +374,40 @@ extern "C" int grt_shade_backward_material(const grt_bvh* b, const grt_surfels* 
     cudaFreeAsync(buf, st);
     if (err != cudaSuccess) return check_cuda(err, "material adjoint kernels");
     return GRT_OK;
+}
+
+extern "C" int grt_shade_relight_mesh(const grt_bvh* b, const grt_mesh* m, const grt_trace_params* p,
+                                      const grt_gbuffer* g, const grt_envmap* e, const void* prefiltered,
+                                      const grt_sampling* smp, const int32_t* pixel_list, int32_t n_pixels,
+                                      float* out_color, float* out_vis, float* out_ind, void* stream) {
+    if (!b || !m) return set_error(GRT_ERR_ARG, "mesh bvh or mesh is NULL");
+    if (m->n_triangles != b->n) return set_error(GRT_ERR_ARG, "mesh has %d triangles, the tree %d", m->n_triangles, b->n);
+    if (m->n_triangles > 0 && (!m->tri || !m->normal || !m->albedo || !m->rough || !m->metal))
+        return set_error(GRT_ERR_ARG, "mesh attributes must be non-NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (n_pixels > 0 && !out_color) return set_error(GRT_ERR_ARG, "out_color is NULL");
+    if (!prefiltered || ((uintptr_t)prefiltered & 15))
+        return set_error(GRT_ERR_ARG, "prefiltered must be a 16-byte aligned device pointer");
+    grt_surfels none{};
+    none.n = b->n;
+    none.color_dim = 3;
+    JobTable<1> T;
+    T.P = to_params(*p);
+    T.n_jobs = 1;
+    rc = make_job(b, &none, g, e, smp, pixel_list, n_pixels, out_color, out_vis, out_ind, &T.job[0]);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_pixels == 0) return GRT_OK;
+    if (T.job[0].n_pixels == 0) {
+        k_zero_outputs<<<(n_pixels + 255) / 256, 256, 0, st>>>(out_color, out_vis, out_ind, n_pixels);
+        return launch_error("k_zero_outputs");
+    }
+    const PrefLayout L = pref_layout();
+    const float* f = static_cast<const float*>(prefiltered);
+    const RelightDev E{f + L.diff, f + L.spec, f + L.lut, f + L.poles};
+    const MeshDev M{m->tri, m->normal, m->albedo, m->rough, m->metal, m->n_vertices};
+    return run_jobs<false>(T, p->k, nullptr, st, nullptr, &E, &M);
 }
 
 extern "C" int grt_shade_batch(const grt_shade_request* req, int32_t n_req, const grt_trace_params* p,

@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "common_args.cuh"
+#include "mesh.cuh"
 #include "relight.cuh"
 #include "shade.cuh"
 
@@ -418,6 +419,39 @@ inline void launch_trace_relight(const JobTable<CAP>& T, const float4* dirs, flo
     long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
     if (grid > blocks_max) grid = blocks_max;
     k_trace_rays_relight<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, E, next_ray);
+}
+
+// Relighting rays with the mesh backend of Eq. 14: closest triangle hit, one thread per
+// ray; res = (SplitSum of the hit, 0) or (0, 0, 0, 1) for a miss.
+template <int CAP>
+__global__ void __launch_bounds__(kShadeThreads) k_trace_rays_mesh(const __grid_constant__ JobTable<CAP> T,
+                                                                   const float4* __restrict__ dirs,
+                                                                   float4* __restrict__ res,
+                                                                   const __grid_constant__ RelightDev E,
+                                                                   const __grid_constant__ MeshDev M) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= T.total_rays) return;
+    const float4 dw = __ldg(dirs + r);
+    if (dw.w == 0.f) {
+        res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
+        return;
+    }
+    const ShadeJob& J = T.job[T.find_ray(r)];
+    const int li = (int)((r - J.ray_begin) / J.Nr);
+    const int pix = J.pixel_list ? __ldg(J.pixel_list + li) : J.pixel_offset + li;
+    const f3 o = mk3(__ldg(J.gb.pos + 3 * (size_t)pix), __ldg(J.gb.pos + 3 * (size_t)pix + 1),
+                     __ldg(J.gb.pos + 3 * (size_t)pix + 2));
+    const f3 d = mk3(dw.x, dw.y, dw.z);
+    const MeshHit h = mesh_closest(J.bvh, o, d, T.P.t_min, T.P.t_max);
+    if (h.id < 0) {
+        res[r] = make_float4(0.f, 0.f, 0.f, 1.f);
+        return;
+    }
+    float a[3], rr, mm, ss[3];
+    f3 n;
+    mesh_attr(M, h, d, J.bvh.status, a, &rr, &mm, &n);
+    splitsum_d(E, J.env, a, rr, mm, n, mk3(-d.x, -d.y, -d.z), ss);
+    res[r] = make_float4(ss[0], ss[1], ss[2], 0.f);
 }
 
 // Persistent forward trace of every ray of the table (per-ray (c_rt, T) into res).
