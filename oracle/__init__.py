@@ -502,9 +502,6 @@ def shade_relight(scene, gb, env, pre, n_cos, n_ggx, n_env, seed, brdf=1, pixels
 
 # ----------------------------------------------------------------------------- mesh backend
 
-FLAG_MESH = 16
-
-
 class _Mesh(C.Structure):
     _fields_ = [("nv", C.c_int), ("nt", C.c_int), ("pos", C.c_void_p), ("tri", C.c_void_p), ("normal", C.c_void_p),
                 ("albedo", C.c_void_p), ("rough", C.c_void_p), ("metal", C.c_void_p)]
@@ -519,7 +516,8 @@ def _mesh(m, keep):
 
 def mesh_trace_attr(mesh, ray_o, ray_d, params=None, nthreads=0):
     """Trace_attr (Eq. 14), mesh backend: V[R] (0 hit, 1 miss), albedo[R,3], rough[R],
-    metal[R], normal[R,3], flags[R] (FLAG_MESH near an edge or a tie)."""
+    metal[R], normal[R,3], flags[R] (always 0: the hit is decided in FP32, as in the kernel,
+    by the watertight ray/triangle test)."""
     keep = _Keep()
     m = _mesh(mesh, keep); P = _params(params)
     ro = _f32(ray_o).reshape(-1, 3); rd = _f32(ray_d).reshape(-1, 3)

@@ -1580,14 +1580,29 @@ int or_backward_material(const or_scene* sc, const or_params* P, const or_gbuf* 
     return 0;
 }
 
-/* ---------------------------------------------------------------- mesh backend (FP64) */
+/* ---------------------------------------------------------------- mesh backend */
 /* Sec. III-E: the mesh backend answers Eq. 14 with the closest hit of the ray against a
  * triangle mesh: a miss gives V_r = 1 and zero attributes; a hit gives V_r = 0 and the
  * barycentric interpolation of the hit triangle's per-vertex albedo, roughness, metallic
- * and normal (normalised, turned towards the ray origin).  Intersection by the
- * Moeller-Trumbore test in FP64 over every triangle; the nearest t in (t_min, t_max) wins,
- * equal t by triangle index.  Flags: a barycentric coordinate within 1e-6 of an edge, a
- * second hit within 1e-6 (relative) of the nearest, or t within 1e-6 of t_min. */
+ * and normal (normalised, turned towards the ray origin).  Every triangle is tested; the
+ * nearest t in (t_min, t_max) wins, equal t by triangle index.
+ *
+ * Which triangle a ray hits is an integer outcome, so (part A) it is decided in FP32 by
+ * one fixed sequence of correctly rounded operations, the kernel's too: the watertight
+ * ray/triangle test of Woop, Benthin and Wald (JCGT 2(1), 2013), two-sided:
+ *   kz = the axis of the largest |d| (the first on ties), kx = kz+1 mod 3, ky = kx+1 mod 3;
+ *   Sx = d[kx]/d[kz], Sy = d[ky]/d[kz], Sz = 1/d[kz];
+ *   A = v0 - o, B = v1 - o, C = v2 - o; for P in {A, B, C}: Px = P[kx] - Sx P[kz],
+ *   Py = P[ky] - Sy P[kz];
+ *   U = Cx By - Cy Bx, V = Ax Cy - Ay Cx, W = Bx Ay - By Ax (two rounded products, then
+ *   their rounded difference); if one of U, V, W is 0 all three are recomputed from the
+ *   same FP32 operands in FP64 (exact products, one rounding) and rounded to FP32;
+ *   a hit needs U, V, W of one sign (zeros allowed) and det = (U + V) + W != 0;
+ *   t = ((U (Sz A[kz]) + V (Sz B[kz])) + W (Sz C[kz])) / det in (t_min, t_max).
+ * An edge shared by two triangles is evaluated from the same vertex values in both, to
+ * the same magnitude with opposite sign, so no ray passes between them.  The barycentric
+ * weights of (v0, v1, v2), continuous quantities, come from FP64 Moeller-Trumbore on the
+ * chosen triangle. */
 typedef struct or_mesh_s {
     int nv, nt;
     const float *pos;
@@ -1595,45 +1610,67 @@ typedef struct or_mesh_s {
     const float *normal, *albedo, *rough, *metal;
 } or_mesh;
 
-#define OR_FLAG_MESH 16
-
 static d3 crossd(d3 a, d3 b) { return md3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+
+static inline float f3c(f3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+/* The ray's shear (kx, ky, kz, Sx, Sy, Sz). */
+typedef struct { f3 o; int kx, ky, kz; float Sx, Sy, Sz; } wt_ray;
+
+static wt_ray wt_setup(f3 o, f3 d) {
+    wt_ray r;
+    r.o = o;
+    int kz = 0;
+    if (fabsf(d.y) > fabsf(f3c(d, kz))) kz = 1;
+    if (fabsf(d.z) > fabsf(f3c(d, kz))) kz = 2;
+    r.kz = kz; r.kx = (kz + 1) % 3; r.ky = (r.kx + 1) % 3;
+    float dz = f3c(d, kz);
+    r.Sx = f3c(d, r.kx) / dz;
+    r.Sy = f3c(d, r.ky) / dz;
+    r.Sz = 1.0f / dz;
+    return r;
+}
+
+/* 1 and (t, U, V, W, det) for a hit with t in (t_min, t_max); 0 otherwise. */
+static int wt_hit(const wt_ray* r, const float* p0, const float* p1, const float* p2, float tmin, float tmax,
+                  float* t_out, float* U_out, float* V_out, float* W_out, float* det_out) {
+    f3 A = mk3(p0[0] - r->o.x, p0[1] - r->o.y, p0[2] - r->o.z);
+    f3 B = mk3(p1[0] - r->o.x, p1[1] - r->o.y, p1[2] - r->o.z);
+    f3 C = mk3(p2[0] - r->o.x, p2[1] - r->o.y, p2[2] - r->o.z);
+    float Az = f3c(A, r->kz), Bz = f3c(B, r->kz), Cz = f3c(C, r->kz);
+    float Ax = f3c(A, r->kx) - r->Sx * Az, Ay = f3c(A, r->ky) - r->Sy * Az;
+    float Bx = f3c(B, r->kx) - r->Sx * Bz, By = f3c(B, r->ky) - r->Sy * Bz;
+    float Cx = f3c(C, r->kx) - r->Sx * Cz, Cy = f3c(C, r->ky) - r->Sy * Cz;
+    float U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return 0;
+    float det = (U + V) + W;
+    if (det == 0.0f) return 0;
+    float T = (U * (r->Sz * Az) + V * (r->Sz * Bz)) + W * (r->Sz * Cz);
+    float t = T / det;
+    if (!(t > tmin && t < tmax)) return 0;
+    *t_out = t; *U_out = U; *V_out = V; *W_out = W; *det_out = det;
+    return 1;
+}
 
 static void mesh_attr_one(const or_mesh* m, const or_params* P, f3 o32, f3 d32, double* V, double a[3],
                           double* r, double* mm, double n[3], uint32_t* flags) {
-    d3 o = f2d(o32), d = f2d(d32);
-    double best = (double)P->t_max, second = (double)P->t_max, bu = 0, bv = 0;
+    (void)flags;
+    wt_ray ray = wt_setup(o32, d32);
+    float best = P->t_max, bU = 0, bV = 0, bW = 0, bdet = 1;
     int bt = -1;
     for (int t = 0; t < m->nt; ++t) {
         const float* p0 = m->pos + 3 * (size_t)m->tri[3 * t];
         const float* p1 = m->pos + 3 * (size_t)m->tri[3 * t + 1];
         const float* p2 = m->pos + 3 * (size_t)m->tri[3 * t + 2];
-        d3 v0 = md3(p0[0], p0[1], p0[2]);
-        d3 e1 = md3(p1[0] - v0.x, p1[1] - v0.y, p1[2] - v0.z), e2 = md3(p2[0] - v0.x, p2[1] - v0.y, p2[2] - v0.z);
-        d3 pv = crossd(d, e2);
-        double det = dotd(e1, pv);
-        if (fabs(det) < 1e-12 * sqrt(dotd(e1, e1) * dotd(e2, e2))) continue;
-        double inv = 1.0 / det;
-        d3 sv = addd(o, muld(v0, -1.0));
-        double u = dotd(sv, pv) * inv;
-        if (u < -1e-6 || u > 1.0 + 1e-6) continue;
-        d3 qv = crossd(sv, e1);
-        double v = dotd(d, qv) * inv;
-        if (v < -1e-6 || u + v > 1.0 + 1e-6) continue;
-        double tt = dotd(e2, qv) * inv;
-        if (!(tt > (double)P->t_min * (1 - 1e-6) && tt < (double)P->t_max)) continue;
-        int inside = u >= 0 && v >= 0 && u + v <= 1.0 && tt > (double)P->t_min;
-        if (!inside || fmin(fmin(u, v), 1.0 - u - v) < 1e-6 || fabs(tt - (double)P->t_min) < 1e-6 * (double)P->t_min)
-            *flags |= OR_FLAG_MESH;  /* near an edge or t_min: a decision FP32 may take the other way */
-        if (!inside) continue;
-        if (tt < best) {
-            second = best;
-            best = tt; bu = u; bv = v; bt = t;
-        } else if (tt < second) {
-            second = tt;
-        }
+        float tt, U, Vv, W, det;
+        if (!wt_hit(&ray, p0, p1, p2, P->t_min, best, &tt, &U, &Vv, &W, &det)) continue;
+        best = tt; bU = U; bV = Vv; bW = W; bdet = det; bt = t;   /* strict <: the lower index keeps a tie */
     }
-    if (bt >= 0 && second < (double)P->t_max && fabs(second - best) <= 1e-6 * best) *flags |= OR_FLAG_MESH;
     if (bt < 0) {
         *V = 1.0;
         a[0] = a[1] = a[2] = 0; *r = 0; *mm = 0; n[0] = n[1] = n[2] = 0;
@@ -1641,7 +1678,21 @@ static void mesh_attr_one(const or_mesh* m, const or_params* P, f3 o32, f3 d32, 
     }
     *V = 0.0;
     const int32_t* tv = m->tri + 3 * bt;
-    double w[3] = {1.0 - bu - bv, bu, bv};
+    /* the weights are continuous: FP64 Moeller-Trumbore on the chosen triangle */
+    double w[3] = {(double)bU / bdet, (double)bV / bdet, (double)bW / bdet};
+    {
+        const float *p0 = m->pos + 3 * (size_t)tv[0], *p1 = m->pos + 3 * (size_t)tv[1], *p2 = m->pos + 3 * (size_t)tv[2];
+        d3 v0 = md3(p0[0], p0[1], p0[2]), d = f2d(d32);
+        d3 e1 = md3((double)p1[0] - v0.x, (double)p1[1] - v0.y, (double)p1[2] - v0.z);
+        d3 e2 = md3((double)p2[0] - v0.x, (double)p2[1] - v0.y, (double)p2[2] - v0.z);
+        d3 pv = crossd(d, e2), sv = addd(f2d(o32), muld(v0, -1.0)), qv = crossd(sv, e1);
+        double det = dotd(e1, pv);
+        if (det != 0.0) {
+            w[1] = dotd(sv, pv) / det;
+            w[2] = dotd(d, qv) / det;
+            w[0] = 1.0 - w[1] - w[2];
+        }
+    }
     double na[3] = {0, 0, 0};
     a[0] = a[1] = a[2] = 0; *r = 0; *mm = 0;
     for (int k = 0; k < 3; ++k) {
@@ -1654,7 +1705,7 @@ static void mesh_attr_one(const or_mesh* m, const or_params* P, f3 o32, f3 d32, 
         *mm += w[k] * m->metal[vi];
     }
     double nl = sqrt(na[0] * na[0] + na[1] * na[1] + na[2] * na[2]);
-    double sgn = (na[0] * d.x + na[1] * d.y + na[2] * d.z) > 0 ? -1.0 : 1.0;
+    double sgn = (na[0] * (double)d32.x + na[1] * (double)d32.y + na[2] * (double)d32.z) > 0 ? -1.0 : 1.0;
     for (int ch = 0; ch < 3; ++ch) n[ch] = nl > 0 ? sgn * na[ch] / nl : 0.0;
 }
 

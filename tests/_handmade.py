@@ -48,3 +48,28 @@ def random_gbuffer(rng, P, eye=(0.0, 0.0, 5.0)):
     n[flip] *= -1
     return gbuffer(pos, n, rng.uniform(0.05, 1.0, size=(P, 3)), rng.uniform(0.1, 1.0, P),
                    (rng.uniform(size=P) < 0.5).astype(np.float32), eye)
+
+
+def icosphere(levels):
+    """Closed unit icosphere with shared vertices (each edge split at its midpoint, pushed
+    to the sphere), every face wound outwards."""
+    g = (1 + 5 ** 0.5) / 2
+    v = [(-1, g, 0), (1, g, 0), (-1, -g, 0), (1, -g, 0), (0, -1, g), (0, 1, g), (0, -1, -g), (0, 1, -g),
+         (g, 0, -1), (g, 0, 1), (-g, 0, -1), (-g, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6),
+         (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10),
+         (8, 6, 7), (9, 8, 1)]
+    v = [np.array(x, float) / np.linalg.norm(x) for x in v]
+    for _ in range(levels):
+        mid = {}
+
+        def m_(a, b):
+            k = (min(a, b), max(a, b))
+            if k not in mid:
+                x = v[a] + v[b]
+                v.append(x / np.linalg.norm(x))
+                mid[k] = len(v) - 1
+            return mid[k]
+        f = [t for a, b, c in f for t in ((a, m_(a, b), m_(c, a)), (b, m_(b, c), m_(a, b)),
+                                          (c, m_(c, a), m_(b, c)), (m_(a, b), m_(b, c), m_(c, a)))]
+    return np.array(v), np.array(f)

@@ -1,14 +1,14 @@
-"""GPU parity of the mesh backend of Eq. 14 (Sec. III-E) against the FP64 oracle: the LBVH of
-triangles, the closest hit and its barycentric attributes per ray (1e-4; normals 5e-4), and
-the relit MIS estimate on unflagged pixels within 1e-4 max(1, |ref|).  Rays or pixels the
-oracle flags (a hit within 1e-6 of an edge or of t_min, a near tie) may be decided either way
-in FP32 and are left out."""
+"""GPU parity of the mesh backend of Eq. 14 (Sec. III-E) against the oracle: the LBVH of
+triangles, the closest hit (decided in FP32 by the same watertight test on both sides, so
+hit or miss agrees on every ray) and its barycentric attributes (1e-4; normals 5e-4), and
+the relit MIS estimate within 1e-4 max(1, |ref|)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from tests._gpu import hdr_tol, random_rays, t, unflagged, upsample_gbuffer
+from tests._handmade import icosphere
 from paper_2607_22780_b300 import _lib as L, api, workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -30,12 +30,12 @@ def _attr(M, o, d, params=None):
 def _check_attr(got, ref, min_hits):
     V, a, r, m, n = got
     keep = unflagged(ref["flags"])
-    assert keep.mean() > 0.98 and (ref["V"][keep] == 0).sum() >= min_hits
+    assert keep.all() and (ref["V"] == 0).sum() >= min_hits
     np.testing.assert_array_equal(V[keep], ref["V"][keep])
     for x, want, tol in ((a, ref["albedo"], 1e-4), (r, ref["rough"], 1e-4), (m, ref["metal"], 1e-4),
                          (n, ref["normal"], 5e-4)):
         err = np.abs(x - want).reshape(len(V), -1).max(1)
-        assert err[keep].max() < tol, (tol, err[keep].max())
+        assert err[keep].max() < tol, (tol, np.nonzero(keep & (err >= tol))[0][:8], err[keep].max())
 
 
 def test_single_triangle_closed_form():
@@ -85,6 +85,25 @@ def test_trace_attr_matches_oracle(res):
     assert M.status() == 0
 
 
+def test_closed_mesh_blocks_every_ray_from_inside():
+    # watertightness: rays from inside a closed icosphere, many aimed exactly at shared
+    # vertices and edge midpoints, all hit
+    v, f = icosphere(4)
+    m = _mesh(1.7 * v + [0.2, -0.1, 0.3], f, normal=v)
+    rng = np.random.default_rng(9)
+    c = np.array([0.2, -0.1, 0.3]) + rng.uniform(-0.3, 0.3, (8, 3))
+    tgt = np.concatenate([m.pos, 0.5 * (m.pos[f[:, 0]] + m.pos[f[:, 1]])])
+    o = np.repeat(c, len(tgt), 0).astype(np.float32)
+    dd = np.tile(tgt, (len(c), 1)) - o
+    d = (dd / np.linalg.norm(dd, axis=1, keepdims=True)).astype(np.float32)
+    M = api.MeshScene.from_workload(m)
+    V, a, r, mm, n = _attr(M, o, d)
+    assert (V == 0).all()
+    sub = np.random.default_rng(1).choice(len(o), 2000, replace=False)
+    _check_attr([x[sub] for x in (V, a, r, mm, n)], oracle.mesh_trace_attr(m, o[sub], d[sub]), 2000)
+    assert M.status() == 0
+
+
 def test_bad_vertex_index_is_reported():
     m = _mesh([[0, 0, 0], [1, 0, 0], [0, 1, 0]], [[0, 1, 7]])
     M = api.MeshScene.from_workload(m)
@@ -94,7 +113,7 @@ def test_bad_vertex_index_is_reported():
 
 def _check_relit(got, ref, pix=None):
     m = unflagged(ref["flags"])
-    assert m.mean() > 0.9, m.mean()
+    assert m.mean() > 0.95, m.mean()
     for a, r in zip(got, (ref["color"], ref["vis"], ref["ind"])):
         a = a.cpu().numpy()
         if pix is not None:

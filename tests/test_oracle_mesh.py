@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from tests._handmade import gbuffer, random_gbuffer, scene
+from tests._handmade import gbuffer, icosphere, random_gbuffer, scene
 from paper_2607_22780_b300 import workloads as wl
 
 
@@ -32,8 +32,10 @@ def test_single_triangle_barycentric_attributes():
     np.testing.assert_allclose(r["normal"][0], [0, 0, -1], atol=1e-12)   # turned towards the origin
     miss = oracle.mesh_trace_attr(m, np.array([[0.8, 0.8, -1.0]], np.float32), d)
     assert miss["V"][0] == 1 and not miss["albedo"].any()
+    # on the hypotenuse: an edge hit, weights (0, 1/2, 1/2)
     edge = oracle.mesh_trace_attr(m, np.array([[0.5, 0.5, -1.0]], np.float32), d)
-    assert edge["flags"][0] & oracle.FLAG_MESH
+    assert edge["V"][0] == 0
+    np.testing.assert_allclose(edge["albedo"][0], [0, 0.5, 0.5], atol=1e-12)
 
 
 def test_nearest_of_stacked_triangles_and_t_range():
@@ -48,11 +50,14 @@ def test_nearest_of_stacked_triangles_and_t_range():
     assert oracle.mesh_trace_attr(m, o, d, params=p)["V"][0] == 1          # both beyond t_max
 
 
-def _brute_hits(m, o, d):
+def _brute_hits(m, o, d, tmin=0.01):
+    """FP64 closest hit per ray by Cramer's rule over every triangle, and whether the ray is
+    clear of FP32 ambiguity: no triangle within 1e-4 (barycentric) of its boundary in front
+    of the origin, and the two nearest hits more than 1e-5 (relative) apart."""
     p = m.pos.astype(np.float64); t = m.tri
     v0, v1, v2 = p[t[:, 0]], p[t[:, 1]], p[t[:, 2]]
     e1, e2 = v1 - v0, v2 - v0
-    best = np.full(len(o), np.inf); arg = np.full(len(o), -1)
+    best = np.full(len(o), np.inf); arg = np.full(len(o), -1); clear = np.ones(len(o), bool)
     for i in range(len(o)):
         di = d[i].astype(np.float64); oi = o[i].astype(np.float64)
         # solve oi + t di = v0 + u e1 + v e2 by Cramer's rule per triangle
@@ -63,11 +68,18 @@ def _brute_hits(m, o, d):
         sol = np.full((len(t), 3), np.nan)
         sol[ok] = np.linalg.solve(M[ok], rhs[ok][..., None])[..., 0]
         tt, u, v = sol[:, 0], sol[:, 1], sol[:, 2]
-        hit = ok & (u >= 0) & (v >= 0) & (u + v <= 1) & (tt > 0.01)
+        margin = np.minimum(np.minimum(u, v), 1 - u - v)
+        front = ok & (tt > tmin)
+        hit = front & (margin >= 0)
+        if (front & (np.abs(margin) < 1e-4)).any():
+            clear[i] = False
         if hit.any():
+            ts = np.sort(tt[hit])
             j = np.argmin(np.where(hit, tt, np.inf))
             best[i], arg[i] = tt[j], j
-    return best, arg
+            if len(ts) > 1 and ts[1] - ts[0] <= 1e-5 * ts[0]:
+                clear[i] = False
+    return best, arg, clear
 
 
 def test_closest_hit_against_independent_brute_force():
@@ -77,8 +89,8 @@ def test_closest_hit_against_independent_brute_force():
     tg = rng.uniform(-1.0, 0.5, (150, 3))
     d = tg - o; d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
     r = oracle.mesh_trace_attr(m, o, d)
-    best, arg = _brute_hits(m, o, d)
-    keep = r["flags"] == 0
+    assert not r["flags"].any()
+    best, arg, keep = _brute_hits(m, o, d)
     assert keep.mean() > 0.9 and (best[keep] < np.inf).sum() > 50
     np.testing.assert_array_equal(r["V"][keep] == 0, best[keep] < np.inf)
     hit = keep & (best < np.inf)
@@ -94,6 +106,25 @@ def test_closest_hit_against_independent_brute_force():
     w[:, 2] = np.linalg.norm(np.cross(v0 - x, v1 - x), axis=1) / tot
     alb = (w[..., None] * m.albedo[tri]).sum(1)
     np.testing.assert_allclose(r["albedo"][hit], alb, atol=1e-6)
+
+
+def test_closed_mesh_blocks_every_ray_from_inside():
+    # watertightness: seen from inside a closed mesh every ray hits, including rays aimed
+    # exactly at shared vertices and edge midpoints, where a test that is not watertight
+    # lets rays through the cracks between neighbours
+    v, f = icosphere(3)
+    m = _mesh(1.7 * v + [0.2, -0.1, 0.3], f, normal=v)
+    rng = np.random.default_rng(9)
+    c = np.array([0.2, -0.1, 0.3]) + rng.uniform(-0.3, 0.3, (4, 3))
+    tgt = np.concatenate([m.pos, 0.5 * (m.pos[f[:, 0]] + m.pos[f[:, 1]]), rng.normal(size=(500, 3))])
+    o = np.repeat(c, len(tgt), 0).astype(np.float32)
+    dd = np.tile(tgt, (len(c), 1)) - np.repeat(c, len(tgt), 0)
+    dd[len(tgt) - 500:len(tgt)] = tgt[-500:]
+    d = (dd / np.linalg.norm(dd, axis=1, keepdims=True)).astype(np.float32)
+    r = oracle.mesh_trace_attr(m, o, d)
+    assert (r["V"] == 0).all()
+    # hit normals are turned towards the (inside) origin
+    assert (np.einsum("ij,ij->i", r["normal"], d) < 0).all()
 
 
 def test_relight_reductions():
