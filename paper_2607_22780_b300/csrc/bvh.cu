@@ -254,7 +254,7 @@ __global__ void k_sort_scatter(const MortonKey* __restrict__ keys_in, const int*
 
 // ---------------------------------------------------------------- triangles (mesh backend)
 // The same tree over triangles: each leaf is one triangle, bounded by the box of its three
-// vertices; the record of leaf j is (v0, triangle id), (v1 - v0), (v2 - v0), unused.
+// vertices; the record of leaf j is (v0, triangle id), (v1, 0), (v2, 0), unused.
 struct TriIn {
     const float* pos;
     const int* tri;
@@ -308,8 +308,8 @@ __global__ void k_tri_records(TriIn t, const int* __restrict__ sorted, float4* _
     tri_box(t, i, lo, hi, v);
     float4* rec = records + 4 * (size_t)j;
     rec[0] = make_float4(v[0].x, v[0].y, v[0].z, __int_as_float(i));
-    rec[1] = make_float4(v[1].x - v[0].x, v[1].y - v[0].y, v[1].z - v[0].z, 0.f);
-    rec[2] = make_float4(v[2].x - v[0].x, v[2].y - v[0].y, v[2].z - v[0].z, 0.f);
+    rec[1] = make_float4(v[1].x, v[1].y, v[1].z, 0.f);
+    rec[2] = make_float4(v[2].x, v[2].y, v[2].z, 0.f);
     rec[3] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {

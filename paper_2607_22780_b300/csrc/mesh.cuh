@@ -1,10 +1,21 @@
 // mesh.cuh -- mesh backend of the relighting query (Sec. III-E): closest triangle hit in the
 // 4-wide LBVH built by grt_build_mesh_bvh, and the barycentric attributes of Eq. 14.
 //
-// Leaf records (64 bytes, one triangle): (v0, triangle id), (v1 - v0), (v2 - v0), unused.
-// Intersection by the Moeller-Trumbore test; the nearest t in (t_min, t_max) wins, equal t
-// by triangle index.  The walk visits children near to far and culls every box beyond the
-// nearest hit found so far.
+// Leaf records (64 bytes, one triangle): (v0, triangle id), (v1, 0), (v2, 0), unused.
+// Which triangle a ray hits is decided in FP32 by the watertight ray/triangle test of Woop,
+// Benthin and Wald (JCGT 2(1), 2013), two-sided, through one fixed sequence of correctly
+// rounded operations (no contraction into FMA):
+//   kz = the axis of the largest |d| (the first on ties), kx = kz+1 mod 3, ky = kx+1 mod 3;
+//   Sx = d[kx]/d[kz], Sy = d[ky]/d[kz], Sz = 1/d[kz];
+//   A = v0 - o, B = v1 - o, C = v2 - o;  Px = P[kx] - Sx P[kz], Py = P[ky] - Sy P[kz];
+//   U = Cx By - Cy Bx, V = Ax Cy - Ay Cx, W = Bx Ay - By Ax, recomputed in FP64 from the
+//   same operands (exact products, one rounding) when one of them is 0;
+//   hit iff U, V, W share a sign (zeros allowed) and det = (U + V) + W != 0, and
+//   t = ((U (Sz A[kz]) + V (Sz B[kz])) + W (Sz C[kz])) / det lies in (t_min, t_max).
+// A shared edge gives the two triangles edge functions of equal magnitude and opposite
+// sign, so no ray passes between neighbours.  The nearest t wins, equal t by triangle
+// index; the weights of (v0, v1, v2) are (U, V, W) / det.  The walk visits children near to
+// far and culls every box beyond the nearest hit found so far.
 #pragma once
 
 #include "relight.cuh"
@@ -19,16 +30,37 @@ struct MeshDev {
 };
 
 struct MeshHit {
-    int id;       // triangle index, -1 for a miss
-    float u, v;   // barycentrics of v1 and v2
+    int id;        // triangle index, -1 for a miss
+    float w[3];    // barycentric weights of v0, v1, v2
 };
 
-__device__ __forceinline__ f3 cross3(f3 a, f3 b) {
-    return mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+// The ray's shear for the watertight test.
+struct ShearRay {
+    f3 o;
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float comp(f3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+__device__ __forceinline__ ShearRay shear_ray(f3 o, f3 d) {
+    ShearRay r;
+    r.o = o;
+    int kz = 0;
+    if (fabsf(d.y) > fabsf(comp(d, kz))) kz = 1;
+    if (fabsf(d.z) > fabsf(comp(d, kz))) kz = 2;
+    r.kz = kz;
+    r.kx = kz == 2 ? 0 : kz + 1;
+    r.ky = r.kx == 2 ? 0 : r.kx + 1;
+    const float dz = comp(d, kz);
+    r.Sx = __fdiv_rn(comp(d, r.kx), dz);
+    r.Sy = __fdiv_rn(comp(d, r.ky), dz);
+    r.Sz = __fdiv_rn(1.f, dz);
+    return r;
 }
 
-__device__ __forceinline__ void mesh_test_leaf(const DevBvh& bvh, int ref, const RayState& r, float tmin, float tmax,
-                                               float& best, MeshHit& h) {
+__device__ __forceinline__ void mesh_test_leaf(const DevBvh& bvh, int ref, const ShearRay& r, float tmin, float& best,
+                                               MeshHit& h) {
     const int first = leaf_first(ref), count = leaf_count(ref);
     if (first + count > bvh.n) {
         atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
@@ -37,43 +69,83 @@ __device__ __forceinline__ void mesh_test_leaf(const DevBvh& bvh, int ref, const
     for (int i = 0; i < count; ++i) {
         const float4* R = bvh.records + 4 * (size_t)(first + i);
         const float4 r0 = __ldg(R), r1 = __ldg(R + 1), r2 = __ldg(R + 2);
-        const f3 e1 = mk3(r1.x, r1.y, r1.z), e2 = mk3(r2.x, r2.y, r2.z);
-        const f3 pv = cross3(r.d, e2);
-        const float det = dot3(e1, pv);
-        if (!(fabsf(det) >= 1e-12f * sqrtf(dot3(e1, e1) * dot3(e2, e2)))) continue;
-        const float inv = 1.f / det;
-        const f3 sv = mk3(r.o.x - r0.x, r.o.y - r0.y, r.o.z - r0.z);
-        const float u = dot3(sv, pv) * inv;
-        if (u < 0.f || u > 1.f) continue;
-        const f3 qv = cross3(sv, e1);
-        const float v = dot3(r.d, qv) * inv;
-        if (v < 0.f || u + v > 1.f) continue;
-        const float t = dot3(e2, qv) * inv;
-        if (!(t > tmin && t < tmax)) continue;
+        const f3 A = mk3(__fsub_rn(r0.x, r.o.x), __fsub_rn(r0.y, r.o.y), __fsub_rn(r0.z, r.o.z));
+        const f3 B = mk3(__fsub_rn(r1.x, r.o.x), __fsub_rn(r1.y, r.o.y), __fsub_rn(r1.z, r.o.z));
+        const f3 C = mk3(__fsub_rn(r2.x, r.o.x), __fsub_rn(r2.y, r.o.y), __fsub_rn(r2.z, r.o.z));
+        const float Az = comp(A, r.kz), Bz = comp(B, r.kz), Cz = comp(C, r.kz);
+        const float Ax = __fsub_rn(comp(A, r.kx), __fmul_rn(r.Sx, Az)), Ay = __fsub_rn(comp(A, r.ky), __fmul_rn(r.Sy, Az));
+        const float Bx = __fsub_rn(comp(B, r.kx), __fmul_rn(r.Sx, Bz)), By = __fsub_rn(comp(B, r.ky), __fmul_rn(r.Sy, Bz));
+        const float Cx = __fsub_rn(comp(C, r.kx), __fmul_rn(r.Sx, Cz)), Cy = __fsub_rn(comp(C, r.ky), __fmul_rn(r.Sy, Cz));
+        float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+        float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+        float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+        if (U == 0.f || V == 0.f || W == 0.f) {
+            U = __double2float_rn(__dsub_rn(__dmul_rn(Cx, By), __dmul_rn(Cy, Bx)));
+            V = __double2float_rn(__dsub_rn(__dmul_rn(Ax, Cy), __dmul_rn(Ay, Cx)));
+            W = __double2float_rn(__dsub_rn(__dmul_rn(Bx, Ay), __dmul_rn(By, Ax)));
+        }
+        if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) continue;
+        const float det = __fadd_rn(__fadd_rn(U, V), W);
+        if (det == 0.f) continue;
+        const float T = __fadd_rn(__fadd_rn(__fmul_rn(U, __fmul_rn(r.Sz, Az)), __fmul_rn(V, __fmul_rn(r.Sz, Bz))),
+                                  __fmul_rn(W, __fmul_rn(r.Sz, Cz)));
+        const float t = __fdiv_rn(T, det);
+        if (!(t > tmin && t <= best)) continue;
         const int id = __float_as_int(r0.w);
-        if (t < best || (t == best && id < h.id)) {
+        if (h.id < 0 || t < best || id < h.id) {
             best = t;
             h.id = id;
-            h.u = u;
-            h.v = v;
+            const float inv = 1.f / det;
+            h.w[0] = U * inv;
+            h.w[1] = V * inv;
+            h.w[2] = W * inv;
         }
     }
 }
 
 // Closest hit of the ray (o, d) with t in (tmin, tmax).
 __device__ __forceinline__ MeshHit mesh_closest(const DevBvh& bvh, f3 o, f3 d, float tmin, float tmax) {
-    MeshHit h{-1, 0.f, 0.f};
+    MeshHit h{-1, {0.f, 0.f, 0.f}};
     if (bvh.n == 0 || bvh.root == kRefEmpty) return h;
     const RayState r = make_ray(o, d);
-    float best = tmax;
+    const ShearRay sr = shear_ray(o, d);
+    // best starts just below t_max: a hit needs t < t_max, and t <= best afterwards keeps
+    // equal-t hits for the index tie-break
+    float best = __int_as_float(__float_as_int(tmax) - 1);
     if (bvh.root < 0) {  // a single triangle
-        mesh_test_leaf(bvh, bvh.root, r, tmin, tmax, best, h);
+        mesh_test_leaf(bvh, bvh.root, sr, tmin, best, h);
         return h;
     }
     int2 stack[kStackDepth];
     int sp = 0, node = bvh.root, budget = bvh.cap + 8;
     const float tlo = fmaf(tmin, 0.99999f, -r.eps);
     const int ox = r.inv.x >= 0.f ? 0 : 3, oy = r.inv.y >= 0.f ? 1 : 4, oz = r.inv.z >= 0.f ? 2 : 5;
+    // Conservative slabs.  fmaf(plane, inv, oinv) differs from (plane - o) / d by at most
+    // 4 * 2^-24 (C + |o|) |inv| on an axis whose planes satisfy |plane| <= C; every slab is
+    // widened by 2^-20 (C + |o|) |inv|, C the largest |coordinate| of the root's boxes, so
+    // that no box whose exact slab interval meets the ray is culled.  Triangles in an
+    // axis-aligned plane have boxes of zero thickness, where an unwidened test drops hits
+    // near the box edges at grazing incidence.
+    f3 oN, oF;
+    {
+        const float4* N = bvh.nodes + 8 * (size_t)bvh.root;
+        const int4 ref = __ldg(reinterpret_cast<const int4*>(N + 6));
+        const int refs[4] = {ref.x, ref.y, ref.z, ref.w};
+        float C[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float4 lo = __ldg(N + a), hi = __ldg(N + 3 + a);
+            const float los[4] = {lo.x, lo.y, lo.z, lo.w}, his[4] = {hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (refs[c] != kRefEmpty) C[a] = fmaxf(C[a], fmaxf(fabsf(los[c]), fabsf(his[c])));
+        }
+        const float sx = 0x1p-20f * (C[0] + fabsf(o.x)) * fabsf(r.inv.x);
+        const float sy = 0x1p-20f * (C[1] + fabsf(o.y)) * fabsf(r.inv.y);
+        const float sz = 0x1p-20f * (C[2] + fabsf(o.z)) * fabsf(r.inv.z);
+        oN = mk3(r.oinv.x - sx, r.oinv.y - sy, r.oinv.z - sz);
+        oF = mk3(r.oinv.x + sx, r.oinv.y + sy, r.oinv.z + sz);
+    }
     while (true) {
         if ((unsigned)node >= (unsigned)bvh.cap || --budget < 0) {
             atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
@@ -93,17 +165,17 @@ __device__ __forceinline__ MeshHit mesh_closest(const DevBvh& bvh, f3 o, f3 d, f
         const float thi0 = fmaf(best, 1.00001f, r.eps);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const float t0 = fmaxf(fmaxf(fmaf(nxs[c], r.inv.x, r.oinv.x), fmaf(nys[c], r.inv.y, r.oinv.y)),
-                                   fmaxf(fmaf(nzs[c], r.inv.z, r.oinv.z), tlo));
-            const float t1 = fminf(fminf(fmaf(fxs[c], r.inv.x, r.oinv.x), fmaf(fys[c], r.inv.y, r.oinv.y)),
-                                   fminf(fmaf(fzs[c], r.inv.z, r.oinv.z), thi0));
+            const float t0 = fmaxf(fmaxf(fmaf(nxs[c], r.inv.x, oN.x), fmaf(nys[c], r.inv.y, oN.y)),
+                                   fmaxf(fmaf(nzs[c], r.inv.z, oN.z), tlo));
+            const float t1 = fminf(fminf(fmaf(fxs[c], r.inv.x, oF.x), fmaf(fys[c], r.inv.y, oF.y)),
+                                   fminf(fmaf(fzs[c], r.inv.z, oF.z), thi0));
             tn[c] = t0;
             hit[c] = t0 <= t1 && refs[c] != kRefEmpty;
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c)
             if (hit[c] && refs[c] < 0) {
-                mesh_test_leaf(bvh, refs[c], r, tmin, tmax, best, h);
+                mesh_test_leaf(bvh, refs[c], sr, tmin, best, h);
                 hit[c] = false;
             }
         const float thi = fmaf(best, 1.00001f, r.eps);
@@ -155,7 +227,7 @@ __device__ __forceinline__ MeshHit mesh_closest(const DevBvh& bvh, f3 o, f3 d, f
 // Barycentric material state of a hit (Eq. 14, mesh backend); the normal faces the ray origin.
 __device__ __forceinline__ void mesh_attr(const MeshDev& M, const MeshHit& h, f3 d, int* status, float a[3], float* r,
                                           float* m, f3* n) {
-    const float w[3] = {1.f - h.u - h.v, h.u, h.v};
+    const float* w = h.w;
     float na[3] = {0.f, 0.f, 0.f};
     a[0] = a[1] = a[2] = 0.f;
     *r = 0.f;
