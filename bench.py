@@ -1,7 +1,7 @@
 """Benchmark of the 2DGRT secondary-ray hot path on synthetic workloads.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grt|reference]
-                    [--mode shade|train|serve] [--no-cpu-baseline]
+                    [--mode shade|train|serve|large|relight] [--no-cpu-baseline]
 
 Default workload (mode "shade"): 300,000 SH surfels on 3 spheres, 2 tori, a box and a
 ground plane; an 800x800 G-buffer; 32 secondary rays per pixel by MIS (16 cosine / 8 GGX /
@@ -14,6 +14,8 @@ L2 loss against a seeded target (shade_pixels + shade_backward).
 Mode "large": 2M surfels (ground plane, 50 primitives, background shell), 1920x1080,
 16 rays/pixel (8/4/4), forward and forward + backward with recomputed hit lists.
 Mode "serve": the relight request loop (see paper_2607_22780_b300.serve).
+Mode "relight": split-sum relighting of the default frame (Eq. 14-15), Gaussian backend and
+mesh backend (the same objects as 310,670 triangles).
 
 Under torchrun every rank renders its own frame (weak scaling, no data-path collective);
 ranks meet only at the barriers around the timed region and in the final max/sum.
@@ -402,6 +404,19 @@ def run_train_only(args):
     print(json.dumps(time_train(api, S, cam, E, torch.device("cuda"), args)), flush=True)
 
 
+def run_relight_only(args):
+    """Relighting of the shading frame only, Gaussian and mesh backends (profiling entry)."""
+    import torch
+    from paper_2607_22780_b300 import api
+    torch.cuda.set_device(0)
+    sc, cam, env = make_inputs(0)
+    S = api.Scene.from_workload(sc, params=api.trace_params(k=args.k))
+    E = api.Environment(torch.from_numpy(env).cuda())
+    G = api.gbuffer_primary(S, cam)
+    R = int(G.valid.sum().item()) * sum(ALLOC)
+    print(json.dumps(time_relight(api, S, G, E, R, args)), flush=True)
+
+
 def time_train(api, S, cam, E, dev, args):
     import torch
     from paper_2607_22780_b300 import workloads as wl
@@ -640,7 +655,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="grt", choices=["grt", "reference"])
-    ap.add_argument("--mode", default="shade", choices=["shade", "serve", "train", "large"])
+    ap.add_argument("--mode", default="shade", choices=["shade", "serve", "train", "large", "relight"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
@@ -663,6 +678,8 @@ def main():
         serve.bench_main(args)
     elif args.mode == "train":
         run_train_only(args)
+    elif args.mode == "relight":
+        run_relight_only(args)
     elif args.mode == "large":
         import torch
         from paper_2607_22780_b300 import api
