@@ -188,36 +188,54 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
     T.total_units = units;
     if (rays == 0) return GRT_OK;
     float4* buf = nullptr;
+    char* order_buf = nullptr;
     float4 *dirs, *res;
     unsigned long long* next_ray;
+    // the persistent walks take their rays in bucket order (the thread-per-ray mesh walk
+    // and the counting pass keep slot order)
+    const bool ord = GRT_RAY_ORDER && !COUNT && !(rel && mesh);
+    const size_t extra = ord ? order_scratch_bytes(rays) : 0;
+    keep_pool_memory();
     if (save) {
         dirs = save->dirs;
         res = save->res;
         next_ray = save->next;
+        if (ord) GRT_CUDA(cudaMallocAsync((void**)&order_buf, extra, st));
     } else {
-        keep_pool_memory();
-        GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1), st));
+        GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1) + extra, st));
         dirs = buf;
         res = buf + rays;
         next_ray = reinterpret_cast<unsigned long long*>(buf + 2 * rays);
+        if (ord) order_buf = reinterpret_cast<char*>(buf + 2 * rays + 1);
     }
     const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
     g_timing.mark(0, st);
-    k_sample_rays<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
+    unsigned *ohist = nullptr, *okeys = nullptr, *oorder = nullptr;
+    if (order_buf) {
+        ohist = reinterpret_cast<unsigned*>(order_buf);
+        okeys = ohist + kAllBuckets;
+        oorder = okeys + rays;
+        cudaMemsetAsync(ohist, 0, 4 * (size_t)kAllBuckets, st);
+    }
+    k_sample_rays<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, okeys, ohist);
+    if (oorder) {
+        k_bucket_scan<<<1, 1024, 0, st>>>(ohist, (int)kAllBuckets);
+        k_ray_scatter<<<(unsigned)((rays + 255) / 256), 256, 0, st>>>(rays, okeys, ohist, oorder);
+    }
     g_timing.mark(1, st);
     dispatch_k(k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
         if (COUNT) {  // counting pass: one ray per thread, same traversal
             k_trace_rays<K, COUNT, CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, counters);
         } else if (save) {
-            if constexpr (CAP == 1) launch_trace_save<K, CAP>(T, dirs, res, save->hits, next_ray, gr, st);
+            if constexpr (CAP == 1) launch_trace_save<K, CAP>(T, dirs, res, save->hits, next_ray, gr, st, oorder);
         } else if (rel && mesh) {
             if constexpr (CAP == 1)
                 k_trace_rays_mesh<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, *rel, *mesh);
         } else if (rel) {
-            if constexpr (CAP == 1) launch_trace_relight<K, CAP>(T, dirs, res, *rel, next_ray, gr, st);
+            if constexpr (CAP == 1) launch_trace_relight<K, CAP>(T, dirs, res, *rel, next_ray, gr, st, oorder);
         } else {
-            launch_trace_dyn<K, CAP>(T, dirs, res, next_ray, gr, st);
+            launch_trace_dyn<K, CAP>(T, dirs, res, next_ray, gr, st, oorder);
         }
     });
     if (!COUNT) {
@@ -229,6 +247,7 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
     }
     cudaError_t e = cudaGetLastError();
     if (buf) cudaFreeAsync(buf, st);
+    else if (order_buf) cudaFreeAsync(order_buf, st);
     if (e != cudaSuccess) return check_cuda(e, "shade kernels");
     return GRT_OK;
 }

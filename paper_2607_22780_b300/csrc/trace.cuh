@@ -619,7 +619,8 @@ constexpr int kPersistentThreads = 128;  // block size of every persistent_trace
 
 template <int K, class Task>
 __device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& P, unsigned long long* next,
-                                                 long long total, int* q, int qstride) {
+                                                 long long total, int* q, int qstride,
+                                                 const unsigned* __restrict__ order = nullptr) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     SplitStack stack;
@@ -647,8 +648,8 @@ __device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& 
             if (!act) {
                 long long r = (long long)base + __popc(idle & lt);
                 if (r < total) {
-                    ray = r;
-                    act = task.begin(r, ts, vis, bvh);
+                    ray = order ? (long long)__ldg(order + r) : r;
+                    act = task.begin(ray, ts, vis, bvh);
                     nq = 0;
                 }
             }
