@@ -49,7 +49,7 @@ RAY_IO_BYTES = 44   # direction 16 + origin 12 read, (c_rt, T) 16 written
 COLLAPSE_LEVELS = 60
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace_rays_ww launch of the default
 # workload (k = 16, 800x800) from one ncu capture of the current kernel; None until taken
-TRACE_DRAM_BYTES = 979_275_776  # 667.1 MB read + 312.2 MB written
+TRACE_DRAM_BYTES = 1_182_328_576  # 850.9 MB read + 331.4 MB written (rays taken in bucket order)
 LARGE_N = 2_000_000          # unbounded scene: ground plane, 50 primitives, r = 50 shell
 LARGE_W, LARGE_H = 1920, 1080
 LARGE_ALLOC = (8, 4, 4)
