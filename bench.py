@@ -295,9 +295,11 @@ def run_grt(args):
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         host = {k: pin(v) for k, v in sc.arrays().items()}
         henv = pin(env)
-        hout = torch.empty((P, 7), dtype=torch.float32).pin_memory()
+        # contiguous pinned destinations: a strided host destination makes torch stage the
+        # copy through pageable memory
+        hout = [torch.empty(shape, dtype=torch.float32).pin_memory() for shape in ((P, 3), (P,), (P, 3))]
         h2d = sum(v.numel() * 4 for v in host.values()) + henv.numel() * 4
-        d2h = hout.numel() * 4
+        d2h = sum(h.numel() * 4 for h in hout)
         dev_in = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()}
         denv = torch.empty(henv.shape, device=dev)
         S2 = api.Scene(**dev_in)
@@ -313,9 +315,8 @@ def run_grt(args):
             E2.update(denv)
             api.gbuffer_primary(S2, cam, out=G2)
             api.shade_pixels(S2, G2, E2, *ALLOC, seed=SEED, outputs=(oc, ov, oi))
-            hout[:, 0:3].copy_(oc, non_blocking=True)
-            hout[:, 3].copy_(ov, non_blocking=True)
-            hout[:, 4:7].copy_(oi, non_blocking=True)
+            for h, d in zip(hout, (oc, ov, oi)):
+                h.copy_(d, non_blocking=True)
 
         for _ in range(2):
             e2e_step()
