@@ -275,8 +275,8 @@ int grt_shade_pixels_light(const grt_bvh* bvh, const grt_surfels* surfels, const
  *   grad_env[H][W][3]    += (1/N_r) sum_j (dL/dc g_j + dL/dlight) V_j at the texel of w_j,
  *   grad_albedo[n][3], grad_rough[n], grad_metal[n] += (1/N_r) sum_j dL/dc (df/dx) (cos/q)_j L_i,j
  * (per list entry; no roughness gradient where max(r^2, 1e-4) clamps).  Every gradient
- * pointer may be NULL; all accumulate.  The samples are drawn and traced again (32 bytes per
- * ray of pool scratch during the call); map gradients are float atomics. */
+ * pointer may be NULL; all accumulate.  The samples are drawn and traced again (40 bytes per
+ * ray slot of pool scratch during the call); map gradients are float atomics. */
 int grt_shade_backward_material(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
                                 const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
                                 const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,

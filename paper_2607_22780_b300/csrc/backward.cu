@@ -501,7 +501,8 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
         const long long n_chunks = (J.n_pixels + chunk_px - 1) / chunk_px;
         const long long Rc = chunk_px * J.Nr;
         const SavedLayout lay = saved_layout(Rc, kRecomputeHits);
-        const size_t per = (lay.total + (sizeof(float4) + sizeof(long long)) * (size_t)Rc + 16 + 255) & ~(size_t)255;
+        const size_t ord_off = (lay.total + (sizeof(float4) + sizeof(long long)) * (size_t)Rc + 16 + 255) & ~(size_t)255;
+        const size_t per = (ord_off + (GRT_RAY_ORDER ? order_scratch_bytes(Rc) : 0) + 255) & ~(size_t)255;
         const int nbuf = n_chunks > 1 ? 2 : 1;
         AuxStreams* aux = nullptr;
         if (nbuf > 1) {
@@ -535,10 +536,23 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
                                  Tc.total_rays, kRecomputeHits};
             const AdjIn in{dL_dcolor + 3 * p0, dL_dvis ? dL_dvis + p0 : nullptr, dL_dind ? dL_dind + 3 * p0 : nullptr};
             const long long gr = (Tc.total_rays + kShadeThreads - 1) / kShadeThreads;
-            k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, cs>>>(Tc, dirs);
+            // the chunk's rays go to the walk in bucket order, as in the forward
+            unsigned *ohist = nullptr, *okeys = nullptr, *oorder = nullptr;
+            if (GRT_RAY_ORDER) {
+                ohist = reinterpret_cast<unsigned*>(cb + ord_off);
+                okeys = ohist + kAllBuckets;
+                oorder = okeys + Tc.total_rays;
+                cudaMemsetAsync(ohist, 0, 4 * (size_t)kAllBuckets, cs);
+            }
+            k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, cs>>>(Tc, dirs, okeys, ohist);
+            if (oorder) {
+                k_bucket_scan<<<1, 1024, 0, cs>>>(ohist, (int)kAllBuckets);
+                k_ray_scatter<<<(unsigned)((Tc.total_rays + 255) / 256), 256, 0, cs>>>(Tc.total_rays, okeys, ohist,
+                                                                                          oorder);
+            }
             dispatch_k(p->k, [&](auto kc) {
                 constexpr int K = decltype(kc)::value;
-                launch_trace_save<K, 1>(Tc, dirs, res, hits, next_ray, gr, cs);
+                launch_trace_save<K, 1>(Tc, dirs, res, hits, next_ray, gr, cs, oorder);
                 run_adjoint<K>(Tc, dirs, res, hits, adj, work, in, g, cs);
             });
         }

@@ -379,13 +379,27 @@ extern "C" int grt_shade_backward_material(const grt_bvh* b, const grt_surfels* 
     cudaStream_t st = (cudaStream_t)stream;
     keep_pool_memory();
     float4* buf = nullptr;
-    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1), st));
+    const size_t extra = GRT_RAY_ORDER ? order_scratch_bytes(rays) : 0;
+    GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1) + extra, st));
     float4* dirs = buf;
     float4* res = buf + rays;
     unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + 2 * rays);
+    unsigned *ohist = nullptr, *okeys = nullptr, *oorder = nullptr;
+    if (GRT_RAY_ORDER) {
+        ohist = reinterpret_cast<unsigned*>(buf + 2 * rays + 1);
+        okeys = ohist + kAllBuckets;
+        oorder = okeys + rays;
+        cudaMemsetAsync(ohist, 0, 4 * (size_t)kAllBuckets, st);
+    }
     const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
-    k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs);
-    dispatch_k(p->k, [&](auto kc) { launch_trace_dyn<decltype(kc)::value, 1>(T, dirs, res, next_ray, gr, st); });
+    k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, okeys, ohist);
+    if (oorder) {
+        k_bucket_scan<<<1, 1024, 0, st>>>(ohist, (int)kAllBuckets);
+        k_ray_scatter<<<(unsigned)((rays + 255) / 256), 256, 0, st>>>(rays, okeys, ohist, oorder);
+    }
+    dispatch_k(p->k, [&](auto kc) {
+        launch_trace_dyn<decltype(kc)::value, 1>(T, dirs, res, next_ray, gr, st, oorder);
+    });
     const long long ga = (units * 32 + kShadeThreads - 1) / kShadeThreads;
     k_material_adjoint<<<(unsigned)ga, kShadeThreads, 0, st>>>(
         T, dirs, res, MaterialAdj{dL_dcolor, dL_dlight, grad_env, grad_albedo, grad_rough, grad_metal});
