@@ -49,7 +49,7 @@ RAY_IO_BYTES = 44   # direction 16 + origin 12 read, (c_rt, T) 16 written
 COLLAPSE_LEVELS = 60
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace_rays_ww launch of the default
 # workload (k = 16, 800x800) from one ncu capture of the current kernel; None until taken
-TRACE_DRAM_BYTES = 1_182_328_576  # 850.9 MB read + 331.4 MB written (rays taken in bucket order)
+TRACE_DRAM_BYTES = 1_181_220_864  # 850.0 MB read + 331.2 MB written (bucket order, 16-leaf queues)
 LARGE_N = 2_000_000          # unbounded scene: ground plane, 50 primitives, r = 50 shell
 LARGE_W, LARGE_H = 1920, 1080
 LARGE_ALLOC = (8, 4, 4)
@@ -236,8 +236,9 @@ def run_grt(args):
     n_valid = int(G.valid.sum().item())
     R = n_valid * sum(ALLOC)
     # kernel launches per step: rebuild (bounds, Morton, 4 x 3 sort passes, hierarchy, records,
-    # refit, collapse init + one launch per collapse level), G-buffer 1, shade 3
-    launches_per_step = 2 + 12 + 3 + 1 + COLLAPSE_LEVELS + 1 + 3
+    # refit, collapse init + one launch per collapse level), G-buffer 1, shade 5 (sample, bucket
+    # scan, ray scatter, trace, accumulate)
+    launches_per_step = 2 + 12 + 3 + 1 + COLLAPSE_LEVELS + 1 + 5
 
     for _ in range(args.warmup):
         step()

@@ -598,7 +598,7 @@ struct ColourVisitor {
 #define GRT_REFILL 4
 #endif
 #ifndef GRT_QUEUE
-#define GRT_QUEUE 12
+#define GRT_QUEUE 16
 #endif
 #ifndef GRT_LEAF_BATCH
 #define GRT_LEAF_BATCH 1
@@ -610,7 +610,10 @@ struct ColourVisitor {
 // queue 8 / 12 / 16 / 24 leaves: 339 / 364 / 351 / 333; leaf batch 1 / 2 / 4: 339 / 328 /
 // 307; composite batch 1 / 4 / 8 / 16 / 24: 364 / 389 / 394 / 377 / 323 (compositing runs
 // the SH colour of each hit, 22 % of the trace time, at 19 % lane use when unbatched);
-// refill at 4 / 8 / 12 idle lanes: 397 / 394 / 385.
+// refill at 4 / 8 / 12 idle lanes: 397 / 394 / 385.  With rays in bucket order (coherent
+// warps): queue 12 / 16 / 20 / 24: 424 / 430 / 429 / 427; refill 2 / 4 / 8: 424 / 424 / 421;
+// composite batch 4 / 8 / 12: 417 / 424 / 425; shared stack 8 / 16 / 24 entries: 418 / 424 /
+// 424; at least 3 / 4 / 5 blocks per SM: 377 / 424 / 333.
 constexpr int kRefill = GRT_REFILL;         // idle lanes that trigger a refill
 constexpr int kQueue = GRT_QUEUE;           // queued leaves per lane
 constexpr int kLeafBatch = GRT_LEAF_BATCH;  // leaves every walking lane queues before the tests
