@@ -191,9 +191,8 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
     char* order_buf = nullptr;
     float4 *dirs, *res;
     unsigned long long* next_ray;
-    // the persistent walks take their rays in bucket order (the thread-per-ray mesh walk
-    // and the counting pass keep slot order)
-    const bool ord = GRT_RAY_ORDER && !COUNT && !(rel && mesh);
+    // every walk but the counting pass takes its rays in bucket order
+    const bool ord = GRT_RAY_ORDER && !COUNT;
     const size_t extra = ord ? order_scratch_bytes(rays) : 0;
     keep_pool_memory();
     if (save) {
@@ -231,7 +230,7 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
             if constexpr (CAP == 1) launch_trace_save<K, CAP>(T, dirs, res, save->hits, next_ray, gr, st, oorder);
         } else if (rel && mesh) {
             if constexpr (CAP == 1)
-                k_trace_rays_mesh<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, *rel, *mesh);
+                k_trace_rays_mesh<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, *rel, *mesh, oorder);
         } else if (rel) {
             if constexpr (CAP == 1) launch_trace_relight<K, CAP>(T, dirs, res, *rel, next_ray, gr, st, oorder);
         } else {

@@ -533,15 +533,17 @@ inline void launch_trace_relight(const JobTable<CAP>& T, const float4* dirs, flo
 }
 
 // Relighting rays with the mesh backend of Eq. 14: closest triangle hit, one thread per
-// ray; res = (SplitSum of the hit, 0) or (0, 0, 0, 1) for a miss.
+// ray (in bucket order when given); res = (SplitSum of the hit, 0) or (0, 0, 0, 1) for a miss.
 template <int CAP>
 __global__ void __launch_bounds__(kShadeThreads) k_trace_rays_mesh(const __grid_constant__ JobTable<CAP> T,
                                                                    const float4* __restrict__ dirs,
                                                                    float4* __restrict__ res,
                                                                    const __grid_constant__ RelightDev E,
-                                                                   const __grid_constant__ MeshDev M) {
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= T.total_rays) return;
+                                                                   const __grid_constant__ MeshDev M,
+                                                                   const unsigned* __restrict__ order) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T.total_rays) return;
+    const long long r = order ? (long long)__ldg(order + i) : i;
     const float4 dw = __ldg(dirs + r);
     if (dw.w == 0.f) {
         res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
