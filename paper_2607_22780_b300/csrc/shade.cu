@@ -191,8 +191,8 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
     char* order_buf = nullptr;
     float4 *dirs, *res;
     unsigned long long* next_ray;
-    // every walk but the counting pass takes its rays in bucket order
-    const bool ord = GRT_RAY_ORDER && !COUNT;
+    // every walk but the counting pass takes its rays in bucket order (32-bit slot indices)
+    const bool ord = GRT_RAY_ORDER && !COUNT && rays <= 0xFFFFFFFFLL;
     const size_t extra = ord ? order_scratch_bytes(rays) : 0;
     keep_pool_memory();
     if (save) {
@@ -378,13 +378,14 @@ extern "C" int grt_shade_backward_material(const grt_bvh* b, const grt_surfels* 
     cudaStream_t st = (cudaStream_t)stream;
     keep_pool_memory();
     float4* buf = nullptr;
-    const size_t extra = GRT_RAY_ORDER ? order_scratch_bytes(rays) : 0;
+    const bool ord = GRT_RAY_ORDER && rays <= 0xFFFFFFFFLL;
+    const size_t extra = ord ? order_scratch_bytes(rays) : 0;
     GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1) + extra, st));
     float4* dirs = buf;
     float4* res = buf + rays;
     unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + 2 * rays);
     unsigned *ohist = nullptr, *okeys = nullptr, *oorder = nullptr;
-    if (GRT_RAY_ORDER) {
+    if (ord) {
         ohist = reinterpret_cast<unsigned*>(buf + 2 * rays + 1);
         okeys = ohist + kAllBuckets;
         oorder = okeys + rays;
