@@ -214,7 +214,7 @@ typedef struct {
  * out_ind[i][3] = (1/N_r) sum L_ind for i < n_pixels, pixel index pixel_list[i]
  * (NULL = all W*H pixels in order).  Samples below the horizon count V = L_ind = 0.
  * out_vis / out_ind may be NULL.  Ray buffers (32 bytes per ray slot, pixels x N_r) and the
- * order in which the walk takes the rays (8 bytes per slot) come from the stream-ordered
+ * order in which the walk takes the rays (12 bytes per slot) come from the stream-ordered
  * pool. */
 int grt_shade_pixels(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
                      const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
@@ -246,7 +246,7 @@ int grt_shade_backward(const grt_bvh* bvh, const grt_surfels* surfels, const grt
  * sampling, pixel_list, n_pixels and max_hits as the save call, with the surfels unchanged
  * in between (a replayed surfel id outside the scene is skipped and reported as
  * GRT_STATUS_BAD_INDEX).  grt_shade_saved_bytes returns 0 (and sets the error text) for
- * invalid arguments; max_hits is in [0, GRT_MAX_SAVED_HITS].  The save call takes 8 bytes
+ * invalid arguments; max_hits is in [0, GRT_MAX_SAVED_HITS].  The save call takes 12 bytes
  * per ray slot of stream-ordered pool scratch for the walk's ray order. */
 #define GRT_MAX_SAVED_HITS 64
 size_t grt_shade_saved_bytes(int32_t n_pixels, const grt_sampling* sampling, int32_t max_hits);
@@ -275,7 +275,7 @@ int grt_shade_pixels_light(const grt_bvh* bvh, const grt_surfels* surfels, const
  *   grad_env[H][W][3]    += (1/N_r) sum_j (dL/dc g_j + dL/dlight) V_j at the texel of w_j,
  *   grad_albedo[n][3], grad_rough[n], grad_metal[n] += (1/N_r) sum_j dL/dc (df/dx) (cos/q)_j L_i,j
  * (per list entry; no roughness gradient where max(r^2, 1e-4) clamps).  Every gradient
- * pointer may be NULL; all accumulate.  The samples are drawn and traced again (40 bytes per
+ * pointer may be NULL; all accumulate.  The samples are drawn and traced again (44 bytes per
  * ray slot of pool scratch during the call); map gradients are float atomics. */
 int grt_shade_backward_material(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
                                 const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
@@ -306,7 +306,7 @@ typedef struct {
  * resolutions and sample counts) in one wavefront pass: every request's samples go into
  * one ray list, one persistent trace launch serves them all, and each pixel is summed in
  * a fixed order.  Each request's outputs are bit-identical to shading it alone with
- * grt_shade_pixels.  Ray buffers (40 bytes per ray slot) come from the stream-ordered pool. */
+ * grt_shade_pixels.  Ray buffers (44 bytes per ray slot) come from the stream-ordered pool. */
 int grt_shade_batch(const grt_shade_request* requests, int32_t n_requests,
                     const grt_trace_params* params, void* stream);
 

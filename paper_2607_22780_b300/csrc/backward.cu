@@ -537,19 +537,14 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
             const AdjIn in{dL_dcolor + 3 * p0, dL_dvis ? dL_dvis + p0 : nullptr, dL_dind ? dL_dind + 3 * p0 : nullptr};
             const long long gr = (Tc.total_rays + kShadeThreads - 1) / kShadeThreads;
             // the chunk's rays go to the walk in bucket order, as in the forward
-            unsigned *ohist = nullptr, *okeys = nullptr, *oorder = nullptr;
+            RayOrder ro{nullptr, nullptr, nullptr, nullptr};
             if (GRT_RAY_ORDER) {
-                ohist = reinterpret_cast<unsigned*>(cb + ord_off);
-                okeys = ohist + kAllBuckets;
-                oorder = okeys + Tc.total_rays;
-                cudaMemsetAsync(ohist, 0, 4 * (size_t)kAllBuckets, cs);
+                ro = ray_order_bufs(cb + ord_off, Tc.total_rays);
+                cudaMemsetAsync(ro.hist, 0, 4 * (size_t)kAllBuckets, cs);
             }
-            k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, cs>>>(Tc, dirs, okeys, ohist);
-            if (oorder) {
-                k_bucket_scan<<<1, 1024, 0, cs>>>(ohist, (int)kAllBuckets);
-                k_ray_scatter<<<(unsigned)((Tc.total_rays + 255) / 256), 256, 0, cs>>>(Tc.total_rays, okeys, ohist,
-                                                                                          oorder);
-            }
+            k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, cs>>>(Tc, dirs, ro);
+            if (GRT_RAY_ORDER) launch_ray_order(ro, Tc.total_rays, cs);
+            const unsigned* oorder = ro.order;
             dispatch_k(p->k, [&](auto kc) {
                 constexpr int K = decltype(kc)::value;
                 launch_trace_save<K, 1>(Tc, dirs, res, hits, next_ray, gr, cs, oorder);

@@ -209,18 +209,14 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
     }
     const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
     g_timing.mark(0, st);
-    unsigned *ohist = nullptr, *okeys = nullptr, *oorder = nullptr;
+    RayOrder ro{nullptr, nullptr, nullptr, nullptr};
     if (order_buf) {
-        ohist = reinterpret_cast<unsigned*>(order_buf);
-        okeys = ohist + kAllBuckets;
-        oorder = okeys + rays;
-        cudaMemsetAsync(ohist, 0, 4 * (size_t)kAllBuckets, st);
+        ro = ray_order_bufs(order_buf, rays);
+        cudaMemsetAsync(ro.hist, 0, 4 * (size_t)kAllBuckets, st);
     }
-    k_sample_rays<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, okeys, ohist);
-    if (oorder) {
-        k_bucket_scan<<<1, 1024, 0, st>>>(ohist, (int)kAllBuckets);
-        k_ray_scatter<<<(unsigned)((rays + 255) / 256), 256, 0, st>>>(rays, okeys, ohist, oorder);
-    }
+    k_sample_rays<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, ro);
+    if (order_buf) launch_ray_order(ro, rays, st);
+    const unsigned* oorder = ro.order;
     g_timing.mark(1, st);
     dispatch_k(k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
@@ -384,19 +380,15 @@ extern "C" int grt_shade_backward_material(const grt_bvh* b, const grt_surfels* 
     float4* dirs = buf;
     float4* res = buf + rays;
     unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(buf + 2 * rays);
-    unsigned *ohist = nullptr, *okeys = nullptr, *oorder = nullptr;
+    RayOrder ro{nullptr, nullptr, nullptr, nullptr};
     if (ord) {
-        ohist = reinterpret_cast<unsigned*>(buf + 2 * rays + 1);
-        okeys = ohist + kAllBuckets;
-        oorder = okeys + rays;
-        cudaMemsetAsync(ohist, 0, 4 * (size_t)kAllBuckets, st);
+        ro = ray_order_bufs(buf + 2 * rays + 1, rays);
+        cudaMemsetAsync(ro.hist, 0, 4 * (size_t)kAllBuckets, st);
     }
     const long long gr = (rays + kShadeThreads - 1) / kShadeThreads;
-    k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, okeys, ohist);
-    if (oorder) {
-        k_bucket_scan<<<1, 1024, 0, st>>>(ohist, (int)kAllBuckets);
-        k_ray_scatter<<<(unsigned)((rays + 255) / 256), 256, 0, st>>>(rays, okeys, ohist, oorder);
-    }
+    k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, ro);
+    if (ord) launch_ray_order(ro, rays, st);
+    const unsigned* oorder = ro.order;
     dispatch_k(p->k, [&](auto kc) {
         launch_trace_dyn<decltype(kc)::value, 1>(T, dirs, res, next_ray, gr, st, oorder);
     });

@@ -71,8 +71,9 @@ __device__ __forceinline__ int pixel_of(const ShadeJob& J, int li) {
 // tile (Morton order of 2^kTileBits x 2^kTileBits tiles) in one direction cell (octahedral
 // map of d, 2^kDirBits x 2^kDirBits cells), so the 32 lanes of a warp start from nearby
 // points in similar directions and visit the same nodes.  The order only schedules the
-// walk: every ray computes the same result.  Keys are made by the sampler, a one-pass
-// counting sort (warp-aggregated bucket atomics) gives the order; 8 bytes of pool scratch
+// walk: every ray computes the same result.  The sampler writes each slot's bucket and
+// its rank in the bucket (one warp-aggregated atomic per distinct bucket in a warp); a scan
+// of the bucket counts and an atomic-free scatter give the order; 12 bytes of pool scratch
 // per ray slot.  Measured on the 300k-surfel 800x800 workload (M rays/s, whole step): slot
 // order 395; buckets of 32x32 tiles x 8x8 direction cells 416.6, 64x64 x 4x4 416.1,
 // 16x16 x 16x16 415.8, 32x32 x 16x16 416.5, 64x64 x 8x8 416.0; direction-major keys
@@ -121,13 +122,29 @@ __device__ __forceinline__ unsigned ray_bucket(const GbufDev& g, int pix, float4
     return (tile << (2 * kDirBits)) | (unsigned)(cv * nd + cu);
 }
 
-// ray buffer entry: (direction, 1) for a traced sample, (0, 0, 0, 0) for none; with keys,
-// also the slot's bucket and its count in hist
+// Buffers of the ray order over n slots (order_scratch_bytes(n) bytes from `base`):
+// hist[kAllBuckets] bucket counts, then exclusive offsets; per slot its bucket, its rank in
+// the bucket, and order[] = the slots bucket by bucket.
+struct RayOrder {
+    unsigned *hist, *key, *rank, *order;
+};
+inline size_t order_scratch_bytes(long long n) { return 4 * (3 * (size_t)n + kAllBuckets); }
+inline RayOrder ray_order_bufs(void* base, long long n) {
+    RayOrder o;
+    o.hist = static_cast<unsigned*>(base);
+    o.key = o.hist + kAllBuckets;
+    o.rank = o.key + n;
+    o.order = o.rank + n;
+    return o;
+}
+
+// ray buffer entry: (direction, 1) for a traced sample, (0, 0, 0, 0) for none; with an
+// order (o.key != nullptr), also the slot's bucket and its rank among the bucket's slots
 template <int CAP>
 __global__ void __launch_bounds__(kShadeThreads) k_sample_rays(const __grid_constant__ JobTable<CAP> T,
                                                                float4* __restrict__ dirs,
-                                                               unsigned* __restrict__ keys = nullptr,
-                                                               unsigned* __restrict__ hist = nullptr) {
+                                                               RayOrder o = RayOrder{nullptr, nullptr, nullptr,
+                                                                                     nullptr}) {
     long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= T.total_rays) return;
     const ShadeJob& J = T.job[T.find_ray(r)];
@@ -141,12 +158,16 @@ __global__ void __launch_bounds__(kShadeThreads) k_sample_rays(const __grid_cons
         if (draw_direction(J.S, J.env, ps, pix, j, &w)) out = make_float4(w.x, w.y, w.z, 1.f);
     }
     dirs[r] = out;
-    if (keys) {
+    if (o.key) {
         const unsigned key = ray_bucket(J.gb, pix, out, r);
-        keys[r] = key;
-        // one atomic per distinct key in the warp (a pixel's slots often share a bucket)
+        // one atomic per distinct key in the warp; its old value ranks the warp's slots
         const unsigned peers = __match_any_sync(__activemask(), key);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + key, (unsigned)__popc(peers));
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(o.hist + key, (unsigned)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        o.key[r] = key;
+        o.rank[r] = base + (unsigned)__popc(peers & ((1u << lane) - 1u));
     }
 }
 
@@ -175,21 +196,18 @@ __global__ void k_bucket_scan(unsigned* __restrict__ hist, int n) {
     }
 }
 
-__global__ void k_ray_scatter(long long n, const unsigned* __restrict__ keys, unsigned* __restrict__ offs,
-                              unsigned* __restrict__ order) {
+// order[offset of the slot's bucket + its rank] = slot (hist holds the exclusive offsets).
+__global__ void k_ray_scatter(long long n, RayOrder o) {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    const unsigned key = keys[r];
-    const unsigned peers = __match_any_sync(__activemask(), key);
-    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(offs + key, (unsigned)__popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    order[base + __popc(peers & ((1u << lane) - 1u))] = (unsigned)r;
+    o.order[__ldg(o.hist + o.key[r]) + o.rank[r]] = (unsigned)r;
 }
 
-// Scratch of the ray order over n slots: hist[kAllBuckets], keys[n], order[n].
-inline size_t order_scratch_bytes(long long n) { return 4 * (2 * (size_t)n + kAllBuckets); }
+// Bucket offsets and the order, after k_sample_rays has filled hist, key and rank.
+inline void launch_ray_order(const RayOrder& o, long long n, cudaStream_t st) {
+    k_bucket_scan<<<1, 1024, 0, st>>>(o.hist, (int)kAllBuckets);
+    k_ray_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, o);
+}
 
 
 // (c_rt, T) per ray; T = -1 marks "no ray"
