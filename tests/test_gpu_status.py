@@ -89,3 +89,21 @@ def test_shading_and_gradients_are_deterministic():
         x, y = getattr(g1, f), getattr(g2, f)
         assert torch.allclose(x, y, rtol=1e-4, atol=1e-6 * float(x.abs().max())), f
     assert S.status() == 0
+
+
+def test_results_do_not_depend_on_the_walk_order():
+    # the walk takes rays bucket by bucket (screen tile x direction cell); listing the pixels
+    # in another order changes every slot index, bucket rank and walk order, and must change
+    # no pixel's result by a single bit (per-ray work is independent, per-pixel sums fixed)
+    sc, gb32, env = _case(n=30000, W=40, H=30, seed=47)
+    S = scene_gpu(sc)
+    G = api.GBuffer.from_arrays(gb32)
+    E = api.Environment(t(env))
+    full = api.shade_pixels(S, G, E, 16, 8, 8, seed=5)
+    perm = np.random.default_rng(3).permutation(40 * 30).astype(np.int32)
+    part = api.shade_pixels(S, G, E, 16, 8, 8, seed=5, pixels=t(perm, torch.int32))
+    at = torch.from_numpy(perm).long().cuda()
+    for x, y in zip(full, part):
+        assert torch.equal(x[at], y)
+    assert float(full[0].abs().sum()) > 0 and S.status() == 0
+
