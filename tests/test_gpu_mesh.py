@@ -111,6 +111,24 @@ def test_bad_vertex_index_is_reported():
     assert M.status() & L.STATUS_BAD_INDEX
 
 
+def test_relight_with_an_empty_mesh_equals_shading_without_occluders():
+    # no triangle: every relighting ray misses (V = 1, no indirect), which is the training
+    # estimate of a scene whose rays all escape
+    from tests._handmade import random_gbuffer
+    rng = np.random.default_rng(4)
+    gb = random_gbuffer(rng, 300, eye=(0.0, 0.0, 3.0))
+    M = api.MeshScene.from_workload(_mesh(np.zeros((3, 3)), np.zeros((0, 3))))
+    sc = wl.scene_random_soup(10, seed=1, extent=0.1, scale_lo=0.01, scale_hi=0.02)
+    sc.mu[:] += 50.0  # far away from every ray
+    S = api.Scene.from_workload(sc)
+    G = api.GBuffer.from_arrays(gb)
+    E = api.Environment(t(wl.envmap_hdr(9, 64, 32)))
+    a = api.shade_relight_mesh(M, G, E, 8, 4, 4, seed=3)
+    b = api.shade_pixels(S, G, E, 8, 4, 4, seed=3)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
 def _check_relit(got, ref, pix=None):
     m = unflagged(ref["flags"])
     assert m.mean() > 0.95, m.mean()
