@@ -134,6 +134,9 @@ struct KBuf {
         thi = t_max;
     }
 
+    // Branch-free insertion (one compare-swap pass over the buffer).  An append branch for
+    // keys beyond the current maximum (the common case front to back) measured slower:
+    // 431 -> 368 M rays/s, lanes of a warp split between the two paths.
     __device__ __forceinline__ void insert(uint64_t k, float al, float T0, float T_min, float t_max, float eps) {
         const bool full = cnt == K;
         uint64_t ck = k;
