@@ -1596,11 +1596,14 @@ int or_backward_material(const or_scene* sc, const or_params* P, const or_gbuf* 
  *   Py = P[ky] - Sy P[kz];
  *   U = Cx By - Cy Bx, V = Ax Cy - Ay Cx, W = Bx Ay - By Ax (two rounded products, then
  *   their rounded difference); if one of U, V, W is 0 all three are recomputed from the
- *   same FP32 operands in FP64 (exact products, one rounding) and rounded to FP32;
+ *   same FP32 operands by Kahan's difference of products in FP32 with fused multiply-adds
+ *   (w = c d, e = fma(-c, d, w), (fma(a, b, -w)) + e; relative error below 2 ulp after
+ *   Jeannerod, Louvet and Muller, Math. Comp. 2013, so its sign and zeros are exact);
  *   a hit needs U, V, W of one sign (zeros allowed) and det = (U + V) + W != 0;
  *   t = ((U (Sz A[kz]) + V (Sz B[kz])) + W (Sz C[kz])) / det in (t_min, t_max).
- * An edge shared by two triangles is evaluated from the same vertex values in both, to
- * the same magnitude with opposite sign, so no ray passes between them.  The barycentric
+ * An edge shared by two triangles is evaluated from the same vertex values in both: the
+ * plain difference to the same magnitude with opposite sign, and when it is 0 in one it is
+ * 0 in both and both take the exact-sign difference, so no ray passes between them.  The barycentric
  * weights of (v0, v1, v2), continuous quantities, come from FP64 Moeller-Trumbore on the
  * chosen triangle. */
 typedef struct or_mesh_s {
@@ -1611,6 +1614,14 @@ typedef struct or_mesh_s {
 } or_mesh;
 
 static d3 crossd(d3 a, d3 b) { return md3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+
+/* a b - c d by Kahan's algorithm (exact sign; see above). */
+static inline float diff_prod(float a, float b, float c, float d) {
+    float w = c * d;
+    float e = fmaf(-c, d, w);
+    float f = fmaf(a, b, -w);
+    return f + e;
+}
 
 static inline float f3c(f3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
 
@@ -1643,9 +1654,9 @@ static int wt_hit(const wt_ray* r, const float* p0, const float* p1, const float
     float Cx = f3c(C, r->kx) - r->Sx * Cz, Cy = f3c(C, r->ky) - r->Sy * Cz;
     float U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
     if (U == 0.0f || V == 0.0f || W == 0.0f) {
-        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
-        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
-        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+        U = diff_prod(Cx, By, Cy, Bx);
+        V = diff_prod(Ax, Cy, Ay, Cx);
+        W = diff_prod(Bx, Ay, By, Ax);
     }
     if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return 0;
     float det = (U + V) + W;

@@ -8,12 +8,14 @@
 //   kz = the axis of the largest |d| (the first on ties), kx = kz+1 mod 3, ky = kx+1 mod 3;
 //   Sx = d[kx]/d[kz], Sy = d[ky]/d[kz], Sz = 1/d[kz];
 //   A = v0 - o, B = v1 - o, C = v2 - o;  Px = P[kx] - Sx P[kz], Py = P[ky] - Sy P[kz];
-//   U = Cx By - Cy Bx, V = Ax Cy - Ay Cx, W = Bx Ay - By Ax, recomputed in FP64 from the
-//   same operands (exact products, one rounding) when one of them is 0;
+//   U = Cx By - Cy Bx, V = Ax Cy - Ay Cx, W = Bx Ay - By Ax, recomputed when one of them is
+//   0 by Kahan's difference of products with fused multiply-adds (relative error below
+//   2 ulp, Jeannerod, Louvet and Muller 2013: exact sign and zeros), FP32 throughout;
 //   hit iff U, V, W share a sign (zeros allowed) and det = (U + V) + W != 0, and
 //   t = ((U (Sz A[kz]) + V (Sz B[kz])) + W (Sz C[kz])) / det lies in (t_min, t_max).
 // A shared edge gives the two triangles edge functions of equal magnitude and opposite
-// sign, so no ray passes between neighbours.  The nearest t wins, equal t by triangle
+// sign, and when it is 0 in one it is 0 in both and both take the exact-sign difference,
+// so no ray passes between neighbours.  The nearest t wins, equal t by triangle
 // index; the weights of (v0, v1, v2) are (U, V, W) / det.  The walk visits children near to
 // far and culls every box beyond the nearest hit found so far.
 #pragma once
@@ -40,6 +42,14 @@ struct ShearRay {
     int kx, ky, kz;
     float Sx, Sy, Sz;
 };
+
+// a b - c d by Kahan's algorithm (exact sign).
+__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
+    const float w = __fmul_rn(c, d);
+    const float e = __fmaf_rn(-c, d, w);
+    const float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, e);
+}
 
 __device__ __forceinline__ float comp(f3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
 
@@ -80,9 +90,9 @@ __device__ __forceinline__ void mesh_test_leaf(const DevBvh& bvh, int ref, const
         float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
         float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
         if (U == 0.f || V == 0.f || W == 0.f) {
-            U = __double2float_rn(__dsub_rn(__dmul_rn(Cx, By), __dmul_rn(Cy, Bx)));
-            V = __double2float_rn(__dsub_rn(__dmul_rn(Ax, Cy), __dmul_rn(Ay, Cx)));
-            W = __double2float_rn(__dsub_rn(__dmul_rn(Bx, Ay), __dmul_rn(By, Ax)));
+            U = diff_prod(Cx, By, Cy, Bx);
+            V = diff_prod(Ax, Cy, Ay, Cx);
+            W = diff_prod(Bx, Ay, By, Ax);
         }
         if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) continue;
         const float det = __fadd_rn(__fadd_rn(U, V), W);
