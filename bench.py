@@ -45,6 +45,10 @@ TRAIN_ALLOC = (8, 4, 4)
 REC_BYTES = 64      # packed surfel record read per surfel test
 NODE_BYTES = 112    # 4-wide node visit: 6 child-plane float4 + 1 child-ref float4
 SH_BYTES = 192      # 48 SH coefficients read per composited hit
+HIT_REC_BYTES = 12  # recorded hit (surfel id, tau, alpha), written by the saving trace, read by the replay
+SURFEL_BYTES = 232  # mu 12 + quat 16 + scale 8 + opacity 4 + SH 192, read per replayed hit
+GRAD_RMW_BYTES = 464  # the same 232 B of gradients read and written (atomics) per replayed hit
+REPLAY_RAY_BYTES = 64  # per traced ray in the replay: hit count 4, direction 16, origin 12, (c_rt, T) 16, adjoint 16
 RAY_IO_BYTES = 44   # direction 16 + origin 12 read, (c_rt, T) 16 written
 COLLAPSE_LEVELS = 60
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace_rays_ww launch of the default
@@ -508,11 +512,39 @@ def time_train(api, S, cam, E, dev, args):
         ms[name] = a.elapsed_time(b) / n
     nv = int(G.valid.sum().item())
     R = nv * sum(TRAIN_ALLOC)
+    # rooflines of the stored form's two dominant kernels, event-timed inside the library on
+    # the call's stream: the saving trace (forward walk + hit record) and the replay
+    cnt = [int(x) for x in api.shade_count(S, G, E, *TRAIN_ALLOC, seed=SEED).cpu()]
+    api.phase_timing(True)
+    api.adjoint_timing(True)
+    tr, rp = [], []
+    for _ in range(3):
+        step_stored()
+        tr.append(api.phase_timing(read=True)[1])
+        rp.append(api.adjoint_timing(read=True)[1])
+    api.phase_timing(False)
+    api.adjoint_timing(False)
+    peak, peak_kind = measured_peaks()
+    save_bytes = (NODE_BYTES * cnt[0] + REC_BYTES * cnt[1] + (SH_BYTES + HIT_REC_BYTES) * cnt[2] +
+                  (RAY_IO_BYTES + 4) * R)
+    replay_bytes = (HIT_REC_BYTES + SURFEL_BYTES + GRAD_RMW_BYTES) * cnt[2] + REPLAY_RAY_BYTES * R
+
+    def roof(kernel, nbytes, t_ms, unit_note):
+        ach = nbytes / (t_ms * 1e-3) / 1e9
+        return {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_kind": peak_kind, "alg_bytes_per_launch": nbytes, "kernel_ms": t_ms, "bytes": unit_note}
+
+    tr_ms, rp_ms = float(np.median(tr)), float(np.median(rp))
     return {"workload": "train_300k_400x400_16spp", "rays": R, "fwd_ms": ms["fwd"], "fwd_bwd_ms": ms["fwd_bwd"],
             "fwd_bwd_recompute_ms": ms["fwd_bwd_recompute"], "stored_hits": 64,
             "fwd_bwd_material_ms": ms["fwd_bwd_material"],
             "fwd_rays_per_s": R / (ms["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (ms["fwd_bwd"] * 1e-3),
-            "fwd_bwd_recompute_rays_per_s": R / (ms["fwd_bwd_recompute"] * 1e-3)}
+            "fwd_bwd_recompute_rays_per_s": R / (ms["fwd_bwd_recompute"] * 1e-3),
+            "per_ray": {"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R},
+            "roofline_save_trace": roof("k_trace_rays_save", save_bytes, tr_ms,
+                                        "112 per node + 64 per test + (192 + 12) per composited hit + 48 per ray"),
+            "roofline_replay": roof("k_adjoint_replay", replay_bytes, rp_ms,
+                                    "(12 + 232 + 464) per composited hit + 64 per ray")}
 
 
 def time_relight(api, S, G, E, R, args):

@@ -414,6 +414,15 @@ int grt_shade_count(const grt_bvh* bvh, const grt_surfels* surfels, const grt_tr
  * the most recent timed shading call and writes its three durations in milliseconds. */
 int grt_phase_timing(int32_t enable, float* ms_out);
 
+/* Kernel timing of the adjoint (for roofline accounting; the same conventions as
+ * grt_phase_timing): with enable = 1 the following grt_shade_backward /
+ * grt_shade_backward_saved calls of the calling thread record CUDA events on their stream
+ * around the adjoint weights, the replay of the recorded rays and the traced adjoint walk
+ * of rays the record does not hold; with ms_out non-NULL the call waits for the most recent
+ * timed adjoint pass (the last chunk of a recomputing backward) and writes the three
+ * durations in milliseconds. */
+int grt_adjoint_timing(int32_t enable, float* ms_out);
+
 const char* grt_last_error(void);
 const char* grt_version(void);
 

@@ -114,6 +114,7 @@ SIGNATURES = {
     "grt_shade_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                   C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P]),
     "grt_phase_timing": (C.c_int, [C.c_int32, C.POINTER(C.c_float)]),
+    "grt_adjoint_timing": (C.c_int, [C.c_int32, C.POINTER(C.c_float)]),
     "grt_denoise": (C.c_int, [P, P, P, P, C.c_int32, C.c_int32, C.POINTER(DenoiseParams), P, P]),
     "grt_trace_attr": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), P, P, C.c_int32, P, P, P, P, P, P]),
     "grt_env_prefilter_bytes": (C.c_size_t, []),

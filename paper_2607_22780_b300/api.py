@@ -623,5 +623,13 @@ def phase_timing(enable: Optional[bool] = None, read: bool = False):
     return tuple(ms) if read else None
 
 
+def adjoint_timing(enable: Optional[bool] = None, read: bool = False):
+    """Turn per-kernel timing of adjoint passes on/off; with read=True return the last
+    pass's (weights_ms, replay_ms, walk_ms)."""
+    ms = (C.c_float * 3)() if read else None
+    L.check(L.load().grt_adjoint_timing(-1 if enable is None else int(bool(enable)), ms))
+    return tuple(ms) if read else None
+
+
 def version() -> str:
     return L.load().grt_version().decode()

@@ -413,6 +413,20 @@ extern "C" int grt_trace_backward(const grt_bvh* b, const grt_surfels* s, const 
 constexpr long long kRecomputeChunkRays = GRT_RECOMPUTE_CHUNK_RAYS;
 constexpr int kRecomputeHits = 64;
 
+// Optional timing (grt_adjoint_timing): events on the call's stream around the three
+// kernels of the most recent adjoint pass of this thread.
+struct AdjointTiming {
+    bool on = false;
+    bool have = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    void mark(int i, cudaStream_t st) {
+        if (!on) return;
+        if (!ev[i]) cudaEventCreate(&ev[i]);
+        cudaEventRecord(ev[i], st);
+    }
+};
+thread_local AdjointTiming g_adj_timing;
+
 // Adjoint weights, replay of the recorded rays, and a traced adjoint walk for the rays
 // the record does not hold (all rays when hits.L == 0).  `work` holds two counters and,
 // with a record, room for a list of every ray.
@@ -424,8 +438,11 @@ static void run_adjoint(const JobTable<1>& T, const float4* dirs, const float4* 
     unsigned long long* n_over = work + 1;
     long long* over = reinterpret_cast<long long*>(work + 2);
     cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), st);
+    g_adj_timing.mark(0, st);
     k_adjoint_weights<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, in, adj);
+    g_adj_timing.mark(1, st);
     if (hits.L > 0) k_adjoint_replay<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, adj, hits, g, n_over, over);
+    g_adj_timing.mark(2, st);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -434,6 +451,8 @@ static void run_adjoint(const JobTable<1>& T, const float4* dirs, const float4* 
     if (grid > gr) grid = gr;
     k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, hits.L > 0 ? n_over : nullptr,
                                                               hits.L > 0 ? over : nullptr, hits, next_ray);
+    g_adj_timing.mark(3, st);
+    g_adj_timing.have = g_adj_timing.on;
 }
 
 // Two library streams per host thread and device: consecutive chunks of the recomputing
@@ -582,4 +601,17 @@ extern "C" int grt_shade_backward_saved(const grt_bvh* b, const grt_surfels* s, 
     if (rc) return rc;
     return shade_backward_impl(b, s, p, gb, e, smp, pixel_list, n_pixels, dL_dcolor, dL_dvis, dL_dind, grads, &sb,
                                (cudaStream_t)stream);
+}
+
+extern "C" int grt_adjoint_timing(int32_t enable, float* ms_out) {
+    if (enable >= 0) {
+        g_adj_timing.on = enable != 0;
+        g_adj_timing.have = false;
+    }
+    if (!ms_out) return GRT_OK;
+    if (!g_adj_timing.have) return set_error(GRT_ERR_ARG, "no timed adjoint pass on this thread");
+    GRT_CUDA(cudaEventSynchronize(g_adj_timing.ev[3]));
+    for (int i = 0; i < 3; ++i)
+        GRT_CUDA(cudaEventElapsedTime(ms_out + i, g_adj_timing.ev[i], g_adj_timing.ev[i + 1]));
+    return GRT_OK;
 }
