@@ -39,6 +39,12 @@ struct AdjointVisitor {
 
     // out of line: round_end unrolls its K slots, and this body is large
     __device__ __noinline__ void composite(int, int id, float tau, float alpha, float Tb) {
+        // geometry of the hit, loaded first so that its latency overlaps the colour's
+        const float op = __ldg(opacity + id);
+        const float4 q = make_float4(__ldg(quat + 4 * (size_t)id), __ldg(quat + 4 * (size_t)id + 1),
+                                     __ldg(quat + 4 * (size_t)id + 2), __ldg(quat + 4 * (size_t)id + 3));
+        const float su = __ldg(scale + 2 * (size_t)id), sv = __ldg(scale + 2 * (size_t)id + 1);
+        const f3 m = mk3(__ldg(mu + 3 * (size_t)id), __ldg(mu + 3 * (size_t)id + 1), __ldg(mu + 3 * (size_t)id + 2));
         // colour of the hit and, for SH, which channels are live
         float Y[16];
         float c[3];
@@ -94,18 +100,12 @@ struct AdjointVisitor {
                 }
             }
         }
-        // geometry of the hit
-        float op = __ldg(opacity + id);
-        float4 q = make_float4(__ldg(quat + 4 * (size_t)id), __ldg(quat + 4 * (size_t)id + 1),
-                               __ldg(quat + 4 * (size_t)id + 2), __ldg(quat + 4 * (size_t)id + 3));
         float ql = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
         float iql = 1.f / ql;
         float qw = q.x * iql, qx = q.y * iql, qy = q.z * iql, qz = q.w * iql;
         f3 tu = mk3(1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy + qw * qz), 2.f * (qx * qz - qw * qy));
         f3 tv = mk3(2.f * (qx * qy - qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz + qw * qx));
         f3 n = mk3(2.f * (qx * qz + qw * qy), 2.f * (qy * qz - qw * qx), 1.f - 2.f * (qx * qx + qy * qy));
-        float su = __ldg(scale + 2 * (size_t)id), sv = __ldg(scale + 2 * (size_t)id + 1);
-        f3 m = mk3(__ldg(mu + 3 * (size_t)id), __ldg(mu + 3 * (size_t)id + 1), __ldg(mu + 3 * (size_t)id + 2));
         f3 dp = mk3(fmaf(tau, d.x, o.x) - m.x, fmaf(tau, d.y, o.y) - m.y, fmaf(tau, d.z, o.z) - m.z);
         float u = dot3(dp, tu) / su, v = dot3(dp, tv) / sv;
         float G = __expf(-0.5f * fmaf(u, u, v * v));
@@ -332,16 +332,27 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_replay(const __grid_c
     adjoint_init(av, J, T.P, g, a, rr, ray_origin(J, r), mk3(dw.x, dw.y, dw.z));
     const int ns = J.bvh.n;
     float Tb = 1.f;
+    // the next hit's record is loaded while the current one is composited
+    int id = __ldg(sv.ids + r);
+    float tau = __ldg(sv.tau + r), alpha = __ldg(sv.alpha + r);
     for (int k = 0; k < n; ++k) {
-        const size_t i = (size_t)k * sv.R + r;
-        const int id = __ldg(sv.ids + i);
-        const float tau = __ldg(sv.tau + i), alpha = __ldg(sv.alpha + i);
+        int idn = 0;
+        float taun = 0.f, alphan = 0.f;
+        if (k + 1 < n) {
+            const size_t i = (size_t)(k + 1) * sv.R + r;
+            idn = __ldg(sv.ids + i);
+            taun = __ldg(sv.tau + i);
+            alphan = __ldg(sv.alpha + i);
+        }
         if ((unsigned)id >= (unsigned)ns) {
             atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
             return;
         }
         av.composite(k, id, tau, alpha, Tb);
         Tb = mul_d(Tb, sub_d(1.0f, alpha));
+        id = idn;
+        tau = taun;
+        alpha = alphan;
     }
 }
 
