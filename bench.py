@@ -16,6 +16,9 @@ Mode "large": 2M surfels (ground plane, 50 primitives, background shell), 1920x1
 Mode "serve": the relight request loop (see paper_2607_22780_b300.serve).
 Mode "relight": split-sum relighting of the default frame (Eq. 14-15), Gaussian backend and
 mesh backend (the same objects as 310,670 triangles).
+Mode "c1": the plain forward (8k RGB surfels, 64x64, 4 cosine rays, constant white map).
+Mode "cpu": the FP64 oracle timed on the host cores for C1 (whole frame), C2 and C4
+(4,096-ray samples) and the C3 backward at 32x32.
 
 Under torchrun every rank renders its own frame (weak scaling, no data-path collective);
 ranks meet only at the barriers around the timed region and in the final max/sum.
@@ -42,6 +45,15 @@ ALLOC = (16, 8, 8)
 ENV_W, ENV_H = 512, 256
 TRAIN_IMG = 400
 TRAIN_ALLOC = (8, 4, 4)
+# Algorithmic bytes per ray of the trace (the survey's count, which the roofline fraction
+# uses): 64 per internal node visited, 48 per surfel record tested, 192 per composited SH
+# hit, plus the shading call's ray I/O (48 B of G-buffer in and 28 B out per pixel over the
+# N_r rays of the pixel, ~4 B of environment-table reads per environment sample).
+ALG_NODE_BYTES = 64
+ALG_REC_BYTES = 48
+# Bytes the kernels' own layouts move (second field of each roofline): a 4-wide node visit
+# loads 6 child-plane float4 + 1 child-ref float4, a record is 64 B, a ray reads its
+# direction (16) and origin (12) and writes (c_rt, T) (16).
 REC_BYTES = 64      # packed surfel record read per surfel test
 NODE_BYTES = 112    # 4-wide node visit: 6 child-plane float4 + 1 child-ref float4
 SH_BYTES = 192      # 48 SH coefficients read per composited hit
@@ -50,14 +62,44 @@ SURFEL_BYTES = 232  # mu 12 + quat 16 + scale 8 + opacity 4 + SH 192, read per r
 GRAD_RMW_BYTES = 464  # the same 232 B of gradients read and written (atomics) per replayed hit
 REPLAY_RAY_BYTES = 64  # per traced ray in the replay: hit count 4, direction 16, origin 12, (c_rt, T) 16, adjoint 16
 RAY_IO_BYTES = 44   # direction 16 + origin 12 read, (c_rt, T) 16 written
-COLLAPSE_LEVELS = 60
+COLLAPSE_LAUNCHES = 1  # the 4-wide collapse is one launch (device work queue)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace_rays_ww launch of the default
 # workload (k = 16, 800x800) from one ncu capture of the current kernel; None until taken
 TRACE_DRAM_BYTES = 1_181_220_864  # 850.0 MB read + 331.2 MB written (bucket order, 16-leaf queues)
+# L2 traffic of the same kernel (lts__t_bytes.sum) and its throughput fraction, from one ncu
+# capture; None until taken for the current kernel
+TRACE_L2 = None
 LARGE_N = 2_000_000          # unbounded scene: ground plane, 50 primitives, r = 50 shell
 LARGE_W, LARGE_H = 1920, 1080
 LARGE_ALLOC = (8, 4, 4)
 LARGE_DISTANCE = 12.0
+
+
+def alg_bytes(cnt, R, alloc, extra_per_hit=0.0, extra_per_ray=0.0):
+    """Algorithmic bytes of one trace launch over R rays from its traversal counters
+    (nodes, tests, composited), by the survey's count."""
+    nr = float(sum(alloc))
+    io = (48.0 + 28.0) / nr + 4.0 * alloc[2] / nr
+    return (ALG_NODE_BYTES * cnt[0] + ALG_REC_BYTES * cnt[1] + (SH_BYTES + extra_per_hit) * cnt[2] +
+            (io + extra_per_ray) * R)
+
+
+def layout_bytes(cnt, R, extra_per_hit=0.0, extra_per_ray=0.0):
+    """Bytes the kernel's own node and record layout loads for the same traversal."""
+    return (NODE_BYTES * cnt[0] + REC_BYTES * cnt[1] + (SH_BYTES + extra_per_hit) * cnt[2] +
+            (RAY_IO_BYTES + extra_per_ray) * R)
+
+
+def roofline(kernel, nbytes, lbytes, t_ms, peak, peak_kind, **extra):
+    ach = nbytes / (t_ms * 1e-3) / 1e9
+    lach = lbytes / (t_ms * 1e-3) / 1e9
+    out = {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "frac_of_8tbs": ach / 8000.0, "peak_kind": peak_kind, "alg_bytes_per_launch": nbytes, "kernel_ms": t_ms,
+           "bytes": "survey count: 64 per node visit + 48 per record test + 192 per SH hit + ray I/O",
+           "layout": {"bytes_per_launch": lbytes, "achieved": lach, "frac": lach / peak,
+                      "bytes": "kernel layout: 112 per 4-wide node visit + 64 per record + 192 per SH hit + 44 per ray"}}
+    out.update(extra)
+    return out
 
 
 def reduce_ranks(ms: float, rays: float, device) -> tuple:
@@ -240,9 +282,9 @@ def run_grt(args):
     n_valid = int(G.valid.sum().item())
     R = n_valid * sum(ALLOC)
     # kernel launches per step: rebuild (bounds, Morton, 4 x 3 sort passes, hierarchy, records,
-    # refit, collapse init + one launch per collapse level), G-buffer 1, shade 5 (sample, bucket
-    # scan, ray scatter, trace, accumulate)
-    launches_per_step = 2 + 12 + 3 + 1 + COLLAPSE_LEVELS + 1 + 5
+    # refit, collapse init + the collapse), G-buffer 1, shade 5 (sample, bucket scan, ray
+    # scatter, trace, accumulate)
+    launches_per_step = 2 + 12 + 3 + 1 + COLLAPSE_LAUNCHES + 1 + 5
 
     for _ in range(args.warmup):
         step()
@@ -287,12 +329,10 @@ def run_grt(args):
     # ---- algorithmic bytes of the dominant kernel (the persistent trace kernel), from the
     # traversal counters of the same rays (counting pass outside the timed region)
     cnt = api.shade_count(S, G, E, *ALLOC, seed=SEED).cpu().numpy().astype(np.float64)
-    alg_bytes = NODE_BYTES * cnt[0] + REC_BYTES * cnt[1] + SH_BYTES * cnt[2] + RAY_IO_BYTES * R
     ph = np.array(phases)
     trace_s = float(np.mean(ph[:, 1])) * 1e-3
     shade_s = float(np.mean(shade_ms)) * 1e-3
     peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / trace_s / 1e9
 
     # ---- end to end through the public API with host buffers
     # Every step uploads its scene and map from pinned host memory and downloads its image.
@@ -371,6 +411,7 @@ def run_grt(args):
     if rank == 0 and world == 1 and not args.no_large:
         large = time_large(api, dev, args)
     den = time_denoise(api, G, outs[0], args) if rank == 0 else None
+    c1 = time_c1(api, dev, args) if rank == 0 else None
     rel = time_relight(api, S, G, E, R, args) if rank == 0 else None
 
     cpu = None
@@ -392,16 +433,14 @@ def run_grt(args):
                           "l2": "flushed between steps (256 MB write outside the timed events)",
                           "parallelism": f"replicas x{world}"},
                "gpu_launches": launches_per_step * args.steps,
-               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak,
-                            "traffic": TRACE_DRAM_BYTES if (args.k == 16 and W_IMG == 800) else None,
-                            "kernel": "k_trace_rays_ww",
-                            "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
-                            "kernel_ms": trace_s * 1e3,
-                            "phase_ms": {"sample": float(np.mean(ph[:, 0])), "trace": float(np.mean(ph[:, 1])),
-                                         "accumulate": float(np.mean(ph[:, 2])), "shade_call": shade_s * 1e3},
-                            "per_ray": {"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R}},
-               "clocks": clk, "e2e": e2e, "fwd_bwd": fb, "large": large, "denoise": den, "relight": rel, "cpu_baseline": cpu, "serving": serving,
+               "roofline": roofline(
+                   "k_trace_rays_ww", alg_bytes(cnt, R, ALLOC), layout_bytes(cnt, R), trace_s * 1e3, peak, peak_kind,
+                   traffic=TRACE_DRAM_BYTES if (args.k == 16 and W_IMG == 800) else None,
+                   l2=TRACE_L2 if (args.k == 16 and W_IMG == 800) else None,
+                   phase_ms={"sample": float(np.mean(ph[:, 0])), "trace": float(np.mean(ph[:, 1])),
+                             "accumulate": float(np.mean(ph[:, 2])), "shade_call": shade_s * 1e3},
+                   per_ray={"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R}),
+               "clocks": clk, "e2e": e2e, "fwd_bwd": fb, "large": large, "c1": c1, "denoise": den, "relight": rel, "cpu_baseline": cpu, "serving": serving,
                "wall_s_timed": t_wall}
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -525,26 +564,20 @@ def time_train(api, S, cam, E, dev, args):
     api.phase_timing(False)
     api.adjoint_timing(False)
     peak, peak_kind = measured_peaks()
-    save_bytes = (NODE_BYTES * cnt[0] + REC_BYTES * cnt[1] + (SH_BYTES + HIT_REC_BYTES) * cnt[2] +
-                  (RAY_IO_BYTES + 4) * R)
     replay_bytes = (HIT_REC_BYTES + SURFEL_BYTES + GRAD_RMW_BYTES) * cnt[2] + REPLAY_RAY_BYTES * R
 
-    def roof(kernel, nbytes, t_ms, unit_note):
-        ach = nbytes / (t_ms * 1e-3) / 1e9
-        return {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "peak_kind": peak_kind, "alg_bytes_per_launch": nbytes, "kernel_ms": t_ms, "bytes": unit_note}
-
     tr_ms, rp_ms = float(np.median(tr)), float(np.median(rp))
+    replay = roofline("k_adjoint_replay", replay_bytes, replay_bytes, rp_ms, peak, peak_kind)
+    replay["bytes"] = replay["layout"]["bytes"] = "(12 + 232 + 464) per composited hit + 64 per ray"
+    save = roofline("k_trace_rays_save", alg_bytes(cnt, R, TRAIN_ALLOC, HIT_REC_BYTES, 4),
+                    layout_bytes(cnt, R, HIT_REC_BYTES, 4), tr_ms, peak, peak_kind)
     return {"workload": "train_300k_400x400_16spp", "rays": R, "fwd_ms": ms["fwd"], "fwd_bwd_ms": ms["fwd_bwd"],
             "fwd_bwd_recompute_ms": ms["fwd_bwd_recompute"], "stored_hits": 64,
             "fwd_bwd_material_ms": ms["fwd_bwd_material"],
             "fwd_rays_per_s": R / (ms["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (ms["fwd_bwd"] * 1e-3),
             "fwd_bwd_recompute_rays_per_s": R / (ms["fwd_bwd_recompute"] * 1e-3),
             "per_ray": {"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R},
-            "roofline_save_trace": roof("k_trace_rays_save", save_bytes, tr_ms,
-                                        "112 per node + 64 per test + (192 + 12) per composited hit + 48 per ray"),
-            "roofline_replay": roof("k_adjoint_replay", replay_bytes, rp_ms,
-                                    "(12 + 232 + 464) per composited hit + 64 per ray")}
+            "roofline_save_trace": save, "roofline_replay": replay}
 
 
 def time_relight(api, S, G, E, R, args):
@@ -617,6 +650,108 @@ def time_relight_mesh(api, G, E, R):
     M.close()
     return {"triangles": int(len(m.tri)), "build_ms_incl_upload": build_ms, "ms": ms, "trace_ms": float(np.median(tr)),
             "rays_per_s": R / (ms * 1e-3), "status": st}
+
+
+def time_c1(api, dev, args):
+    """Plain forward of the sphere + plane scene: 8,000 RGB surfels, 64x64 G-buffer from the
+    camera at distance 3 (60 degree fov), 4 cosine rays per pixel, Lambert, constant white
+    map.  The frame is tiny and launch-bound: reported per frame (shading alone, G-buffer +
+    shading, and with the LBVH rebuild) as well as in rays/s."""
+    import torch
+    from paper_2607_22780_b300 import workloads as wl
+    sc = wl.scene_sphere_plane(8000, seed=SEED)
+    cam = wl.camera_c1(64, 64)
+    S = api.Scene.from_workload(sc, device=dev)
+    E = api.Environment(torch.from_numpy(wl.envmap_constant(1.0)).to(dev))
+    G = api.gbuffer_primary(S, cam)
+    outs = (torch.empty((64 * 64, 3), device=dev), torch.empty((64 * 64,), device=dev),
+            torch.empty((64 * 64, 3), device=dev))
+
+    def shade():
+        api.shade_pixels(S, G, E, 4, 0, 0, seed=SEED, brdf=0, outputs=outs)
+
+    def frame():
+        api.gbuffer_primary(S, cam, out=G)
+        shade()
+
+    def step():
+        S.rebuild()
+        frame()
+
+    res = {}
+    n = 200
+    for name, fn in (("shade", shade), ("gbuffer_shade", frame), ("rebuild_gbuffer_shade", step)):
+        for _ in range(10):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        res[name + "_us"] = a.elapsed_time(b) / n * 1e3
+    R = int(G.valid.sum().item()) * 4
+    return {"workload": "plain_8k_64x64_4cos", "surfels": 8000, "rays": R,
+            "rays_per_s_shade": R / (res["shade_us"] * 1e-6),
+            "rays_per_s_gbuffer_shade": R / (res["gbuffer_shade_us"] * 1e-6), **res, "frames_timed": n,
+            "l2": "scene (1 MB) L2-resident; launch-bound"}
+
+
+def run_cpu_baselines(args):
+    """The FP64 oracle timed on this host's cores for every configuration the survey lists:
+    the C1 frame whole, 4,096-ray samples of C2 and C4, the C3 backward at 32x32."""
+    import platform
+    import oracle
+    from paper_2607_22780_b300 import workloads as wl
+    cpu = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                cpu = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    out = {"metric": "oracle_rays_per_s", "cores": os.cpu_count(), "cpu": cpu, "host": platform.node()}
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    # C1: whole 64x64 frame, 4 cosine rays, constant white map, Lambert
+    sc1 = wl.scene_sphere_plane(8000, seed=SEED)
+    gb1 = oracle.gbuffer_f32(oracle.gbuffer(sc1, wl.camera_c1(64, 64)))
+    dt = timed(lambda: oracle.shade_pixels(sc1, gb1, wl.envmap_constant(1.0), 4, 0, 0, seed=SEED, brdf=0))
+    r1 = int(gb1["valid"].sum()) * 4
+    out["c1"] = {"rays": r1, "s": dt, "rays_per_s": r1 / dt, "sample": "whole frame"}
+    # C2: 128 valid pixels x 32 MIS rays = 4,096 rays of the 300k-surfel frame (80x80 view)
+    sc2, cam2, env2 = make_inputs(0)
+    gb2 = oracle_view_gbuffer(sc2, cam2)
+    pix = np.random.default_rng(0).choice(np.nonzero(gb2["valid"])[0], 128, replace=False).astype(np.int32)
+    dt = timed(lambda: oracle.shade_pixels(sc2, gb2, env2, *ALLOC, seed=SEED, pixels=pix))
+    out["c2"] = {"rays": 4096, "s": dt, "rays_per_s": 4096 / dt,
+                 "sample": "128 valid pixels x 32 rays of an 80x80 view from the benchmark camera",
+                 "full_frame_s_extrapolated": dt / 4096 * 10_071_424}
+    # C3: backward of the L2 loss at 32x32 (central crop of the 400x400 frame), 16 rays
+    from paper_2607_22780_b300 import workloads as wl2
+    c3 = wl2.Camera(cam2.eye, cam2.target, cam2.up, cam2.tan_half_fovy, 32, 32)
+    gb3 = oracle.gbuffer_f32(oracle.gbuffer(sc2, c3))
+    tgt = wl.target_image(SEED, 32, 32).reshape(-1, 3)
+    fw = oracle.shade_pixels(sc2, gb3, env2, *TRAIN_ALLOC, seed=SEED)
+    dl = (fw["color"] - tgt) * gb3["valid"][:, None]
+    dt = timed(lambda: oracle.backward_pixels(sc2, gb3, env2, *TRAIN_ALLOC, SEED, dl))
+    r3 = int(gb3["valid"].sum()) * sum(TRAIN_ALLOC)
+    out["c3_backward"] = {"rays": r3, "s": dt, "rays_per_s": r3 / dt, "sample": "32x32 view, whole"}
+    # C4: 256 valid pixels x 16 rays = 4,096 rays of the 2M-surfel scene (48x27 view)
+    sc4 = wl.scene_large(LARGE_N, seed=SEED)
+    gb4 = oracle.gbuffer_f32(oracle.gbuffer(sc4, wl.camera_orbit(SEED, 48, 27, LARGE_DISTANCE)))
+    env4 = wl.envmap_hdr(SEED + 1, ENV_W, ENV_H)
+    pix4 = np.random.default_rng(1).choice(np.nonzero(gb4["valid"])[0], 256, replace=False).astype(np.int32)
+    dt = timed(lambda: oracle.shade_pixels(sc4, gb4, env4, *LARGE_ALLOC, seed=SEED, pixels=pix4))
+    out["c4"] = {"rays": 4096, "s": dt, "rays_per_s": 4096 / dt,
+                 "sample": "256 valid pixels x 16 rays of a 48x27 view from the benchmark camera"}
+    print(json.dumps(out), flush=True)
 
 
 def time_denoise(api, G, color, args):
@@ -697,7 +832,6 @@ def time_large(api, dev, args):
         tr.append(api.phase_timing(read=True)[1])
     api.phase_timing(False)
     cnt = api.shade_count(S, G, E, *LARGE_ALLOC, seed=SEED).cpu().numpy().astype(np.float64)
-    alg = NODE_BYTES * cnt[0] + REC_BYTES * cnt[1] + SH_BYTES * cnt[2] + RAY_IO_BYTES * R
     trace_ms = float(np.median(tr))
     peak, peak_kind = measured_peaks()
     assert S.status() == 0
@@ -705,8 +839,8 @@ def time_large(api, dev, args):
             "fwd_ms": res["fwd"], "fwd_bwd_ms": res["fwd_bwd"],
             "fwd_rays_per_s": R / (res["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (res["fwd_bwd"] * 1e-3),
             "trace_kernel_ms": trace_ms, "per_ray": {"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R},
-            "roofline_trace": {"bound": "hbm", "achieved": alg / (trace_ms * 1e-3) / 1e9, "peak": peak,
-                               "unit": "GB/s", "frac": alg / (trace_ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind},
+            "roofline_trace": roofline("k_trace_rays_ww", alg_bytes(cnt, R, LARGE_ALLOC), layout_bytes(cnt, R),
+                                       trace_ms, peak, peak_kind),
             "steps": n, "l2": "inputs larger than L2"}
 
 
@@ -716,7 +850,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="grt", choices=["grt", "reference"])
-    ap.add_argument("--mode", default="shade", choices=["shade", "serve", "train", "large", "relight"])
+    ap.add_argument("--mode", default="shade", choices=["shade", "serve", "train", "large", "relight", "c1", "cpu"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
@@ -741,6 +875,13 @@ def main():
         run_train_only(args)
     elif args.mode == "relight":
         run_relight_only(args)
+    elif args.mode == "cpu":
+        run_cpu_baselines(args)
+    elif args.mode == "c1":
+        import torch
+        from paper_2607_22780_b300 import api
+        torch.cuda.set_device(0)
+        print(json.dumps(time_c1(api, torch.device("cuda"), args)), flush=True)
     elif args.mode == "large":
         import torch
         from paper_2607_22780_b300 import api

@@ -46,6 +46,7 @@ extern "C" {
 #define GRT_STATUS_NONFINITE 2  /* a ray with a NaN or infinite origin or direction was traced as a miss */
 #define GRT_STATUS_BAD_TREE 4   /* node reference out of range or walk longer than the tree */
 #define GRT_STATUS_BAD_INDEX 8  /* a pixel index outside the G-buffer was skipped            */
+#define GRT_STATUS_TIMEOUT 16   /* a bounded wait of the tree build gave up (tree incomplete) */
 
 /* Surfels (Sec. III-A "2D Gaussian splatting"; Sec. III-B "Bounding proxy").
  * mu[n][3] centre; quat[n][4] rotation (w,x,y,z), any non-zero norm, normalised inside:
@@ -116,8 +117,12 @@ int grt_rebuild_bvh(grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_pa
  * for GRT_NOALLOC_MAX_SURFELS surfels), which every device that loads libgrt keeps until
  * the process exits.
  *   - n > GRT_NOALLOC_MAX_SURFELS is rejected with GRT_ERR_ARG before any device work.
+ *   - The device that built `bvh` must be current; a call made while another device is
+ *     current is rejected with GRT_ERR_ARG.
  *   - The first call on a device looks up the scratch array's device address (with that
- *     device current); make that first call before any stream capture.
+ *     device current); make that first call before any stream capture.  The address is
+ *     cached per device for the life of the process: after cudaDeviceReset the library
+ *     (and every BVH built before the reset) is no longer usable on that device.
  *   - All calls share the one array: calls that may overlap on the GPU (other streams,
  *     other host threads) race on it and must be serialised by the caller.
  * Asynchronous on `stream`; results are identical to grt_rebuild_bvh. */
@@ -210,16 +215,43 @@ typedef struct {
     uint64_t seed;
 } grt_sampling;
 
+/* Workspace convention of the shading calls (grt_shade_pixels, grt_shade_pixels_save,
+ * grt_shade_backward, grt_shade_backward_saved, grt_shade_batch): the last two arguments
+ * before `stream` are an optional device workspace and its size in bytes.  NULL: the call
+ * takes its scratch from the device's stream-ordered pool (cudaMallocAsync) and returns it
+ * on `stream` before it returns.  Non-NULL: a caller-owned device buffer, 256-byte aligned
+ * and at least the size the matching *_workspace_size call reports (else GRT_ERR_ARG, no
+ * device work), used instead of the pool; the call reads and writes it on `stream` only, so
+ * the caller may reuse it for the next call on the same stream.  The contents need no
+ * initialisation and are meaningless afterwards.  The other calls (G-buffer, relighting,
+ * material adjoint, tree builds) take their scratch from the pool. */
+
+/* Bytes of workspace of grt_shade_pixels and grt_shade_batch over n_rays ray slots (the
+ * sum of n_pixels x N_r over the requests): direction and traced (c_rt, T) per slot (32
+ * bytes), a ray counter, and the order in which the walk takes the rays (12 bytes per slot
+ * and 266 KB of bucket counters).  grt_shade_pixels_save keeps directions and totals in its
+ * `saved` buffer, so this size bounds its workspace too.  0 (with the error text) for
+ * n_rays < 0. */
+size_t grt_shade_workspace_size(int64_t n_rays);
+
+/* Bytes of workspace of grt_shade_backward (saved = 0: the recomputing form, one or two
+ * chunk buffers of at most 8M rays holding directions, totals, a transient record of 64
+ * hits per ray, adjoints and the ray order) or grt_shade_backward_saved (saved = 1: the
+ * adjoint per ray and the list of rays longer than the record, 24 bytes per ray slot).
+ * 0 (with the error text) for invalid arguments. */
+size_t grt_shade_backward_workspace_size(int32_t n_pixels, const grt_sampling* sampling, int32_t saved);
+
 /* Shade pixels (Eq. 13): out_color[i][3] = (1/N_r) sum g/q, out_vis[i] = (1/N_r) sum V,
  * out_ind[i][3] = (1/N_r) sum L_ind for i < n_pixels, pixel index pixel_list[i]
  * (NULL = all W*H pixels in order).  Samples below the horizon count V = L_ind = 0.
  * out_vis / out_ind may be NULL.  Ray buffers (32 bytes per ray slot, pixels x N_r) and the
- * order in which the walk takes the rays (12 bytes per slot) come from the stream-ordered
- * pool. */
+ * order in which the walk takes the rays (12 bytes per slot) live in `workspace`
+ * (grt_shade_workspace_size(n_pixels x N_r) bytes) or, with workspace NULL, in the
+ * stream-ordered pool. */
 int grt_shade_pixels(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
                      const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
                      const int32_t* pixel_list, int32_t n_pixels, float* out_color, float* out_vis,
-                     float* out_ind, void* stream);
+                     float* out_ind, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Adjoint of grt_shade_pixels with respect to the surfels, given dL_dcolor[n_pixels][3]
  * and optional dL_dvis[n_pixels], dL_dind[n_pixels][3] (NULL = 0).  Nothing is kept from
@@ -231,7 +263,7 @@ int grt_shade_backward(const grt_bvh* bvh, const grt_surfels* surfels, const grt
                        const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
                        const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
                        const float* dL_dvis, const float* dL_dind, const grt_grads* grads,
-                       void* stream);
+                       void* workspace, size_t workspace_bytes, void* stream);
 
 /* Stored forward record for the backward pass (Sec. III-B: the loss gradient flows back
  * through the secondary trace into the surfels).  grt_shade_pixels_save does what
@@ -246,19 +278,21 @@ int grt_shade_backward(const grt_bvh* bvh, const grt_surfels* surfels, const grt
  * sampling, pixel_list, n_pixels and max_hits as the save call, with the surfels unchanged
  * in between (a replayed surfel id outside the scene is skipped and reported as
  * GRT_STATUS_BAD_INDEX).  grt_shade_saved_bytes returns 0 (and sets the error text) for
- * invalid arguments; max_hits is in [0, GRT_MAX_SAVED_HITS].  The save call takes 12 bytes
- * per ray slot of stream-ordered pool scratch for the walk's ray order. */
+ * invalid arguments; max_hits is in [0, GRT_MAX_SAVED_HITS].  The save call's workspace
+ * (or pool scratch) holds the walk's ray order, 12 bytes per ray slot. */
 #define GRT_MAX_SAVED_HITS 64
 size_t grt_shade_saved_bytes(int32_t n_pixels, const grt_sampling* sampling, int32_t max_hits);
 int grt_shade_pixels_save(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
                           const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
                           const int32_t* pixel_list, int32_t n_pixels, float* out_color, float* out_vis,
-                          float* out_ind, int32_t max_hits, void* saved, size_t saved_bytes, void* stream);
+                          float* out_ind, int32_t max_hits, void* saved, size_t saved_bytes, void* workspace,
+                          size_t workspace_bytes, void* stream);
 int grt_shade_backward_saved(const grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
                              const grt_gbuffer* gbuffer, const grt_envmap* env, const grt_sampling* sampling,
                              const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
                              const float* dL_dvis, const float* dL_dind, int32_t max_hits, const void* saved,
-                             size_t saved_bytes, const grt_grads* grads, void* stream);
+                             size_t saved_bytes, const grt_grads* grads, void* workspace, size_t workspace_bytes,
+                             void* stream);
 
 /* grt_shade_pixels plus out_light[n_pixels][3] = (1/N_r) sum_j L_i(w_j), the mean incident
  * radiance of the lighting regulariser (Eq. 16), L_i = V L_env + L_ind (samples below the
@@ -306,9 +340,11 @@ typedef struct {
  * resolutions and sample counts) in one wavefront pass: every request's samples go into
  * one ray list, one persistent trace launch serves them all, and each pixel is summed in
  * a fixed order.  Each request's outputs are bit-identical to shading it alone with
- * grt_shade_pixels.  Ray buffers (44 bytes per ray slot) come from the stream-ordered pool. */
+ * grt_shade_pixels.  Ray buffers (44 bytes per ray slot) live in `workspace`
+ * (grt_shade_workspace_size of the requests' total ray slots) or, with workspace NULL, in the
+ * stream-ordered pool. */
 int grt_shade_batch(const grt_shade_request* requests, int32_t n_requests,
-                    const grt_trace_params* params, void* stream);
+                    const grt_trace_params* params, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Relighting under a novel map (Sec. III-E).
  * Trace_attr (Eq. 14), Gaussian backend: the hits of Trace (Eq. 8), same order and

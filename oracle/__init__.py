@@ -27,6 +27,13 @@ FLAG_ALPHA_MIN = 1
 FLAG_ALPHA_MAX = 2
 FLAG_T_MIN = 4
 FLAG_VALID = 8
+# audit flags (audit_rays / audit_pixels): near-boundary causes of an FP32/FP64 decision split
+AUDIT_TIE = 16
+AUDIT_PLANE_TIE = 32
+AUDIT_RANGE = 64
+AUDIT_GRAZE = 128
+AUDIT_HORIZON = 256
+AUDIT_DIR = 512
 
 
 def build(force: bool = False) -> str:
@@ -86,6 +93,9 @@ def _declare(L):
     L.or_backward_material.argtypes = [P, P, P, P, P, P, C.c_int, P, P, P, P, P, P, P, C.c_int]
     L.or_backward_rays.argtypes = [P, P, C.c_int, P, P, P, P, P, P, C.c_int]
     L.or_backward_pixels.argtypes = [P, P, P, P, P, P, C.c_int, P, P, P, P, P, C.c_int]
+    L.or_audit_rays.argtypes = [P, P, C.c_int, P, P, P, C.c_int, P, P, P, P, P, C.c_int]
+    L.or_audit_pixels.argtypes = [P, P, P, P, P, P, C.c_int, C.c_int, P, P, P, P, P, C.c_int]
+    L.or_sample_direction_d64.argtypes = [P, P, P, P, P, C.c_float, C.c_int, C.c_int, P, P]
     L.or_philox4x32_10.argtypes = [P, P, P]
     L.or_sincos2pi.argtypes = [C.c_float, P, P]
     L.or_atan2f.argtypes = [C.c_float, C.c_float]
@@ -204,6 +214,41 @@ def trace_rays(scene, ray_o, ray_d, params=None, max_hits=64, nthreads=0):
     lib().or_trace_rays(_ref(s), _ref(P), R, _ptr(ro), _ptr(rd), _ptr(rgb), _ptr(op), _ptr(T),
                         max_hits, _ptr(hits), _ptr(nh), _ptr(fl), nthreads)
     return dict(rgb=rgb, opacity=op, T=T, hits=hits, nhits=nh, flags=fl)
+
+
+def audit_rays(scene, ray_o, ray_d, ray_d64=None, params=None, max_hits=64, nthreads=0):
+    """The rays traced twice: list A with the FP32 decisions of every other function here
+    (plane test and depth order of Eq. 7-8), list B with those decisions in FP64 (along
+    ray_d64 when given).  Returns dict hits_a, n_a, hits_b, n_b (composited ids and counts)
+    and flags (FLAG_* / AUDIT_* near-boundary causes, each from an a-priori bound)."""
+    keep = _Keep()
+    ro, rd = _f32(ray_o).reshape(-1, 3), _f32(ray_d).reshape(-1, 3)
+    R = ro.shape[0]
+    d64 = None if ray_d64 is None else np.ascontiguousarray(ray_d64, np.float64).reshape(R, 3)
+    out = dict(hits_a=np.full((R, max_hits), -1, np.int32), n_a=np.zeros(R, np.int32),
+               hits_b=np.full((R, max_hits), -1, np.int32), n_b=np.zeros(R, np.int32), flags=np.zeros(R, np.uint32))
+    s = _scene(scene, keep); P = _params(params)
+    lib().or_audit_rays(_ref(s), _ref(P), R, _ptr(ro), _ptr(rd), _ptr(d64), max_hits, _ptr(out["hits_a"]),
+                        _ptr(out["n_a"]), _ptr(out["hits_b"]), _ptr(out["n_b"]), _ptr(out["flags"]), nthreads)
+    return out
+
+
+def audit_pixels(scene, gb, env, n_cos, n_ggx, n_env, seed, pixels, brdf=1, params=None, max_hits=64, nthreads=0):
+    """audit_rays for the MIS shading rays of `pixels` (slot i * N_r + j = sample j of
+    pixels[i]): list A from the FP32 sampler and decisions, list B from an FP64 sampler
+    (same uniforms and texel choice, libm trigonometry) and FP64 decisions.  n_a = n_b = -1
+    marks a slot with no sample on either side."""
+    keep = _Keep()
+    s = _scene(scene, keep); P = _params(params); g = _gbuf(gb, keep); e = _env(env, keep)
+    S = _sampling(n_cos, n_ggx, n_env, seed, brdf)
+    pl = np.ascontiguousarray(pixels, np.int32)
+    R = pl.shape[0] * (n_cos + n_ggx + n_env)
+    out = dict(hits_a=np.full((R, max_hits), -1, np.int32), n_a=np.zeros(R, np.int32),
+               hits_b=np.full((R, max_hits), -1, np.int32), n_b=np.zeros(R, np.int32), flags=np.zeros(R, np.uint32))
+    lib().or_audit_pixels(_ref(s), _ref(P), _ref(g), _ref(e), _ref(S), _ptr(pl), pl.shape[0], max_hits,
+                          _ptr(out["hits_a"]), _ptr(out["n_a"]), _ptr(out["hits_b"]), _ptr(out["n_b"]),
+                          _ptr(out["flags"]), nthreads)
+    return out
 
 
 def gbuffer(scene, camera, params=None, pixels=None, nthreads=0):

@@ -1744,3 +1744,334 @@ int or_shade_relight_mesh(const or_mesh* m, const or_params* P, const or_gbuf* g
                    nthreads);
     return 0;
 }
+
+/* ========================================================================== *
+ * Audit of the FP32 decisions.  The same rays with every decision of Part A    *
+ * taken in FP64 instead -- the plane test and depth order of Eq. 7-8 from the  *
+ * FP64 surfel frame, and the sampled direction of Sec. III-D from FP64 frames  *
+ * and libm trigonometry (the texel of an environment sample is still chosen    *
+ * from the FP32 tables with the same uniforms) -- so that the FP32 decision    *
+ * reading can be checked against the FP64 one.  A ray whose two composited     *
+ * lists differ must be near a boundary; the flags below say which, each with   *
+ * an a-priori bound on the FP32 error of the quantity that decides.            *
+ * ========================================================================== */
+
+#define OR_AUDIT_TIE 16u        /* consecutive hits whose FP64 depths lie within their FP32 depth errors */
+#define OR_AUDIT_PLANE_TIE 32u  /* such a tie between coplanar surfels: geometry leaves their order open   */
+#define OR_AUDIT_RANGE 64u      /* a depth within its FP32 error of t_min or t_max                          */
+#define OR_AUDIT_GRAZE 128u     /* |n.d| within its FP32 error of eps_nd                                   */
+#define OR_AUDIT_HORIZON 256u   /* a sampled direction (or w_o for GGX) within 1e-6 of the horizon         */
+#define OR_AUDIT_DIR 512u       /* an alpha_min decision flips between the FP32 and the FP64 direction     */
+
+static const double U32_D = 5.9604644775390625e-08; /* 2^-24, unit roundoff of FP32 */
+
+/* Duff et al.'s orthonormal basis in FP64. */
+static void frame_d64(d3 n, d3* b1, d3* b2) {
+    double sign = n.z >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sign + n.z);
+    double b = n.x * n.y * a;
+    *b1 = md3(1.0 + sign * n.x * n.x * a, sign * b, -sign * n.x);
+    *b2 = md3(b, sign + n.y * n.y * a, -n.y);
+}
+
+static d3 to_world_d64(d3 b1, d3 b2, d3 n, d3 l) {
+    return md3(b1.x * l.x + b2.x * l.y + n.x * l.z, b1.y * l.x + b2.y * l.y + n.y * l.z,
+               b1.z * l.x + b2.z * l.y + n.z * l.z);
+}
+
+/* The samplers of Part A (Malley's cosine sampling; Heitz's visible normals) in FP64. */
+static d3 sample_cos_d64(d3 n, d3 b1, d3 b2, double u0, double u1) {
+    double r = sqrt(u0), ph = 2.0 * PI_D * u1;
+    double lz = 1.0 - u0;
+    return to_world_d64(b1, b2, n, md3(r * cos(ph), r * sin(ph), sqrt(lz > 0.0 ? lz : 0.0)));
+}
+
+static int sample_ggx_d64(d3 n, d3 b1, d3 b2, d3 wo, double rough, double u0, double u1, d3* out, uint32_t* fl) {
+    d3 v = md3(dotd(wo, b1), dotd(wo, b2), dotd(wo, n));
+    if (fabs(v.z) <= 1e-6) *fl |= OR_AUDIT_HORIZON;
+    if (!(v.z > 0.0)) return 0;
+    double a = rough * rough;
+    if (a < 1e-4) a = 1e-4;
+    d3 vh = normd(md3(a * v.x, a * v.y, v.z));
+    double lensq = vh.x * vh.x + vh.y * vh.y;
+    d3 T1 = lensq > 0.0 ? md3(-vh.y / sqrt(lensq), vh.x / sqrt(lensq), 0.0) : md3(1.0, 0.0, 0.0);
+    d3 T2 = md3(vh.y * T1.z - vh.z * T1.y, vh.z * T1.x - vh.x * T1.z, vh.x * T1.y - vh.y * T1.x);
+    double r = sqrt(u0), ph = 2.0 * PI_D * u1;
+    double t1 = r * cos(ph), t2 = r * sin(ph);
+    double sh = 0.5 * (1.0 + vh.z);
+    double q1 = 1.0 - t1 * t1;
+    t2 = (1.0 - sh) * sqrt(q1 > 0.0 ? q1 : 0.0) + sh * t2;
+    double q2 = q1 - t2 * t2;
+    double nz = sqrt(q2 > 0.0 ? q2 : 0.0);
+    d3 nh = md3(t1 * T1.x + t2 * T2.x + nz * vh.x, t1 * T1.y + t2 * T2.y + nz * vh.y, t1 * T1.z + t2 * T2.z + nz * vh.z);
+    d3 ne = md3(a * nh.x, a * nh.y, nh.z > 0.0 ? nh.z : 0.0);
+    ne = dotd(ne, ne) > 0.0 ? normd(ne) : md3(0.0, 0.0, 1.0);
+    double d2 = 2.0 * dotd(v, ne);
+    *out = to_world_d64(b1, b2, n, md3(d2 * ne.x - v.x, d2 * ne.y - v.y, d2 * ne.z - v.z));
+    return 1;
+}
+
+/* Sample j of pixel p with FP64 directions (same uniforms and texel choice as draw_sample). */
+static int draw_sample_d64(const or_sampling* S, const env_tab* et, const or_env* env, int pix, int j, d3 n, d3 b1,
+                           d3 b2, d3 wo, double rough, d3* w, uint32_t* fl) {
+    uint32_t ctr[4] = {(uint32_t)pix, (uint32_t)j, 0u, 0u}, key[2] = {S->seed_lo, S->seed_hi}, r[4];
+    or_philox4x32_10(ctr, key, r);
+    float u0 = unif24(r[0]), u1 = unif24(r[1]), u2 = unif24(r[2]), u3 = unif24(r[3]);
+    int ok = 1;
+    if (j < S->n_cos) {
+        *w = sample_cos_d64(n, b1, b2, u0, u1);
+    } else if (j < S->n_cos + S->n_ggx) {
+        ok = sample_ggx_d64(n, b1, b2, wo, rough, u0, u1, w, fl);
+    } else {
+        int row = cdf_search(et->marg, env->H, u0);
+        int col = cdf_search(et->cond + (size_t)row * (env->W + 1), env->W, u1);
+        double ph = 2.0 * PI_D * (((double)col + u3) / env->W), th = PI_D * (((double)row + u2) / env->H);
+        *w = md3(sin(th) * sin(ph), cos(th), sin(th) * cos(ph));
+    }
+    if (ok) {
+        double c = dotd(*w, n);
+        if (fabs(c) <= 1e-6) *fl |= OR_AUDIT_HORIZON;
+        if (!(c > 0.0)) ok = 0;
+    }
+    return ok;
+}
+
+typedef struct { double tau, alpha, err; int id; } ahit_t;
+
+static int ahit_cmp(const void* pa, const void* pb) {
+    const ahit_t* a = (const ahit_t*)pa;
+    const ahit_t* b = (const ahit_t*)pb;
+    if (a->tau < b->tau) return -1;
+    if (a->tau > b->tau) return 1;
+    return (a->id > b->id) - (a->id < b->id);
+}
+
+typedef struct { double tau; uint32_t flag; } aevent_t;
+
+typedef struct {
+    hit_t* A; int capA;
+    ahit_t* B; int capB;
+    aevent_t* E; int capE;
+    double* Tk; int capT;
+} audit_ws;
+
+static void* grow(void* p, int* cap, int need, size_t elem) {
+    if (need <= *cap) return p;
+    while (*cap < need) *cap = *cap ? 2 * *cap : 64;
+    return realloc(p, elem * (size_t)*cap);
+}
+
+/* One ray: list A with the FP32 decisions of Part A along d32 (as trace_one), list B with
+ * the plane test and depth order in FP64 along d64.  Both admit a hit by o G >= alpha_min
+ * in FP64 along their own direction and composite with FP64 alphas.  Writes the first
+ * maxl composited ids of each, the composited counts, and the audit flags. */
+static void audit_ray(const or_scene* sc, const surf_pre* pre, const or_params* P, f3 o32, f3 d32, d3 d64,
+                      audit_ws* ws, int maxl, int32_t* la, int32_t* na, int32_t* lb, int32_t* nb, uint32_t* flags) {
+    const d3 o = f2d(o32), dA = f2d(d32);
+    const double amin = P->alpha_min;
+    int nA = 0, nB = 0, nE = 0;
+    uint32_t fl = 0, dummy = 0;
+    for (int i = 0; i < sc->n; ++i) {
+        const double* m = sc->mu + 3 * (size_t)i;
+        const d3 mu = md3(m[0], m[1], m[2]), n = pre[i].n, w = subd(mu, o);
+        const double su = sc->scale[2 * (size_t)i], sv = sc->scale[2 * (size_t)i + 1];
+        /* world B: FP64 plane test along d64, with the FP32 error bound of its quantities */
+        const double den = dotd(n, d64), num = dotd(n, w);
+        const double sn = fabs(n.x * w.x) + fabs(n.y * w.y) + fabs(n.z * w.z);
+        const double sd = fabs(n.x * d64.x) + fabs(n.y * d64.y) + fabs(n.z * d64.z);
+        const double dd = fabs(n.x) * fabs(dA.x - d64.x) + fabs(n.y) * fabs(dA.y - d64.y) +
+                          fabs(n.z) * fabs(dA.z - d64.z);
+        const double den_err = 16.0 * U32_D * sd + dd;
+        const double tauB = den != 0.0 ? num / den : INFINITY;
+        const double tau_err = fabs(den) > 0.0 ? (16.0 * U32_D * sn + fabs(tauB) * den_err) / fabs(den) +
+                                                     4.0 * U32_D * fabs(tauB) : INFINITY;
+        const int planeB = fabs(den) >= P->eps_nd && tauB > P->t_min && tauB < P->t_max;
+        /* world A: the FP32 plane test of Part A along d32 */
+        float tau32 = 0.f, den32 = 0.f;
+        const int planeA = plane_test_f(pre[i].n32, pre[i].mu32, o32, d32, P->t_min, P->t_max, P->eps_nd, &tau32,
+                                        &den32);
+        if (!planeA && !planeB) continue;
+        /* alpha along each direction (FP64 geometry) */
+        double oG[2];
+        const d3 dirs[2] = {dA, d64};
+        for (int k = 0; k < 2; ++k) {
+            const double nd = dotd(n, dirs[k]);
+            const double t = num / nd;
+            const d3 dp = subd(addd(o, muld(dirs[k], t)), mu);
+            const double u = dotd(dp, pre[i].tu) / su, v = dotd(dp, pre[i].tv) / sv;
+            oG[k] = sc->opacity[i] * exp(-0.5 * (u * u + v * v));
+        }
+        /* the plane decisions matter only for a surfel that the Gaussian admits */
+        uint32_t pf = 0;
+        if (oG[0] >= amin * (1.0 - 1e-4) || oG[1] >= amin * (1.0 - 1e-4)) {
+            if (fabs(fabs(den) - P->eps_nd) <= den_err) pf |= OR_AUDIT_GRAZE;
+            if (fabs(tauB - P->t_min) <= tau_err || fabs(tauB - P->t_max) <= tau_err) pf |= OR_AUDIT_RANGE;
+        }
+        if (pf) {
+            ws->E = grow(ws->E, &ws->capE, nE + 1, sizeof(aevent_t));
+            ws->E[nE++] = (aevent_t){tauB, pf};
+        }
+        uint32_t af = 0;
+        if (fabs(oG[1] / amin - 1.0) < 1e-4) af |= OR_FLAG_ALPHA_MIN;
+        if ((oG[0] >= amin) != (oG[1] >= amin)) af |= OR_AUDIT_DIR;
+        if (af) {
+            ws->E = grow(ws->E, &ws->capE, nE + 1, sizeof(aevent_t));
+            ws->E[nE++] = (aevent_t){tauB, af};
+        }
+        const double amax = P->alpha_max;
+        if (planeA && oG[0] >= amin) {
+            ws->A = grow(ws->A, &ws->capA, nA + 1, sizeof(hit_t));
+            hit_t* h = &ws->A[nA++];
+            memset(h, 0, sizeof(*h));
+            h->tau32 = tau32; h->id = i; h->alpha = oG[0] > amax ? amax : oG[0];
+        }
+        if (planeB && oG[1] >= amin) {
+            ws->B = grow(ws->B, &ws->capB, nB + 1, sizeof(ahit_t));
+            ws->B[nB++] = (ahit_t){tauB, oG[1] > amax ? amax : oG[1], tau_err, i};
+        }
+    }
+    qsort(ws->A, (size_t)nA, sizeof(hit_t), hit_cmp);
+    qsort(ws->B, (size_t)nB, sizeof(ahit_t), ahit_cmp);
+    ws->Tk = grow(ws->Tk, &ws->capT, (nA > nB ? nA : nB) + 1, sizeof(double));
+    double T;
+    const int KA = composite_count(ws->A, nA, P, ws->Tk, &T, &dummy);
+    /* list B: the same termination rule, T_min flags from the FP64 decisions */
+    double TB = 1.0;
+    int KB = 0;
+    for (; KB < nB; ++KB) {
+        TB *= 1.0 - ws->B[KB].alpha;
+        if (fabs(TB / (double)P->T_min - 1.0) < 1e-4) fl |= OR_FLAG_T_MIN;
+        if (TB < (double)P->T_min) { ++KB; break; }
+    }
+    /* events count up to the depth where either list stops (one hit beyond) */
+    double stop = INFINITY;
+    if (KB < nB || KA < nA) {
+        double sb = KB < nB ? ws->B[KB].tau + ws->B[KB].err : INFINITY;
+        double sa = KA < nA ? (double)ws->A[KA].tau32 : INFINITY;
+        stop = sb > sa ? sb : sa;
+        if (!isfinite(stop)) stop = INFINITY;
+    }
+    for (int e = 0; e < nE; ++e)
+        if (ws->E[e].tau <= stop) fl |= ws->E[e].flag;
+    for (int k = 0; k + 1 < nB && k <= KB; ++k) {
+        const ahit_t* h0 = &ws->B[k];
+        const ahit_t* h1 = &ws->B[k + 1];
+        if (h1->tau - h0->tau <= h0->err + h1->err) {
+            fl |= OR_AUDIT_TIE;
+            const surf_pre* p0 = &pre[h0->id];
+            const surf_pre* p1 = &pre[h1->id];
+            const double* m0 = sc->mu + 3 * (size_t)h0->id;
+            const double* m1 = sc->mu + 3 * (size_t)h1->id;
+            const d3 dm = md3(m1[0] - m0[0], m1[1] - m0[1], m1[2] - m0[2]);
+            if (fabs(dotd(p0->n, p1->n)) >= 1.0 - 1e-12 && fabs(dotd(p0->n, dm)) <= 1e-6) fl |= OR_AUDIT_PLANE_TIE;
+        }
+    }
+    for (int k = 0; k < maxl; ++k) {
+        la[k] = k < KA ? ws->A[k].id : -1;
+        lb[k] = k < KB ? ws->B[k].id : -1;
+    }
+    *na = KA;
+    *nb = KB;
+    *flags = fl;
+}
+
+static void audit_ws_free(audit_ws* ws) { free(ws->A); free(ws->B); free(ws->E); free(ws->Tk); }
+
+/* Audit of R given rays: d32 the FP32 direction both lists start from (d64 = d32 exactly
+ * when ray_d64 is NULL). */
+int or_audit_rays(const or_scene* sc, const or_params* P, int R, const float* ray_o, const float* ray_d,
+                  const double* ray_d64, int maxl, int32_t* list_a, int32_t* n_a, int32_t* list_b, int32_t* n_b,
+                  uint32_t* out_flags, int nthreads) {
+    surf_pre* pre = precompute(sc);
+    int nt = nthreads_or_default(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        audit_ws ws = {0};
+#pragma omp for schedule(dynamic, 4)
+        for (int r = 0; r < R; ++r) {
+            f3 o = mk3(ray_o[3 * r], ray_o[3 * r + 1], ray_o[3 * r + 2]);
+            f3 d = mk3(ray_d[3 * r], ray_d[3 * r + 1], ray_d[3 * r + 2]);
+            d3 d64 = ray_d64 ? md3(ray_d64[3 * r], ray_d64[3 * r + 1], ray_d64[3 * r + 2]) : f2d(d);
+            audit_ray(sc, pre, P, o, d, d64, &ws, maxl, list_a + (size_t)r * maxl, n_a + r,
+                      list_b + (size_t)r * maxl, n_b + r, out_flags + r);
+        }
+        audit_ws_free(&ws);
+    }
+    free(pre);
+    return 0;
+}
+
+/* Audit of the shading rays of a pixel list: slot i * N_r + j holds sample j of pixel
+ * pixel_list[i], drawn by the FP32 sampler of Part A (list A) and by its FP64 restatement
+ * (list B).  A slot without a sample on one side and one on the other gets an empty list
+ * there; n_a = n_b = -1 marks a slot without a sample on both sides. */
+int or_audit_pixels(const or_scene* sc, const or_params* P, const or_gbuf* gb, const or_env* env,
+                    const or_sampling* S, const int32_t* pixel_list, int n_pixels, int maxl, int32_t* list_a,
+                    int32_t* n_a, int32_t* list_b, int32_t* n_b, uint32_t* out_flags, int nthreads) {
+    surf_pre* pre = precompute(sc);
+    env_tab et;
+    env_tab_build(env, &et);
+    const int Nr = S->n_cos + S->n_ggx + S->n_env;
+    int nt = nthreads_or_default(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        audit_ws ws = {0};
+#pragma omp for schedule(dynamic, 1)
+        for (int i = 0; i < n_pixels; ++i) {
+            const int p = pixel_list[i];
+            f3 x32, n32, b1, b2, wo32;
+            d3 n, wo;
+            pixel_setup(gb, p, &x32, &n32, &b1, &b2, &wo32, &n, &wo);
+            d3 c1, c2;
+            frame_d64(n, &c1, &c2);
+            for (int j = 0; j < Nr; ++j) {
+                const size_t s = (size_t)i * Nr + j;
+                int32_t* la = list_a + s * maxl;
+                int32_t* lb = list_b + s * maxl;
+                uint32_t fl = 0;
+                sample_t a = gb->valid[p] ? draw_sample(S, &et, env, p, j, n32, b1, b2, wo32, gb->rough[p])
+                                          : (sample_t){mk3(0, 0, 0), 0};
+                d3 w64 = md3(0, 0, 0);
+                int okb = gb->valid[p] ? draw_sample_d64(S, &et, env, p, j, n, c1, c2, wo, gb->rough[p], &w64, &fl) : 0;
+                if (!a.ok && !okb) {
+                    for (int k = 0; k < maxl; ++k) la[k] = lb[k] = -1;
+                    n_a[s] = n_b[s] = -1;
+                    out_flags[s] = fl;
+                    continue;
+                }
+                uint32_t rf = 0;
+                int32_t ka = 0, kb = 0;
+                audit_ray(sc, pre, P, x32, a.ok ? a.w32 : mk3((float)w64.x, (float)w64.y, (float)w64.z),
+                          okb ? w64 : f2d(a.w32), &ws, maxl, la, &ka, lb, &kb, &rf);
+                if (!a.ok) { for (int k = 0; k < maxl; ++k) la[k] = -1; ka = 0; }
+                if (!okb) { for (int k = 0; k < maxl; ++k) lb[k] = -1; kb = 0; }
+                n_a[s] = ka;
+                n_b[s] = kb;
+                out_flags[s] = fl | rf;
+            }
+        }
+        audit_ws_free(&ws);
+    }
+    env_tab_free(&et);
+    free(pre);
+    return 0;
+}
+
+/* Sample j of a pixel drawn by the audit's FP64 sampler (for checks against the FP32
+ * sampler of or_sample_direction).  Returns 1 when a direction was drawn above the horizon;
+ * *flags gets OR_AUDIT_HORIZON for a direction (or GGX w_o) within 1e-6 of the horizon. */
+int or_sample_direction_d64(const or_sampling* S, const or_env* env, const float* pos, const float* nrm,
+                            const float* eye, float rough, int pix, int j, double* w_out, uint32_t* flags) {
+    env_tab et;
+    env_tab_build(env, &et);
+    d3 n = normd(md3(nrm[0], nrm[1], nrm[2])), b1, b2;
+    frame_d64(n, &b1, &b2);
+    d3 wo = normd(md3((double)eye[0] - pos[0], (double)eye[1] - pos[1], (double)eye[2] - pos[2]));
+    d3 w = md3(0, 0, 0);
+    uint32_t fl = 0;
+    int ok = draw_sample_d64(S, &et, env, pix, j, n, b1, b2, wo, rough, &w, &fl);
+    env_tab_free(&et);
+    w_out[0] = w.x; w_out[1] = w.y; w_out[2] = w.z;
+    *flags = fl;
+    return ok;
+}

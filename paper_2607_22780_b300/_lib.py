@@ -22,6 +22,7 @@ STATUS_STACK_OVERFLOW = 1
 STATUS_NONFINITE = 2
 STATUS_BAD_TREE = 4
 STATUS_BAD_INDEX = 8
+STATUS_TIMEOUT = 16
 
 P = C.c_void_p
 
@@ -92,24 +93,27 @@ SIGNATURES = {
                                       C.c_int32, C.c_int32, P, P, P, P, P, P, P, P, P]),
     "grt_env_tables_bytes": (C.c_size_t, [C.c_int32, C.c_int32]),
     "grt_env_prepare": (C.c_int, [P, C.c_int32, C.c_int32, P, P]),
+    "grt_shade_workspace_size": (C.c_size_t, [C.c_int64]),
+    "grt_shade_backward_workspace_size": (C.c_size_t, [C.c_int32, C.POINTER(Sampling), C.c_int32]),
     "grt_shade_pixels": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
-                                   C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P, P]),
+                                   C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P, P, C.c_size_t,
+                                   P]),
     "grt_shade_backward": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                      C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P,
-                                     C.POINTER(Grads), P]),
+                                     C.POINTER(Grads), P, C.c_size_t, P]),
     "grt_shade_saved_bytes": (C.c_size_t, [C.c_int32, C.POINTER(Sampling), C.c_int32]),
     "grt_shade_pixels_save": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                         C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P,
-                                        C.c_int32, P, C.c_size_t, P]),
+                                        C.c_int32, P, C.c_size_t, P, C.c_size_t, P]),
     "grt_shade_backward_saved": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                            C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P,
-                                           C.c_int32, P, C.c_size_t, C.POINTER(Grads), P]),
+                                           C.c_int32, P, C.c_size_t, C.POINTER(Grads), P, C.c_size_t, P]),
     "grt_shade_pixels_light": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                          C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P, P, P]),
     "grt_shade_backward_material": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                               C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P, P, P,
                                               P, P, P]),
-    "grt_shade_batch": (C.c_int, [C.POINTER(ShadeRequest), C.c_int32, C.POINTER(TraceParams), P]),
+    "grt_shade_batch": (C.c_int, [C.POINTER(ShadeRequest), C.c_int32, C.POINTER(TraceParams), P, C.c_size_t, P]),
     "grt_trace_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), P, P, C.c_int32, P, P]),
     "grt_shade_count": (C.c_int, [P, C.POINTER(Surfels), C.POINTER(TraceParams), C.POINTER(GBuffer),
                                   C.POINTER(EnvMap), C.POINTER(Sampling), P, C.c_int32, P, P]),

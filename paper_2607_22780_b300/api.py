@@ -278,10 +278,37 @@ def sampling(n_cos, n_ggx, n_env, seed, brdf=1) -> L.Sampling:
     return L.Sampling(int(n_cos), int(n_ggx), int(n_env), int(brdf), int(seed) & 0xFFFFFFFFFFFFFFFF)
 
 
+def _workspace(ws):
+    """(pointer, bytes) of an optional caller workspace (a CUDA uint8 tensor, 256-byte aligned)."""
+    if ws is None:
+        return None, 0
+    _dev(ws, dtype=torch.uint8, name="workspace")
+    return ws.data_ptr(), int(ws.numel())
+
+
+def shade_workspace_size(n_rays: int) -> int:
+    """Workspace bytes of shade_pixels / shade_batch over n_rays ray slots (pixels x N_r)."""
+    nb = L.load().grt_shade_workspace_size(int(n_rays))
+    if nb == 0:
+        raise L.GrtError(L.GRT_ERR_ARG, L.load().grt_last_error().decode())
+    return int(nb)
+
+
+def shade_backward_workspace_size(n_pixels: int, n_cos, n_ggx, n_env, saved: bool = False) -> int:
+    """Workspace bytes of shade_backward (recomputing, or with a saved forward record)."""
+    s = sampling(n_cos, n_ggx, n_env, 0, 1)
+    nb = L.load().grt_shade_backward_workspace_size(int(n_pixels), C.byref(s), int(bool(saved)))
+    if nb == 0:
+        raise L.GrtError(L.GRT_ERR_ARG, L.load().grt_last_error().decode())
+    return int(nb)
+
+
 def shade_pixels(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
-                 params=None, outputs=None, light: bool = False, stream=None):
+                 params=None, outputs=None, light: bool = False, workspace=None, stream=None):
     """MIS shading (Eq. 13): colour[P,3], visibility[P], indirect[P,3] for the pixel list,
-    and with light=True also the mean incident radiance light[P,3] of Eq. 16."""
+    and with light=True also the mean incident radiance light[P,3] of Eq. 16.  `workspace`:
+    optional caller buffer (uint8 CUDA tensor of at least shade_workspace_size(P x N_r)
+    bytes) used instead of the stream-ordered pool."""
     n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
     if pixels is not None:
         _dev(pixels, dtype=torch.int32, name="pixels", shape=(n,))
@@ -298,9 +325,10 @@ def shade_pixels(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_en
                                                 _ptr(pixels), n, _ptr(col), _ptr(vis), _ptr(ind), _ptr(lt),
                                                 _stream(stream)))
         return col, vis, ind, lt
+    wp, wn = _workspace(workspace)
     L.check(L.load().grt_shade_pixels(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
                                       C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(col), _ptr(vis),
-                                      _ptr(ind), _stream(stream)))
+                                      _ptr(ind), wp, wn, _stream(stream)))
     return col, vis, ind
 
 
@@ -363,7 +391,7 @@ def shade_saved_bytes(n_pixels: int, n_cos, n_ggx, n_env, max_hits: int = 64) ->
 
 
 def shade_pixels_save(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
-                      max_hits: int = 64, params=None, outputs=None, stream=None):
+                      max_hits: int = 64, params=None, outputs=None, workspace=None, stream=None):
     """shade_pixels that also keeps the forward record for shade_backward(saved=...):
     36 + 12 max_hits bytes per ray slot (pixels x N_r).  Returns (colour, visibility,
     indirect, SavedShade)."""
@@ -380,7 +408,8 @@ def shade_pixels_save(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx,
     p = params if params is not None else scene.params
     L.check(L.load().grt_shade_pixels_save(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
                                            C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(col), _ptr(vis),
-                                           _ptr(ind), int(max_hits), _ptr(buf), nb, _stream(stream)))
+                                           _ptr(ind), int(max_hits), _ptr(buf), nb, *_workspace(workspace),
+                                           _stream(stream)))
     return col, vis, ind, SavedShade(buf, n, (n_cos, n_ggx, n_env, seed, brdf), int(max_hits), pixels)
 
 
@@ -397,10 +426,11 @@ def shade_count(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env
 
 def shade_backward(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, dL_dcolor, dL_dvis=None,
                    dL_dind=None, brdf=1, pixels=None, grads: Optional[SurfelGrads] = None, params=None,
-                   saved: Optional[SavedShade] = None, stream=None) -> SurfelGrads:
+                   saved: Optional[SavedShade] = None, workspace=None, stream=None) -> SurfelGrads:
     """Adjoint of shade_pixels w.r.t. the surfels (gradients accumulate into `grads`).
     With `saved` (from shade_pixels_save with the same arguments) the forward record is
-    replayed; otherwise samples and hit lists are recomputed."""
+    replayed; otherwise samples and hit lists are recomputed.  `workspace`: optional caller
+    buffer of at least shade_backward_workspace_size(...) bytes instead of the pool."""
     n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
     _dev(dL_dcolor, name="dL_dcolor", shape=(n, 3))
     _dev(dL_dvis, name="dL_dvis", shape=(n,))
@@ -412,14 +442,15 @@ def shade_backward(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_
     if saved is None:
         L.check(lib.grt_shade_backward(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
                                        C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(dL_dcolor),
-                                       _ptr(dL_dvis), _ptr(dL_dind), C.byref(g.struct()), _stream(stream)))
+                                       _ptr(dL_dvis), _ptr(dL_dind), C.byref(g.struct()), *_workspace(workspace),
+                                       _stream(stream)))
         return g
     if saved.n_pixels != n or saved.sampling_args != (n_cos, n_ggx, n_env, seed, brdf) or saved.pixels is not pixels:
         raise ValueError("saved record was made with other pixels or sampling")
     L.check(lib.grt_shade_backward_saved(scene.handle, C.byref(scene.surfels()), C.byref(p), C.byref(gb.struct()),
                                          C.byref(env.struct()), C.byref(s), _ptr(pixels), n, _ptr(dL_dcolor),
                                          _ptr(dL_dvis), _ptr(dL_dind), saved.max_hits, _ptr(saved.buf), saved.nbytes,
-                                         C.byref(g.struct()), _stream(stream)))
+                                         C.byref(g.struct()), *_workspace(workspace), _stream(stream)))
     return g
 
 
@@ -448,8 +479,9 @@ class ShadeRequest:
         return self.count if self.count is not None else self.gbuffer.W * self.gbuffer.H - self.pixel_offset
 
 
-def shade_batch(requests, params=None, stream=None):
-    """Shade several requests in one persistent launch; fills each request's outputs."""
+def shade_batch(requests, params=None, workspace=None, stream=None):
+    """Shade several requests in one persistent launch; fills each request's outputs.
+    `workspace`: optional caller buffer of at least shade_workspace_size(total ray slots)."""
     if not requests:
         return
     if len(requests) > L.GRT_MAX_BATCH:
@@ -468,7 +500,7 @@ def shade_batch(requests, params=None, stream=None):
                                 0 if r.pixels is not None else int(r.pixel_offset),
                                 _ptr(r.color), _ptr(r.vis), _ptr(r.ind))
     p = params if params is not None else requests[0].scene.params
-    L.check(L.load().grt_shade_batch(arr, len(requests), C.byref(p), _stream(stream)))
+    L.check(L.load().grt_shade_batch(arr, len(requests), C.byref(p), *_workspace(workspace), _stream(stream)))
 
 
 def trace_attr(scene: Scene, ray_o, ray_d, params=None, stream=None):

@@ -271,7 +271,7 @@ struct AdjointTask {
     GradPtrs g;
     const long long* list;  // rays to walk (those the replay could not take), or all rays
     const SavedHits* sv;    // with a list: their records, replayed before the walk resumes
-    __device__ __forceinline__ bool begin(long long i, TraceState<K>& ts, Visitor& av, const DevBvh*& bvh) {
+    __device__ __forceinline__ bool begin(long long i, WalkState<K>& ts, Visitor& av, const DevBvh*& bvh) {
         const long long r = list ? __ldg(list + i) : i;
         float4 a = __ldg(adj + r);
         if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f) return false;
@@ -303,7 +303,7 @@ struct AdjointTask {
         trace_resume(J.bvh, ts, o, d, T->P, make_key(tau, id), Tb, sv->L);
         return true;
     }
-    __device__ __forceinline__ void end(long long, const TraceState<K>&, Visitor&) {}
+    __device__ __forceinline__ void end(long long, const WalkState<K>&, Visitor&) {}
 };
 
 // Replay of the saved hit records: one thread per ray with at most L composited hits
@@ -429,11 +429,28 @@ constexpr int kRecomputeHits = 64;
 struct AdjointTiming {
     bool on = false;
     bool have = false;
+    bool ok = false;  // every mark of the current pass was recorded
+    int device = -1;  // device the events belong to
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // Events are made on the current device and made again when a pass runs on another
+    // one; a failed record leaves the pass without timings (`have` stays false).
     void mark(int i, cudaStream_t st) {
         if (!on) return;
-        if (!ev[i]) cudaEventCreate(&ev[i]);
-        cudaEventRecord(ev[i], st);
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (dev != device) {
+            for (auto& e : ev) {
+                if (e) cudaEventDestroy(e);  // an event of another device: released, not reused
+                e = nullptr;
+            }
+            device = dev;
+        }
+        if (i == 0) ok = true;
+        if (!ev[i] && cudaEventCreate(&ev[i]) != cudaSuccess) ev[i] = nullptr;
+        if (!ev[i] || cudaEventRecord(ev[i], st) != cudaSuccess) ok = false;
     }
 };
 thread_local AdjointTiming g_adj_timing;
@@ -454,16 +471,12 @@ static void run_adjoint(const JobTable<1>& T, const float4* dirs, const float4* 
     g_adj_timing.mark(1, st);
     if (hits.L > 0) k_adjoint_replay<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, adj, hits, g, n_over, over);
     g_adj_timing.mark(2, st);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_ww<K>, kShadeThreads, 0);
-    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    if (grid > gr) grid = gr;
-    k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, adj, g, hits.L > 0 ? n_over : nullptr,
+    constexpr size_t smem = walk_smem_bytes<K>();
+    const long long grid = persistent_grid(k_adjoint_ww<K>, smem, gr);
+    k_adjoint_ww<K><<<(unsigned)grid, kShadeThreads, smem, st>>>(T, dirs, res, adj, g, hits.L > 0 ? n_over : nullptr,
                                                               hits.L > 0 ? over : nullptr, hits, next_ray);
     g_adj_timing.mark(3, st);
-    g_adj_timing.have = g_adj_timing.on;
+    g_adj_timing.have = g_adj_timing.on && g_adj_timing.ok;
 }
 
 // Two library streams per host thread and device: consecutive chunks of the recomputing
@@ -494,12 +507,40 @@ static int aux_streams(AuxStreams** out) {
     return GRT_OK;
 }
 
+// Device workspace of a shading adjoint over `rays` ray slots (n_pixels x N_r): with a
+// forward record, the adjoint per ray and the overflow list; recomputing, one or two chunk
+// buffers (directions, totals, transient hit record, adjoints, ray order).
+struct BackwardLayout {
+    long long chunk_px, n_chunks, Rc;
+    SavedLayout lay;
+    size_t ord_off, per, total;
+    int nbuf;
+};
+
+static BackwardLayout backward_layout(long long n_pixels, int Nr, bool saved) {
+    BackwardLayout b{};
+    const long long rays = n_pixels * Nr;
+    if (saved) {
+        b.total = (sizeof(float4) + sizeof(long long)) * (size_t)rays + 16;
+        return b;
+    }
+    b.chunk_px = std::min<long long>(n_pixels, std::max<long long>(1, kRecomputeChunkRays / Nr));
+    b.n_chunks = (n_pixels + b.chunk_px - 1) / b.chunk_px;
+    b.Rc = b.chunk_px * Nr;
+    b.lay = saved_layout(b.Rc, kRecomputeHits);
+    b.ord_off = (b.lay.total + (sizeof(float4) + sizeof(long long)) * (size_t)b.Rc + 16 + 255) & ~(size_t)255;
+    b.per = (b.ord_off + (GRT_RAY_ORDER ? order_scratch_bytes(b.Rc) : 0) + 255) & ~(size_t)255;
+    b.nbuf = b.n_chunks > 1 ? 2 : 1;
+    b.total = b.per * b.nbuf;
+    return b;
+}
+
 // Shading adjoint, from a caller's forward record (save) or recomputing (save == NULL).
 static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
                                const grt_gbuffer* gb, const grt_envmap* e, const grt_sampling* smp,
                                const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
                                const float* dL_dvis, const float* dL_dind, const grt_grads* grads,
-                               const SaveBufs* save, cudaStream_t st) {
+                               const SaveBufs* save, const Workspace& ws, cudaStream_t st) {
     int rc = check_trace_inputs(b, s, p);
     if (rc) return rc;
     rc = check_grads(grads, s);
@@ -516,10 +557,18 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
     T.total_rays = rays;
     T.total_units = 0;
     GradPtrs g{grads->mu, grads->quat, grads->scale, grads->opacity, grads->color};
-    keep_pool_memory();
+    const BackwardLayout BL = backward_layout(J.n_pixels, J.Nr, save != nullptr);
+    char* mem = nullptr;  // pool memory of this call (no caller workspace)
     char* buf = nullptr;
+    if (ws.ptr) {
+        if (ws.bytes < BL.total) return set_error(GRT_ERR_ARG, "workspace holds %zu bytes, %zu needed", ws.bytes, BL.total);
+        buf = static_cast<char*>(ws.ptr);
+    } else {
+        keep_pool_memory();
+        GRT_CUDA(cudaMallocAsync((void**)&mem, BL.total, st));
+        buf = mem;
+    }
     if (save) {
-        GRT_CUDA(cudaMallocAsync((void**)&buf, (sizeof(float4) + sizeof(long long)) * (size_t)rays + 16, st));
         float4* adj = reinterpret_cast<float4*>(buf);
         unsigned long long* work = reinterpret_cast<unsigned long long*>(adj + rays);
         dispatch_k(p->k, [&](auto kc) {
@@ -527,19 +576,17 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
                                              AdjIn{dL_dcolor, dL_dvis, dL_dind}, g, st);
         });
     } else {
-        const long long chunk_px = std::min<long long>(J.n_pixels, std::max<long long>(1, kRecomputeChunkRays / J.Nr));
-        const long long n_chunks = (J.n_pixels + chunk_px - 1) / chunk_px;
-        const long long Rc = chunk_px * J.Nr;
-        const SavedLayout lay = saved_layout(Rc, kRecomputeHits);
-        const size_t ord_off = (lay.total + (sizeof(float4) + sizeof(long long)) * (size_t)Rc + 16 + 255) & ~(size_t)255;
-        const size_t per = (ord_off + (GRT_RAY_ORDER ? order_scratch_bytes(Rc) : 0) + 255) & ~(size_t)255;
-        const int nbuf = n_chunks > 1 ? 2 : 1;
+        const long long chunk_px = BL.chunk_px, n_chunks = BL.n_chunks, Rc = BL.Rc;
+        const SavedLayout lay = BL.lay;
+        const size_t ord_off = BL.ord_off, per = BL.per;
         AuxStreams* aux = nullptr;
-        if (nbuf > 1) {
+        if (BL.nbuf > 1) {
             rc = aux_streams(&aux);
-            if (rc) return rc;
+            if (rc) {
+                if (mem) cudaFreeAsync(mem, st);
+                return rc;
+            }
         }
-        GRT_CUDA(cudaMallocAsync((void**)&buf, per * nbuf, st));
         if (aux) {
             GRT_CUDA(cudaEventRecord(aux->fork, st));
             for (int i = 0; i < 2; ++i) GRT_CUDA(cudaStreamWaitEvent(aux->s[i], aux->fork, 0));
@@ -589,7 +636,7 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
         }
     }
     cudaError_t err = cudaGetLastError();
-    cudaFreeAsync(buf, st);
+    if (mem) cudaFreeAsync(mem, st);
     if (err != cudaSuccess) return check_cuda(err, "shade backward kernels");
     return GRT_OK;
 }
@@ -597,21 +644,39 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
 extern "C" int grt_shade_backward(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
                                   const grt_gbuffer* gb, const grt_envmap* e, const grt_sampling* smp,
                                   const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
-                                  const float* dL_dvis, const float* dL_dind, const grt_grads* grads, void* stream) {
+                                  const float* dL_dvis, const float* dL_dind, const grt_grads* grads,
+                                  void* workspace, size_t workspace_bytes, void* stream) {
+    Workspace ws;
+    int rc = workspace_arg(workspace, workspace_bytes, &ws);
+    if (rc) return rc;
     return shade_backward_impl(b, s, p, gb, e, smp, pixel_list, n_pixels, dL_dcolor, dL_dvis, dL_dind, grads, nullptr,
-                               (cudaStream_t)stream);
+                               ws, (cudaStream_t)stream);
+}
+
+extern "C" size_t grt_shade_backward_workspace_size(int32_t n_pixels, const grt_sampling* smp, int32_t saved) {
+    if (n_pixels < 0 || !smp || smp->n_cos < 0 || smp->n_ggx < 0 || smp->n_env < 0) {
+        set_error(GRT_ERR_ARG, "bad n_pixels or sampling");
+        return 0;
+    }
+    const int Nr = smp->n_cos + smp->n_ggx + smp->n_env;
+    if (Nr <= 0 || n_pixels == 0) return 256;
+    return backward_layout(n_pixels, Nr, saved != 0).total;
 }
 
 extern "C" int grt_shade_backward_saved(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
                                         const grt_gbuffer* gb, const grt_envmap* e, const grt_sampling* smp,
                                         const int32_t* pixel_list, int32_t n_pixels, const float* dL_dcolor,
                                         const float* dL_dvis, const float* dL_dind, int32_t max_hits,
-                                        const void* saved, size_t saved_bytes, const grt_grads* grads, void* stream) {
+                                        const void* saved, size_t saved_bytes, const grt_grads* grads,
+                                        void* workspace, size_t workspace_bytes, void* stream) {
     SaveBufs sb;
     int rc = saved_buffers(saved, saved_bytes, n_pixels, smp, max_hits, &sb);
     if (rc) return rc;
+    Workspace ws;
+    rc = workspace_arg(workspace, workspace_bytes, &ws);
+    if (rc) return rc;
     return shade_backward_impl(b, s, p, gb, e, smp, pixel_list, n_pixels, dL_dcolor, dL_dvis, dL_dind, grads, &sb,
-                               (cudaStream_t)stream);
+                               ws, (cudaStream_t)stream);
 }
 
 extern "C" int grt_adjoint_timing(int32_t enable, float* ms_out) {

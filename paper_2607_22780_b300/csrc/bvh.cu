@@ -12,6 +12,7 @@
 //   6. hierarchy binary radix tree over the sorted codes (Karras, HPG 2012), duplicate
 //                codes split by position, so the depth is at most 30 + log2(n)
 //   7. refit     bottom-up box union, second arriving thread continues (atomic flags)
+//   8. collapse  4-wide tree for traversal, top down in one launch (device work queue)
 #include <cfloat>
 #include <climits>
 #include <cmath>
@@ -422,10 +423,7 @@ __global__ void k_refit(const float* __restrict__ leaf_box, const int* __restric
 }
 
 // ---------------------------------------------------------------- 4-wide collapse
-// Top down, one frontier per level: a wide node made from binary node b starts with b's
-// two children and twice replaces the candidate of largest surface area that is too big
-// for a leaf by its two children; candidates of at most kLeafMax surfels become leaves
-// over their contiguous run of sorted records, larger ones become new wide nodes.
+// Top down from the root, one launch with a device-side work queue (k_collapse_queue).
 __device__ __forceinline__ int bin_size(const float4* bn, int ref) {
     if (ref < 0) return 1;
     const float* f = reinterpret_cast<const float*>(bn + 4 * (size_t)ref);
@@ -444,11 +442,10 @@ struct CollapseIn {
     const float* bin_box;
     const float* leaf_box;
     float4* wnodes;
-    const int2* fin;
-    int2* fout;
-    int* counts;  // [0] wide nodes allocated, [1 + level] frontier sizes
+    int* queue;   // [cap]: binary node of each wide node, -1 until its parent publishes it
+    int* counts;  // [0] wide nodes allocated, [1] next wide node to take, [2] wide nodes written
     int* status;
-    int level, cap;
+    int cap;
 };
 
 __device__ __forceinline__ void write_slot(float4* W, int s, const float* box, int ref, int bref) {
@@ -459,64 +456,111 @@ __device__ __forceinline__ void write_slot(float4* W, int s, const float* box, i
     f[28 + s] = __int_as_float(bref);
 }
 
-__global__ void k_collapse(CollapseIn c) {
-    const int nitems = c.counts[1 + c.level];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nitems; i += gridDim.x * blockDim.x) {
-        int2 it = c.fin[i];
-        const float* fb = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)it.y);
-        int cand[kWide];
-        int nc = 2;
-        cand[0] = __float_as_int(fb[12]);
-        cand[1] = __float_as_int(fb[13]);
-        for (int rep = 2; rep < kWide; ++rep) {
-            int best = -1;
-            float ba = -1.f;
-            for (int s = 0; s < nc; ++s) {
-                int r = cand[s];
-                if (r >= 0 && bin_size(c.bnodes, r) > kLeafMax) {
-                    float a = half_area(c.bin_box + 6 * (size_t)r);
-                    if (a > ba) {
-                        ba = a;
-                        best = s;
-                    }
-                }
-            }
-            if (best < 0) break;
-            const float* fr = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)cand[best]);
-            cand[best] = __float_as_int(fr[12]);
-            cand[nc++] = __float_as_int(fr[13]);
-        }
-        float4* W = c.wnodes + 8 * (size_t)it.x;
-        for (int s = 0; s < kWide; ++s) {
-            if (s >= nc) {
-                const float empty[6] = {1e38f, 1e38f, 1e38f, -1e38f, -1e38f, -1e38f};
-                write_slot(W, s, empty, kRefEmpty, kRefEmpty);
-                continue;
-            }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wide node w made from binary node b: starts with b's two children and twice replaces the
+// candidate of largest surface area that is too big for a leaf by its two children;
+// candidates of at most kLeafMax surfels become leaves over their contiguous run of sorted
+// records, larger ones become new wide nodes, published to the queue for any thread to take.
+__device__ void collapse_node(const CollapseIn& c, int w, int b) {
+    const float* fb = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)b);
+    int cand[kWide];
+    int nc = 2;
+    cand[0] = __float_as_int(fb[12]);
+    cand[1] = __float_as_int(fb[13]);
+    for (int rep = 2; rep < kWide; ++rep) {
+        int best = -1;
+        float ba = -1.f;
+        for (int s = 0; s < nc; ++s) {
             int r = cand[s];
-            const float* box = bin_box_of(c.bin_box, c.leaf_box, r);
-            int ref;
-            if (r < 0) {
-                ref = leaf_ref(~r, 1);
-            } else {
-                const float* fr = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)r);
-                int first = __float_as_int(fr[14]), size = __float_as_int(fr[15]) - first + 1;
-                if (size <= kLeafMax) {
-                    ref = leaf_ref(first, size);
-                } else {
-                    int w2 = atomicAdd(c.counts, 1);
-                    if (w2 >= c.cap) {
-                        atomicOr(c.status, GRT_STATUS_BAD_TREE);
-                        ref = kRefEmpty;
-                    } else {
-                        int pos = atomicAdd(c.counts + 2 + c.level, 1);
-                        c.fout[pos] = make_int2(w2, r);
-                        ref = w2;
-                    }
+            if (r >= 0 && bin_size(c.bnodes, r) > kLeafMax) {
+                float a = half_area(c.bin_box + 6 * (size_t)r);
+                if (a > ba) {
+                    ba = a;
+                    best = s;
                 }
             }
-            write_slot(W, s, box, ref, r);
         }
+        if (best < 0) break;
+        const float* fr = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)cand[best]);
+        cand[best] = __float_as_int(fr[12]);
+        cand[nc++] = __float_as_int(fr[13]);
+    }
+    float4* W = c.wnodes + 8 * (size_t)w;
+    for (int s = 0; s < kWide; ++s) {
+        if (s >= nc) {
+            const float empty[6] = {1e38f, 1e38f, 1e38f, -1e38f, -1e38f, -1e38f};
+            write_slot(W, s, empty, kRefEmpty, kRefEmpty);
+            continue;
+        }
+        int r = cand[s];
+        const float* box = bin_box_of(c.bin_box, c.leaf_box, r);
+        int ref;
+        if (r < 0) {
+            ref = leaf_ref(~r, 1);
+        } else {
+            const float* fr = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)r);
+            int first = __float_as_int(fr[14]), size = __float_as_int(fr[15]) - first + 1;
+            if (size <= kLeafMax) {
+                ref = leaf_ref(first, size);
+            } else {
+                int w2 = atomicAdd(c.counts, 1);
+                if (w2 >= c.cap) {
+                    // more wide nodes than binary ones: a corrupt tree; the index counts as
+                    // written so that the queue still drains
+                    atomicOr(c.status, GRT_STATUS_BAD_TREE);
+                    __threadfence();
+                    atomicAdd(c.counts + 2, 1);
+                    ref = kRefEmpty;
+                } else {
+                    atomicExch(c.queue + w2, r);
+                    ref = w2;
+                }
+            }
+        }
+        write_slot(W, s, box, ref, r);
+    }
+}
+
+// The whole 4-wide collapse in one launch.  Wide node indices are handed out in order from
+// counts[1]; a thread waits until the parent of its wide node has published it (queue entry
+// >= 0), or until every allocated wide node has been written (counts[2] == counts[0]: no
+// node is in progress, so none can be published any more).  Every wait is bounded: after
+// kCollapseWaitNs the thread sets GRT_STATUS_TIMEOUT and returns.
+constexpr unsigned long long kCollapseWaitNs = 1000000000ull;
+
+__global__ void k_collapse_queue(CollapseIn c) {
+    while (true) {
+        const int w = atomicAdd(c.counts + 1, 1);
+        if (w >= c.cap) return;  // more threads than wide nodes can exist
+        const unsigned long long t0 = global_ns();
+        int b = -1;
+        unsigned sleep = 32;
+        for (int spin = 0;; ++spin) {
+            b = *reinterpret_cast<volatile int*>(c.queue + w);
+            if (b >= 0) break;
+            // the shared counters are read now and then only: every waiting thread polls
+            // its own queue entry, the producers' atomics on the counters stay uncontended
+            if ((spin & 7) == 7) {
+                const int done = *reinterpret_cast<volatile int*>(c.counts + 2);
+                __threadfence();
+                const int alloc = *reinterpret_cast<volatile int*>(c.counts);
+                if (done == alloc && w >= min(alloc, c.cap)) return;
+                if (global_ns() - t0 > kCollapseWaitNs) {
+                    atomicOr(c.status, GRT_STATUS_TIMEOUT);
+                    return;
+                }
+            }
+            __nanosleep(sleep);
+            sleep = sleep < 1024 ? 2 * sleep : 1024;
+        }
+        collapse_node(c, w, b);
+        __threadfence();  // the children's allocations are visible before this node counts as written
+        atomicAdd(c.counts + 2, 1);
     }
 }
 
@@ -535,13 +579,12 @@ __global__ void k_wide_refit(float4* __restrict__ wnodes, const int* __restrict_
     }
 }
 
-__global__ void k_collapse_init(int* counts, int2* f0) {
-    if (threadIdx.x < kMaxCollapseLevels + 2) counts[threadIdx.x] = 0;
-    __syncthreads();
+__global__ void k_collapse_init(int* counts, int* queue) {
     if (threadIdx.x == 0) {
-        counts[0] = 1;  // wide node 0 = root
-        counts[1] = 1;  // the level-0 frontier holds it
-        f0[0] = make_int2(0, 0);
+        counts[0] = 1;  // wide node 0 = root, made from binary node 0
+        counts[1] = 0;
+        counts[2] = 0;
+        queue[0] = 0;
     }
 }
 
@@ -562,6 +605,9 @@ static void launch_records(const TriIn& in, grt_bvh* b, int g, cudaStream_t st) 
     k_tri_records<<<g, kThreads, 0, st>>>(in, b->sorted_ids, b->records, b->leaf_box);
 }
 
+// Blocks of the one-launch collapse (a few per SM; threads take wide nodes as they appear).
+constexpr int kCollapseBlocks = 148 * 4;
+
 // Records, binary refit and the 4-wide collapse (or its refit): shared tail of the builds.
 template <class In>
 static int finish_build(grt_bvh* b, const In& in, bool collapse, cudaStream_t st) {
@@ -573,14 +619,11 @@ static int finish_build(grt_bvh* b, const In& in, bool collapse, cudaStream_t st
         k_refit<<<g, kThreads, 0, st>>>(b->leaf_box, b->parent, n, b->nodes, b->refit_flags, b->status, b->bin_box);
         const int cg = std::min((b->n_int + 127) / 128, 1184);
         if (collapse) {
-            k_collapse_init<<<1, 128, 0, st>>>(b->wcounts, b->frontier);
-            for (int level = 0; level < kMaxCollapseLevels; ++level) {
-                const int2* fin = b->frontier + (size_t)(level & 1) * b->n_int;
-                int2* fout = b->frontier + (size_t)((level + 1) & 1) * b->n_int;
-                CollapseIn c{b->nodes, b->bin_box, b->leaf_box, b->wnodes, fin, fout, b->wcounts, b->status,
-                             level, b->n_int};
-                k_collapse<<<cg, 128, 0, st>>>(c);
-            }
+            // every queue entry starts unpublished (-1); one launch collapses the whole tree
+            GRT_CUDA(cudaMemsetAsync(b->wqueue, 0xFF, sizeof(int) * (size_t)b->n_int, st));
+            k_collapse_init<<<1, 32, 0, st>>>(b->wcounts, b->wqueue);
+            CollapseIn c{b->nodes, b->bin_box, b->leaf_box, b->wnodes, b->wqueue, b->wcounts, b->status, b->n_int};
+            k_collapse_queue<<<std::min((b->n_int + 127) / 128, kCollapseBlocks), 128, 0, st>>>(c);
         } else {
             k_wide_refit<<<cg, 128, 0, st>>>(b->wnodes, b->wcounts, b->n_int, b->bin_box, b->leaf_box);
         }
@@ -719,6 +762,12 @@ extern "C" int grt_rebuild_bvh_noalloc(grt_bvh* b, const grt_surfels* s, const g
     if (s->n > GRT_NOALLOC_MAX_SURFELS)
         return set_error(GRT_ERR_ARG, "grt_rebuild_bvh_noalloc: n = %d exceeds its fixed scratch for %d surfels",
                          s->n, GRT_NOALLOC_MAX_SURFELS);
+    // the scratch is looked up for the current device: it must be the BVH's own
+    int dev = 0;
+    GRT_CUDA(cudaGetDevice(&dev));
+    if (dev != b->device)
+        return set_error(GRT_ERR_ARG, "grt_rebuild_bvh_noalloc: device %d is current, the BVH lives on device %d", dev,
+                         b->device);
     return launch_build_noalloc(b, s, params->alpha_min, (cudaStream_t)stream);
 }
 
@@ -731,8 +780,8 @@ static grt_bvh* alloc_bvh(int nleaf, cudaStream_t st, int* rc_out) {
     size_t n = (size_t)nleaf, ni = (size_t)b->n_int;
     size_t bytes = sizeof(float4) * 4 * (ni + n) + sizeof(int) * (n + ni + 1) + sizeof(int) * (ni + 1) +
                    sizeof(float) * 6 * n + sizeof(int) * n + 64 + 64 +
-                   sizeof(float) * 6 * ni + sizeof(float4) * 8 * ni + sizeof(int2) * 2 * ni +
-                   sizeof(int) * (kMaxCollapseLevels + 2) + 256 * 4;
+                   sizeof(float) * 6 * ni + sizeof(float4) * 8 * ni + sizeof(int) * ni +
+                   sizeof(int) * 4 + 256 * 4;
     char* base = nullptr;
     cudaError_t e = cudaMalloc((void**)&base, bytes);
     if (e != cudaSuccess) {
@@ -755,8 +804,8 @@ static grt_bvh* alloc_bvh(int nleaf, cudaStream_t st, int* rc_out) {
     b->wnodes = (float4*)p; p += sizeof(float4) * 8 * ni;
     b->bin_box = (float*)p; p += sizeof(float) * 6 * ni;
     p = (char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-    b->frontier = (int2*)p; p += sizeof(int2) * 2 * ni;
-    b->wcounts = (int*)p; p += sizeof(int) * (kMaxCollapseLevels + 2);
+    b->wqueue = (int*)p; p += sizeof(int) * ni;
+    b->wcounts = (int*)p; p += sizeof(int) * 4;
     b->bytes = bytes;
     e = cudaMemsetAsync(b->status, 0, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->bounds, 0, 32, st);

@@ -76,7 +76,7 @@ struct GbufTask {
     const TraceParams* P;
     int W, H;
     GbufOut out;
-    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& v, const DevBvh*& b) {
+    __device__ __forceinline__ bool begin(long long r, WalkState<K>& ts, Visitor& v, const DevBvh*& b) {
         f3 o, d;
         camera_ray_d(*cam, W, H, (int)(r % W), (int)(r / W), &o, &d);
         trace_begin(*bvh, ts, o, d, *P);
@@ -84,7 +84,7 @@ struct GbufTask {
         b = bvh;
         return true;
     }
-    __device__ __forceinline__ void end(long long r, const TraceState<K>& ts, Visitor& v) {
+    __device__ __forceinline__ void end(long long r, const WalkState<K>& ts, Visitor& v) {
         const size_t p = (size_t)r;
         const f3 o = ts.r.o, d = ts.r.d;
         float a = 1.f - v.T;
@@ -149,16 +149,11 @@ extern "C" int grt_gbuffer_primary(const grt_bvh* b, const grt_surfels* s, const
     unsigned long long* next = nullptr;
     GRT_CUDA(cudaMallocAsync((void**)&next, sizeof(unsigned long long), st));
     GRT_CUDA(cudaMemsetAsync(next, 0, sizeof(unsigned long long), st));
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     dispatch_k(p->k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gbuffer<K>, 128, 0);
-        int grid = sms * (per_sm > 0 ? per_sm : 1);
-        if (grid > gmax) grid = gmax;
-        k_gbuffer<K><<<grid, 128, 0, st>>>(bvh, P, sc, cam, W, H, out, next);
+        constexpr size_t smem = walk_smem_bytes<K>();
+        const long long grid = persistent_grid(k_gbuffer<K>, smem, gmax);
+        k_gbuffer<K><<<(unsigned)grid, 128, smem, st>>>(bvh, P, sc, cam, W, H, out, next);
     });
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(next, st);

@@ -255,7 +255,6 @@ constexpr int kWide = 4;
 #define GRT_LEAF_MAX 1
 #endif
 constexpr int kLeafMax = GRT_LEAF_MAX;  // surfels per wide-tree leaf (at most 8)
-constexpr int kMaxCollapseLevels = 60;  // >= binary depth: 30 code bits + 27 position bits
 __host__ __device__ __forceinline__ int leaf_ref(int first, int count) { return -(1 + (first << 3) + (count - 1)); }
 __host__ __device__ __forceinline__ int leaf_first(int ref) { return (-ref - 1) >> 3; }
 __host__ __device__ __forceinline__ int leaf_count(int ref) { return ((-ref - 1) & 7) + 1; }
@@ -296,8 +295,8 @@ struct grt_bvh {
     int* sorted_ids;   // [n]
     float4* wnodes;    // [n_int * 8] 4-wide nodes
     float* bin_box;    // [n_int * 6] box of each binary node
-    int2* frontier;    // [2][n_int] collapse frontiers
-    int* wcounts;      // [kMaxCollapseLevels + 2] collapse counters
+    int* wqueue;       // [n_int] binary node of each wide node (collapse work queue)
+    int* wcounts;      // [4] collapse counters
     int* status;       // device status word
     float* bounds;     // [6] scene bounds (device)
     size_t bytes;

@@ -149,7 +149,7 @@ struct RayAttrTask {
     const AttrSrc* src;
     const float *ro, *rd;
     AttrOut out;
-    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& v, const DevBvh*& b) {
+    __device__ __forceinline__ bool begin(long long r, WalkState<K>& ts, Visitor& v, const DevBvh*& b) {
         const f3 o = mk3(__ldg(ro + 3 * r), __ldg(ro + 3 * r + 1), __ldg(ro + 3 * r + 2));
         const f3 d = mk3(__ldg(rd + 3 * r), __ldg(rd + 3 * r + 1), __ldg(rd + 3 * r + 2));
         trace_begin(*bvh, ts, o, d, *P);
@@ -157,7 +157,7 @@ struct RayAttrTask {
         b = bvh;
         return true;
     }
-    __device__ __forceinline__ void end(long long r, const TraceState<K>& ts, Visitor& v) {
+    __device__ __forceinline__ void end(long long r, const WalkState<K>& ts, Visitor& v) {
         v.resolve();
         out.vis[r] = ts.T;
         out.rough[r] = v.r;
@@ -233,17 +233,12 @@ extern "C" int grt_trace_attr(const grt_bvh* b, const grt_surfels* s, const grt_
     TraceParams P = to_params(*p);
     AttrSrc src{s->quat, s->albedo, s->rough, s->metal};
     AttrOut out{out_vis, out_albedo, out_rough, out_metal, out_normal};
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long gmax = (R + 127) / 128;
     dispatch_k(p->k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_attr<K>, 128, 0);
-        long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
-        if (grid > gmax) grid = gmax;
-        k_trace_attr<K><<<(unsigned)grid, 128, 0, st>>>(bvh, P, src, ray_o, ray_d, R, out, next);
+        constexpr size_t smem = walk_smem_bytes<K>();
+        const long long grid = persistent_grid(k_trace_attr<K>, smem, gmax);
+        k_trace_attr<K><<<(unsigned)grid, 128, smem, st>>>(bvh, P, src, ray_o, ray_d, R, out, next);
     });
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(next, st);

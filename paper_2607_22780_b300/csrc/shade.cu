@@ -164,18 +164,35 @@ __global__ void __launch_bounds__(kShadeThreads) k_material_adjoint(const __grid
 struct PhaseTiming {
     bool on = false;
     bool have = false;
+    bool ok = false;  // every mark of the current pass was recorded
+    int device = -1;  // device the events belong to
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // Events are made on the current device and made again when a pass runs on another
+    // one; a failed record leaves the pass without timings (`have` stays false).
     void mark(int i, cudaStream_t st) {
         if (!on) return;
-        if (!ev[i]) cudaEventCreate(&ev[i]);
-        cudaEventRecord(ev[i], st);
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (dev != device) {
+            for (auto& e : ev) {
+                if (e) cudaEventDestroy(e);  // an event of another device: released, not reused
+                e = nullptr;
+            }
+            device = dev;
+        }
+        if (i == 0) ok = true;
+        if (!ev[i] && cudaEventCreate(&ev[i]) != cudaSuccess) ev[i] = nullptr;
+        if (!ev[i] || cudaEventRecord(ev[i], st) != cudaSuccess) ok = false;
     }
 };
 thread_local PhaseTiming g_timing;
 
 template <bool COUNT, int CAP>
 int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, const SaveBufs* save = nullptr,
-             const RelightDev* rel = nullptr, const MeshDev* mesh = nullptr) {
+             const RelightDev* rel = nullptr, const MeshDev* mesh = nullptr, const Workspace& ws = Workspace{}) {
     long long rays = 0, units = 0;
     for (int i = 0; i < T.n_jobs; ++i) {
         ShadeJob& J = T.job[i];
@@ -194,14 +211,24 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
     // every walk but the counting pass takes its rays in bucket order (32-bit slot indices)
     const bool ord = GRT_RAY_ORDER && !COUNT && rays <= 0xFFFFFFFFLL;
     const size_t extra = ord ? order_scratch_bytes(rays) : 0;
-    keep_pool_memory();
+    const size_t need = save ? extra : shade_ws_bytes(rays, ord);
+    char* mem = nullptr;    // from the pool, freed at the end of the call
+    char* base = nullptr;   // the call's ray buffers: caller workspace or `mem`
+    if (ws.ptr) {
+        if (ws.bytes < need) return set_error(GRT_ERR_ARG, "workspace holds %zu bytes, %zu needed", ws.bytes, need);
+        base = static_cast<char*>(ws.ptr);
+    } else if (need > 0) {
+        keep_pool_memory();
+        GRT_CUDA(cudaMallocAsync((void**)&mem, need, st));
+        base = mem;
+    }
     if (save) {
         dirs = save->dirs;
         res = save->res;
         next_ray = save->next;
-        if (ord) GRT_CUDA(cudaMallocAsync((void**)&order_buf, extra, st));
+        if (ord) order_buf = base;
     } else {
-        GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1) + extra, st));
+        buf = reinterpret_cast<float4*>(base);
         dirs = buf;
         res = buf + rays;
         next_ray = reinterpret_cast<unsigned long long*>(buf + 2 * rays);
@@ -238,11 +265,10 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
         g_timing.mark(2, st);
         k_accumulate<CAP><<<(unsigned)ga, kShadeThreads, 0, st>>>(T, dirs, res);
         g_timing.mark(3, st);
-        g_timing.have = g_timing.on;
+        g_timing.have = g_timing.on && g_timing.ok;
     }
     cudaError_t e = cudaGetLastError();
-    if (buf) cudaFreeAsync(buf, st);
-    else if (order_buf) cudaFreeAsync(order_buf, st);
+    if (mem) cudaFreeAsync(mem, st);
     if (e != cudaSuccess) return check_cuda(e, "shade kernels");
     return GRT_OK;
 }
@@ -251,7 +277,7 @@ template <bool COUNT>
 int launch_single(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p, const grt_gbuffer* g,
                   const grt_envmap* e, const grt_sampling* smp, const int* pl, int n, float* oc, float* ov, float* oi,
                   long long* counters, cudaStream_t st, const SaveBufs* save = nullptr,
-                  const RelightDev* rel = nullptr) {
+                  const RelightDev* rel = nullptr, const Workspace& ws = Workspace{}) {
     int rc = check_trace_inputs(b, s, p);
     if (rc) return rc;
     JobTable<1> T;
@@ -264,7 +290,7 @@ int launch_single(const grt_bvh* b, const grt_surfels* s, const grt_trace_params
         if (oc) k_zero_outputs<<<(n + 255) / 256, 256, 0, st>>>(oc, ov, oi, n);
         return launch_error("k_zero_outputs");
     }
-    return run_jobs<COUNT>(T, p->k, counters, st, save, rel);
+    return run_jobs<COUNT>(T, p->k, counters, st, save, rel, nullptr, ws);
 }
 
 }  // namespace
@@ -274,10 +300,22 @@ using namespace grt;
 
 extern "C" int grt_shade_pixels(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p, const grt_gbuffer* g,
                                 const grt_envmap* e, const grt_sampling* smp, const int32_t* pixel_list,
-                                int32_t n_pixels, float* out_color, float* out_vis, float* out_ind, void* stream) {
+                                int32_t n_pixels, float* out_color, float* out_vis, float* out_ind, void* workspace,
+                                size_t workspace_bytes, void* stream) {
     if (n_pixels > 0 && !out_color) return set_error(GRT_ERR_ARG, "out_color is NULL");
+    Workspace ws;
+    int rc = workspace_arg(workspace, workspace_bytes, &ws);
+    if (rc) return rc;
     return launch_single<false>(b, s, p, g, e, smp, pixel_list, n_pixels, out_color, out_vis, out_ind, nullptr,
-                                (cudaStream_t)stream);
+                                (cudaStream_t)stream, nullptr, nullptr, ws);
+}
+
+extern "C" size_t grt_shade_workspace_size(int64_t n_rays) {
+    if (n_rays < 0) {
+        set_error(GRT_ERR_ARG, "n_rays < 0");
+        return 0;
+    }
+    return shade_ws_bytes(n_rays, GRT_RAY_ORDER && n_rays <= 0xFFFFFFFFLL);
 }
 
 extern "C" int grt_shade_count(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p, const grt_gbuffer* g,
@@ -304,13 +342,17 @@ extern "C" size_t grt_shade_saved_bytes(int32_t n_pixels, const grt_sampling* sm
 extern "C" int grt_shade_pixels_save(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
                                      const grt_gbuffer* g, const grt_envmap* e, const grt_sampling* smp,
                                      const int32_t* pixel_list, int32_t n_pixels, float* out_color, float* out_vis,
-                                     float* out_ind, int32_t max_hits, void* saved, size_t saved_bytes, void* stream) {
+                                     float* out_ind, int32_t max_hits, void* saved, size_t saved_bytes,
+                                     void* workspace, size_t workspace_bytes, void* stream) {
     if (n_pixels > 0 && !out_color) return set_error(GRT_ERR_ARG, "out_color is NULL");
     SaveBufs sb;
     int rc = saved_buffers(saved, saved_bytes, n_pixels, smp, max_hits, &sb);
     if (rc) return rc;
+    Workspace ws;
+    rc = workspace_arg(workspace, workspace_bytes, &ws);
+    if (rc) return rc;
     return launch_single<false>(b, s, p, g, e, smp, pixel_list, n_pixels, out_color, out_vis, out_ind, nullptr,
-                                (cudaStream_t)stream, &sb);
+                                (cudaStream_t)stream, &sb, nullptr, ws);
 }
 
 extern "C" int grt_shade_relight(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p,
@@ -436,10 +478,13 @@ extern "C" int grt_shade_relight_mesh(const grt_bvh* b, const grt_mesh* m, const
 }
 
 extern "C" int grt_shade_batch(const grt_shade_request* req, int32_t n_req, const grt_trace_params* p,
-                               void* stream) {
+                               void* workspace, size_t workspace_bytes, void* stream) {
     if (!req || n_req <= 0 || n_req > GRT_MAX_BATCH)
         return set_error(GRT_ERR_ARG, "need 1 <= n_requests <= %d", GRT_MAX_BATCH);
     int rc = check_params(p);
+    if (rc) return rc;
+    Workspace ws;
+    rc = workspace_arg(workspace, workspace_bytes, &ws);
     if (rc) return rc;
     static thread_local JobTable<GRT_MAX_BATCH> T;
     T.P = to_params(*p);
@@ -468,7 +513,7 @@ extern "C" int grt_shade_batch(const grt_shade_request* req, int32_t n_req, cons
         T.job[T.n_jobs++] = J;
     }
     if (T.n_jobs == 0) return launch_error("k_zero_outputs");
-    return run_jobs<false>(T, p->k, nullptr, st);
+    return run_jobs<false>(T, p->k, nullptr, st, nullptr, nullptr, nullptr, ws);
 }
 
 extern "C" int grt_phase_timing(int32_t enable, float* ms_out) {

@@ -35,7 +35,7 @@ constexpr uint64_t kNoKey = ~0ull;
 // node and record lines for L1 (16 shared entries: 328.5 -> 339.8 M rays/s on the
 // 300k-surfel 800x800 workload; 8 or 32 gained less).
 #ifndef GRT_SMEM_STACK
-#define GRT_SMEM_STACK 16
+#define GRT_SMEM_STACK 8
 #endif
 constexpr int kSharedStack = GRT_SMEM_STACK;
 
@@ -113,6 +113,7 @@ struct Counters {
 
 template <int K>
 struct KBuf {
+    static constexpr bool kShared = false;
     uint64_t key[K];
     float a[K];
     int cnt;         // valid entries, a prefix of key[]
@@ -170,12 +171,67 @@ struct KBuf {
     }
 };
 
+// The same k-buffer for the persistent walks, kept in shared memory as a sorted array
+// instead of registers: entry j of the lane whose column starts at key/a sits at
+// key[j * kKbufThreads] (one 8-byte key and one 4-byte alpha word per lane and
+// entry, bank-conflict free across a warp).  A hit is placed by shifting the larger keys
+// up by one; hits mostly arrive near to far, so the shift is short, where the register
+// buffer pays a compare-swap over all K entries for every hit.  When the buffer is full
+// the largest entry drops off its end.  The cut and termination rules are those of KBuf,
+// so the composited sequence is the same.
+constexpr int kKbufThreads = 128;  // lanes of a block sharing the k-buffer arrays
+
+template <int K>
+struct KBufShared {
+    static constexpr bool kShared = true;
+    uint64_t* key;   // this lane's column: key[j * kKbufThreads]
+    float* a;
+    int cnt;
+    float Tall;      // product of (1 - a) over the entries while the buffer is not full
+    uint64_t cut;
+    float thi;
+
+    __device__ __forceinline__ uint64_t key_at(int j) const { return key[j * kKbufThreads]; }
+    __device__ __forceinline__ float a_at(int j) const { return a[j * kKbufThreads]; }
+
+    __device__ __forceinline__ void reset(float t_max) {
+        cnt = 0;
+        Tall = 1.f;
+        cut = kNoKey;
+        thi = t_max;
+    }
+
+    __device__ __forceinline__ void insert(uint64_t k, float al, float T0, float T_min, float t_max, float eps) {
+        int pos = cnt < K ? cnt : K - 1;  // a full buffer loses its largest entry
+        while (pos > 0) {
+            const uint64_t kp = key[(pos - 1) * kKbufThreads];
+            if (kp < k) break;  // keys are distinct: (tau, id) with distinct ids
+            key[pos * kKbufThreads] = kp;
+            a[pos * kKbufThreads] = a[(pos - 1) * kKbufThreads];
+            --pos;
+        }
+        key[pos * kKbufThreads] = k;
+        a[pos * kKbufThreads] = al;
+        if (cnt < K) {
+            ++cnt;
+            Tall *= sub_d(1.0f, al);  // once full the product is no longer needed this round
+        }
+        // T0 * Tall rounds within 2K ulps of the sequential product the compositor forms
+        if (cnt == K || T0 * Tall < T_min * 0.9999f) {
+            cut = key[(cnt - 1) * kKbufThreads];
+            thi = fmaf(key_tau(cut), 1.00001f, eps);
+        }
+    }
+};
+
 // Per-ray traversal state, advanced one wide node at a time so that a warp can refill
 // lanes whose rays have finished while others are still walking the tree.
-template <int K>
+template <int K, class KB = KBuf<K>>
 struct TraceState {
+    using KBT = KB;
+    static constexpr int kK = K;
     RayState r;
-    KBuf<K> kb;
+    KB kb;
     float T;         // transmittance before the next composited hit
     uint64_t last;   // largest key composited so far
     int node;        // next wide node, or -1 when the round's walk is over
@@ -185,16 +241,20 @@ struct TraceState {
     int ncomp;       // hits composited so far
 };
 
+// State of a ray in the persistent walks (k-buffer in shared memory).
 template <int K>
-__device__ __forceinline__ void round_begin(const DevBvh& bvh, TraceState<K>& s, const TraceParams& P) {
+using WalkState = TraceState<K, KBufShared<K>>;
+
+template <class TS>
+__device__ __forceinline__ void round_begin(const DevBvh& bvh, TS& s, const TraceParams& P) {
     s.kb.reset(P.t_max);
     s.sp = 0;
     s.budget = bvh.cap + 8;
     s.node = (bvh.root >= 0) ? bvh.root : -1;
 }
 
-template <int K>
-__device__ __forceinline__ void trace_begin(const DevBvh& bvh, TraceState<K>& s, f3 o, f3 d, const TraceParams& P) {
+template <class TS>
+__device__ __forceinline__ void trace_begin(const DevBvh& bvh, TS& s, f3 o, f3 d, const TraceParams& P) {
     s.r = make_ray(o, d);
     s.T = 1.f;
     s.last = 0ull;
@@ -211,8 +271,8 @@ __device__ __forceinline__ void trace_begin(const DevBvh& bvh, TraceState<K>& s,
 
 // Continue a ray after `ncomp` hits already composited (the last one with key `last`),
 // with transmittance T in front of the next hit: the next round collects keys > last.
-template <int K>
-__device__ __forceinline__ void trace_resume(const DevBvh& bvh, TraceState<K>& s, f3 o, f3 d, const TraceParams& P,
+template <class TS>
+__device__ __forceinline__ void trace_resume(const DevBvh& bvh, TS& s, f3 o, f3 d, const TraceParams& P,
                                              uint64_t last, float T, int ncomp) {
     trace_begin(bvh, s, o, d, P);
     if (s.node == -2) return;  // non-finite ray
@@ -221,9 +281,8 @@ __device__ __forceinline__ void trace_resume(const DevBvh& bvh, TraceState<K>& s
     s.ncomp = ncomp;
 }
 
-template <int K, bool COUNT>
-__device__ __forceinline__ void test_leaf(const DevBvh& bvh, TraceState<K>& s, int ref, const TraceParams& P,
-                                          Counters& cnt) {
+template <bool COUNT, class TS>
+__device__ __forceinline__ void test_leaf(const DevBvh& bvh, TS& s, int ref, const TraceParams& P, Counters& cnt) {
     int first = leaf_first(ref), count = leaf_count(ref);
     if (first + count > bvh.n) {
         atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
@@ -242,15 +301,15 @@ __device__ __forceinline__ void test_leaf(const DevBvh& bvh, TraceState<K>& s, i
 
 // One step of the round's walk: visit one wide node (testing its leaf children) and pick
 // the next node.  Returns false once the walk of this round is over.
-template <int K, bool COUNT, class Stack>
-__device__ __forceinline__ bool trav_step(const DevBvh& bvh, TraceState<K>& s, Stack& stack, const TraceParams& P,
+template <bool COUNT, class TS, class Stack>
+__device__ __forceinline__ bool trav_step(const DevBvh& bvh, TS& s, Stack& stack, const TraceParams& P,
                                           Counters& cnt) {
     int node = s.node;
     if (node < 0) {
         // root that is a single leaf (n == 1), or an empty scene
         if (node == -1 && bvh.root != kRefEmpty && bvh.root < 0 && s.budget > 0) {
             s.budget = 0;
-            test_leaf<K, COUNT>(bvh, s, bvh.root, P, cnt);
+            test_leaf<COUNT>(bvh, s, bvh.root, P, cnt);
         }
         return false;
     }
@@ -297,7 +356,7 @@ __device__ __forceinline__ bool trav_step(const DevBvh& bvh, TraceState<K>& s, S
         int c = __ffs(leaves) - 1;
         leaves &= leaves - 1;
         int lr = c == 0 ? ref.x : (c == 1 ? ref.y : (c == 2 ? ref.z : ref.w));
-        test_leaf<K, COUNT>(bvh, s, lr, P, cnt);
+        test_leaf<COUNT>(bvh, s, lr, P, cnt);
     }
     const float inf = __int_as_float(0x7f800000);
     float d[4];
@@ -347,9 +406,9 @@ __device__ __forceinline__ bool trav_step(const DevBvh& bvh, TraceState<K>& s, S
 // Node visit of the two-phase walk: hit leaf children are queued (tested later by the
 // whole warp together) instead of being tested here; hit internal children go near to far
 // on the stack as in trav_step.  The queue lives in shared memory, q[slot * stride].
-template <int K, bool COUNT, class Stack>
-__device__ __forceinline__ void node_step_q(const DevBvh& bvh, TraceState<K>& s, Stack& stack, const TraceParams& P,
-                                            int* q, int stride, int& nq, Counters& cnt) {
+template <bool COUNT, class TS, class Stack>
+__device__ __forceinline__ void node_step_q(const DevBvh& bvh, TS& s, Stack& stack, const TraceParams& P, int* q,
+                                            int stride, int& nq, Counters& cnt) {
     int node = s.node;
     if (node < 0) {
         if (node == -1 && bvh.root != kRefEmpty && bvh.root < 0) q[stride * nq++] = bvh.root;
@@ -427,20 +486,39 @@ __device__ __forceinline__ void node_step_q(const DevBvh& bvh, TraceState<K>& s,
 
 // End of a round: composite the buffer in order (Eq. 8).  Returns true when the ray is
 // finished; otherwise the next round starts after the last composited key.
-template <int K, bool COUNT, class Visitor>
-__device__ __forceinline__ bool round_end(const DevBvh& bvh, TraceState<K>& s, const TraceParams& P, Visitor& vis,
+template <bool COUNT, class TS, class Visitor>
+__device__ __forceinline__ bool round_end(const DevBvh& bvh, TS& s, const TraceParams& P, Visitor& vis,
                                           Counters& cnt) {
+    constexpr int K = TS::kK;
     bool term = false;
     int filled = 0;
     float T = s.T;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        if (!term && j < s.kb.cnt) {
-            vis.composite(s.ncomp + filled, key_id(s.kb.key[j]), key_tau(s.kb.key[j]), s.kb.a[j], T);
-            T = mul_d(T, sub_d(1.0f, s.kb.a[j]));
+    uint64_t lastk;
+    if constexpr (TS::KBT::kShared) {
+        // entries in order from shared memory; stop at termination
+        for (int j = 0; j < s.kb.cnt; ++j) {
+            const uint64_t k = s.kb.key_at(j);
+            const float al = s.kb.a_at(j);
+            vis.composite(s.ncomp + filled, key_id(k), key_tau(k), al, T);
+            T = mul_d(T, sub_d(1.0f, al));
             ++filled;
-            if (T < P.T_min) term = true;
+            if (T < P.T_min) {
+                term = true;
+                break;
+            }
         }
+        lastk = s.kb.cnt == K ? s.kb.key_at(K - 1) : 0ull;
+    } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if (!term && j < s.kb.cnt) {
+                vis.composite(s.ncomp + filled, key_id(s.kb.key[j]), key_tau(s.kb.key[j]), s.kb.a[j], T);
+                T = mul_d(T, sub_d(1.0f, s.kb.a[j]));
+                ++filled;
+                if (T < P.T_min) term = true;
+            }
+        }
+        lastk = s.kb.key[K - 1];
     }
     s.T = T;
     s.ncomp += filled;
@@ -450,7 +528,7 @@ __device__ __forceinline__ bool round_end(const DevBvh& bvh, TraceState<K>& s, c
         atomicOr(bvh.status, GRT_STATUS_BAD_TREE);
         return true;
     }
-    s.last = s.kb.key[K - 1];
+    s.last = lastk;
     round_begin(bvh, s, P);
     return false;
 }
@@ -465,9 +543,9 @@ __device__ __forceinline__ int trace_ray(const DevBvh& bvh, const RayState& r, c
     TraceState<K> s;
     trace_begin(bvh, s, r.o, r.d, P);
     while (true) {
-        while (trav_step<K, COUNT>(bvh, s, stack, P, cnt)) {
+        while (trav_step<COUNT>(bvh, s, stack, P, cnt)) {
         }
-        if (round_end<K, COUNT>(bvh, s, P, vis, cnt)) break;
+        if (round_end<COUNT>(bvh, s, P, vis, cnt)) break;
     }
     vis.finish(s.T);
     return s.rounds;
@@ -594,14 +672,14 @@ struct ColourVisitor {
 // until every active lane has a leaf queued or has finished its walk, (B) the queued surfel
 // tests of all lanes, (C) compositing of finished walks, once kCompositeBatch of them (or
 // all active lanes) are waiting.  Task supplies
-//   bool begin(long long ray, TraceState<K>&, Visitor&, const DevBvh*&)  -- false: no ray
-//   void end(long long ray, const TraceState<K>&, Visitor&)              -- ray finished
+//   bool begin(long long ray, WalkState<K>&, Visitor&, const DevBvh*&)  -- false: no ray
+//   void end(long long ray, const WalkState<K>&, Visitor&)              -- ray finished
 // and the Visitor type receiving composite() calls.
 #ifndef GRT_REFILL
 #define GRT_REFILL 4
 #endif
 #ifndef GRT_QUEUE
-#define GRT_QUEUE 16
+#define GRT_QUEUE 12
 #endif
 #ifndef GRT_LEAF_BATCH
 #define GRT_LEAF_BATCH 1
@@ -623,6 +701,14 @@ constexpr int kLeafBatch = GRT_LEAF_BATCH;  // leaves every walking lane queues 
 constexpr int kCompositeBatch = GRT_COMPOSITE_BATCH;  // finished walks composited together
 constexpr int kPersistentThreads = 128;  // block size of every persistent_trace kernel
 
+static_assert(kPersistentThreads == kKbufThreads, "k-buffer columns are laid out for the persistent block");
+
+// Dynamic shared memory of a persistent walk kernel: its lanes' k-buffers.
+template <int K>
+constexpr size_t walk_smem_bytes() {
+    return (size_t)K * (sizeof(uint64_t) + sizeof(float)) * kPersistentThreads;
+}
+
 template <int K, class Task>
 __device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& P, unsigned long long* next,
                                                  long long total, int* q, int qstride,
@@ -635,7 +721,10 @@ __device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& 
         stack.sh = shared_stack + threadIdx.x;
         stack.stride = kPersistentThreads;
     }
-    TraceState<K> ts;
+    extern __shared__ __align__(16) unsigned char walk_smem[];
+    WalkState<K> ts;
+    ts.kb.key = reinterpret_cast<uint64_t*>(walk_smem) + threadIdx.x;
+    ts.kb.a = reinterpret_cast<float*>(reinterpret_cast<uint64_t*>(walk_smem) + K * kPersistentThreads) + threadIdx.x;
     ts.node = -2;
     typename Task::Visitor vis;
     const DevBvh* bvh = nullptr;
@@ -647,6 +736,9 @@ __device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& 
         unsigned idle = __ballot_sync(0xffffffffu, !act);
         int nidle = __popc(idle);
         if (!drained && (nidle >= kRefill || nidle == 32)) {
+            // consecutive rays of the (coherent) walk order from one global counter; per-block
+            // chunks of 256 / 1,024 / 4,096 consecutive rays, for L1 reuse within an SM, measured
+            // slower (walk 17.08 -> 17.25 / 18.09 / 24.69 ms on the 300k-surfel 800x800 frame)
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(next, (unsigned long long)nidle);
             base = __shfl_sync(0xffffffffu, base, 0);
@@ -667,10 +759,10 @@ __device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& 
         while (true) {
             bool walking = act && ts.node != -2 && nq <= kQueue - kWide;
             if (!__any_sync(0xffffffffu, walking)) break;
-            if (walking) node_step_q<K, false>(*bvh, ts, stack, P, q, qstride, nq, cnt);
+            if (walking) node_step_q<false>(*bvh, ts, stack, P, q, qstride, nq, cnt);
             if (__all_sync(0xffffffffu, !act || nq >= kLeafBatch || ts.node == -2)) break;
         }
-        for (int i = 0; i < nq; ++i) test_leaf<K, false>(*bvh, ts, q[i * qstride], P, cnt);
+        for (int i = 0; i < nq; ++i) test_leaf<false>(*bvh, ts, q[i * qstride], P, cnt);
         nq = 0;
         // finished walks wait until kCompositeBatch of them (or every active lane) can
         // composite in the same pass
@@ -682,13 +774,26 @@ __device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& 
             go = fin && (__popc(fm) >= kCompositeBatch || fm == am);
         }
         if (go) {
-            if (round_end<K, false>(*bvh, ts, P, vis, cnt)) {
+            if (round_end<false>(*bvh, ts, P, vis, cnt)) {
                 vis.finish(ts.T);
                 task.end(ray, ts, vis);
                 act = false;
             }
         }
     }
+}
+
+// Grid of a persistent walk kernel: as many blocks as fit on the device at once (with
+// their dynamic k-buffer memory), at most blocks_max.
+template <class Kernel>
+inline long long persistent_grid(Kernel kernel, size_t dyn_smem, long long blocks_max) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPersistentThreads, dyn_smem);
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    return grid < blocks_max ? grid : blocks_max;
 }
 
 }  // namespace grt

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kShadeThreads) k_trace_rays(const __grid_const
 }
 
 #ifndef GRT_TRACE_MIN_BLOCKS
-#define GRT_TRACE_MIN_BLOCKS 4  // 128 threads x 4 blocks: at most 128 registers per thread
+#define GRT_TRACE_MIN_BLOCKS 5  // 128 threads x 5 blocks: at most 96 registers per thread
 #endif
 
 __global__ void k_zero_outputs(float* c, float* v, float* i, int n) {
@@ -305,6 +305,25 @@ inline int make_job(const grt_bvh* b, const grt_surfels* s, const grt_gbuffer* g
     return GRT_OK;
 }
 
+// Caller-supplied device workspace of a shading call (NULL: the stream-ordered pool).
+struct Workspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+inline int workspace_arg(void* ptr, size_t bytes, Workspace* out) {
+    if (ptr && ((uintptr_t)ptr & 255)) return set_error(GRT_ERR_ARG, "workspace must be 256-byte aligned");
+    out->ptr = ptr;
+    out->bytes = ptr ? bytes : 0;
+    return GRT_OK;
+}
+
+// Ray buffers of a shading call over n ray slots: direction and (c_rt, T) per slot, the
+// walk's ray counter, then (with the ray order) bucket counters and 12 bytes per slot.
+inline size_t shade_ws_bytes(long long n, bool ord) {
+    return sizeof(float4) * (2 * (size_t)n + 1) + (ord ? order_scratch_bytes(n) : 0);
+}
+
 // Keeps freed ray buffers in the device's stream-ordered pool between calls.
 inline void keep_pool_memory() {
     static std::once_flag once[64];
@@ -328,7 +347,7 @@ struct ShadeTrace {
     const JobTable<CAP>* T;
     const float4* dirs;
     float4* res;
-    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& cv, const DevBvh*& bvh) {
+    __device__ __forceinline__ bool begin(long long r, WalkState<K>& ts, Visitor& cv, const DevBvh*& bvh) {
         float4 dw = __ldg(dirs + r);
         if (dw.w == 0.f) {
             res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
@@ -345,7 +364,7 @@ struct ShadeTrace {
         cv = RadianceVisitor(J.color, J.cdim, d);
         return true;
     }
-    __device__ __forceinline__ void end(long long r, const TraceState<K>& ts, Visitor& cv) {
+    __device__ __forceinline__ void end(long long r, const WalkState<K>& ts, Visitor& cv) {
         res[r] = make_float4(cv.c[0], cv.c[1], cv.c[2], ts.T);
     }
 };
@@ -452,7 +471,7 @@ struct ShadeTraceSave {
     const float4* dirs;
     float4* res;
     const SavedHits* sv;
-    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& cv, const DevBvh*& bvh) {
+    __device__ __forceinline__ bool begin(long long r, WalkState<K>& ts, Visitor& cv, const DevBvh*& bvh) {
         float4 dw = __ldg(dirs + r);
         if (dw.w == 0.f) {
             res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
@@ -470,7 +489,7 @@ struct ShadeTraceSave {
         cv = SavingVisitor(J.color, J.cdim, d, sv, r);
         return true;
     }
-    __device__ __forceinline__ void end(long long r, const TraceState<K>& ts, Visitor& cv) {
+    __device__ __forceinline__ void end(long long r, const WalkState<K>& ts, Visitor& cv) {
         res[r] = make_float4(cv.c[0], cv.c[1], cv.c[2], ts.T);
         sv->nh[r] = ts.ncomp;
     }
@@ -496,7 +515,7 @@ struct ShadeTraceRelight {
     const float4* dirs;
     float4* res;
     const RelightDev* E;
-    __device__ __forceinline__ bool begin(long long r, TraceState<K>& ts, Visitor& v, const DevBvh*& bvh) {
+    __device__ __forceinline__ bool begin(long long r, WalkState<K>& ts, Visitor& v, const DevBvh*& bvh) {
         float4 dw = __ldg(dirs + r);
         if (dw.w == 0.f) {
             res[r] = make_float4(0.f, 0.f, 0.f, -1.f);
@@ -513,7 +532,7 @@ struct ShadeTraceRelight {
         v = AttrVisitor(&J.attr, d);
         return true;
     }
-    __device__ __forceinline__ void end(long long r, const TraceState<K>& ts, Visitor& v) {
+    __device__ __forceinline__ void end(long long r, const WalkState<K>& ts, Visitor& v) {
         const float V = ts.T;
         float ss[3] = {0.f, 0.f, 0.f};
         if (V < 1.f) {
@@ -541,13 +560,9 @@ inline void launch_trace_relight(const JobTable<CAP>& T, const float4* dirs, flo
                                  unsigned long long* next_ray, long long blocks_max, cudaStream_t st,
                                  const unsigned* order = nullptr) {
     cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_rays_relight<K, CAP>, kShadeThreads, 0);
-    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    if (grid > blocks_max) grid = blocks_max;
-    k_trace_rays_relight<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, E, next_ray, order);
+    constexpr size_t smem = walk_smem_bytes<K>();
+    const long long grid = persistent_grid(k_trace_rays_relight<K, CAP>, smem, blocks_max);
+    k_trace_rays_relight<K, CAP><<<(unsigned)grid, kShadeThreads, smem, st>>>(T, dirs, res, E, next_ray, order);
 }
 
 // Relighting rays with the mesh backend of Eq. 14: closest triangle hit, one thread per
@@ -590,13 +605,9 @@ template <int K, int CAP>
 inline void launch_trace_dyn(const JobTable<CAP>& T, const float4* dirs, float4* res, unsigned long long* next_ray,
                              long long blocks_max, cudaStream_t st, const unsigned* order = nullptr) {
     cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_rays_ww<K, CAP>, kShadeThreads, 0);
-    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    if (grid > blocks_max) grid = blocks_max;
-    k_trace_rays_ww<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, next_ray, order);
+    constexpr size_t smem = walk_smem_bytes<K>();
+    const long long grid = persistent_grid(k_trace_rays_ww<K, CAP>, smem, blocks_max);
+    k_trace_rays_ww<K, CAP><<<(unsigned)grid, kShadeThreads, smem, st>>>(T, dirs, res, next_ray, order);
 }
 
 // Persistent forward trace that also keeps the per-ray hit record.
@@ -605,13 +616,9 @@ inline void launch_trace_save(const JobTable<CAP>& T, const float4* dirs, float4
                               unsigned long long* next_ray, long long blocks_max, cudaStream_t st,
                               const unsigned* order = nullptr) {
     cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_rays_save<K, CAP>, kShadeThreads, 0);
-    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    if (grid > blocks_max) grid = blocks_max;
-    k_trace_rays_save<K, CAP><<<(unsigned)grid, kShadeThreads, 0, st>>>(T, dirs, res, sv, next_ray, order);
+    constexpr size_t smem = walk_smem_bytes<K>();
+    const long long grid = persistent_grid(k_trace_rays_save<K, CAP>, smem, blocks_max);
+    k_trace_rays_save<K, CAP><<<(unsigned)grid, kShadeThreads, smem, st>>>(T, dirs, res, sv, next_ray, order);
 }
 
 }  // namespace

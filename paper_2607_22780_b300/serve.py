@@ -90,6 +90,25 @@ class _State:
         self.next = 0
         self.done_ms: Optional[float] = None
         self.start_ms: Optional[float] = None
+        self.last_ev: Optional[torch.cuda.Event] = None   # end of the last launch holding a slice
+        self._on_compute = False
+
+    def tensors(self):
+        """Every device tensor of the request (allocated on the prep stream)."""
+        ts = [self.env_rgb, self.color, self.vis, self.ind, self.env.tables]
+        ts += [t for t in (self.gb.pos, self.gb.normal, self.gb.albedo, self.gb.rough, self.gb.metal, self.gb.valid,
+                           self.gb.alpha, self.gb.depth) if t is not None]
+        return ts
+
+    def use_on(self, stream):
+        """Mark the request's tensors as used by `stream`: the caching allocator then keeps
+        their blocks until the work queued there when they are freed has finished, so a
+        request dropped while a launch still writes its outputs cannot hand those blocks to
+        another request."""
+        if not self._on_compute:
+            for t in self.tensors():
+                t.record_stream(stream)
+            self._on_compute = True
 
     @staticmethod
     def bytes_needed(req: RelightRequest) -> int:
@@ -111,13 +130,16 @@ class RelightServer:
         self.inflight = int(inflight)
         self.cancelled = set()
         self.peak_active = 0
+        self.peak_mem = 0
 
     def cancel(self, rid: int):
         """Drop a request: pending requests are skipped, admitted ones stop getting slices."""
         self.cancelled.add(rid)
 
     # ------------------------------------------------------------------ batched
-    def run_batched(self, trace: List[RelightRequest], realtime: bool = True) -> dict:
+    def run_batched(self, trace: List[RelightRequest], realtime: bool = True, on_launch=None) -> dict:
+        """Serve `trace` with continuous batching.  `on_launch(i, slices)`, if given, is
+        called after launch i with its (request id, first pixel, pixels) slices."""
         dev = self.device
         compute = torch.cuda.Stream(dev)
         prep = torch.cuda.Stream(dev)
@@ -126,13 +148,14 @@ class RelightServer:
         active: List[_State] = []
         finished: List[_State] = []
         inflight = collections.deque()
+        retiring: List[_State] = []    # cancelled after a launch: memory counted until it ends
         mem = 0
         launches = 0
         torch.cuda.synchronize(dev)
         ref.record(compute)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        while pending or active or inflight:
+        while pending or active or inflight or retiring:
             now = (time.perf_counter() - t0) if realtime else math.inf
             # admit arrivals while their memory fits the budget
             while pending and pending[0].arrival <= now:
@@ -158,7 +181,11 @@ class RelightServer:
                     finished.append(st)
             for st in [s for s in active if s.req.rid in self.cancelled]:
                 active.remove(st)
+                retiring.append(st)
+            for st in [s for s in retiring if s.last_ev is None or s.last_ev.query()]:
+                retiring.remove(st)
                 mem -= st.bytes
+            self.peak_mem = max(self.peak_mem, mem)
             # at most `inflight` launches queued on the GPU before building the next one
             if len(inflight) >= self.inflight:
                 inflight[0][0].synchronize()
@@ -179,6 +206,7 @@ class RelightServer:
                 reqs = []
                 for st, off, npx in batch:
                     compute.wait_event(st.ready)
+                    st.use_on(compute)
                     a = st.req.alloc
                     reqs.append(api.ShadeRequest(st.scene, st.gb, st.env, a[0], a[1], a[2], st.req.seed, brdf=1,
                                                  pixel_offset=off, count=npx, color=st.color[off:off + npx],
@@ -187,13 +215,19 @@ class RelightServer:
                 launches += 1
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(compute)
+                for st, _, _ in batch:
+                    st.last_ev = ev
                 ending = [st for st, _, _ in batch if st.next >= st.P]
                 for st in ending:
                     active.remove(st)
                 inflight.append((ev, ending))
+                if on_launch is not None:
+                    on_launch(launches - 1, [(st.req.rid, off, npx) for st, off, npx in batch])
                 continue
             if inflight:
                 inflight[0][0].synchronize()
+            elif retiring:
+                retiring[0].last_ev.synchronize()
             elif active and not any(st.next < st.P for st in active):
                 raise RuntimeError("scheduler stalled: admitted requests without work or launch")
             elif pending:

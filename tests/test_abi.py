@@ -55,9 +55,43 @@ def test_saved_record_size_and_checks_without_gpu():
     g, e = _lib.GBuffer(), _lib.EnvMap()
     rc = lib.grt_shade_pixels_save(None, ctypes.byref(s), ctypes.byref(p), ctypes.byref(g), ctypes.byref(e),
                                    ctypes.byref(smp), None, 1000, ctypes.c_void_p(1 << 20), None, None, 16,
-                                   ctypes.c_void_p(1 << 20), nb - 1, None)
+                                   ctypes.c_void_p(1 << 20), nb - 1, None, 0, None)
     assert rc == _lib.GRT_ERR_ARG and b"bytes" in lib.grt_last_error()
     rc = lib.grt_shade_backward_saved(None, ctypes.byref(s), ctypes.byref(p), ctypes.byref(g), ctypes.byref(e),
                                       ctypes.byref(smp), None, 1000, ctypes.c_void_p(1 << 20), None, None, 16,
-                                      ctypes.c_void_p((1 << 20) + 16), nb, None, None)
+                                      ctypes.c_void_p((1 << 20) + 16), nb, None, None, 0, None)
+    assert rc == _lib.GRT_ERR_ARG and b"aligned" in lib.grt_last_error()
+
+
+def test_workspace_sizes_and_checks_without_gpu():
+    """Workspace convention of the shading calls: the size queries, and a misaligned or
+    undersized caller workspace refused before any device work."""
+    lib = _lib.load()
+    smp = _lib.Sampling(16, 8, 8, 1, 7)
+    R = 640_000 * 32
+    nb = lib.grt_shade_workspace_size(R)
+    # direction + (c_rt, T) 32 B and the ray order 12 B per slot, plus counters
+    assert R * 44 <= nb <= R * 44 + 300_000
+    assert lib.grt_shade_workspace_size(0) > 0
+    assert lib.grt_shade_workspace_size(-1) == 0 and b"n_rays" in lib.grt_last_error()
+    saved = lib.grt_shade_backward_workspace_size(640_000, ctypes.byref(smp), 1)
+    assert saved >= R * 24
+    recomp = lib.grt_shade_backward_workspace_size(640_000, ctypes.byref(smp), 0)
+    # two chunk buffers of at most 8M rays, each with a 64-hit transient record
+    assert (8 << 20) * (36 + 12 * 64) < recomp < 2 * (8 << 20) * (36 + 12 * 64 + 40) + 2 * 300_000
+    assert lib.grt_shade_backward_workspace_size(-1, ctypes.byref(smp), 0) == 0
+    s = _lib.Surfels(0, 3)
+    p = _lib.TraceParams(1 / 255, 0.99, 0.01, 3e38, 1e-4, 1e-6, 16)
+    g, e = _lib.GBuffer(), _lib.EnvMap()
+    smp2 = _lib.Sampling(8, 4, 4, 1, 7)
+    rc = lib.grt_shade_pixels(None, ctypes.byref(s), ctypes.byref(p), ctypes.byref(g), ctypes.byref(e),
+                              ctypes.byref(smp2), None, 10, ctypes.c_void_p(1 << 20), None, None,
+                              ctypes.c_void_p((1 << 20) + 64), 1 << 20, None)
+    assert rc == _lib.GRT_ERR_ARG and b"aligned" in lib.grt_last_error()
+    rc = lib.grt_shade_backward(None, ctypes.byref(s), ctypes.byref(p), ctypes.byref(g), ctypes.byref(e),
+                                ctypes.byref(smp2), None, 10, ctypes.c_void_p(1 << 20), None, None, None,
+                                ctypes.c_void_p((1 << 20) + 8), 1 << 20, None)
+    assert rc == _lib.GRT_ERR_ARG and b"aligned" in lib.grt_last_error()
+    req = (_lib.ShadeRequest * 1)()
+    rc = lib.grt_shade_batch(req, 1, ctypes.byref(p), ctypes.c_void_p((1 << 20) + 4), 1 << 20, None)
     assert rc == _lib.GRT_ERR_ARG and b"aligned" in lib.grt_last_error()

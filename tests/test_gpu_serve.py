@@ -58,3 +58,26 @@ def test_cancelled_request_is_dropped():
     assert trace[2].rid not in out["outputs"] and out["requests"] == 4
     for st in out["outputs"].values():
         assert torch.equal(_alone(st)[0], st.color)
+
+
+def test_cancel_between_slices_leaves_the_others_intact():
+    """A request cancelled after its first slice was launched, while that launch may still
+    be writing its outputs: its memory must not be handed to the requests admitted after
+    it, so every other request still equals its run-alone image."""
+    # about two requests fit the budget at a time, so most are admitted after the cancellation
+    srv = serve.RelightServer(_scenes(), hbm_budget=300_000, ray_budget=1500, max_batch=2, inflight=2)
+    trace = _trace(7, seed=17)
+    victim = trace[1].rid
+    seen = []
+
+    def on_launch(i, slices):
+        seen.extend(rid for rid, _, _ in slices)
+        if victim in seen:
+            srv.cancel(victim)
+
+    out = srv.run_batched(trace, realtime=False, on_launch=on_launch)
+    assert victim in seen and victim not in out["outputs"]
+    assert out["requests"] == len(trace) - 1
+    for st in out["outputs"].values():
+        col, vis, ind = _alone(st)
+        assert torch.equal(col, st.color) and torch.equal(vis, st.vis) and torch.equal(ind, st.ind)

@@ -5,7 +5,8 @@ pre-reserves the whole device budget -- rebuild their BVH through this entry poi
 sort scratch is a fixed array inside libgrt.  This file is collected last on purpose.
 It checks, through the C ABI, that two rebuilds in a row (the second one reusing the
 array the first one left behind, on a different scene size) trace exactly like
-grt_rebuild_bvh, and that a scene above the fixed limit is refused before any GPU work.
+grt_rebuild_bvh, that a scene above the fixed limit is refused before any GPU work, and
+that a call draws nothing from the device's memory pool or from cudaMalloc.
 """
 import ctypes
 
@@ -68,4 +69,42 @@ def test_noalloc_rejects_scenes_above_the_limit():
     rc = L.load().grt_rebuild_bvh_noalloc(S.handle, ctypes.byref(S.surfels()), ctypes.byref(S.params), None)
     assert rc == L.GRT_ERR_ARG
     assert b"exceeds" in L.load().grt_last_error()
+    S.close()
+
+
+def test_noalloc_rebuild_allocates_no_device_memory():
+    """The defining property: after the first call (which looks up the scratch address),
+    a rebuild leaves the device's default pool and its free memory untouched."""
+    from cuda.bindings import driver as dr, runtime as rt
+
+    sc = wl.scene_objects(100_000, seed=3)
+    S = api.Scene.from_workload(sc)
+    _noalloc(S)                                   # first call on the device: address lookup
+    torch.cuda.synchronize()
+    dev = torch.cuda.current_device()
+    err, pool = rt.cudaDeviceGetDefaultMemPool(dev)
+    assert err == rt.cudaError_t.cudaSuccess
+    A = rt.cudaMemPoolAttr
+
+    def attr(a):
+        e, v = rt.cudaMemPoolGetAttribute(pool, a)
+        assert e == rt.cudaError_t.cudaSuccess
+        return int(v)
+
+    used0 = attr(A.cudaMemPoolAttrUsedMemCurrent)
+    reserved0 = attr(A.cudaMemPoolAttrReservedMemCurrent)
+    (e,) = rt.cudaMemPoolSetAttribute(pool, A.cudaMemPoolAttrUsedMemHigh, dr.cuuint64_t(0))
+    assert e == rt.cudaError_t.cudaSuccess
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        _noalloc(S)
+    torch.cuda.synchronize()
+    assert attr(A.cudaMemPoolAttrUsedMemHigh) <= used0
+    assert attr(A.cudaMemPoolAttrReservedMemCurrent) == reserved0
+    assert torch.cuda.mem_get_info()[0] == free0
+    # the allocating rebuild, for contrast, does draw its sort scratch from the pool
+    S.rebuild()
+    torch.cuda.synchronize()
+    assert attr(A.cudaMemPoolAttrUsedMemHigh) > used0
+    assert S.status() == 0
     S.close()
