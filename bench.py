@@ -691,7 +691,31 @@ def time_c1(api, dev, args):
         b.record()
         torch.cuda.synchronize()
         res[name + "_us"] = a.elapsed_time(b) / n * 1e3
+    # the same frame replayed from a CUDA graph: the device time without the host-side
+    # launch overhead of the per-frame calls
+    try:
+        gstream = torch.cuda.Stream(device=dev)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(gstream):
+            frame()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=gstream):
+                frame()
+        for _ in range(10):
+            graph.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            graph.replay()
+        b.record()
+        torch.cuda.synchronize()
+        res["gbuffer_shade_graph_us"] = a.elapsed_time(b) / n * 1e3
+    except Exception as e:  # capture not possible here: reported, not fatal
+        res["graph_error"] = repr(e)[:200]
     R = int(G.valid.sum().item()) * 4
+    if "gbuffer_shade_graph_us" in res:
+        res["rays_per_s_gbuffer_shade_graph"] = R / (res["gbuffer_shade_graph_us"] * 1e-6)
     return {"workload": "plain_8k_64x64_4cos", "surfels": 8000, "rays": R,
             "rays_per_s_shade": R / (res["shade_us"] * 1e-6),
             "rays_per_s_gbuffer_shade": R / (res["gbuffer_shade_us"] * 1e-6), **res, "frames_timed": n,

@@ -270,7 +270,10 @@ int grt_shade_backward(const grt_bvh* bvh, const grt_surfels* surfels, const grt
  * grt_shade_pixels does and also keeps, in the caller's device buffer `saved` (256-byte
  * aligned, at least grt_shade_saved_bytes() bytes), every secondary ray's sampled
  * direction, its traced (c_rt, T) and its first max_hits composited hits (surfel id,
- * tau, alpha) in compositing order: 36 + 12 max_hits bytes per ray.
+ * tau, alpha) in compositing order: 36 + 12 max_hits bytes per ray.  Rays with more than
+ * max_hits hits keep their next 192 hits in an overflow area of one slot per 256 rays (at
+ * least 64 slots, 2,308 bytes each), so that the backward replays them without a traversal;
+ * only rays longer than that, or beyond the slots, are traced again.
  * grt_shade_backward_saved is grt_shade_backward without the resampling and the forward
  * re-trace: rays with at most max_hits hits are replayed from the record, longer ones are
  * traced again.  Gradients equal grt_shade_backward's up to the order of the float atomic

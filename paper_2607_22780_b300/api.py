@@ -393,7 +393,8 @@ def shade_saved_bytes(n_pixels: int, n_cos, n_ggx, n_env, max_hits: int = 64) ->
 def shade_pixels_save(scene: Scene, gb: GBuffer, env: Environment, n_cos, n_ggx, n_env, seed, brdf=1, pixels=None,
                       max_hits: int = 64, params=None, outputs=None, workspace=None, stream=None):
     """shade_pixels that also keeps the forward record for shade_backward(saved=...):
-    36 + 12 max_hits bytes per ray slot (pixels x N_r).  Returns (colour, visibility,
+    36 + 12 max_hits bytes per ray slot (pixels x N_r) plus an overflow area for rays with
+    more hits (192 more hits each for one ray in 256).  Returns (colour, visibility,
     indirect, SavedShade)."""
     n = int(pixels.shape[0]) if pixels is not None else gb.W * gb.H
     if pixels is not None:

@@ -25,6 +25,7 @@ DevBvh dev_bvh(const grt_bvh* b) {
     DevBvh d;
     d.nodes = b->wnodes;
     d.records = b->records;
+    d.normals = b->normals;
     d.n = b->n;
     d.cap = b->n_int;
     d.root = b->n == 0 ? kRefEmpty : (b->n == 1 ? leaf_ref(0, 1) : 0);

@@ -306,9 +306,27 @@ struct AdjointTask {
     __device__ __forceinline__ void end(long long, const WalkState<K>&, Visitor&) {}
 };
 
-// Replay of the saved hit records: one thread per ray with at most L composited hits
-// walks its (id, tau, alpha) list in compositing order, rebuilding T_k exactly as the
-// forward compositor did.
+// Replay of the saved hit records: one thread per ray walks its (id, tau, alpha) list in
+// compositing order, rebuilding T_k exactly as the forward compositor did.  The first
+// ov_cap threads take the rays that hold an overflow slot (more than L hits), so that the
+// longest lists start first and do not trail the launch; the other threads take every
+// ray with at most L hits.  Rays longer than the record and its overflow slot, and rays
+// that found no slot free, are listed for the traced adjoint walk.
+__device__ __forceinline__ void replay_hit(const SavedHits& sv, long long r, int slot, int k, int* id, float* tau,
+                                           float* alpha) {
+    if (k < sv.L) {
+        const size_t i = (size_t)k * sv.R + r;
+        *id = __ldg(sv.ids + i);
+        *tau = __ldg(sv.tau + i);
+        *alpha = __ldg(sv.alpha + i);
+    } else {
+        const size_t i = (size_t)(k - sv.L) * sv.ov_cap + slot;
+        *id = __ldg(sv.ov_ids + i);
+        *tau = __ldg(sv.ov_tau + i);
+        *alpha = __ldg(sv.ov_alpha + i);
+    }
+}
+
 __global__ void __launch_bounds__(kShadeThreads) k_adjoint_replay(const __grid_constant__ JobTable<1> T,
                                                                   const float4* __restrict__ dirs,
                                                                   const float4* __restrict__ res,
@@ -316,15 +334,36 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_replay(const __grid_c
                                                                   const __grid_constant__ SavedHits sv, GradPtrs g,
                                                                   unsigned long long* __restrict__ over_count,
                                                                   long long* __restrict__ over_list) {
-    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= T.total_rays) return;
-    const int n = __ldg(sv.nh + r);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long r;
+    int slot = -1;
+    if (t < sv.ov_cap) {
+        const unsigned used = *sv.ov_count;
+        if (t >= (long long)(used < (unsigned)sv.ov_cap ? used : (unsigned)sv.ov_cap)) return;
+        slot = (int)t;
+        r = __ldg(sv.ov_ray + slot);
+        if ((unsigned long long)r >= (unsigned long long)T.total_rays) {
+            atomicOr(T.job[0].bvh.status, GRT_STATUS_BAD_INDEX);
+            return;
+        }
+    } else {
+        r = t - sv.ov_cap;
+        if (r >= T.total_rays) return;
+    }
+    const int raw = __ldg(sv.nh + r);
+    const int n = raw & (kNoSlot - 1);
     if (n == 0) return;
     float4 a = __ldg(adj + r);
     if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f) return;
-    if (n > sv.L) {  // longer than the record: left to the traced adjoint walk
-        over_list[atomicAdd(over_count, 1ull)] = r;
-        return;
+    if (n > sv.L) {
+        if (slot < 0) {  // a long ray: its slot thread takes it, or, without a slot, the walk
+            if (raw & kNoSlot) over_list[atomicAdd(over_count, 1ull)] = r;
+            return;
+        }
+        if (n > sv.L + kOverflowHits) {  // longer than record and slot: left to the walk
+            over_list[atomicAdd(over_count, 1ull)] = r;
+            return;
+        }
     }
     const ShadeJob& J = T.job[0];
     float4 rr = __ldg(res + r), dw = __ldg(dirs + r);
@@ -333,17 +372,13 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_replay(const __grid_c
     const int ns = J.bvh.n;
     float Tb = 1.f;
     // the next hit's record is loaded while the current one is composited
-    int id = __ldg(sv.ids + r);
-    float tau = __ldg(sv.tau + r), alpha = __ldg(sv.alpha + r);
+    int id;
+    float tau, alpha;
+    replay_hit(sv, r, slot, 0, &id, &tau, &alpha);
     for (int k = 0; k < n; ++k) {
         int idn = 0;
         float taun = 0.f, alphan = 0.f;
-        if (k + 1 < n) {
-            const size_t i = (size_t)(k + 1) * sv.R + r;
-            idn = __ldg(sv.ids + i);
-            taun = __ldg(sv.tau + i);
-            alphan = __ldg(sv.alpha + i);
-        }
+        if (k + 1 < n) replay_hit(sv, r, slot, k + 1, &idn, &taun, &alphan);
         if ((unsigned)id >= (unsigned)ns) {
             atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
             return;
@@ -469,7 +504,10 @@ static void run_adjoint(const JobTable<1>& T, const float4* dirs, const float4* 
     g_adj_timing.mark(0, st);
     k_adjoint_weights<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, in, adj);
     g_adj_timing.mark(1, st);
-    if (hits.L > 0) k_adjoint_replay<<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, res, adj, hits, g, n_over, over);
+    if (hits.L > 0) {
+        const long long gp = (T.total_rays + hits.ov_cap + kShadeThreads - 1) / kShadeThreads;
+        k_adjoint_replay<<<(unsigned)gp, kShadeThreads, 0, st>>>(T, dirs, res, adj, hits, g, n_over, over);
+    }
     g_adj_timing.mark(2, st);
     constexpr size_t smem = walk_smem_bytes<K>();
     const long long grid = persistent_grid(k_adjoint_ww<K>, smem, gr);
@@ -529,7 +567,7 @@ static BackwardLayout backward_layout(long long n_pixels, int Nr, bool saved) {
     b.Rc = b.chunk_px * Nr;
     b.lay = saved_layout(b.Rc, kRecomputeHits);
     b.ord_off = (b.lay.total + (sizeof(float4) + sizeof(long long)) * (size_t)b.Rc + 16 + 255) & ~(size_t)255;
-    b.per = (b.ord_off + (GRT_RAY_ORDER ? order_scratch_bytes(b.Rc) : 0) + 255) & ~(size_t)255;
+    b.per = (b.ord_off + (use_ray_order(b.Rc) ? order_scratch_bytes(b.Rc) : 0) + 255) & ~(size_t)255;
     b.nbuf = b.n_chunks > 1 ? 2 : 1;
     b.total = b.per * b.nbuf;
     return b;
@@ -608,19 +646,18 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
             else
                 Jc.pixel_offset += (int)p0;
             Tc.total_rays = (long long)Jc.n_pixels * Jc.Nr;
-            const SavedHits hits{reinterpret_cast<int*>(cb + lay.nh), reinterpret_cast<int*>(cb + lay.ids),
-                                 reinterpret_cast<float*>(cb + lay.tau), reinterpret_cast<float*>(cb + lay.alpha),
-                                 Tc.total_rays, kRecomputeHits};
+            const SavedHits hits = saved_hits(cb, lay, Tc.total_rays, kRecomputeHits);
             const AdjIn in{dL_dcolor + 3 * p0, dL_dvis ? dL_dvis + p0 : nullptr, dL_dind ? dL_dind + 3 * p0 : nullptr};
             const long long gr = (Tc.total_rays + kShadeThreads - 1) / kShadeThreads;
             // the chunk's rays go to the walk in bucket order, as in the forward
             RayOrder ro{nullptr, nullptr, nullptr, nullptr};
-            if (GRT_RAY_ORDER) {
+            const bool ord = use_ray_order(Tc.total_rays);
+            if (ord) {
                 ro = ray_order_bufs(cb + ord_off, Tc.total_rays);
                 cudaMemsetAsync(ro.hist, 0, 4 * (size_t)kAllBuckets, cs);
             }
             k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, cs>>>(Tc, dirs, ro);
-            if (GRT_RAY_ORDER) launch_ray_order(ro, Tc.total_rays, cs);
+            if (ord) launch_ray_order(ro, Tc.total_rays, cs);
             const unsigned* oorder = ro.order;
             dispatch_k(p->k, [&](auto kc) {
                 constexpr int K = decltype(kc)::value;

@@ -324,6 +324,7 @@ struct RecordIn {
     SurfelIn s;
     const int* sorted;
     float4* records;
+    float4* normals;
     float* leaf_box;
 };
 
@@ -342,6 +343,7 @@ __global__ void k_records(RecordIn r) {
     rec[1] = make_float4(nd.x, nd.y, nd.z, __int_as_float(i));
     rec[2] = make_float4(tu.x / su, tu.y / su, tu.z / su, r2cut);
     rec[3] = make_float4(tv.x / sv, tv.y / sv, tv.z / sv, 0.f);
+    r.normals[i] = make_float4(nd.x, nd.y, nd.z, 0.f);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         r.leaf_box[6 * (size_t)j + k] = lo[k];
@@ -598,7 +600,7 @@ static void launch_prep(const TriIn& in, float* centre, unsigned int* bounds_u, 
     k_tri_prep<<<g, kThreads, 0, st>>>(in, centre, bounds_u);
 }
 static void launch_records(const SurfelIn& in, grt_bvh* b, int g, cudaStream_t st) {
-    RecordIn r{in, b->sorted_ids, b->records, b->leaf_box};
+    RecordIn r{in, b->sorted_ids, b->records, b->normals, b->leaf_box};
     k_records<<<g, kThreads, 0, st>>>(r);
 }
 static void launch_records(const TriIn& in, grt_bvh* b, int g, cudaStream_t st) {
@@ -778,7 +780,7 @@ static grt_bvh* alloc_bvh(int nleaf, cudaStream_t st, int* rc_out) {
     b->n_int = nleaf > 1 ? nleaf - 1 : 0;
     cudaGetDevice(&b->device);
     size_t n = (size_t)nleaf, ni = (size_t)b->n_int;
-    size_t bytes = sizeof(float4) * 4 * (ni + n) + sizeof(int) * (n + ni + 1) + sizeof(int) * (ni + 1) +
+    size_t bytes = sizeof(float4) * 4 * (ni + n) + sizeof(float4) * n + sizeof(int) * (n + ni + 1) + sizeof(int) * (ni + 1) +
                    sizeof(float) * 6 * n + sizeof(int) * n + 64 + 64 +
                    sizeof(float) * 6 * ni + sizeof(float4) * 8 * ni + sizeof(int) * ni +
                    sizeof(int) * 4 + 256 * 4;
@@ -793,6 +795,7 @@ static grt_bvh* alloc_bvh(int nleaf, cudaStream_t st, int* rc_out) {
     b->base = base;
     b->nodes = (float4*)p; p += sizeof(float4) * 4 * ni;
     b->records = (float4*)p; p += sizeof(float4) * 4 * n;
+    b->normals = (float4*)p; p += sizeof(float4) * n;
     b->leaf_box = (float*)p; p += sizeof(float) * 6 * n;
     b->parent = (int*)p; p += sizeof(int) * (n + ni + 1);
     b->refit_flags = (int*)p; p += sizeof(int) * (ni + 1);

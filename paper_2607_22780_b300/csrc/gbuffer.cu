@@ -35,17 +35,18 @@ __device__ __forceinline__ void camera_ray_d(const Camera& c, int W, int H, int 
 }
 
 struct GbufVisitor {
-    const float *quat, *albedo, *rough, *metal;
+    const float4* nrm;  // the tree's decision normals (R(q/|q|) third column, by surfel id)
+    const float *albedo, *rough, *metal;
     f3 d;
     float D, wsum, nx, ny, nz, ar, ag, ab, ro, me, T;
     __device__ __forceinline__ GbufVisitor() {}
-    __device__ __forceinline__ GbufVisitor(const grt_surfels& s, f3 dir)
-        : quat(s.quat), albedo(s.albedo), rough(s.rough), metal(s.metal), d(dir), D(0), wsum(0), nx(0), ny(0), nz(0),
+    __device__ __forceinline__ GbufVisitor(const grt_surfels& s, const float4* normals, f3 dir)
+        : nrm(normals), albedo(s.albedo), rough(s.rough), metal(s.metal), d(dir), D(0), wsum(0), nx(0), ny(0), nz(0),
           ar(0), ag(0), ab(0), ro(0), me(0), T(1) {}
     __device__ __forceinline__ void composite(int, int id, float tau, float alpha, float Tb) {
         float w = Tb * alpha;
-        const float* q = quat + 4 * (size_t)id;
-        f3 n = normal_from_quat_d(__ldg(q), __ldg(q + 1), __ldg(q + 2), __ldg(q + 3));
+        const float4 nv = __ldg(nrm + id);
+        const f3 n = mk3(nv.x, nv.y, nv.z);
         float sgn = dot_d(n, d) > 0.f ? -1.f : 1.f;  // face the camera
         D = fmaf(w, tau, D);
         nx = fmaf(w * sgn, n.x, nx);
@@ -80,7 +81,7 @@ struct GbufTask {
         f3 o, d;
         camera_ray_d(*cam, W, H, (int)(r % W), (int)(r / W), &o, &d);
         trace_begin(*bvh, ts, o, d, *P);
-        v = GbufVisitor(*s, d);
+        v = GbufVisitor(*s, bvh->normals, d);
         b = bvh;
         return true;
     }
@@ -111,7 +112,7 @@ struct GbufTask {
 };
 
 template <int K>
-__global__ void __launch_bounds__(128, K >= 32 ? 3 : 4) k_gbuffer(DevBvh bvh, TraceParams P, grt_surfels s, Camera cam,
+__global__ void __launch_bounds__(128, K >= 32 ? 3 : GRT_TRACE_MIN_BLOCKS) k_gbuffer(DevBvh bvh, TraceParams P, grt_surfels s, Camera cam,
                                                                   int W, int H, GbufOut out,
                                                                   unsigned long long* next) {
     __shared__ int q[kQueue * 128];

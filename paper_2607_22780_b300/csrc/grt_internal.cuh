@@ -274,6 +274,7 @@ constexpr int kRefEmpty = (int)0x80000000;
 struct DevBvh {
     const float4* nodes;    // wide nodes [cap * 8]
     const float4* records;  // [n * 4]
+    const float4* normals;  // [n] decision normal of each surfel by id (xyz, 0), from the build
     int root;               // wide node 0, a leaf ref when n == 1, kRefEmpty when n == 0
     int n;
     int cap;                // wide node capacity (n - 1)
@@ -289,6 +290,7 @@ struct grt_bvh {
     int n_int;
     float4* nodes;
     float4* records;
+    float4* normals;   // [n] decision normal of surfel i at i (surfel trees only)
     int* parent;       // [n + n_int]: (parent node << 1) | slot, root has -1
     int* refit_flags;  // [n_int]
     float* leaf_box;   // [n * 6] in sorted order

@@ -171,7 +171,7 @@ struct RayAttrTask {
 };
 
 template <int K>
-__global__ void __launch_bounds__(128, K >= 32 ? 3 : 4) k_trace_attr(DevBvh bvh, TraceParams P, AttrSrc src,
+__global__ void __launch_bounds__(128, K >= 32 ? 3 : GRT_TRACE_MIN_BLOCKS) k_trace_attr(DevBvh bvh, TraceParams P, AttrSrc src,
                                                                      const float* __restrict__ ro,
                                                                      const float* __restrict__ rd, long long R,
                                                                      AttrOut out, unsigned long long* next) {
@@ -231,7 +231,7 @@ extern "C" int grt_trace_attr(const grt_bvh* b, const grt_surfels* s, const grt_
     GRT_CUDA(cudaMemsetAsync(next, 0, sizeof(unsigned long long), st));
     DevBvh bvh = dev_bvh(b);
     TraceParams P = to_params(*p);
-    AttrSrc src{s->quat, s->albedo, s->rough, s->metal};
+    AttrSrc src{b->normals, s->albedo, s->rough, s->metal};
     AttrOut out{out_vis, out_albedo, out_rough, out_metal, out_normal};
     const long long gmax = (R + 127) / 128;
     dispatch_k(p->k, [&](auto kc) {

@@ -139,7 +139,8 @@ __device__ __forceinline__ void splitsum_d(const RelightDev& E, const EnvDev& en
 
 // Surfel material arrays read by the attribute visitor.
 struct AttrSrc {
-    const float *quat, *albedo, *rough, *metal;
+    const float4* nrm;  // the tree's decision normals (R(q/|q|) third column, by surfel id)
+    const float *albedo, *rough, *metal;
 };
 
 // Trace_attr visitor: blends the material state of the composited hits.
@@ -154,8 +155,8 @@ struct AttrVisitor {
     }
     __device__ __noinline__ void composite(int, int id, float, float alpha, float Tb) {
         const float w = Tb * alpha;
-        const float* q = src->quat + 4 * (size_t)id;
-        const f3 nn = normal_from_quat_d(__ldg(q), __ldg(q + 1), __ldg(q + 2), __ldg(q + 3));
+        const float4 nv = __ldg(src->nrm + id);
+        const f3 nn = mk3(nv.x, nv.y, nv.z);
         const float sw = dot_d(nn, d) > 0.f ? -w : w;  // turned towards the ray origin
         n[0] = fmaf(sw, nn.x, n[0]);
         n[1] = fmaf(sw, nn.y, n[1]);

@@ -209,7 +209,7 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
     float4 *dirs, *res;
     unsigned long long* next_ray;
     // every walk but the counting pass takes its rays in bucket order (32-bit slot indices)
-    const bool ord = GRT_RAY_ORDER && !COUNT && rays <= 0xFFFFFFFFLL;
+    const bool ord = !COUNT && use_ray_order(rays);
     const size_t extra = ord ? order_scratch_bytes(rays) : 0;
     const size_t need = save ? extra : shade_ws_bytes(rays, ord);
     char* mem = nullptr;    // from the pool, freed at the end of the call
@@ -315,7 +315,7 @@ extern "C" size_t grt_shade_workspace_size(int64_t n_rays) {
         set_error(GRT_ERR_ARG, "n_rays < 0");
         return 0;
     }
-    return shade_ws_bytes(n_rays, GRT_RAY_ORDER && n_rays <= 0xFFFFFFFFLL);
+    return shade_ws_bytes(n_rays, use_ray_order(n_rays));
 }
 
 extern "C" int grt_shade_count(const grt_bvh* b, const grt_surfels* s, const grt_trace_params* p, const grt_gbuffer* g,
@@ -416,7 +416,7 @@ extern "C" int grt_shade_backward_material(const grt_bvh* b, const grt_surfels* 
     cudaStream_t st = (cudaStream_t)stream;
     keep_pool_memory();
     float4* buf = nullptr;
-    const bool ord = GRT_RAY_ORDER && rays <= 0xFFFFFFFFLL;
+    const bool ord = use_ray_order(rays);
     const size_t extra = ord ? order_scratch_bytes(rays) : 0;
     GRT_CUDA(cudaMallocAsync((void**)&buf, sizeof(float4) * (2 * (size_t)rays + 1) + extra, st));
     float4* dirs = buf;

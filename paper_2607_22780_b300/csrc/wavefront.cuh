@@ -88,6 +88,11 @@ __device__ __forceinline__ int pixel_of(const ShadeJob& J, int li) {
 #define GRT_ORDER_DIR_BITS 3
 #endif
 constexpr int kTileBits = GRT_ORDER_TILE_BITS, kDirBits = GRT_ORDER_DIR_BITS;
+// Launches with fewer ray slots keep the slot order: their walk is bound by the latency of
+// their longest ray, and sorting them cost more than it saved (the 64x64 frame of 7,400
+// rays: bucket scan 54 us against a 265 us walk).
+constexpr long long kOrderMinRays = 1ll << 16;
+inline bool use_ray_order(long long rays) { return GRT_RAY_ORDER && rays >= kOrderMinRays && rays <= 0xFFFFFFFFLL; }
 constexpr unsigned kRayBuckets = 1u << (2 * (kTileBits + kDirBits));
 // slots without a ray go last, spread over kEmptyBuckets buckets by slot group so that
 // their counting does not serialise on one address
@@ -249,9 +254,6 @@ __global__ void __launch_bounds__(kShadeThreads) k_trace_rays(const __grid_const
     }
 }
 
-#ifndef GRT_TRACE_MIN_BLOCKS
-#define GRT_TRACE_MIN_BLOCKS 5  // 128 threads x 5 blocks: at most 96 registers per thread
-#endif
 
 __global__ void k_zero_outputs(float* c, float* v, float* i, int n) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -281,7 +283,7 @@ inline int make_job(const grt_bvh* b, const grt_surfels* s, const grt_gbuffer* g
     J->quat = s->quat;
     J->scale = s->scale;
     J->opacity = s->opacity;
-    J->attr = AttrSrc{s->quat, s->albedo, s->rough, s->metal};
+    J->attr = AttrSrc{b->normals, s->albedo, s->rough, s->metal};
     J->cdim = s->color_dim;
     J->gb = GbufDev{g->pos, g->normal, g->albedo, g->rough, g->metal, g->valid, g->eye[0], g->eye[1], g->eye[2], g->W, g->H};
     EnvLayout l = env_layout(e->W, e->H);
@@ -381,7 +383,14 @@ __global__ void __launch_bounds__(kShadeThreads, K >= 32 ? 3 : GRT_TRACE_MIN_BLO
 
 // Forward record kept for the backward pass (grt_shade_pixels_save): per ray the number
 // of composited hits and, slot-major ([slot][ray], coalesced across a warp), the surfel id,
-// tau and alpha of its first L hits in compositing order.
+// tau and alpha of its first L hits in compositing order.  Rays with more than L hits
+// continue in an overflow area: the first ov_cap of them (in the order they reach hit L)
+// each take an overflow slot holding hits L .. L + kOverflowHits - 1 ([k - L][slot]), the
+// ray of slot s in ov_ray[s], the slots handed out counted in *ov_count (zeroed before the
+// forward).  A ray that found no slot free has kNoSlot set in its hit count.
+constexpr int kOverflowHits = 192;
+constexpr int kNoSlot = 1 << 30;
+
 struct SavedHits {
     int* nh;
     int* ids;
@@ -389,12 +398,27 @@ struct SavedHits {
     float* alpha;
     long long R;
     int L;
+    int* ov_ray;
+    int* ov_ids;
+    float* ov_tau;
+    float* ov_alpha;
+    unsigned* ov_count;
+    int ov_cap;
 };
 
+// Overflow slots of a record over R rays: one ray in 256, at least 64 (0 without a record).
+inline int overflow_slots(long long R, int L) {
+    if (L <= 0) return 0;
+    long long c = R / 256;
+    return (int)(c < 64 ? 64 : (c > (1ll << 24) ? (1ll << 24) : c));
+}
+
 // Layout of the caller's saved-forward buffer: ray directions and traced (c_rt, T) as in
-// the shading pass, the persistent kernel's ray counter, then the hit record.
+// the shading pass, the persistent kernel's ray counter, then the hit record and its
+// overflow area.
 struct SavedLayout {
-    size_t dirs, res, next, nh, ids, tau, alpha, total;
+    size_t dirs, res, next, nh, ids, tau, alpha, ov_count, ov_ray, ov_ids, ov_tau, ov_alpha, total;
+    int ov_cap;
 };
 
 inline SavedLayout saved_layout(long long R, int L) {
@@ -415,8 +439,29 @@ inline SavedLayout saved_layout(long long R, int L) {
     off = up(off + 4 * (size_t)L * R);
     o.alpha = off;
     off = up(off + 4 * (size_t)L * R);
+    o.ov_cap = overflow_slots(R, L);
+    const size_t oh = (size_t)kOverflowHits * o.ov_cap;
+    o.ov_count = off;
+    off = up(off + 8);
+    o.ov_ray = off;
+    off = up(off + 4 * (size_t)o.ov_cap);
+    o.ov_ids = off;
+    off = up(off + 4 * oh);
+    o.ov_tau = off;
+    off = up(off + 4 * oh);
+    o.ov_alpha = off;
+    off = up(off + 4 * oh);
     o.total = off;
     return o;
+}
+
+inline SavedHits saved_hits(char* base, const SavedLayout& L, long long R, int max_hits) {
+    return SavedHits{reinterpret_cast<int*>(base + L.nh),        reinterpret_cast<int*>(base + L.ids),
+                     reinterpret_cast<float*>(base + L.tau),     reinterpret_cast<float*>(base + L.alpha),
+                     R,                                          max_hits,
+                     reinterpret_cast<int*>(base + L.ov_ray),    reinterpret_cast<int*>(base + L.ov_ids),
+                     reinterpret_cast<float*>(base + L.ov_tau),  reinterpret_cast<float*>(base + L.ov_alpha),
+                     reinterpret_cast<unsigned*>(base + L.ov_count), L.ov_cap};
 }
 
 // Caller-owned buffers of grt_shade_pixels_save / grt_shade_backward_saved.
@@ -441,25 +486,42 @@ inline int saved_buffers(const void* saved, size_t saved_bytes, int32_t n_pixels
     out->dirs = reinterpret_cast<float4*>(base + L.dirs);
     out->res = reinterpret_cast<float4*>(base + L.res);
     out->next = reinterpret_cast<unsigned long long*>(base + L.next);
-    out->hits = SavedHits{reinterpret_cast<int*>(base + L.nh), reinterpret_cast<int*>(base + L.ids),
-                          reinterpret_cast<float*>(base + L.tau), reinterpret_cast<float*>(base + L.alpha), R, max_hits};
+    out->hits = saved_hits(base, L, R, max_hits);
     return GRT_OK;
 }
 
-// Radiance visitor that also writes the first L composited hits of its ray.
+// Radiance visitor that also writes the composited hits of its ray into the record: the
+// first L in place, the next kOverflowHits in an overflow slot taken at hit L.
 struct SavingVisitor : RadianceVisitor {
     const SavedHits* sv;
     long long r;
+    int slot;  // overflow slot, -1 until hit L (and when none was left)
     __device__ __forceinline__ SavingVisitor() {}
     __device__ __forceinline__ SavingVisitor(const float* col, int cd, f3 dir, const SavedHits* s, long long ray)
-        : RadianceVisitor(col, cd, dir), sv(s), r(ray) {}
+        : RadianceVisitor(col, cd, dir), sv(s), r(ray), slot(-1) {}
     __device__ __forceinline__ void composite(int k, int id, float tau, float alpha, float Tb) {
         RadianceVisitor::composite(k, id, tau, alpha, Tb);
+        record(k, id, tau, alpha);
+    }
+    __device__ __forceinline__ void record(int k, int id, float tau, float alpha) {
         if (k < sv->L) {
             const size_t i = (size_t)k * sv->R + r;
             sv->ids[i] = id;
             sv->tau[i] = tau;
             sv->alpha[i] = alpha;
+            return;
+        }
+        if (sv->L == 0) return;
+        if (k == sv->L) {
+            const unsigned s = atomicAdd(sv->ov_count, 1u);
+            slot = s < (unsigned)sv->ov_cap ? (int)s : -1;
+            if (slot >= 0) sv->ov_ray[slot] = (int)r;
+        }
+        if (slot >= 0 && k - sv->L < kOverflowHits) {
+            const size_t i = (size_t)(k - sv->L) * sv->ov_cap + slot;
+            sv->ov_ids[i] = id;
+            sv->ov_tau[i] = tau;
+            sv->ov_alpha[i] = alpha;
         }
     }
 };
@@ -491,7 +553,7 @@ struct ShadeTraceSave {
     }
     __device__ __forceinline__ void end(long long r, const WalkState<K>& ts, Visitor& cv) {
         res[r] = make_float4(cv.c[0], cv.c[1], cv.c[2], ts.T);
-        sv->nh[r] = ts.ncomp;
+        sv->nh[r] = ts.ncomp | (ts.ncomp > sv->L && cv.slot < 0 ? kNoSlot : 0);
     }
 };
 
@@ -616,6 +678,7 @@ inline void launch_trace_save(const JobTable<CAP>& T, const float4* dirs, float4
                               unsigned long long* next_ray, long long blocks_max, cudaStream_t st,
                               const unsigned* order = nullptr) {
     cudaMemsetAsync(next_ray, 0, sizeof(unsigned long long), st);
+    if (sv.ov_count) cudaMemsetAsync(sv.ov_count, 0, sizeof(unsigned), st);
     constexpr size_t smem = walk_smem_bytes<K>();
     const long long grid = persistent_grid(k_trace_rays_save<K, CAP>, smem, blocks_max);
     k_trace_rays_save<K, CAP><<<(unsigned)grid, kShadeThreads, smem, st>>>(T, dirs, res, sv, next_ray, order);

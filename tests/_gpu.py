@@ -63,15 +63,34 @@ def gbuffer_to_arrays(g, eye, W, H):
                 eye=np.asarray(eye, np.float32), W=W, H=H)
 
 
+# G-buffer tolerances (FP32 kernel against the FP64 oracle).  The error comes from the FP32
+# hit point p = o + tau d, rounded at the scale of |p|, against surfel scales down to 1e-3:
+# it perturbs each alpha, hence the normalised weights of Eq. 9, so depth and position errors
+# grow with the depth D (observed at most 3.4e-5 D on 2M-surfel 1080p views at D ~ 20,
+# 7e-6 D on the 300k-surfel and C1 views), the unit normal's error with the spread of the
+# blended normals (observed 1.6e-4), weighted attributes in [0, 1] by at most 8.1e-5.
+GB_TOL_DEPTH_REL = 1e-4   # depth and position: 1e-4 max(1, D)
+GB_TOL_NORMAL = 3e-4
+GB_TOL_ATTR = 1e-4        # albedo, roughness, metallic, opacity
+
+
+def gbuffer_tolerance(k, depth):
+    """Per-pixel tolerance of G-buffer field k (depth: the oracle's depth of the pixels)."""
+    if k in ("pos", "depth"):
+        return GB_TOL_DEPTH_REL * np.maximum(1.0, np.abs(depth))
+    return GB_TOL_NORMAL if k == "normal" else GB_TOL_ATTR
+
+
 def check_gbuffer_rows(got, ref, pix, min_valid):
     """GPU G-buffer rows at pixels `pix` against the oracle's rows for the same pixels."""
     m = unflagged(ref["flags"])
     assert np.array_equal(got["valid"][pix][m], ref["valid"][m])
     v = m & (ref["valid"] == 1)
     assert v.sum() >= min_valid, v.sum()
-    for k, tol in (("pos", 5e-4), ("normal", 5e-4), ("albedo", 1e-4), ("rough", 1e-4), ("metal", 1e-4)):
-        err = np.abs(got[k][pix][v] - ref[k][v])
-        assert err.max() < tol, (k, err.max())
+    for k in ("pos", "normal", "albedo", "rough", "metal"):
+        err = np.abs(got[k][pix][v] - ref[k][v]).reshape(int(v.sum()), -1).max(1)
+        tol = gbuffer_tolerance(k, ref["depth"][v])
+        assert np.all(err < tol), (k, float(err.max()), float((err / tol).max()))
 
 
 GRAD_FIELDS = ("mu", "quat", "scale", "opacity", "color")

@@ -43,8 +43,10 @@ def test_saved_record_size_and_checks_without_gpu():
     smp = _lib.Sampling(8, 4, 4, 1, 7)
     R = 1000 * 16
     nb = lib.grt_shade_saved_bytes(1000, ctypes.byref(smp), 16)
-    # directions and (c_rt, T) 32 B, hit count 4 B, (id, tau, alpha) 12 B per slot, per ray
-    assert R * (36 + 12 * 16) <= nb <= R * (36 + 12 * 16) + 7 * 256
+    # directions and (c_rt, T) 32 B, hit count 4 B, (id, tau, alpha) 12 B per slot, per ray;
+    # an overflow area of max(64, R / 256) slots of 4 + 12 x 192 B
+    ov = max(64, R // 256) * (4 + 12 * 192)
+    assert R * (36 + 12 * 16) + ov <= nb <= R * (36 + 12 * 16) + ov + 12 * 256
     assert lib.grt_shade_saved_bytes(1000, ctypes.byref(smp), 0) < nb
     assert lib.grt_shade_saved_bytes(1000, ctypes.byref(smp), _lib.GRT_MAX_SAVED_HITS + 1) == 0
     assert b"max_hits" in lib.grt_last_error()
@@ -77,8 +79,10 @@ def test_workspace_sizes_and_checks_without_gpu():
     saved = lib.grt_shade_backward_workspace_size(640_000, ctypes.byref(smp), 1)
     assert saved >= R * 24
     recomp = lib.grt_shade_backward_workspace_size(640_000, ctypes.byref(smp), 0)
-    # two chunk buffers of at most 8M rays, each with a 64-hit transient record
-    assert (8 << 20) * (36 + 12 * 64) < recomp < 2 * (8 << 20) * (36 + 12 * 64 + 40) + 2 * 300_000
+    # two chunk buffers of at most 8M rays, each with a 64-hit transient record and its
+    # overflow area (one slot of 4 + 12 x 192 bytes per 256 rays)
+    chunk = (8 << 20) * (36 + 12 * 64 + 40) + ((8 << 20) // 256) * (4 + 12 * 192)
+    assert (8 << 20) * (36 + 12 * 64) < recomp < 2 * chunk + 2 * 300_000
     assert lib.grt_shade_backward_workspace_size(-1, ctypes.byref(smp), 0) == 0
     s = _lib.Surfels(0, 3)
     p = _lib.TraceParams(1 / 255, 0.99, 0.01, 3e38, 1e-4, 1e-6, 16)
