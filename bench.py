@@ -448,21 +448,13 @@ def run_grt(args):
 
 
 def serve_summary(args):
-    """Relight serving on the three resident scenes (300k, 1M, 2M surfels): a Poisson trace
-    at 80% of the one-at-a-time capacity, served with continuous batching and one request
-    at a time; p50/p99 latency and rays/s of both."""
+    """Relight serving on the three resident scenes (300k, 1M, 2M surfels): a Poisson trace at
+    200 requests/s and one at 80% of the batched arm's capacity, each served with continuous
+    batching and one request at a time; p50/p99 latency and rays/s.  The default line runs a
+    shortened trace (30 warm-up + 100 measured requests each); --mode serve runs the full one
+    (100 + 2,000)."""
     from paper_2607_22780_b300 import serve
-    scenes = serve.default_scenes()
-    dist = serve.scene_distances(scenes)
-    srv = serve.RelightServer(scenes)
-    cap = srv.run_serial(serve.make_trace(8, 0.0, dist, seed=1), realtime=False)
-    rate = 0.8 * cap["requests"] / cap["span_s"]
-    trace = serve.make_trace(args.serve_requests, rate, dist, seed=7)
-    b = srv.run_batched(trace)
-    o = srv.run_serial(trace)
-    keep = ("requests", "launches", "rays", "rays_per_s", "p50_ms", "p99_ms", "mean_ms")
-    return {"workload": "relight_3scenes_300k_1M_2M_poisson", "rate_per_s": rate,
-            "batched": {k: b[k] for k in keep}, "one_at_a_time": {k: o[k] for k in keep}}
+    return serve.serve_benchmark(n_warm=30, n_meas=100, n_warm80=10, n_meas80=60)
 
 
 def run_train_only(args):
@@ -880,7 +872,7 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-surfel 1080p forward/backward line")
     ap.add_argument("--k", type=int, default=16, help="k-buffer size (results do not depend on it)")
-    ap.add_argument("--serve-requests", type=int, default=40, help="requests of the 80%%-load serving trace")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="measured requests of --mode serve")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--image", type=int, default=0,
                     help="square image size override (small profiling case); default 800")

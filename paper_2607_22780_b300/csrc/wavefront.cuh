@@ -107,12 +107,15 @@ __device__ __forceinline__ unsigned spread2(unsigned x) {
     return x;
 }
 
-__device__ __forceinline__ unsigned ray_bucket(const GbufDev& g, int pix, float4 dw, long long r) {
+// Bucket of a ray: 2^tb x 2^tb screen tiles (Morton order) x 2^db x 2^db octahedral
+// direction cells, offset by `base`.
+__device__ __forceinline__ unsigned ray_bucket(const GbufDev& g, int pix, float4 dw, long long r, int tb, int db,
+                                               unsigned base) {
     if (dw.w == 0.f) return kRayBuckets + (unsigned)((r >> 5) & (kEmptyBuckets - 1));
     const int px = pix % g.W, py = pix / g.W;
     const int m = (g.W > g.H ? g.W : g.H) - 1;
     int sh = 0;
-    while ((m >> sh) >= (1 << kTileBits)) ++sh;
+    while ((m >> sh) >= (1 << tb)) ++sh;
     const unsigned tile = spread2((unsigned)(px >> sh)) | (spread2((unsigned)(py >> sh)) << 1);
     const float l1 = fabsf(dw.x) + fabsf(dw.y) + fabsf(dw.z);
     float u = dw.x / l1, v = dw.y / l1;
@@ -121,11 +124,21 @@ __device__ __forceinline__ unsigned ray_bucket(const GbufDev& g, int pix, float4
         v = (1.f - fabsf(u)) * (v >= 0.f ? 1.f : -1.f);
         u = uu;
     }
-    constexpr int nd = 1 << kDirBits;
+    const int nd = 1 << db;
     const int cu = min(nd - 1, max(0, (int)((u + 1.f) * (0.5f * nd))));
     const int cv = min(nd - 1, max(0, (int)((v + 1.f) * (0.5f * nd))));
-    return (tile << (2 * kDirBits)) | (unsigned)(cv * nd + cu);
+    return base | (tile << (2 * db)) | (unsigned)(cv * nd + cu);
 }
+
+// In a launch of several requests (scenes, cameras) the buckets are request-major, each
+// request getting kJobBuckets of them (8 x 8 tiles x 4 x 4 direction cells), so that a warp's
+// rays come from one request and walk one tree; a single request uses all kRayBuckets.
+#ifndef GRT_BATCH_JOB_MAJOR
+#define GRT_BATCH_JOB_MAJOR 1
+#endif
+constexpr int kJobTileBits = 3, kJobDirBits = 2;
+constexpr unsigned kJobBuckets = 1u << (2 * (kJobTileBits + kJobDirBits));
+static_assert(kJobBuckets * 64 <= kRayBuckets, "request-major buckets of up to 64 requests");
 
 // Buffers of the ray order over n slots (order_scratch_bytes(n) bytes from `base`):
 // hist[kAllBuckets] bucket counts, then exclusive offsets; per slot its bucket, its rank in
@@ -152,7 +165,8 @@ __global__ void __launch_bounds__(kShadeThreads) k_sample_rays(const __grid_cons
                                                                                      nullptr}) {
     long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= T.total_rays) return;
-    const ShadeJob& J = T.job[T.find_ray(r)];
+    const int job = T.find_ray(r);
+    const ShadeJob& J = T.job[job];
     long long lr = r - J.ray_begin;
     int li = (int)(lr / J.Nr), j = (int)(lr - (long long)li * J.Nr);
     int pix = pixel_of(J, li);
@@ -164,7 +178,9 @@ __global__ void __launch_bounds__(kShadeThreads) k_sample_rays(const __grid_cons
     }
     dirs[r] = out;
     if (o.key) {
-        const unsigned key = ray_bucket(J.gb, pix, out, r);
+        const unsigned key = (GRT_BATCH_JOB_MAJOR && T.n_jobs > 1)
+                                 ? ray_bucket(J.gb, pix, out, r, kJobTileBits, kJobDirBits, (unsigned)job * kJobBuckets)
+                                 : ray_bucket(J.gb, pix, out, r, kTileBits, kDirBits, 0u);
         // one atomic per distinct key in the warp; its old value ranks the warp's slots
         const unsigned peers = __match_any_sync(__activemask(), key);
         const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
