@@ -411,8 +411,8 @@ def run_grt(args):
     if rank == 0 and world == 1 and not args.no_large:
         large = time_large(api, dev, args)
     den = time_denoise(api, G, outs[0], args) if rank == 0 else None
-    c1 = time_c1(api, dev, args) if rank == 0 else None
-    rel = time_relight(api, S, G, E, R, args) if rank == 0 else None
+    c1 = time_c1(api, dev, args) if rank == 0 and not args.no_c1 else None
+    rel = time_relight(api, S, G, E, R, args) if rank == 0 and not args.no_relight else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -871,6 +871,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-surfel 1080p forward/backward line")
+    ap.add_argument("--no-relight", action="store_true", help="skip the relighting lines")
+    ap.add_argument("--no-c1", action="store_true", help="skip the plain-forward 64x64 line")
     ap.add_argument("--k", type=int, default=16, help="k-buffer size (results do not depend on it)")
     ap.add_argument("--serve-requests", type=int, default=2000, help="measured requests of --mode serve")
     ap.add_argument("--no-serve", action="store_true")

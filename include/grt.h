@@ -113,7 +113,7 @@ int grt_rebuild_bvh(grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_pa
  * pool allocation inside a call as a failure risk at an arbitrary moment and as memory
  * it cannot account for.  This call does what grt_rebuild_bvh does -- Morton codes,
  * sort, hierarchy, refit, into the existing BVH that the caller already owns -- without
- * allocating: its sort scratch is a fixed array compiled into the library (about 17 MB
+ * allocating: its sort scratch is a fixed array compiled into the library (about 15 MB
  * for GRT_NOALLOC_MAX_SURFELS surfels), which every device that loads libgrt keeps until
  * the process exits.
  *   - n > GRT_NOALLOC_MAX_SURFELS is rejected with GRT_ERR_ARG before any device work.

@@ -139,6 +139,8 @@ struct AdjointVisitor {
                       make_float4((gw - qw * qd) * iql, (gx - qx * qd) * iql, (gy - qy * qd) * iql, (gz - qz * qd) * iql));
         }
     }
+    template <class KB>
+    __device__ __forceinline__ void prefetch(const KB&) const {}
     __device__ __forceinline__ void finish(float) {}
 };
 
@@ -312,6 +314,9 @@ struct AdjointTask {
 // longest lists start first and do not trail the launch; the other threads take every
 // ray with at most L hits.  Rays longer than the record and its overflow slot, and rays
 // that found no slot free, are listed for the traced adjoint walk.
+#ifndef GRT_REPLAY_ORDER
+#define GRT_REPLAY_ORDER 1
+#endif
 __device__ __forceinline__ void replay_hit(const SavedHits& sv, long long r, int slot, int k, int* id, float* tau,
                                            float* alpha) {
     if (k < sv.L) {
@@ -349,6 +354,7 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_replay(const __grid_c
     } else {
         r = t - sv.ov_cap;
         if (r >= T.total_rays) return;
+        if (GRT_REPLAY_ORDER && sv.order) r = __ldg(sv.order + r);  // the forward's coherent ray order
     }
     const int raw = __ldg(sv.nh + r);
     const int n = raw & (kNoSlot - 1);
@@ -646,14 +652,15 @@ static int shade_backward_impl(const grt_bvh* b, const grt_surfels* s, const grt
             else
                 Jc.pixel_offset += (int)p0;
             Tc.total_rays = (long long)Jc.n_pixels * Jc.Nr;
-            const SavedHits hits = saved_hits(cb, lay, Tc.total_rays, kRecomputeHits);
+            SavedHits hits = saved_hits(cb, lay, Tc.total_rays, kRecomputeHits);
             const AdjIn in{dL_dcolor + 3 * p0, dL_dvis ? dL_dvis + p0 : nullptr, dL_dind ? dL_dind + 3 * p0 : nullptr};
             const long long gr = (Tc.total_rays + kShadeThreads - 1) / kShadeThreads;
             // the chunk's rays go to the walk in bucket order, as in the forward
             RayOrder ro{nullptr, nullptr, nullptr, nullptr};
             const bool ord = use_ray_order(Tc.total_rays);
+            if (!ord) hits.order = nullptr;  // a short last chunk is walked in slot order
             if (ord) {
-                ro = ray_order_bufs(cb + ord_off, Tc.total_rays);
+                ro = ray_order_bufs(cb + ord_off, Tc.total_rays, hits.order);
                 cudaMemsetAsync(ro.hist, 0, 4 * (size_t)kAllBuckets, cs);
             }
             k_sample_rays<1><<<(unsigned)gr, kShadeThreads, 0, cs>>>(Tc, dirs, ro);

@@ -82,52 +82,42 @@ __device__ __forceinline__ void surfel_box(const SurfelIn& s, int i, float lo[3]
 }
 
 __device__ __forceinline__ void reduce_bounds(const float cl[3], const float ch[3], const float lo[3],
-                                              const float hi[3], float ext, unsigned int* __restrict__ bounds_u);
+                                              const float hi[3], unsigned int* __restrict__ bounds_u);
 
-// Largest side of a box (0 for an empty one).
-__device__ __forceinline__ float box_extent(const float lo[3], const float hi[3]) {
-    return fmaxf(0.f, fmaxf(hi[0] - lo[0], fmaxf(hi[1] - lo[1], hi[2] - lo[2])));
-}
-
-// Per primitive: centre of its box and the box's largest side (4 floats), and the scene
-// bounds of the centres, of the boxes and of the sides.
-__global__ void k_prep_bounds(SurfelIn s, float4* __restrict__ centre, unsigned int* __restrict__ bounds_u) {
+__global__ void k_prep_bounds(SurfelIn s, float* __restrict__ centre, unsigned int* __restrict__ bounds_u) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
     float cl[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, ch[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    float e = 0.f;
     if (i < s.n) {
         f3 tu, tv;
         float r2;
         surfel_box(s, i, lo, hi, &tu, &tv, &r2);
-        float c[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            c[k] = 0.5f * (lo[k] + hi[k]);
-            cl[k] = c[k];
-            ch[k] = c[k];
+            float c = 0.5f * (lo[k] + hi[k]);
+            centre[3 * i + k] = c;
+            cl[k] = c;
+            ch[k] = c;
         }
-        e = box_extent(lo, hi);
-        centre[i] = make_float4(c[0], c[1], c[2], e);
     }
-    reduce_bounds(cl, ch, lo, hi, e, bounds_u);
+    reduce_bounds(cl, ch, lo, hi, bounds_u);
 }
 
 // Warp then block reduction of centre bounds and box bounds into bounds_u (ordered ints:
-// [0..2] min centre, [3..5] -max centre, [6..8] min box, [9..11] -max box, [12] -max side).
+// [0..2] min centre, [3..5] -max centre, [6..8] min box, [9..11] -max box).
 __device__ __forceinline__ void reduce_bounds(const float cl[3], const float ch[3], const float lo[3],
-                                              const float hi[3], float ext, unsigned int* __restrict__ bounds_u) {
-    __shared__ float red[13][kThreads / 32];
-    float v[13] = {cl[0], cl[1], cl[2], -ch[0], -ch[1], -ch[2], lo[0], lo[1], lo[2], -hi[0], -hi[1], -hi[2], -ext};
+                                              const float hi[3], unsigned int* __restrict__ bounds_u) {
+    __shared__ float red[12][kThreads / 32];
+    float v[12] = {cl[0], cl[1], cl[2], -ch[0], -ch[1], -ch[2], lo[0], lo[1], lo[2], -hi[0], -hi[1], -hi[2]};
 #pragma unroll
-    for (int k = 0; k < 13; ++k) {
+    for (int k = 0; k < 12; ++k) {
         float x = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
         if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = x;
     }
     __syncthreads();
-    if (threadIdx.x < 13) {
+    if (threadIdx.x < 12) {
         float x = red[threadIdx.x][0];
         for (int w = 1; w < kThreads / 32; ++w) x = fminf(x, red[threadIdx.x][w]);
         atomicMin(bounds_u + threadIdx.x, float_to_ordered(x));
@@ -143,22 +133,7 @@ __device__ __forceinline__ unsigned int expand_bits10(unsigned int v) {
     return v;
 }
 
-// Size-aware code (after Vinkler, Bittner and Havran's extended Morton codes, HPG 2017):
-// kEmcBits bits of the primitive's size class -- floor(log2(largest side in the scene /
-// its side) / kEmcStep), clamped -- are inserted after the first kEmcPos bits of the 30-bit
-// Morton code, so that within a coarse spatial cell large and small primitives fall into
-// separate subtrees.  kEmcPos < 0 keeps the plain Morton code.
-#ifndef GRT_EMC_POS
-#define GRT_EMC_POS -1
-#endif
-#ifndef GRT_EMC_STEP
-#define GRT_EMC_STEP 1.0f
-#endif
-constexpr int kEmcPos = GRT_EMC_POS;
-constexpr int kEmcBits = 2;
-constexpr float kEmcStep = GRT_EMC_STEP;
-
-__global__ void k_morton(const float4* __restrict__ centre, const unsigned int* __restrict__ bounds_u, int n,
+__global__ void k_morton(const float* __restrict__ centre, const unsigned int* __restrict__ bounds_u, int n,
                          MortonKey* __restrict__ keys, int* __restrict__ vals, float* __restrict__ bounds_out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float lo[3], ext[3];
@@ -176,25 +151,14 @@ __global__ void k_morton(const float4* __restrict__ centre, const unsigned int* 
         }
     }
     if (i >= n) return;
-    const float4 c4 = centre[i];
-    const float cc[3] = {c4.x, c4.y, c4.z};
     unsigned int q[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float t = (cc[k] - lo[k]) / ext[k];
+        float t = (centre[3 * i + k] - lo[k]) / ext[k];
         t = fminf(fmaxf(t * 1024.f, 0.f), 1023.f);
         q[k] = (unsigned int)t;
     }
-    unsigned int code = (expand_bits10(q[0]) << 2) | (expand_bits10(q[1]) << 1) | expand_bits10(q[2]);
-    if (kEmcPos >= 0) {
-        const float emax = -ordered_to_float(bounds_u[12]);
-        int cls = (emax > 0.f && c4.w > 0.f) ? (int)floorf(log2f(emax / c4.w) / kEmcStep) : 0;
-        cls = cls < 0 ? 0 : (cls > (1 << kEmcBits) - 1 ? (1 << kEmcBits) - 1 : cls);
-        const unsigned int high = kEmcPos > 0 ? (code >> (30 - kEmcPos)) : 0u;
-        const unsigned int low = code & ((1u << (30 - kEmcPos)) - 1u);
-        code = (high << (32 - kEmcPos)) | ((unsigned int)cls << (30 - kEmcPos)) | low;
-    }
-    keys[i] = code;
+    keys[i] = (expand_bits10(q[0]) << 2) | (expand_bits10(q[1]) << 1) | expand_bits10(q[2]);
     vals[i] = i;
 }
 
@@ -317,25 +281,22 @@ __device__ __forceinline__ void tri_box(const TriIn& t, int i, float lo[3], floa
     hi[2] = fmaxf(v[0].z, fmaxf(v[1].z, v[2].z));
 }
 
-__global__ void k_tri_prep(TriIn t, float4* __restrict__ centre, unsigned int* __restrict__ bounds_u) {
+__global__ void k_tri_prep(TriIn t, float* __restrict__ centre, unsigned int* __restrict__ bounds_u) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
     float cl[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, ch[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    float e = 0.f;
     if (i < t.n) {
         f3 v[3];
         tri_box(t, i, lo, hi, v);
-        float c[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            c[k] = 0.5f * (lo[k] + hi[k]);
-            cl[k] = c[k];
-            ch[k] = c[k];
+            float c = 0.5f * (lo[k] + hi[k]);
+            centre[3 * i + k] = c;
+            cl[k] = c;
+            ch[k] = c;
         }
-        e = box_extent(lo, hi);
-        centre[i] = make_float4(c[0], c[1], c[2], e);
     }
-    reduce_bounds(cl, ch, lo, hi, e, bounds_u);
+    reduce_bounds(cl, ch, lo, hi, bounds_u);
 }
 
 __global__ void k_tri_records(TriIn t, const int* __restrict__ sorted, float4* __restrict__ records,
@@ -632,10 +593,10 @@ __global__ void k_collapse_init(int* counts, int* queue) {
 }  // namespace
 
 // Per-primitive steps of a build: leaf boxes and centres, and the packed records.
-static void launch_prep(const SurfelIn& in, float4* centre, unsigned int* bounds_u, int g, cudaStream_t st) {
+static void launch_prep(const SurfelIn& in, float* centre, unsigned int* bounds_u, int g, cudaStream_t st) {
     k_prep_bounds<<<g, kThreads, 0, st>>>(in, centre, bounds_u);
 }
-static void launch_prep(const TriIn& in, float4* centre, unsigned int* bounds_u, int g, cudaStream_t st) {
+static void launch_prep(const TriIn& in, float* centre, unsigned int* bounds_u, int g, cudaStream_t st) {
     k_tri_prep<<<g, kThreads, 0, st>>>(in, centre, bounds_u);
 }
 static void launch_records(const SurfelIn& in, grt_bvh* b, int g, cudaStream_t st) {
@@ -676,7 +637,7 @@ static int finish_build(grt_bvh* b, const In& in, bool collapse, cudaStream_t st
 // Device scratch of one topology build: centres, bounds, keys x2, ids x2, histograms.
 static constexpr size_t build_scratch_bytes(size_t n) {
     const size_t nblocks = (n + kSortTile - 1) / kSortTile;
-    return sizeof(float4) * n + 256 + 64 + 2 * sizeof(MortonKey) * n + 2 * sizeof(int) * n +
+    return sizeof(float) * 3 * n + 256 + 64 + 2 * sizeof(MortonKey) * n + 2 * sizeof(int) * n +
            sizeof(unsigned int) * 256 * nblocks + 256;
 }
 
@@ -687,7 +648,7 @@ static int build_topology(grt_bvh* b, const In& in, char* scratch, cudaStream_t 
     const int g = (n + kThreads - 1) / kThreads;
     const int nblocks = (n + kSortTile - 1) / kSortTile;
     char* p = scratch;
-    float4* centre = (float4*)p; p += sizeof(float4) * (size_t)n;
+    float* centre = (float*)p; p += sizeof(float) * 3 * (size_t)n;
     p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
     unsigned int* bounds_u = (unsigned int*)p; p += 64;
     MortonKey* keys0 = (MortonKey*)p; p += sizeof(MortonKey) * (size_t)n;
@@ -748,7 +709,7 @@ static int check_surfels(const grt_surfels* s) {
 // libgrt holds these bytes until the process exits.  Layout as in launch_build, sized for
 // GRT_NOALLOC_MAX_SURFELS surfels.
 constexpr size_t kNoallocBlocks = (GRT_NOALLOC_MAX_SURFELS + kSortTile - 1) / kSortTile;
-constexpr size_t kNoallocBytes = 16ull * GRT_NOALLOC_MAX_SURFELS + 256 + 64 +     // centres and sides, bounds
+constexpr size_t kNoallocBytes = 4ull * 3 * GRT_NOALLOC_MAX_SURFELS + 256 + 64 +   // centres, bounds
                                  4ull * 2 * GRT_NOALLOC_MAX_SURFELS +              // keys x2
                                  4ull * 2 * GRT_NOALLOC_MAX_SURFELS +              // ids x2
                                  4ull * 256 * kNoallocBlocks + 256;                // digit histograms

@@ -238,7 +238,8 @@ int run_jobs(JobTable<CAP>& T, int k, long long* counters, cudaStream_t st, cons
     g_timing.mark(0, st);
     RayOrder ro{nullptr, nullptr, nullptr, nullptr};
     if (order_buf) {
-        ro = ray_order_bufs(order_buf, rays);
+        // a saving pass keeps its order in the record, for the replay
+        ro = ray_order_bufs(order_buf, rays, save ? save->hits.order : nullptr);
         cudaMemsetAsync(ro.hist, 0, 4 * (size_t)kAllBuckets, st);
     }
     k_sample_rays<CAP><<<(unsigned)gr, kShadeThreads, 0, st>>>(T, dirs, ro);

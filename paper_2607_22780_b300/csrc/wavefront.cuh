@@ -147,12 +147,12 @@ struct RayOrder {
     unsigned *hist, *key, *rank, *order;
 };
 inline size_t order_scratch_bytes(long long n) { return 4 * (3 * (size_t)n + kAllBuckets); }
-inline RayOrder ray_order_bufs(void* base, long long n) {
+inline RayOrder ray_order_bufs(void* base, long long n, unsigned* order = nullptr) {
     RayOrder o;
     o.hist = static_cast<unsigned*>(base);
     o.key = o.hist + kAllBuckets;
     o.rank = o.key + n;
-    o.order = o.rank + n;
+    o.order = order ? order : o.rank + n;
     return o;
 }
 
@@ -420,6 +420,7 @@ struct SavedHits {
     float* ov_alpha;
     unsigned* ov_count;
     int ov_cap;
+    unsigned* order;  // the forward walk's ray order (the replay takes rays in it), or NULL
 };
 
 // Overflow slots of a record over R rays: one ray in 256, at least 64 (0 without a record).
@@ -433,8 +434,9 @@ inline int overflow_slots(long long R, int L) {
 // the shading pass, the persistent kernel's ray counter, then the hit record and its
 // overflow area.
 struct SavedLayout {
-    size_t dirs, res, next, nh, ids, tau, alpha, ov_count, ov_ray, ov_ids, ov_tau, ov_alpha, total;
+    size_t dirs, res, next, nh, ids, tau, alpha, ov_count, ov_ray, ov_ids, ov_tau, ov_alpha, order, total;
     int ov_cap;
+    bool has_order;
 };
 
 inline SavedLayout saved_layout(long long R, int L) {
@@ -467,6 +469,10 @@ inline SavedLayout saved_layout(long long R, int L) {
     off = up(off + 4 * oh);
     o.ov_alpha = off;
     off = up(off + 4 * oh);
+    // the coherent order in which the forward walked the rays, kept for the replay
+    o.has_order = L > 0 && use_ray_order(R);
+    o.order = off;
+    if (o.has_order) off = up(off + 4 * (size_t)R);
     o.total = off;
     return o;
 }
@@ -477,7 +483,8 @@ inline SavedHits saved_hits(char* base, const SavedLayout& L, long long R, int m
                      R,                                          max_hits,
                      reinterpret_cast<int*>(base + L.ov_ray),    reinterpret_cast<int*>(base + L.ov_ids),
                      reinterpret_cast<float*>(base + L.ov_tau),  reinterpret_cast<float*>(base + L.ov_alpha),
-                     reinterpret_cast<unsigned*>(base + L.ov_count), L.ov_cap};
+                     reinterpret_cast<unsigned*>(base + L.ov_count), L.ov_cap,
+                     L.has_order ? reinterpret_cast<unsigned*>(base + L.order) : nullptr};
 }
 
 // Caller-owned buffers of grt_shade_pixels_save / grt_shade_backward_saved.

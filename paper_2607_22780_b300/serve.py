@@ -38,7 +38,7 @@ class RelightRequest:
     arrival: float          # seconds after the start of the trace
     scene: str
     camera: wl.Camera
-    env: np.ndarray         # [H, W, 3] float32 HDR map
+    env: object             # [H, W, 3] float32 HDR map (numpy array, or a pinned torch tensor)
     res: int
     rays: int               # N_r
     seed: int
@@ -48,9 +48,10 @@ class RelightRequest:
         return (self.rays // 2, self.rays // 4, self.rays - self.rays // 2 - self.rays // 4)
 
 
-def env_pool(n: int, seed: int, env_size=(512, 256)) -> List[np.ndarray]:
-    """n distinct seeded log-normal HDR maps (the C2 recipe) for long request traces."""
-    return [wl.envmap_hdr(seed + i, env_size[0], env_size[1]) for i in range(n)]
+def env_pool(n: int, seed: int, env_size=(512, 256)) -> List[torch.Tensor]:
+    """n distinct seeded log-normal HDR maps (the C2 recipe) for long request traces, in
+    pinned host memory (pinned once, uploaded per request)."""
+    return [torch.from_numpy(wl.envmap_hdr(seed + i, env_size[0], env_size[1])).pin_memory() for i in range(n)]
 
 
 def make_trace(n: int, rate: float, scenes: Dict[str, float], seed: int, res_choices=(256, 512, 1024),
@@ -84,7 +85,10 @@ class _State:
         P = req.res * req.res
         self.P = P
         with torch.cuda.stream(stream):
-            henv = torch.from_numpy(req.env).pin_memory()
+            if torch.is_tensor(req.env) and req.env.is_pinned():
+                henv = req.env  # a pinned map of a pool, shared by several requests
+            else:
+                henv = torch.from_numpy(np.ascontiguousarray(req.env)).pin_memory()
             self.env_rgb = torch.empty(henv.shape, dtype=torch.float32, device=dev)
             self.env_rgb.copy_(henv, non_blocking=True)
             self.env = api.Environment(self.env_rgb, stream=stream)
