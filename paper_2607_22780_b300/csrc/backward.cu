@@ -37,8 +37,15 @@ struct AdjointVisitor {
     float alpha_max;
     GradPtrs g;
 
-    // out of line: round_end unrolls its K slots, and this body is large
+    // one call site in the replay loop and in the walks' in-order compositing loop
+#ifndef GRT_ADJ_INLINE
+#define GRT_ADJ_INLINE 1
+#endif
+#if GRT_ADJ_INLINE
+    __device__ __forceinline__ void composite(int, int id, float tau, float alpha, float Tb) {
+#else
     __device__ __noinline__ void composite(int, int id, float tau, float alpha, float Tb) {
+#endif
         // geometry of the hit, loaded first so that its latency overlaps the colour's
         const float op = __ldg(opacity + id);
         const float4 q = make_float4(__ldg(quat + 4 * (size_t)id), __ldg(quat + 4 * (size_t)id + 1),
@@ -139,8 +146,6 @@ struct AdjointVisitor {
                       make_float4((gw - qw * qd) * iql, (gx - qx * qd) * iql, (gy - qy * qd) * iql, (gz - qz * qd) * iql));
         }
     }
-    template <class KB>
-    __device__ __forceinline__ void prefetch(const KB&) const {}
     __device__ __forceinline__ void finish(float) {}
 };
 

@@ -59,8 +59,6 @@ struct GbufVisitor {
         me = fmaf(w, __ldg(metal + id), me);
         wsum += w;
     }
-    template <class KB>
-    __device__ __forceinline__ void prefetch(const KB&) const {}
     __device__ __forceinline__ void finish(float Tf) { T = Tf; }
 };
 

@@ -167,8 +167,6 @@ struct AttrVisitor {
         m = fmaf(w, __ldg(src->metal + id), m);
         wsum += w;
     }
-    template <class KB>
-    __device__ __forceinline__ void prefetch(const KB&) const {}
     __device__ __forceinline__ void finish(float) {}
     // Normalised state after the walk: weighted means and unit normal (zeros without hits).
     __device__ __forceinline__ void resolve() {

@@ -224,10 +224,6 @@ struct KBufShared {
     }
 };
 
-#ifndef GRT_COLOUR_PREFETCH
-#define GRT_COLOUR_PREFETCH 1
-#endif
-
 // Per-ray traversal state, advanced one wide node at a time so that a warp can refill
 // lanes whose rays have finished while others are still walking the tree.
 template <int K, class KB = KBuf<K>>
@@ -499,9 +495,6 @@ __device__ __forceinline__ bool round_end(const DevBvh& bvh, TS& s, const TraceP
     float T = s.T;
     uint64_t lastk;
     if constexpr (TS::KBT::kShared) {
-        // the colour data of every buffered hit is requested up front, so that the in-order
-        // loop below does not wait for one hit's loads before asking for the next one's
-        if constexpr (GRT_COLOUR_PREFETCH) vis.prefetch(s.kb);
         // entries in order from shared memory; stop at termination
         for (int j = 0; j < s.kb.cnt; ++j) {
             const uint64_t k = s.kb.key_at(j);
@@ -586,7 +579,15 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16])
 }
 
 // Surfel colour toward direction d: RGB, or max(0, SH(d) + 0.5) per channel.
-static __device__ __noinline__ void surfel_colour_sh(const float* __restrict__ color, int id, f3 d, float c[3]);
+#ifndef GRT_SH_INLINE
+#define GRT_SH_INLINE 1
+#endif
+#if GRT_SH_INLINE
+#define GRT_SH_ATTR __forceinline__
+#else
+#define GRT_SH_ATTR __noinline__
+#endif
+static __device__ GRT_SH_ATTR void surfel_colour_sh(const float* __restrict__ color, int id, f3 d, float c[3]);
 
 __device__ __forceinline__ void surfel_colour(const float* __restrict__ color, int cdim, int id, f3 d, float c[3]) {
     if (cdim == 3) {
@@ -598,8 +599,9 @@ __device__ __forceinline__ void surfel_colour(const float* __restrict__ color, i
     surfel_colour_sh(color, id, d, c);
 }
 
-// SH colour kept out of line: one copy serves every composite site.
-static __device__ __noinline__ void surfel_colour_sh(const float* __restrict__ color, int id, f3 d, float c[3]) {
+// SH colour: inline where its callers have one call site (the walks' in-order compositing
+// loop), out of line otherwise.
+static __device__ GRT_SH_ATTR void surfel_colour_sh(const float* __restrict__ color, int id, f3 d, float c[3]) {
     float Y[16];
     sh_basis(d.x, d.y, d.z, Y);
     const float4* s = reinterpret_cast<const float4*>(color + 48 * (size_t)id);
@@ -636,17 +638,7 @@ struct RadianceVisitor {
     __device__ __forceinline__ RadianceVisitor(const float* col, int cd, f3 dir) : color(col), cdim(cd), d(dir) {
         c[0] = c[1] = c[2] = 0.f;
     }
-    // L1 prefetch of the SH coefficients (three 64-byte lines) of the hits in a k-buffer
-    template <class KB>
-    __device__ __forceinline__ void prefetch(const KB& kb) const {
-        if (cdim != 48) return;
-        for (int j = 0; j < kb.cnt; ++j) {
-            const char* p = reinterpret_cast<const char*>(color + 48 * (size_t)key_id(kb.key_at(j)));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(p + 64));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(p + 128));
-        }
-    }
+
     __device__ __forceinline__ void composite(int, int id, float, float alpha, float Tb) {
         float ck[3];
         surfel_colour(color, cdim, id, d, ck);

@@ -93,6 +93,7 @@ class _State:
             self.env_rgb.copy_(henv, non_blocking=True)
             self.env = api.Environment(self.env_rgb, stream=stream)
             self.gb = api.gbuffer_primary(scene, req.camera, stream=stream)
+            self.n_valid = self.gb.valid.sum()   # device scalar: the request's traced pixels
             self.color = torch.empty((P, 3), device=dev)
             self.vis = torch.empty((P,), device=dev)
             self.ind = torch.empty((P, 3), device=dev)
@@ -111,6 +112,10 @@ class _State:
         ts += [t for t in (self.gb.pos, self.gb.normal, self.gb.albedo, self.gb.rough, self.gb.metal, self.gb.valid,
                            self.gb.alpha, self.gb.depth) if t is not None]
         return ts
+
+    def release(self):
+        """Drop the request's device buffers (statistics keep only the valid-pixel count)."""
+        self.env_rgb = self.color = self.vis = self.ind = self.env = self.gb = None
 
     def use_on(self, stream):
         """Mark the request's tensors as used by `stream`: the caching allocator then keeps
@@ -150,9 +155,11 @@ class RelightServer:
         self.cancelled.add(rid)
 
     # ------------------------------------------------------------------ batched
-    def run_batched(self, trace: List[RelightRequest], realtime: bool = True, on_launch=None) -> dict:
+    def run_batched(self, trace: List[RelightRequest], realtime: bool = True, on_launch=None,
+                    keep_outputs: bool = True) -> dict:
         """Serve `trace` with continuous batching.  `on_launch(i, slices)`, if given, is
-        called after launch i with its (request id, first pixel, pixels) slices."""
+        called after launch i with its (request id, first pixel, pixels) slices.  With
+        keep_outputs False a finished request's device buffers are released (long traces)."""
         dev = self.device
         compute = torch.cuda.Stream(dev)
         prep = torch.cuda.Stream(dev)
@@ -191,6 +198,8 @@ class RelightServer:
                 for st in ending:
                     st.done_ms = ref.elapsed_time(ev)
                     mem -= st.bytes
+                    if not keep_outputs:
+                        st.release()
                     finished.append(st)
             for st in [s for s in active if s.req.rid in self.cancelled]:
                 active.remove(st)
@@ -251,7 +260,7 @@ class RelightServer:
         return self._stats(finished, launches, "batched", self.skip)
 
     # ------------------------------------------------------------------ one at a time
-    def run_serial(self, trace: List[RelightRequest], realtime: bool = True) -> dict:
+    def run_serial(self, trace: List[RelightRequest], realtime: bool = True, keep_outputs: bool = True) -> dict:
         dev = self.device
         s = torch.cuda.Stream(dev)
         ref = torch.cuda.Event(enable_timing=True)
@@ -276,6 +285,8 @@ class RelightServer:
             ev.record(s)
             ev.synchronize()
             st.done_ms = ref.elapsed_time(ev)
+            if not keep_outputs:
+                st.release()
             finished.append(st)
         return self._stats(finished, len(finished), "serial", self.skip)
 
@@ -287,7 +298,7 @@ class RelightServer:
         if not states:
             return {"mode": mode, "requests": 0}
         lat = np.array([st.done_ms - 1e3 * st.req.arrival for st in states])
-        rays = sum(int(st.gb.valid.sum().item()) * st.req.rays for st in states)
+        rays = sum(int(st.n_valid.item()) * st.req.rays for st in states)
         # the measured requests are served from the first measured arrival, or from the end
         # of the warm-up requests if those finish later (a queue built up by the warm-up)
         first = min(st.req.arrival for st in states) * 1e3
@@ -322,8 +333,8 @@ def poisson_run(srv: RelightServer, scenes_dist: Dict[str, float], rate: float, 
     trace = make_trace(n_warm + n_meas, rate, scenes_dist, seed=seed, envs=envs)
     srv.skip = n_warm
     keep = ("requests", "launches", "rays", "rays_per_s", "span_s", "p50_ms", "p99_ms", "mean_ms", "max_ms")
-    b = srv.run_batched(trace)
-    o = srv.run_serial(trace)
+    b = srv.run_batched(trace, keep_outputs=False)
+    o = srv.run_serial(trace, keep_outputs=False)
     srv.skip = 0
     return {"rate_per_s": rate, "warmup_requests": n_warm, "batched": {k: b[k] for k in keep},
             "one_at_a_time": {k: o[k] for k in keep}}
