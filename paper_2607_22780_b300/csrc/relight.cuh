@@ -153,7 +153,8 @@ struct AttrVisitor {
         a[0] = a[1] = a[2] = 0.f;
         n[0] = n[1] = n[2] = 0.f;
     }
-    __device__ __noinline__ void composite(int, int id, float, float alpha, float Tb) {
+    // one call site: the walks' in-order compositing loop
+    __device__ __forceinline__ void composite(int, int id, float, float alpha, float Tb) {
         const float w = Tb * alpha;
         const float4 nv = __ldg(src->nrm + id);
         const f3 nn = mk3(nv.x, nv.y, nv.z);

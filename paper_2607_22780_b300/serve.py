@@ -9,9 +9,11 @@ Continuous batching (iteration-level scheduling): the loop runs "iterations"; ea
 pixel slices from the admitted requests in arrival order until a ray budget is filled and
 shades them all in ONE grt_shade_batch launch.  Requests that arrive while launches are on
 the GPU are admitted at the next iteration as long as their device memory fits the HBM
-budget; their map upload, tables and G-buffer run on a second stream and overlap the
-shading of the others.  A request completes when the launch holding its last slice ends
-(CUDA event on the GPU timeline); latency = completion - arrival.
+budget; their map upload, tables and G-buffer run on a separate stream and overlap the
+shading of the others.  Launches alternate over two compute streams, so that one launch
+starts while the previous one drains its last rays.  A request completes when every launch
+holding one of its slices has ended (CUDA events on the GPU timeline); latency = completion -
+arrival.
 
 The comparator serves the same arrival trace one request at a time (each request's
 G-buffer and a whole-image grt_shade_pixels launch, back to back).  Results are
@@ -103,8 +105,8 @@ class _State:
         self.next = 0
         self.done_ms: Optional[float] = None
         self.start_ms: Optional[float] = None
-        self.last_ev: Optional[torch.cuda.Event] = None   # end of the last launch holding a slice
-        self._on_compute = False
+        self.evs: Dict[int, torch.cuda.Event] = {}   # compute stream -> end of its last launch with a slice
+        self._streams = set()
 
     def tensors(self):
         """Every device tensor of the request (allocated on the prep stream)."""
@@ -122,10 +124,17 @@ class _State:
         their blocks until the work queued there when they are freed has finished, so a
         request dropped while a launch still writes its outputs cannot hand those blocks to
         another request."""
-        if not self._on_compute:
+        if stream.cuda_stream not in self._streams:
             for t in self.tensors():
                 t.record_stream(stream)
-            self._on_compute = True
+            self._streams.add(stream.cuda_stream)
+
+    def launches_done(self) -> bool:
+        return all(e.query() for e in self.evs.values())
+
+    def wait_launches(self):
+        for e in self.evs.values():
+            e.synchronize()
 
     @staticmethod
     def bytes_needed(req: RelightRequest) -> int:
@@ -138,13 +147,14 @@ class RelightServer:
     """Resident scenes + continuous batching of relight requests on one GPU."""
 
     def __init__(self, scenes: Dict[str, api.Scene], device="cuda", hbm_budget: int = 8 << 30,
-                 ray_budget: int = 8 << 20, max_batch: int = 16, inflight: int = 2):
+                 ray_budget: int = 8 << 20, max_batch: int = 16, inflight: int = 4, streams: int = 2):
         self.scenes = scenes
         self.device = torch.device(device)
         self.hbm_budget = int(hbm_budget)
         self.ray_budget = int(ray_budget)
         self.max_batch = int(max_batch)
         self.inflight = int(inflight)
+        self.streams = max(1, int(streams))
         self.cancelled = set()
         self.peak_active = 0
         self.peak_mem = 0
@@ -159,23 +169,28 @@ class RelightServer:
                     keep_outputs: bool = True) -> dict:
         """Serve `trace` with continuous batching.  `on_launch(i, slices)`, if given, is
         called after launch i with its (request id, first pixel, pixels) slices.  With
-        keep_outputs False a finished request's device buffers are released (long traces)."""
+        keep_outputs False a finished request's device buffers are released (long traces).
+
+        Launches alternate over `streams` compute streams, so that one launch's kernels start
+        while the previous one's persistent walk drains its last rays; a request is complete
+        when every launch holding one of its slices has ended."""
         dev = self.device
-        compute = torch.cuda.Stream(dev)
+        compute = [torch.cuda.Stream(dev) for _ in range(self.streams)]
         prep = torch.cuda.Stream(dev)
         ref = torch.cuda.Event(enable_timing=True)
         pending = collections.deque(sorted(trace, key=lambda r: r.arrival))
         active: List[_State] = []
         finished: List[_State] = []
-        inflight = collections.deque()
-        retiring: List[_State] = []    # cancelled after a launch: memory counted until it ends
+        completing: List[_State] = []  # every slice launched, some launch still running
+        inflight = collections.deque()  # launch end events, oldest first
+        retiring: List[_State] = []     # cancelled after a launch: memory counted until it ends
         mem = 0
         launches = 0
         torch.cuda.synchronize(dev)
-        ref.record(compute)
+        ref.record(compute[0])
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        while pending or active or inflight or retiring:
+        while pending or active or inflight or retiring or completing:
             now = (time.perf_counter() - t0) if realtime else math.inf
             # admit arrivals while their memory fits the budget
             while pending and pending[0].arrival <= now:
@@ -192,25 +207,26 @@ class RelightServer:
                 mem += need
                 active.append(st)
             self.peak_active = max(self.peak_active, len(active))
-            # retire launches that have finished on the GPU
-            while inflight and inflight[0][0].query():
-                ev, ending = inflight.popleft()
-                for st in ending:
-                    st.done_ms = ref.elapsed_time(ev)
-                    mem -= st.bytes
-                    if not keep_outputs:
-                        st.release()
-                    finished.append(st)
+            # requests whose launches have all ended
+            while inflight and inflight[0].query():
+                inflight.popleft()
+            for st in [s for s in completing if s.launches_done()]:
+                completing.remove(st)
+                st.done_ms = max(ref.elapsed_time(e) for e in st.evs.values())
+                mem -= st.bytes
+                if not keep_outputs:
+                    st.release()
+                finished.append(st)
             for st in [s for s in active if s.req.rid in self.cancelled]:
                 active.remove(st)
                 retiring.append(st)
-            for st in [s for s in retiring if s.last_ev is None or s.last_ev.query()]:
+            for st in [s for s in retiring if s.launches_done()]:
                 retiring.remove(st)
                 mem -= st.bytes
             self.peak_mem = max(self.peak_mem, mem)
             # at most `inflight` launches queued on the GPU before building the next one
             if len(inflight) >= self.inflight:
-                inflight[0][0].synchronize()
+                inflight[0].synchronize()
                 continue
             # next iteration: FIFO slices up to the ray budget
             batch, budget = [], self.ray_budget
@@ -225,31 +241,35 @@ class RelightServer:
                 st.next += npx
                 budget -= npx * st.req.rays
             if batch:
+                si = launches % len(compute)
+                cs = compute[si]
                 reqs = []
                 for st, off, npx in batch:
-                    compute.wait_event(st.ready)
-                    st.use_on(compute)
+                    cs.wait_event(st.ready)
+                    st.use_on(cs)
                     a = st.req.alloc
                     reqs.append(api.ShadeRequest(st.scene, st.gb, st.env, a[0], a[1], a[2], st.req.seed, brdf=1,
                                                  pixel_offset=off, count=npx, color=st.color[off:off + npx],
                                                  vis=st.vis[off:off + npx], ind=st.ind[off:off + npx]))
-                api.shade_batch(reqs, stream=compute)
+                api.shade_batch(reqs, stream=cs)
                 launches += 1
                 ev = torch.cuda.Event(enable_timing=True)
-                ev.record(compute)
+                ev.record(cs)
                 for st, _, _ in batch:
-                    st.last_ev = ev
-                ending = [st for st, _, _ in batch if st.next >= st.P]
-                for st in ending:
+                    st.evs[si] = ev
+                for st in [st for st, _, _ in batch if st.next >= st.P]:
                     active.remove(st)
-                inflight.append((ev, ending))
+                    completing.append(st)
+                inflight.append(ev)
                 if on_launch is not None:
                     on_launch(launches - 1, [(st.req.rid, off, npx) for st, off, npx in batch])
                 continue
             if inflight:
-                inflight[0][0].synchronize()
+                inflight[0].synchronize()
             elif retiring:
-                retiring[0].last_ev.synchronize()
+                retiring[0].wait_launches()
+            elif completing:
+                completing[0].wait_launches()
             elif active and not any(st.next < st.P for st in active):
                 raise RuntimeError("scheduler stalled: admitted requests without work or launch")
             elif pending:
