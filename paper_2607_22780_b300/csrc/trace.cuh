@@ -320,7 +320,9 @@ __device__ __forceinline__ bool trav_step(const DevBvh& bvh, TS& s, Stack& stack
         return false;
     }
     const RayState& r = s.r;
-    const float tlo = fmaf(P.t_min, 0.99999f, -r.eps);
+    // near cull: t_min, and in later rounds the last composited depth (a node ending before
+    // it holds only keys <= last), with the far cull's slack
+    const float tlo = fmaf(fmaxf(P.t_min, key_tau(s.last)), 0.99999f, -r.eps);
     // the near plane of each axis is lo for a positive direction, hi otherwise
     const int ox = r.inv.x >= 0.f ? 0 : 3, oy = r.inv.y >= 0.f ? 1 : 4, oz = r.inv.z >= 0.f ? 2 : 5;
     const float4* N = bvh.nodes + 8 * (size_t)node;
@@ -423,7 +425,9 @@ __device__ __forceinline__ void node_step_q(const DevBvh& bvh, TS& s, Stack& sta
         return;
     }
     const RayState& r = s.r;
-    const float tlo = fmaf(P.t_min, 0.99999f, -r.eps);
+    // near cull: t_min, and in later rounds the last composited depth (a node ending before
+    // it holds only keys <= last), with the far cull's slack
+    const float tlo = fmaf(fmaxf(P.t_min, key_tau(s.last)), 0.99999f, -r.eps);
     const int ox = r.inv.x >= 0.f ? 0 : 3, oy = r.inv.y >= 0.f ? 1 : 4, oz = r.inv.z >= 0.f ? 2 : 5;
     const float4* N = bvh.nodes + 8 * (size_t)node;
     const float4 nx = __ldg(N + ox), ny = __ldg(N + oy), nz = __ldg(N + oz);
