@@ -46,7 +46,6 @@ extern "C" {
 #define GRT_STATUS_NONFINITE 2  /* a ray with a NaN or infinite origin or direction was traced as a miss */
 #define GRT_STATUS_BAD_TREE 4   /* node reference out of range or walk longer than the tree */
 #define GRT_STATUS_BAD_INDEX 8  /* a pixel index outside the G-buffer was skipped            */
-#define GRT_STATUS_TIMEOUT 16   /* a bounded wait of the tree build gave up (tree incomplete) */
 
 /* Surfels (Sec. III-A "2D Gaussian splatting"; Sec. III-B "Bounding proxy").
  * mu[n][3] centre; quat[n][4] rotation (w,x,y,z), any non-zero norm, normalised inside:

@@ -22,7 +22,6 @@ STATUS_STACK_OVERFLOW = 1
 STATUS_NONFINITE = 2
 STATUS_BAD_TREE = 4
 STATUS_BAD_INDEX = 8
-STATUS_TIMEOUT = 16
 
 P = C.c_void_p
 

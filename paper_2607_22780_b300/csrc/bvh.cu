@@ -147,32 +147,52 @@ __global__ void k_morton(const float* __restrict__ centre, const unsigned int* _
             bounds_out[3 + k] = -ordered_to_float(bounds_u[9 + k]);
         }
     }
-    if (i >= n) return;
-    int nb[3] = {0, 0, 0};
-    unsigned seq_lo = 0, seq_hi = 0;  // 2 bits per key bit: the axis that bit splits
-    for (int b = 0; b < 30; ++b) {
-        const float c0 = ldexpf(ext[0], -nb[0]), c1 = ldexpf(ext[1], -nb[1]), c2 = ldexpf(ext[2], -nb[2]);
-        int a = (c0 >= c1 && c0 >= c2) ? 0 : (c1 >= c2 ? 1 : 2);
-        if (nb[a] >= 21) a = nb[0] < 21 ? 0 : (nb[1] < 21 ? 1 : 2);
-        ++nb[a];
-        if (b < 16) seq_lo |= (unsigned)a << (2 * b);
-        else seq_hi |= (unsigned)a << (2 * (b - 16));
+    // axis order of the key bits, the same for every surfel: one thread per block derives it
+    __shared__ unsigned int order_s[3];  // seq_lo, seq_hi, nb0 | nb1 << 8 | nb2 << 16
+    if (threadIdx.x == 0) {
+        int nb0 = 0, nb1 = 0, nb2 = 0;
+        float cx = ext[0], cy = ext[1], cz = ext[2];  // cell size per axis (halving is exact)
+        unsigned seq_lo = 0, seq_hi = 0;               // 2 bits per key bit: the axis it splits
+        for (int b = 0; b < 30; ++b) {
+            int a = (cx >= cy && cx >= cz) ? 0 : (cy >= cz ? 1 : 2);
+            if ((a == 0 ? nb0 : a == 1 ? nb1 : nb2) >= 21) a = nb0 < 21 ? 0 : (nb1 < 21 ? 1 : 2);
+            nb0 += a == 0;
+            nb1 += a == 1;
+            nb2 += a == 2;
+            cx = a == 0 ? 0.5f * cx : cx;
+            cy = a == 1 ? 0.5f * cy : cy;
+            cz = a == 2 ? 0.5f * cz : cz;
+            if (b < 16) seq_lo |= (unsigned)a << (2 * b);
+            else seq_hi |= (unsigned)a << (2 * (b - 16));
+        }
+        order_s[0] = seq_lo;
+        order_s[1] = seq_hi;
+        order_s[2] = (unsigned)nb0 | ((unsigned)nb1 << 8) | ((unsigned)nb2 << 16);
     }
+    __syncthreads();
+    if (i >= n) return;
+    const unsigned seq_lo = order_s[0], seq_hi = order_s[1];
+    const int nb0 = (int)(order_s[2] & 0xFF), nb1 = (int)((order_s[2] >> 8) & 0xFF), nb2 = (int)(order_s[2] >> 16);
     unsigned int q[3];
+    const int nbs[3] = {nb0, nb1, nb2};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float cells = (float)(1u << nb[k]);
+        const float cells = (float)(1u << nbs[k]);
         float t = (centre[3 * i + k] - lo[k]) / ext[k];
         t = fminf(fmaxf(t * cells, 0.f), cells - 1.f);
         q[k] = (unsigned int)t;
     }
-    int used[3] = {0, 0, 0};
+    // the bits of each axis, most significant first, in the order above
+    int r0 = nb0, r1 = nb1, r2 = nb2;
     unsigned int code = 0;
     for (int b = 0; b < 30; ++b) {
         const int a = (int)((b < 16 ? seq_lo >> (2 * b) : seq_hi >> (2 * (b - 16))) & 3u);
-        const unsigned bit = (q[a] >> (nb[a] - 1 - used[a])) & 1u;
-        ++used[a];
-        code = (code << 1) | bit;
+        const unsigned qa = a == 0 ? q[0] : a == 1 ? q[1] : q[2];
+        const int ra = a == 0 ? r0 : a == 1 ? r1 : r2;
+        code = (code << 1) | ((qa >> (ra - 1)) & 1u);
+        r0 -= a == 0;
+        r1 -= a == 1;
+        r2 -= a == 2;
     }
     keys[i] = code;
     vals[i] = i;
@@ -180,7 +200,9 @@ __global__ void k_morton(const float* __restrict__ centre, const unsigned int* _
 
 // ---------------------------------------------------------------- radix sort (LSD, 8-bit digits)
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+// 2,048 keys per tile: 147 scatter blocks for 300k keys (4,096-key tiles left half the SMs
+// without a block)
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
 __global__ void k_sort_hist(const MortonKey* __restrict__ keys, int n, int shift, int nblocks,
@@ -197,29 +219,66 @@ __global__ void k_sort_hist(const MortonKey* __restrict__ keys, int n, int shift
     hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of m counts in one block of 1024 threads (digit-major layout).
-__global__ void k_sort_scan(unsigned int* __restrict__ hist, int m) {
-    __shared__ unsigned int part[1024];
-    int per = (m + 1023) / 1024;
-    int b = threadIdx.x * per;
-    unsigned int s = 0;
-    for (int k = 0; k < per; ++k)
-        if (b + k < m) s += hist[b + k];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        unsigned int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    unsigned int run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-    for (int k = 0; k < per; ++k) {
-        if (b + k < m) {
-            unsigned int c = hist[b + k];
-            hist[b + k] = run;
-            run += c;
+// Exclusive scan of m counts in one block of 1024 threads (digit-major layout), 8,192 counts
+// at a time: a coalesced copy into shared memory (one pad word per 32, so that the
+// threads' contiguous runs of 8 fall in distinct banks), a scan of the runs' sums over the
+// block by warp shuffles, and a coalesced copy back.
+constexpr int kScanThreads = 1024, kScanRun = 8, kScanSeg = kScanThreads * kScanRun;
+
+__device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
+
+__global__ void __launch_bounds__(kScanThreads) k_sort_scan(unsigned int* __restrict__ hist, int m) {
+    __shared__ unsigned int seg[kScanSeg + kScanSeg / 32];
+    __shared__ unsigned int wsum[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned int carry = 0;
+    for (int base = 0; base < m; base += kScanSeg) {
+        const int len = min(kScanSeg, m - base);
+#pragma unroll
+        for (int k = 0; k < kScanRun; ++k) {
+            const int i = k * kScanThreads + threadIdx.x;
+            seg[scan_pad(i)] = i < len ? hist[base + i] : 0u;
         }
+        __syncthreads();
+        const int b = threadIdx.x * kScanRun;
+        unsigned int v[kScanRun], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanRun; ++k) {
+            v[k] = seg[scan_pad(b + k)];
+            sum += v[k];
+        }
+        unsigned int x = sum;  // inclusive scan of the run sums within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned int w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        unsigned int run = carry + (warp ? wsum[warp - 1] : 0u) + x - sum;
+#pragma unroll
+        for (int k = 0; k < kScanRun; ++k) {
+            seg[scan_pad(b + k)] = run;
+            run += v[k];
+        }
+        carry += wsum[31];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanRun; ++k) {
+            const int i = k * kScanThreads + threadIdx.x;
+            if (i < len) hist[base + i] = seg[scan_pad(i)];
+        }
+        __syncthreads();  // seg and wsum are reused by the next segment
     }
 }
 
@@ -409,6 +468,12 @@ __global__ void k_hierarchy(const MortonKey* __restrict__ keys, int n, float4* _
     if (i == 0) parent[n] = -1;
 }
 
+__device__ __forceinline__ int atomic_add_acq_rel(int* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __global__ void k_refit(const float* __restrict__ leaf_box, const int* __restrict__ parent, int n,
                         float4* __restrict__ nodes, int* __restrict__ flags, int* status, float* __restrict__ bin_box) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -422,26 +487,27 @@ __global__ void k_refit(const float* __restrict__ leaf_box, const int* __restric
             atomicOr(status, GRT_STATUS_BAD_TREE);
             return;
         }
-        int node = p >> 1, slot = p & 1;
-        volatile float* f = reinterpret_cast<volatile float*>(nodes + 4 * (size_t)node);
+        const int node = p >> 1, slot = p & 1;
+        const int up = parent[n + node];  // read ahead of the handshake
+        float* f = reinterpret_cast<float*>(nodes + 4 * (size_t)node);
 #pragma unroll
         for (int k = 0; k < 6; ++k) f[6 * slot + k] = b[k];
-        __threadfence();
-        if (atomicAdd(flags + node, 1) == 0) return;  // first arrival: the sibling finishes
-        __threadfence();
+        // release: this box is visible to the sibling's thread once it sees the count;
+        // acquire: the sibling's box is visible here once this thread sees its count
+        if (atomic_add_acq_rel(flags + node, 1) == 0) return;  // first arrival: the sibling finishes
+        const float* g = f + 6 * (1 - slot);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            b[k] = fminf(f[k], f[6 + k]);
-            b[3 + k] = fmaxf(f[3 + k], f[9 + k]);
+            b[k] = fminf(b[k], __ldcg(g + k));
+            b[3 + k] = fmaxf(b[3 + k], __ldcg(g + 3 + k));
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) bin_box[6 * (size_t)node + k] = b[k];
-        p = parent[n + node];
+        p = up;
     }
 }
 
 // ---------------------------------------------------------------- 4-wide collapse
-// Top down from the root, one launch with a device-side work queue (k_collapse_queue).
 __device__ __forceinline__ int bin_size(const float4* bn, int ref) {
     if (ref < 0) return 1;
     const float* f = reinterpret_cast<const float*>(bn + 4 * (size_t)ref);
@@ -455,17 +521,6 @@ __device__ __forceinline__ float half_area(const float* b) {
     return dx * dy + dy * dz + dz * dx;
 }
 
-struct CollapseIn {
-    const float4* bnodes;
-    const float* bin_box;
-    const float* leaf_box;
-    float4* wnodes;
-    int* queue;   // [cap]: binary node of each wide node, -1 until its parent publishes it
-    int* counts;  // [0] wide nodes allocated, [1] next wide node to take, [2] wide nodes written
-    int* status;
-    int cap;
-};
-
 __device__ __forceinline__ void write_slot(float4* W, int s, const float* box, int ref, int bref) {
     float* f = reinterpret_cast<float*>(W);
 #pragma unroll
@@ -474,18 +529,19 @@ __device__ __forceinline__ void write_slot(float4* W, int s, const float* box, i
     f[28 + s] = __int_as_float(bref);
 }
 
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wide node w made from binary node b: starts with b's two children and twice replaces the
+// The 4-wide tree keeps the binary tree's numbering: the wide node made from binary node b
+// is wide node b, so that every binary node's wide node is built at once, in parallel,
+// with no allocation.  Its children: start with b's two children and twice replace the
 // candidate of largest surface area that is too big for a leaf by its two children;
 // candidates of at most kLeafMax surfels become leaves over their contiguous run of sorted
-// records, larger ones become new wide nodes, published to the queue for any thread to take.
-__device__ void collapse_node(const CollapseIn& c, int w, int b) {
-    const float* fb = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)b);
+// records, larger ones the wide node of the same index.  Only the nodes reachable from
+// the root (wide node 0 = binary node 0) are ever traversed; the others are built too,
+// since whether a binary node heads a wide node depends on its ancestors' choices.
+__global__ void k_collapse(const float4* __restrict__ bnodes, const float* __restrict__ bin_box,
+                           const float* __restrict__ leaf_box, int n_int, float4* __restrict__ wnodes) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_int) return;
+    const float* fb = reinterpret_cast<const float*>(bnodes + 4 * (size_t)b);
     int cand[kWide];
     int nc = 2;
     cand[0] = __float_as_int(fb[12]);
@@ -495,8 +551,8 @@ __device__ void collapse_node(const CollapseIn& c, int w, int b) {
         float ba = -1.f;
         for (int s = 0; s < nc; ++s) {
             int r = cand[s];
-            if (r >= 0 && bin_size(c.bnodes, r) > kLeafMax) {
-                float a = half_area(c.bin_box + 6 * (size_t)r);
+            if (r >= 0 && bin_size(bnodes, r) > kLeafMax) {
+                float a = half_area(bin_box + 6 * (size_t)r);
                 if (a > ba) {
                     ba = a;
                     best = s;
@@ -504,89 +560,52 @@ __device__ void collapse_node(const CollapseIn& c, int w, int b) {
             }
         }
         if (best < 0) break;
-        const float* fr = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)cand[best]);
+        const float* fr = reinterpret_cast<const float*>(bnodes + 4 * (size_t)cand[best]);
         cand[best] = __float_as_int(fr[12]);
         cand[nc++] = __float_as_int(fr[13]);
     }
-    float4* W = c.wnodes + 8 * (size_t)w;
+    float f[32];  // the node as written: six planes x four slots, refs, binary refs
+#pragma unroll
     for (int s = 0; s < kWide; ++s) {
         if (s >= nc) {
-            const float empty[6] = {1e38f, 1e38f, 1e38f, -1e38f, -1e38f, -1e38f};
-            write_slot(W, s, empty, kRefEmpty, kRefEmpty);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                f[4 * k + s] = 1e38f;
+                f[4 * (3 + k) + s] = -1e38f;
+            }
+            f[24 + s] = __int_as_float(kRefEmpty);
+            f[28 + s] = __int_as_float(kRefEmpty);
             continue;
         }
-        int r = cand[s];
-        const float* box = bin_box_of(c.bin_box, c.leaf_box, r);
+        const int r = cand[s];
         int ref;
         if (r < 0) {
             ref = leaf_ref(~r, 1);
         } else {
-            const float* fr = reinterpret_cast<const float*>(c.bnodes + 4 * (size_t)r);
-            int first = __float_as_int(fr[14]), size = __float_as_int(fr[15]) - first + 1;
-            if (size <= kLeafMax) {
-                ref = leaf_ref(first, size);
-            } else {
-                int w2 = atomicAdd(c.counts, 1);
-                if (w2 >= c.cap) {
-                    // more wide nodes than binary ones: a corrupt tree; the index counts as
-                    // written so that the queue still drains
-                    atomicOr(c.status, GRT_STATUS_BAD_TREE);
-                    __threadfence();
-                    atomicAdd(c.counts + 2, 1);
-                    ref = kRefEmpty;
-                } else {
-                    atomicExch(c.queue + w2, r);
-                    ref = w2;
-                }
-            }
+            const float* fr = reinterpret_cast<const float*>(bnodes + 4 * (size_t)r);
+            const int first = __float_as_int(fr[14]), size = __float_as_int(fr[15]) - first + 1;
+            ref = size <= kLeafMax ? leaf_ref(first, size) : r;
         }
-        write_slot(W, s, box, ref, r);
+        const float2* box = reinterpret_cast<const float2*>(bin_box_of(bin_box, leaf_box, r));
+        const float2 b01 = box[0], b23 = box[1], b45 = box[2];
+        f[s] = b01.x;
+        f[4 + s] = b01.y;
+        f[8 + s] = b23.x;
+        f[12 + s] = b23.y;
+        f[16 + s] = b45.x;
+        f[20 + s] = b45.y;
+        f[24 + s] = __int_as_float(ref);
+        f[28 + s] = __int_as_float(r);
     }
-}
-
-// The whole 4-wide collapse in one launch.  Wide node indices are handed out in order from
-// counts[1]; a thread waits until the parent of its wide node has published it (queue entry
-// >= 0), or until every allocated wide node has been written (counts[2] == counts[0]: no
-// node is in progress, so none can be published any more).  Every wait is bounded: after
-// kCollapseWaitNs the thread sets GRT_STATUS_TIMEOUT and returns.
-constexpr unsigned long long kCollapseWaitNs = 1000000000ull;
-
-__global__ void k_collapse_queue(CollapseIn c) {
-    while (true) {
-        const int w = atomicAdd(c.counts + 1, 1);
-        if (w >= c.cap) return;  // more threads than wide nodes can exist
-        const unsigned long long t0 = global_ns();
-        int b = -1;
-        unsigned sleep = 32;
-        for (int spin = 0;; ++spin) {
-            b = *reinterpret_cast<volatile int*>(c.queue + w);
-            if (b >= 0) break;
-            // the shared counters are read now and then only: every waiting thread polls
-            // its own queue entry, the producers' atomics on the counters stay uncontended
-            if ((spin & 7) == 7) {
-                const int done = *reinterpret_cast<volatile int*>(c.counts + 2);
-                __threadfence();
-                const int alloc = *reinterpret_cast<volatile int*>(c.counts);
-                if (done == alloc && w >= min(alloc, c.cap)) return;
-                if (global_ns() - t0 > kCollapseWaitNs) {
-                    atomicOr(c.status, GRT_STATUS_TIMEOUT);
-                    return;
-                }
-            }
-            __nanosleep(sleep);
-            sleep = sleep < 1024 ? 2 * sleep : 1024;
-        }
-        collapse_node(c, w, b);
-        __threadfence();  // the children's allocations are visible before this node counts as written
-        atomicAdd(c.counts + 2, 1);
-    }
+    float4* W = wnodes + 8 * (size_t)b;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) W[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
 }
 
 // Child boxes of every wide node from the refit binary boxes (topology unchanged).
-__global__ void k_wide_refit(float4* __restrict__ wnodes, const int* __restrict__ counts, int cap,
-                             const float* __restrict__ bin_box, const float* __restrict__ leaf_box) {
-    int nw = min(counts[0], cap);
-    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+__global__ void k_wide_refit(float4* __restrict__ wnodes, int n_int, const float* __restrict__ bin_box,
+                             const float* __restrict__ leaf_box) {
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n_int; w += gridDim.x * blockDim.x) {
         float4* W = wnodes + 8 * (size_t)w;
         const float* f = reinterpret_cast<const float*>(W);
         for (int s = 0; s < kWide; ++s) {
@@ -594,15 +613,6 @@ __global__ void k_wide_refit(float4* __restrict__ wnodes, const int* __restrict_
             if (br == kRefEmpty) continue;
             write_slot(W, s, bin_box_of(bin_box, leaf_box, br), __float_as_int(f[24 + s]), br);
         }
-    }
-}
-
-__global__ void k_collapse_init(int* counts, int* queue) {
-    if (threadIdx.x == 0) {
-        counts[0] = 1;  // wide node 0 = root, made from binary node 0
-        counts[1] = 0;
-        counts[2] = 0;
-        queue[0] = 0;
     }
 }
 
@@ -623,9 +633,6 @@ static void launch_records(const TriIn& in, grt_bvh* b, int g, cudaStream_t st) 
     k_tri_records<<<g, kThreads, 0, st>>>(in, b->sorted_ids, b->records, b->leaf_box);
 }
 
-// Blocks of the one-launch collapse (a few per SM; threads take wide nodes as they appear).
-constexpr int kCollapseBlocks = 148 * 4;
-
 // Records, binary refit and the 4-wide collapse (or its refit): shared tail of the builds.
 template <class In>
 static int finish_build(grt_bvh* b, const In& in, bool collapse, cudaStream_t st) {
@@ -635,16 +642,11 @@ static int finish_build(grt_bvh* b, const In& in, bool collapse, cudaStream_t st
     if (n > 1) {
         GRT_CUDA(cudaMemsetAsync(b->refit_flags, 0, sizeof(int) * (size_t)b->n_int, st));
         k_refit<<<g, kThreads, 0, st>>>(b->leaf_box, b->parent, n, b->nodes, b->refit_flags, b->status, b->bin_box);
-        const int cg = std::min((b->n_int + 127) / 128, 1184);
-        if (collapse) {
-            // every queue entry starts unpublished (-1); one launch collapses the whole tree
-            GRT_CUDA(cudaMemsetAsync(b->wqueue, 0xFF, sizeof(int) * (size_t)b->n_int, st));
-            k_collapse_init<<<1, 32, 0, st>>>(b->wcounts, b->wqueue);
-            CollapseIn c{b->nodes, b->bin_box, b->leaf_box, b->wnodes, b->wqueue, b->wcounts, b->status, b->n_int};
-            k_collapse_queue<<<std::min((b->n_int + 127) / 128, kCollapseBlocks), 128, 0, st>>>(c);
-        } else {
-            k_wide_refit<<<cg, 128, 0, st>>>(b->wnodes, b->wcounts, b->n_int, b->bin_box, b->leaf_box);
-        }
+        const int cg = (b->n_int + 127) / 128;
+        if (collapse)
+            k_collapse<<<cg, 128, 0, st>>>(b->nodes, b->bin_box, b->leaf_box, b->n_int, b->wnodes);
+        else
+            k_wide_refit<<<std::min(cg, 1184), 128, 0, st>>>(b->wnodes, b->n_int, b->bin_box, b->leaf_box);
     }
     GRT_CUDA(cudaGetLastError());
     return GRT_OK;
@@ -682,7 +684,7 @@ static int build_topology(grt_bvh* b, const In& in, char* scratch, cudaStream_t 
     int* vout = vals1;
     for (int shift = 0; shift < 32; shift += 8) {
         k_sort_hist<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, nblocks, hist);
-        k_sort_scan<<<1, 1024, 0, st>>>(hist, 256 * nblocks);
+        k_sort_scan<<<1, kScanThreads, 0, st>>>(hist, 256 * nblocks);
         k_sort_scatter<<<nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, nblocks, hist, kout, vout);
         std::swap(kin, kout);
         std::swap(vin, vout);
@@ -798,8 +800,7 @@ static grt_bvh* alloc_bvh(int nleaf, cudaStream_t st, int* rc_out) {
     size_t n = (size_t)nleaf, ni = (size_t)b->n_int;
     size_t bytes = sizeof(float4) * 4 * (ni + n) + sizeof(float4) * n + sizeof(int) * (n + ni + 1) + sizeof(int) * (ni + 1) +
                    sizeof(float) * 6 * n + sizeof(int) * n + 64 + 64 +
-                   sizeof(float) * 6 * ni + sizeof(float4) * 8 * ni + sizeof(int) * ni +
-                   sizeof(int) * 4 + 256 * 4;
+                   sizeof(float) * 6 * ni + sizeof(float4) * 8 * ni + 256 * 4;
     char* base = nullptr;
     cudaError_t e = cudaMalloc((void**)&base, bytes);
     if (e != cudaSuccess) {
@@ -822,9 +823,6 @@ static grt_bvh* alloc_bvh(int nleaf, cudaStream_t st, int* rc_out) {
     p = (char*)(((uintptr_t)p + 127) & ~(uintptr_t)127);
     b->wnodes = (float4*)p; p += sizeof(float4) * 8 * ni;
     b->bin_box = (float*)p; p += sizeof(float) * 6 * ni;
-    p = (char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-    b->wqueue = (int*)p; p += sizeof(int) * ni;
-    b->wcounts = (int*)p; p += sizeof(int) * 4;
     b->bytes = bytes;
     e = cudaMemsetAsync(b->status, 0, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->bounds, 0, 32, st);

@@ -243,7 +243,9 @@ __device__ __forceinline__ f3 env_dir_d(int row, int col, float u_row, float u_c
 }
 
 // ----------------------------------------------------------------------------- BVH layout
-// Traversal runs on a 4-wide BVH collapsed from the binary radix tree.
+// Traversal runs on a 4-wide BVH collapsed from the binary radix tree.  Wide node b is
+// made from binary node b (the root is 0 in both); nodes that no traversal from the root
+// reaches are built but unused.
 // Wide node: 128 bytes = 8 float4
 //   [0..2] lo.x, lo.y, lo.z of the four children, [3..5] hi.x, hi.y, hi.z
 //   [6]    child refs (int bits): >= 0 wide node, kRefEmpty unused slot, any other
@@ -297,8 +299,6 @@ struct grt_bvh {
     int* sorted_ids;   // [n]
     float4* wnodes;    // [n_int * 8] 4-wide nodes
     float* bin_box;    // [n_int * 6] box of each binary node
-    int* wqueue;       // [n_int] binary node of each wide node (collapse work queue)
-    int* wcounts;      // [4] collapse counters
     int* status;       // device status word
     float* bounds;     // [6] scene bounds (device)
     size_t bytes;
