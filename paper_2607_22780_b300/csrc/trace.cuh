@@ -78,12 +78,35 @@ __device__ __forceinline__ RayState make_ray(f3 o, f3 d) {
     return r;
 }
 
+// 32-byte read-only loads (PTX ld.global.nc.v8.f32, sm_100 and later; the address must be
+// 32-byte aligned).  A divergent warp-wide load costs one L1 wavefront per distinct line
+// it touches, so halving the load instructions of a node visit, a record test and an SH
+// evaluation halves their share of the L1 data pipe, which bounds the walk.
+#ifndef GRT_V8
+#define GRT_V8 1
+#endif
+struct F8 {
+    float4 a, b;
+};
+__device__ __forceinline__ F8 ld_v8(const float4* p) {
+#if GRT_V8
+    F8 r;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r.a.x), "=f"(r.a.y), "=f"(r.a.z), "=f"(r.a.w), "=f"(r.b.x), "=f"(r.b.y), "=f"(r.b.z), "=f"(r.b.w)
+        : "l"(p));
+    return r;
+#else
+    return F8{__ldg(p), __ldg(p + 1)};
+#endif
+}
+
 // Eq. 7 on a packed record.  The plane test (|n.d| >= eps_nd, tau in (t_min, t_max)) is
 // a decision computation; the Gaussian test needs u^2 + v^2 <= 2 ln(o/alpha_min).
 __device__ __forceinline__ bool intersect(const float4* __restrict__ records, int rec, const RayState& r,
                                           const TraceParams& P, float* tau, float* alpha, int* id) {
     const float4* R = records + 4 * (size_t)rec;
-    float4 r0 = __ldg(R), r1 = __ldg(R + 1), r2 = __ldg(R + 2), r3 = __ldg(R + 3);
+    const F8 r01 = ld_v8(R), r23 = ld_v8(R + 2);  // records are 64-byte aligned
+    const float4 r0 = r01.a, r1 = r01.b, r2 = r23.a, r3 = r23.b;
     f3 n = mk3(r1.x, r1.y, r1.z);
     f3 w = mk3(sub_d(r0.x, r.o.x), sub_d(r0.y, r.o.y), sub_d(r0.z, r.o.z));
     float num = dot_d(n, w), den = dot_d(n, r.d);
@@ -323,12 +346,15 @@ __device__ __forceinline__ bool trav_step(const DevBvh& bvh, TS& s, Stack& stack
     // near cull: t_min, and in later rounds the last composited depth (a node ending before
     // it holds only keys <= last), with the far cull's slack
     const float tlo = fmaf(fmaxf(P.t_min, key_tau(s.last)), 0.99999f, -r.eps);
-    // the near plane of each axis is lo for a positive direction, hi otherwise
-    const int ox = r.inv.x >= 0.f ? 0 : 3, oy = r.inv.y >= 0.f ? 1 : 4, oz = r.inv.z >= 0.f ? 2 : 5;
+    // the six child-plane float4 in three 32-byte loads (nodes are 128-byte aligned), the
+    // near plane of each axis chosen by the direction's sign (lo for a positive direction)
     const float4* N = bvh.nodes + 8 * (size_t)node;
-    const float4 nx = __ldg(N + ox), ny = __ldg(N + oy), nz = __ldg(N + oz);
-    const float4 fx = __ldg(N + (3 - ox)), fy = __ldg(N + (5 - oy)), fz = __ldg(N + (7 - oz));
+    const F8 xy = ld_v8(N), zx = ld_v8(N + 2), yz = ld_v8(N + 4);  // (lo.x lo.y) (lo.z hi.x) (hi.y hi.z)
     const int4 ref = __ldg(reinterpret_cast<const int4*>(N + 6));
+    const bool px = r.inv.x >= 0.f, py = r.inv.y >= 0.f, pz = r.inv.z >= 0.f;
+    const float4 nx = px ? xy.a : zx.b, fx = px ? zx.b : xy.a;
+    const float4 ny = py ? xy.b : yz.a, fy = py ? yz.a : xy.b;
+    const float4 nz = pz ? zx.a : yz.b, fz = pz ? yz.b : zx.a;
     const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, nys[4] = {ny.x, ny.y, ny.z, ny.w}, nzs[4] = {nz.x, nz.y, nz.z, nz.w};
     const float fxs[4] = {fx.x, fx.y, fx.z, fx.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
     const int refs[4] = {ref.x, ref.y, ref.z, ref.w};
@@ -428,11 +454,15 @@ __device__ __forceinline__ void node_step_q(const DevBvh& bvh, TS& s, Stack& sta
     // near cull: t_min, and in later rounds the last composited depth (a node ending before
     // it holds only keys <= last), with the far cull's slack
     const float tlo = fmaf(fmaxf(P.t_min, key_tau(s.last)), 0.99999f, -r.eps);
-    const int ox = r.inv.x >= 0.f ? 0 : 3, oy = r.inv.y >= 0.f ? 1 : 4, oz = r.inv.z >= 0.f ? 2 : 5;
+    // the six child-plane float4 in three 32-byte loads (nodes are 128-byte aligned), the
+    // near plane of each axis chosen by the direction's sign (lo for a positive direction)
     const float4* N = bvh.nodes + 8 * (size_t)node;
-    const float4 nx = __ldg(N + ox), ny = __ldg(N + oy), nz = __ldg(N + oz);
-    const float4 fx = __ldg(N + (3 - ox)), fy = __ldg(N + (5 - oy)), fz = __ldg(N + (7 - oz));
+    const F8 xy = ld_v8(N), zx = ld_v8(N + 2), yz = ld_v8(N + 4);  // (lo.x lo.y) (lo.z hi.x) (hi.y hi.z)
     const int4 ref = __ldg(reinterpret_cast<const int4*>(N + 6));
+    const bool px = r.inv.x >= 0.f, py = r.inv.y >= 0.f, pz = r.inv.z >= 0.f;
+    const float4 nx = px ? xy.a : zx.b, fx = px ? zx.b : xy.a;
+    const float4 ny = py ? xy.b : yz.a, fy = py ? yz.a : xy.b;
+    const float4 nz = pz ? zx.a : yz.b, fz = pz ? yz.b : zx.a;
     const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, nys[4] = {ny.x, ny.y, ny.z, ny.w}, nzs[4] = {nz.x, nz.y, nz.z, nz.w};
     const float fxs[4] = {fx.x, fx.y, fx.z, fx.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
     const int refs[4] = {ref.x, ref.y, ref.z, ref.w};
@@ -609,10 +639,22 @@ static __device__ GRT_SH_ATTR void surfel_colour_sh(const float* __restrict__ co
     float Y[16];
     sh_basis(d.x, d.y, d.z, Y);
     const float4* s = reinterpret_cast<const float4*>(color + 48 * (size_t)id);
+    float4 sv[12];
+    if ((reinterpret_cast<uintptr_t>(color) & 31) == 0) {  // 192-byte rows: 32-byte loads
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const F8 v = ld_v8(s + 2 * q);
+            sv[2 * q] = v.a;
+            sv[2 * q + 1] = v.b;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) sv[q] = __ldg(s + q);
+    }
     float acc[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
-        float4 v = __ldg(s + q);
+        const float4 v = sv[q];
         float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
