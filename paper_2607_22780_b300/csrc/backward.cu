@@ -47,10 +47,17 @@ struct AdjointVisitor {
     __device__ __noinline__ void composite(int, int id, float tau, float alpha, float Tb) {
 #endif
         // geometry of the hit, loaded first so that its latency overlaps the colour's
+        // (vector loads where the caller's arrays are aligned for them: fewer memory
+        // instructions per hit for the load/store unit, which throttles this kernel)
         const float op = __ldg(opacity + id);
-        const float4 q = make_float4(__ldg(quat + 4 * (size_t)id), __ldg(quat + 4 * (size_t)id + 1),
-                                     __ldg(quat + 4 * (size_t)id + 2), __ldg(quat + 4 * (size_t)id + 3));
-        const float su = __ldg(scale + 2 * (size_t)id), sv = __ldg(scale + 2 * (size_t)id + 1);
+        const float4 q = (reinterpret_cast<uintptr_t>(quat) & 15) == 0
+                             ? __ldg(reinterpret_cast<const float4*>(quat) + id)
+                             : make_float4(__ldg(quat + 4 * (size_t)id), __ldg(quat + 4 * (size_t)id + 1),
+                                           __ldg(quat + 4 * (size_t)id + 2), __ldg(quat + 4 * (size_t)id + 3));
+        const float2 sc = (reinterpret_cast<uintptr_t>(scale) & 7) == 0
+                              ? __ldg(reinterpret_cast<const float2*>(scale) + id)
+                              : make_float2(__ldg(scale + 2 * (size_t)id), __ldg(scale + 2 * (size_t)id + 1));
+        const float su = sc.x, sv = sc.y;
         const f3 m = mk3(__ldg(mu + 3 * (size_t)id), __ldg(mu + 3 * (size_t)id + 1), __ldg(mu + 3 * (size_t)id + 2));
         // colour of the hit and, for SH, which channels are live
         float Y[16];
@@ -63,10 +70,22 @@ struct AdjointVisitor {
         } else {
             sh_basis(d.x, d.y, d.z, Y);
             const float4* s = reinterpret_cast<const float4*>(color + 48 * (size_t)id);
+            float4 sv4[12];
+            if ((reinterpret_cast<uintptr_t>(color) & 31) == 0) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const F8 v = ld_v8(s + 2 * q);
+                    sv4[2 * q] = v.a;
+                    sv4[2 * q + 1] = v.b;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 12; ++q) sv4[q] = __ldg(s + q);
+            }
             float acc[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
-                float4 v = __ldg(s + q);
+                const float4 v = sv4[q];
                 float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int t = 0; t < 4; ++t) acc[(4 * q + t) % 3] = fmaf(e[t], Y[(4 * q + t) / 3], acc[(4 * q + t) % 3]);
