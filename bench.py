@@ -62,13 +62,15 @@ SURFEL_BYTES = 232  # mu 12 + quat 16 + scale 8 + opacity 4 + SH 192, read per r
 GRAD_RMW_BYTES = 464  # the same 232 B of gradients read and written (atomics) per replayed hit
 REPLAY_RAY_BYTES = 64  # per traced ray in the replay: hit count 4, direction 16, origin 12, (c_rt, T) 16, adjoint 16
 RAY_IO_BYTES = 44   # direction 16 + origin 12 read, (c_rt, T) 16 written
-COLLAPSE_LAUNCHES = 1  # the 4-wide collapse is one launch (device work queue)
+COLLAPSE_LAUNCHES = 1  # the 4-wide collapse is one launch (a thread per binary node)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace_rays_ww launch of the default
 # workload (k = 16, 800x800) from one ncu capture of the current kernel; None until taken
-TRACE_DRAM_BYTES = 1_181_220_864  # 850.0 MB read + 331.2 MB written (bucket order, 16-leaf queues)
-# L2 traffic of the same kernel (lts__t_bytes.sum) and its throughput fraction, from one ncu
-# capture; None until taken for the current kernel
-TRACE_L2 = None
+TRACE_DRAM_BYTES = 1_222_593_792  # 880.2 MB read + 342.4 MB written
+# L2 traffic of the same kernel (lts__t_bytes.sum) per ray and the L2 throughput fraction,
+# from one ncu capture of the 256x256 case of the same step (1,031,680 rays: 5.04 GB in one
+# launch); None until taken for the current kernel
+TRACE_L2 = {"lts_bytes_per_ray": 5_039_327_392 / 1_031_680, "lts_throughput_pct_of_peak": 17.96,
+            "lts_sector_hit_pct": 93.63, "case": "256x256, 300k surfels, 32 rays/pixel (one ncu capture)"}
 LARGE_N = 2_000_000          # unbounded scene: ground plane, 50 primitives, r = 50 shell
 LARGE_W, LARGE_H = 1920, 1080
 LARGE_ALLOC = (8, 4, 4)
@@ -100,6 +102,15 @@ def roofline(kernel, nbytes, lbytes, t_ms, peak, peak_kind, **extra):
                       "bytes": "kernel layout: 112 per 4-wide node visit + 64 per record + 192 per SH hit + 44 per ray"}}
     out.update(extra)
     return out
+
+
+def l2_summary(R, t_ms):
+    """L2 traffic of the trace launch: the captured bytes per ray scaled to this launch's
+    rays, over its event-timed duration."""
+    if TRACE_L2 is None:
+        return None
+    b = TRACE_L2["lts_bytes_per_ray"] * R
+    return dict(TRACE_L2, bytes_per_launch=b, achieved_GBps=b / (t_ms * 1e-3) / 1e9)
 
 
 def reduce_ranks(ms: float, rays: float, device) -> tuple:
@@ -238,7 +249,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": "secondary_rays_per_s", "value": value, "unit": "rays/s",
            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "mis_shade_300k_800x800_32spp", "surfels": N_SURFELS, "image": [W_IMG, H_IMG],
+           "config": {"workload": f"mis_shade_300k_{W_IMG}x{H_IMG}_32spp", "surfels": N_SURFELS, "image": [W_IMG, H_IMG],
                       "rays_per_pixel": sum(ALLOC), "alloc_cos_ggx_env": list(ALLOC), "env": [ENV_W, ENV_H],
                       "k": 16, "sample": "each step shades a bounded random sample of valid pixels of an 80x80 "
                                          "view from the same camera (same scene, map and seeds)"},
@@ -284,7 +295,9 @@ def run_grt(args):
     # kernel launches per step: rebuild (bounds, Morton, 4 x 3 sort passes, hierarchy, records,
     # refit, collapse init + the collapse), G-buffer 1, shade 5 (sample, bucket scan, ray
     # scatter, trace, accumulate)
-    launches_per_step = 2 + 12 + 3 + 1 + COLLAPSE_LAUNCHES + 1 + 5
+    # prep + Morton, 4 x (histogram, scan, scatter), hierarchy + records + refit, collapse,
+    # G-buffer, then sample + bucket scan + ray scatter + trace + accumulate
+    launches_per_step = 2 + 12 + 3 + COLLAPSE_LAUNCHES + 1 + 5
 
     for _ in range(args.warmup):
         step()
@@ -426,7 +439,7 @@ def run_grt(args):
         out = {"metric": "secondary_rays_per_s", "value": value, "unit": "rays/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": "mis_shade_300k_800x800_32spp", "surfels": N_SURFELS,
+               "config": {"workload": f"mis_shade_300k_{W_IMG}x{H_IMG}_32spp", "surfels": N_SURFELS,
                           "image": [W_IMG, H_IMG], "rays_per_pixel": sum(ALLOC), "alloc_cos_ggx_env": list(ALLOC),
                           "env": [ENV_W, ENV_H], "valid_pixels": n_valid, "rays_per_step": R,
                           "step": "rebuild LBVH + primary G-buffer + MIS shade", "k": args.k,
@@ -436,7 +449,7 @@ def run_grt(args):
                "roofline": roofline(
                    "k_trace_rays_ww", alg_bytes(cnt, R, ALLOC), layout_bytes(cnt, R), trace_s * 1e3, peak, peak_kind,
                    traffic=TRACE_DRAM_BYTES if (args.k == 16 and W_IMG == 800) else None,
-                   l2=TRACE_L2 if (args.k == 16 and W_IMG == 800) else None,
+                   l2=l2_summary(R, trace_s * 1e3) if args.k == 16 else None,
                    phase_ms={"sample": float(np.mean(ph[:, 0])), "trace": float(np.mean(ph[:, 1])),
                              "accumulate": float(np.mean(ph[:, 2])), "shade_call": shade_s * 1e3},
                    per_ray={"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R}),
@@ -489,7 +502,6 @@ def time_train(api, S, cam, E, dev, args):
     G = api.gbuffer_primary(S, c)
     tgt = torch.from_numpy(wl.target_image(SEED, img, img).reshape(-1, 3)).to(dev)
     grads = api.SurfelGrads.zeros(S)
-    P = TRAIN_IMG * TRAIN_IMG
 
     valid = G.valid.unsqueeze(1).float()
 
@@ -563,7 +575,7 @@ def time_train(api, S, cam, E, dev, args):
     replay["bytes"] = replay["layout"]["bytes"] = "(12 + 232 + 464) per composited hit + 64 per ray"
     save = roofline("k_trace_rays_save", alg_bytes(cnt, R, TRAIN_ALLOC, HIT_REC_BYTES, 4),
                     layout_bytes(cnt, R, HIT_REC_BYTES, 4), tr_ms, peak, peak_kind)
-    return {"workload": "train_300k_400x400_16spp", "rays": R, "fwd_ms": ms["fwd"], "fwd_bwd_ms": ms["fwd_bwd"],
+    return {"workload": f"train_300k_{img}x{img}_16spp", "rays": R, "fwd_ms": ms["fwd"], "fwd_bwd_ms": ms["fwd_bwd"],
             "fwd_bwd_recompute_ms": ms["fwd_bwd_recompute"], "stored_hits": 64,
             "fwd_bwd_material_ms": ms["fwd_bwd_material"],
             "fwd_rays_per_s": R / (ms["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (ms["fwd_bwd"] * 1e-3),
