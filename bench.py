@@ -292,12 +292,10 @@ def run_grt(args):
     torch.cuda.synchronize()
     n_valid = int(G.valid.sum().item())
     R = n_valid * sum(ALLOC)
-    # kernel launches per step: rebuild (bounds, Morton, 4 x 3 sort passes, hierarchy, records,
-    # refit, collapse init + the collapse), G-buffer 1, shade 5 (sample, bucket scan, ray
-    # scatter, trace, accumulate)
-    # prep + Morton, 4 x (histogram, scan, scatter), hierarchy + records + refit, collapse,
-    # G-buffer, then sample + bucket scan + ray scatter + trace + accumulate
-    launches_per_step = 2 + 12 + 3 + COLLAPSE_LAUNCHES + 1 + 5
+    # kernel launches per step: prep + Morton, 4 x (histogram, scan, scatter), hierarchy + records + refit, one per
+    # treelet-restructuring pass, collapse, G-buffer, then sample + bucket scan + ray scatter
+    # + trace + accumulate
+    launches_per_step = 2 + 12 + 3 + int(S.params.build_passes) + COLLAPSE_LAUNCHES + 1 + 5
 
     for _ in range(args.warmup):
         step()

@@ -17,6 +17,7 @@ GRT_OK, GRT_ERR_ARG, GRT_ERR_OOM, GRT_ERR_CUDA, GRT_ERR_OVERFLOW, GRT_ERR_TIMEOU
 GRT_MAX_BATCH = 48
 GRT_NOALLOC_MAX_SURFELS = 524288
 GRT_MAX_SAVED_HITS = 64
+GRT_MAX_BUILD_PASSES = 4
 GRT_DENOISE_MAX_RADIUS = 8
 STATUS_STACK_OVERFLOW = 1
 STATUS_NONFINITE = 2
@@ -33,7 +34,7 @@ class Surfels(C.Structure):
 
 class TraceParams(C.Structure):
     _fields_ = [(k, C.c_float) for k in ("alpha_min", "alpha_max", "t_min", "t_max", "T_min", "eps_nd")] + \
-        [("k", C.c_int32)]
+        [("k", C.c_int32), ("build_passes", C.c_int32)]
 
 
 class BvhInfo(C.Structure):

@@ -483,7 +483,7 @@ __global__ void k_refit(const float* __restrict__ leaf_box, const int* __restric
     for (int k = 0; k < 6; ++k) b[k] = leaf_box[6 * (size_t)j + k];
     int p = parent[j];
     for (int level = 0; p >= 0; ++level) {
-        if (level > 96 || (p >> 1) >= n - 1) {  // deeper than any radix tree over 32+27 bits
+        if (level > 255 || (p >> 1) >= n - 1) {  // deeper than any tree over 2^27 leaves
             atomicOr(status, GRT_STATUS_BAD_TREE);
             return;
         }
@@ -507,6 +507,257 @@ __global__ void k_refit(const float* __restrict__ leaf_box, const int* __restric
     }
 }
 
+__device__ __forceinline__ float half_area(const float* b) {
+    float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+// ---------------------------------------------------------------- treelet restructuring
+// Agglomerative treelet restructuring of the radix tree (after Domingues & Pedrini 2015, on
+// Karras & Aila's treelet scheme): one bottom-up pass with the refit's arrival counters;
+// the second thread to reach node R forms R's treelet -- R's two children, then repeatedly
+// the treelet leaf of largest surface area replaced by its two children, up to kTreelet
+// treelet leaves -- and rebuilds it by greedy agglomeration (the pair whose union has the
+// smallest area merged first).  The new topology replaces the old one only when the summed
+// surface area of the treelet's internal nodes (the surface-area cost of the treelet, its
+// root and leaves being fixed) drops.  Nodes reuse the treelet's internal indices, R stays
+// the root, so nothing outside the treelet changes.  Every read of the tree goes to L2:
+// other threads rewrote the descendants, ordered by the acq_rel counters.  After a pass an
+// internal node's key range no longer holds: f[14] = 0, f[15] = leaf count - 1, so that
+// only the size survives (multi-surfel leaves need contiguous ranges: kLeafMax == 1 only).
+constexpr int kTreelet = 9;
+
+__device__ __forceinline__ int node_size_cg(const float4* bn, int ref) {
+    if (ref < 0) return 1;
+    const float* f = reinterpret_cast<const float*>(bn + 4 * (size_t)ref);
+    return __float_as_int(__ldcg(f + 15)) - __float_as_int(__ldcg(f + 14)) + 1;
+}
+
+// Pairs (a, b), a < b < kTreelet, in order: pair p is handled by lane p % 32.
+__constant__ unsigned char c_pair_a[36] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2,
+                                           2, 2, 2, 3, 3, 3, 3, 3, 4, 4, 4, 4, 5, 5, 5, 6, 6, 7};
+__constant__ unsigned char c_pair_b[36] = {1, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8, 3, 4, 5,
+                                           6, 7, 8, 4, 5, 6, 7, 8, 5, 6, 7, 8, 6, 7, 8, 7, 8, 8};
+static_assert(kTreelet == 9, "the pair table enumerates the pairs of 9 treelet leaves");
+
+// Argmax (argmin with negated keys) of (key, index) over the warp; ties go to the lower index.
+__device__ __forceinline__ void warp_argmax(float& key, int& idx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ok = __shfl_xor_sync(0xffffffffu, key, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ok > key || (ok == key && oi < idx)) {
+            key = ok;
+            idx = oi;
+        }
+    }
+}
+
+// One treelet at root R, processed by the whole warp (R the same on every lane).  Lane k
+// holds treelet leaf k (its ref, box, leaf count) and, during the agglomeration, cluster
+// k; lane m records merge m; lane k holds the treelet's internal index inner[k].
+__device__ void restructure_treelet(int R, const float* __restrict__ leaf_box, int* __restrict__ parent, int n,
+                                    float4* __restrict__ nodes, float* __restrict__ bin_box, int* status) {
+    const int lane = threadIdx.x & 31;
+    auto bad = [n](int ref) { return ref >= 0 ? ref >= n - 1 : ~ref >= n; };
+    // a binary node holds both children's boxes and refs: one 64-byte load per expansion
+    // (the same address on every lane)
+    auto load_node = [&](int x, float (&cb)[12], int* cl, int* cr) {
+        const float4* q = nodes + 4 * (size_t)x;
+        const float4 v0 = __ldcg(q), v1 = __ldcg(q + 1), v2 = __ldcg(q + 2), v3 = __ldcg(q + 3);
+        cb[0] = v0.x; cb[1] = v0.y; cb[2] = v0.z; cb[3] = v0.w; cb[4] = v1.x; cb[5] = v1.y;
+        cb[6] = v1.z; cb[7] = v1.w; cb[8] = v2.x; cb[9] = v2.y; cb[10] = v2.z; cb[11] = v2.w;
+        *cl = __float_as_int(v3.x);
+        *cr = __float_as_int(v3.y);
+    };
+    int ref = 0;
+    float bx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int inner = R;
+    {
+        float cb[12];
+        int cl, cr;
+        load_node(R, cb, &cl, &cr);
+        if (bad(cl) || bad(cr)) {
+            if (lane == 0) atomicOr(status, GRT_STATUS_BAD_TREE);
+            return;
+        }
+        if (lane < 2) {
+            ref = lane == 0 ? cl : cr;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) bx[c] = lane == 0 ? cb[c] : cb[6 + c];
+        }
+    }
+    int nt = 2;
+    float cost_old = 0.f;
+    for (int it = 0; it < kTreelet - 2; ++it) {
+        float key = (lane < nt && ref >= 0) ? half_area(bx) : -1.f;
+        int best = lane;
+        warp_argmax(key, best);
+        if (key < 0.f) break;  // every treelet leaf is a surfel
+        const int x = __shfl_sync(0xffffffffu, ref, best);
+        float cb[12];
+        int cl, cr;
+        load_node(x, cb, &cl, &cr);
+        if (bad(cl) || bad(cr)) {
+            if (lane == 0) atomicOr(status, GRT_STATUS_BAD_TREE);
+            return;
+        }
+        if (lane == nt - 1) inner = x;
+        cost_old += key;
+        if (lane == best || lane == nt) {
+            const int side = lane == best ? 0 : 1;
+            ref = side ? cr : cl;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) bx[c] = side ? cb[6 + c] : cb[c];
+        }
+        ++nt;
+    }
+    if (nt < 3) return;  // two subtrees: only one topology
+    const int cnt = lane < nt ? node_size_cg(nodes, ref) : 0;
+    float ob[6];  // the treelet leaf's own box (bx becomes the cluster's)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) ob[c] = bx[c];
+    // greedy agglomeration; cluster refs: treelet leaf k, or merge m marked kMerged | m.  The
+    // last merge (m = nt - 2) is the root R = inner[0]; merge m < nt - 2 takes inner[m + 1].
+    constexpr int kMerged = 1 << 30;
+    int cref = lane, ccnt = cnt;
+    int mlft = 0, mrgt = 0, mcnt = 0;
+    float mbox[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    unsigned active = (1u << nt) - 1u;
+    float cost_new = 0.f;
+    const int pa0 = c_pair_a[lane], pb0 = c_pair_b[lane];
+    const int p1 = lane + 32 < 36 ? lane + 32 : 35;
+    const int pa1 = c_pair_a[p1], pb1 = c_pair_b[p1];
+    for (int m = 0; m < nt - 1; ++m) {
+        float d0 = 3.4e38f, d1 = 3.4e38f;
+        {
+            float lo[3], hi[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = fminf(__shfl_sync(0xffffffffu, bx[c], pa0), __shfl_sync(0xffffffffu, bx[c], pb0));
+                hi[c] = fmaxf(__shfl_sync(0xffffffffu, bx[3 + c], pa0), __shfl_sync(0xffffffffu, bx[3 + c], pb0));
+            }
+            if ((active >> pa0) & (active >> pb0) & 1u) {
+                const float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+                d0 = dx * dy + dy * dz + dz * dx;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = fminf(__shfl_sync(0xffffffffu, bx[c], pa1), __shfl_sync(0xffffffffu, bx[c], pb1));
+                hi[c] = fmaxf(__shfl_sync(0xffffffffu, bx[3 + c], pa1), __shfl_sync(0xffffffffu, bx[3 + c], pb1));
+            }
+            if (lane + 32 < 36 && ((active >> pa1) & (active >> pb1) & 1u)) {
+                const float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+                d1 = dx * dy + dy * dz + dz * dx;
+            }
+        }
+        float key = -fminf(d0, d1);
+        int pidx = d0 <= d1 ? lane : lane + 32;
+        warp_argmax(key, pidx);
+        const float bd = -key;
+        const int pa = c_pair_a[pidx], pb = c_pair_b[pidx];
+        float ub[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float va = __shfl_sync(0xffffffffu, bx[c], pa), vb = __shfl_sync(0xffffffffu, bx[c], pb);
+            ub[c] = c < 3 ? fminf(va, vb) : fmaxf(va, vb);
+        }
+        const int ra = __shfl_sync(0xffffffffu, cref, pa), rb = __shfl_sync(0xffffffffu, cref, pb);
+        const int cs = __shfl_sync(0xffffffffu, ccnt, pa) + __shfl_sync(0xffffffffu, ccnt, pb);
+        if (lane == m) {
+            mlft = ra;
+            mrgt = rb;
+            mcnt = cs;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) mbox[c] = ub[c];
+        }
+        if (lane == pa) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) bx[c] = ub[c];
+            cref = kMerged | m;
+            ccnt = cs;
+        }
+        active &= ~(1u << pb);
+        if (m != nt - 2) cost_new += bd;
+    }
+    if (!(cost_new < cost_old * 0.9999f)) return;
+    // lane m < nt - 1 writes merge m's node
+    const bool writer = lane < nt - 1;
+    const int my_slot = !writer ? 0 : (lane == nt - 2 ? 0 : lane + 1);
+    const int my_node = __shfl_sync(0xffffffffu, inner, my_slot);
+    float* f = reinterpret_cast<float*>(nodes + 4 * (size_t)my_node);
+    const int ch[2] = {mlft, mrgt};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const bool merged = (ch[c] & kMerged) != 0;
+        const int src = writer ? (merged ? ch[c] & ~kMerged : ch[c]) : 0;
+        const int node_of_merge = __shfl_sync(0xffffffffu, my_node, src);
+        const int leaf_ref = __shfl_sync(0xffffffffu, ref, src);
+        float b6[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float vm = __shfl_sync(0xffffffffu, mbox[k], src);
+            const float vl = __shfl_sync(0xffffffffu, ob[k], src);
+            b6[k] = merged ? vm : vl;
+        }
+        const int cr = merged ? node_of_merge : leaf_ref;
+        if (writer) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) f[6 * c + k] = b6[k];
+            f[12 + c] = __int_as_float(cr);
+            parent[cr < 0 ? ~cr : n + cr] = (my_node << 1) | c;
+        }
+    }
+    if (writer) {
+        f[14] = __int_as_float(0);
+        f[15] = __int_as_float(mcnt - 1);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) bin_box[6 * (size_t)my_node + k] = mbox[k];
+    }
+}
+
+// One pass: every thread climbs from its surfel; the second arrival at a node owns that
+// node's treelet, and the owners of a warp have their treelets processed one after another
+// by the whole warp.  __syncwarp orders the warp's writes before the owners' next release.
+__global__ void __launch_bounds__(kThreads) k_restructure(const float* __restrict__ leaf_box, int* __restrict__ parent,
+                                                          int n, float4* __restrict__ nodes, int* __restrict__ flags,
+                                                          int* status, float* __restrict__ bin_box) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    bool walking = j < n;
+    int p = walking ? __ldcg(parent + j) : -1;
+    int level = 0;
+    while (true) {
+        int R = -1;
+        if (walking) {
+            if (p < 0) {
+                walking = false;
+            } else if (++level > 256 || (p >> 1) >= n - 1) {
+                atomicOr(status, GRT_STATUS_BAD_TREE);
+                walking = false;
+            } else if (atomic_add_acq_rel(flags + (p >> 1), 1) == 0) {
+                walking = false;  // first arrival: the sibling's thread goes on
+            } else {
+                // a node over two surfels has one topology: no treelet to process
+                const float* f = reinterpret_cast<const float*>(nodes + 4 * (size_t)(p >> 1));
+                if (__float_as_int(__ldcg(f + 12)) < 0 && __float_as_int(__ldcg(f + 13)) < 0)
+                    p = __ldcg(parent + n + (p >> 1));
+                else
+                    R = p >> 1;
+            }
+        }
+        __syncwarp();
+        unsigned todo = __ballot_sync(0xffffffffu, R >= 0);
+        while (todo) {
+            const int L = __ffs(todo) - 1;
+            todo &= todo - 1;
+            restructure_treelet(__shfl_sync(0xffffffffu, R, L), leaf_box, parent, n, nodes, bin_box, status);
+            __syncwarp();
+        }
+        if (R >= 0) p = __ldcg(parent + n + R);
+        if (!__any_sync(0xffffffffu, walking)) break;
+    }
+}
+
 // ---------------------------------------------------------------- 4-wide collapse
 __device__ __forceinline__ int bin_size(const float4* bn, int ref) {
     if (ref < 0) return 1;
@@ -515,10 +766,6 @@ __device__ __forceinline__ int bin_size(const float4* bn, int ref) {
 }
 __device__ __forceinline__ const float* bin_box_of(const float* bin_box, const float* leaf_box, int ref) {
     return ref < 0 ? leaf_box + 6 * (size_t)(~ref) : bin_box + 6 * (size_t)ref;
-}
-__device__ __forceinline__ float half_area(const float* b) {
-    float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
-    return dx * dy + dy * dz + dz * dx;
 }
 
 __device__ __forceinline__ void write_slot(float4* W, int s, const float* box, int ref, int bref) {
@@ -538,15 +785,22 @@ __device__ __forceinline__ void write_slot(float4* W, int s, const float* box, i
 // the root (wide node 0 = binary node 0) are ever traversed; the others are built too,
 // since whether a binary node heads a wide node depends on its ancestors' choices.
 __global__ void k_collapse(const float4* __restrict__ bnodes, const float* __restrict__ bin_box,
-                           const float* __restrict__ leaf_box, int n_int, float4* __restrict__ wnodes) {
+                           const float* __restrict__ leaf_box, int n_int, float4* __restrict__ wnodes,
+                           int* status) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_int) return;
     const float* fb = reinterpret_cast<const float*>(bnodes + 4 * (size_t)b);
+    const int n = n_int + 1;
+    auto bad = [n](int ref) { return ref >= 0 ? ref >= n - 1 : ~ref >= n; };
     int cand[kWide];
     int nc = 2;
     cand[0] = __float_as_int(fb[12]);
     cand[1] = __float_as_int(fb[13]);
-    for (int rep = 2; rep < kWide; ++rep) {
+    if (bad(cand[0]) || bad(cand[1])) {
+        atomicOr(status, GRT_STATUS_BAD_TREE);
+        nc = 0;
+    }
+    for (int rep = 2; rep < kWide && nc > 0; ++rep) {
         int best = -1;
         float ba = -1.f;
         for (int s = 0; s < nc; ++s) {
@@ -561,8 +815,13 @@ __global__ void k_collapse(const float4* __restrict__ bnodes, const float* __res
         }
         if (best < 0) break;
         const float* fr = reinterpret_cast<const float*>(bnodes + 4 * (size_t)cand[best]);
-        cand[best] = __float_as_int(fr[12]);
-        cand[nc++] = __float_as_int(fr[13]);
+        const int cl = __float_as_int(fr[12]), cr = __float_as_int(fr[13]);
+        if (bad(cl) || bad(cr)) {
+            atomicOr(status, GRT_STATUS_BAD_TREE);
+            break;
+        }
+        cand[best] = cl;
+        cand[nc++] = cr;
     }
     float f[32];  // the node as written: six planes x four slots, refs, binary refs
 #pragma unroll
@@ -634,8 +893,10 @@ static void launch_records(const TriIn& in, grt_bvh* b, int g, cudaStream_t st) 
 }
 
 // Records, binary refit and the 4-wide collapse (or its refit): shared tail of the builds.
+// `passes` treelet-restructuring passes run between the refit and the collapse (topology
+// builds only).
 template <class In>
-static int finish_build(grt_bvh* b, const In& in, bool collapse, cudaStream_t st) {
+static int finish_build(grt_bvh* b, const In& in, bool collapse, int passes, cudaStream_t st) {
     const int n = b->n;
     const int g = (n + kThreads - 1) / kThreads;
     launch_records(in, b, g, st);
@@ -643,8 +904,15 @@ static int finish_build(grt_bvh* b, const In& in, bool collapse, cudaStream_t st
         GRT_CUDA(cudaMemsetAsync(b->refit_flags, 0, sizeof(int) * (size_t)b->n_int, st));
         k_refit<<<g, kThreads, 0, st>>>(b->leaf_box, b->parent, n, b->nodes, b->refit_flags, b->status, b->bin_box);
         const int cg = (b->n_int + 127) / 128;
+        if (collapse && kLeafMax == 1) {
+            for (int pass = 0; pass < passes && n > 2; ++pass) {
+                GRT_CUDA(cudaMemsetAsync(b->refit_flags, 0, sizeof(int) * (size_t)b->n_int, st));
+                k_restructure<<<g, kThreads, 0, st>>>(b->leaf_box, b->parent, n, b->nodes, b->refit_flags, b->status,
+                                                      b->bin_box);
+            }
+        }
         if (collapse)
-            k_collapse<<<cg, 128, 0, st>>>(b->nodes, b->bin_box, b->leaf_box, b->n_int, b->wnodes);
+            k_collapse<<<cg, 128, 0, st>>>(b->nodes, b->bin_box, b->leaf_box, b->n_int, b->wnodes, b->status);
         else
             k_wide_refit<<<std::min(cg, 1184), 128, 0, st>>>(b->wnodes, b->n_int, b->bin_box, b->leaf_box);
     }
@@ -698,7 +966,7 @@ static int build_topology(grt_bvh* b, const In& in, char* scratch, cudaStream_t 
     return GRT_OK;
 }
 
-static int launch_build(grt_bvh* b, const grt_surfels* s, float alpha_min, bool rebuild_topology,
+static int launch_build(grt_bvh* b, const grt_surfels* s, float alpha_min, bool rebuild_topology, int passes,
                         cudaStream_t st) {
     const int n = b->n;
     if (n == 0) return GRT_OK;
@@ -710,8 +978,20 @@ static int launch_build(grt_bvh* b, const grt_surfels* s, float alpha_min, bool 
         cudaFreeAsync(scratch, st);
         if (rc) return rc;
     }
-    return finish_build(b, in, rebuild_topology, st);
+    return finish_build(b, in, rebuild_topology, passes, st);
 }
+
+// Parameters a tree build reads: alpha_min (the bounds) and build_passes.
+static int check_build_params(const grt_trace_params* p) {
+    if (!p) return set_error(GRT_ERR_ARG, "params is NULL");
+    if (!(p->alpha_min > 0.f && p->alpha_min < 1.f)) return set_error(GRT_ERR_ARG, "alpha_min must be in (0,1)");
+    if (p->build_passes < 0 || p->build_passes > GRT_MAX_BUILD_PASSES)
+        return set_error(GRT_ERR_ARG, "build_passes = %d outside [0, %d]", p->build_passes, GRT_MAX_BUILD_PASSES);
+    return GRT_OK;
+}
+
+// Treelet-restructuring passes of the mesh backend's tree (its build takes no parameters).
+constexpr int kMeshBuildPasses = 1;
 
 static int check_surfels(const grt_surfels* s) {
     if (!s) return set_error(GRT_ERR_ARG, "surfels is NULL");
@@ -755,7 +1035,7 @@ static int noalloc_scratch(void** out) {
     return GRT_OK;
 }
 
-static int launch_build_noalloc(grt_bvh* b, const grt_surfels* s, float alpha_min, cudaStream_t st) {
+static int launch_build_noalloc(grt_bvh* b, const grt_surfels* s, float alpha_min, int passes, cudaStream_t st) {
     const int n = b->n;
     if (n == 0) return GRT_OK;
     static_assert(kNoallocBytes >= build_scratch_bytes(GRT_NOALLOC_MAX_SURFELS), "fixed scratch too small");
@@ -765,7 +1045,7 @@ static int launch_build_noalloc(grt_bvh* b, const grt_surfels* s, float alpha_mi
     SurfelIn in{s->mu, s->quat, s->scale, s->opacity, n, alpha_min};
     rc = build_topology(b, in, scratch, st);
     if (rc) return rc;
-    return finish_build(b, in, true, st);
+    return finish_build(b, in, true, passes, st);
 }
 
 }  // namespace grt
@@ -777,7 +1057,8 @@ extern "C" int grt_rebuild_bvh_noalloc(grt_bvh* b, const grt_surfels* s, const g
     if (!b) return set_error(GRT_ERR_ARG, "bvh is NULL");
     int rc = check_surfels(s);
     if (rc) return rc;
-    if (!params) return set_error(GRT_ERR_ARG, "params is NULL");
+    rc = check_build_params(params);
+    if (rc) return rc;
     if (s->n != b->n) return set_error(GRT_ERR_ARG, "rebuild with n=%d but the BVH holds %d surfels", s->n, b->n);
     if (s->n > GRT_NOALLOC_MAX_SURFELS)
         return set_error(GRT_ERR_ARG, "grt_rebuild_bvh_noalloc: n = %d exceeds its fixed scratch for %d surfels",
@@ -788,7 +1069,7 @@ extern "C" int grt_rebuild_bvh_noalloc(grt_bvh* b, const grt_surfels* s, const g
     if (dev != b->device)
         return set_error(GRT_ERR_ARG, "grt_rebuild_bvh_noalloc: device %d is current, the BVH lives on device %d", dev,
                          b->device);
-    return launch_build_noalloc(b, s, params->alpha_min, (cudaStream_t)stream);
+    return launch_build_noalloc(b, s, params->alpha_min, params->build_passes, (cudaStream_t)stream);
 }
 
 // Device storage of a tree over n leaves (one allocation); NULL on failure.
@@ -841,14 +1122,13 @@ extern "C" int grt_build_bvh(const grt_surfels* s, const grt_trace_params* param
     *out = nullptr;
     int rc = check_surfels(s);
     if (rc) return rc;
-    if (!params) return set_error(GRT_ERR_ARG, "params is NULL");
-    if (!(params->alpha_min > 0.f && params->alpha_min < 1.f))
-        return set_error(GRT_ERR_ARG, "alpha_min must be in (0,1)");
+    rc = check_build_params(params);
+    if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     grt_bvh* b = alloc_bvh(s->n, st, &rc);
     if (!b) return rc;
     char* base = (char*)b->base;
-    rc = launch_build(b, s, params->alpha_min, true, st);
+    rc = launch_build(b, s, params->alpha_min, true, params->build_passes, st);
     if (rc) {
         cudaStreamSynchronize(st);
         cudaFree(base);
@@ -878,7 +1158,7 @@ extern "C" int grt_build_mesh_bvh(const grt_mesh* m, grt_bvh** out, void* stream
         if (e == cudaSuccess) {
             rc = build_topology(b, in, scratch, st);
             cudaFreeAsync(scratch, st);
-            if (!rc) rc = finish_build(b, in, true, st);
+            if (!rc) rc = finish_build(b, in, true, kMeshBuildPasses, st);
         } else {
             rc = check_cuda(e, "cudaMallocAsync");
         }
@@ -897,18 +1177,20 @@ extern "C" int grt_refit_bvh(grt_bvh* b, const grt_surfels* s, const grt_trace_p
     if (!b) return set_error(GRT_ERR_ARG, "bvh is NULL");
     int rc = check_surfels(s);
     if (rc) return rc;
-    if (!params) return set_error(GRT_ERR_ARG, "params is NULL");
+    rc = check_build_params(params);
+    if (rc) return rc;
     if (s->n != b->n) return set_error(GRT_ERR_ARG, "refit with n=%d but the BVH holds %d surfels", s->n, b->n);
-    return launch_build(b, s, params->alpha_min, false, (cudaStream_t)stream);
+    return launch_build(b, s, params->alpha_min, false, 0, (cudaStream_t)stream);
 }
 
 extern "C" int grt_rebuild_bvh(grt_bvh* b, const grt_surfels* s, const grt_trace_params* params, void* stream) {
     if (!b) return set_error(GRT_ERR_ARG, "bvh is NULL");
     int rc = check_surfels(s);
     if (rc) return rc;
-    if (!params) return set_error(GRT_ERR_ARG, "params is NULL");
+    rc = check_build_params(params);
+    if (rc) return rc;
     if (s->n != b->n) return set_error(GRT_ERR_ARG, "rebuild with n=%d but the BVH holds %d surfels", s->n, b->n);
-    return launch_build(b, s, params->alpha_min, true, (cudaStream_t)stream);
+    return launch_build(b, s, params->alpha_min, true, params->build_passes, (cudaStream_t)stream);
 }
 
 extern "C" void grt_bvh_destroy(grt_bvh* b) {

@@ -18,6 +18,8 @@ inline int check_params(const grt_trace_params* p) {
     if (!(p->eps_nd >= 0.f)) return set_error(GRT_ERR_ARG, "eps_nd must be >= 0");
     if (p->k != 4 && p->k != 8 && p->k != 16 && p->k != 32)
         return set_error(GRT_ERR_UNSUPPORTED, "k = %d; built sizes are 4, 8, 16, 32", p->k);
+    if (p->build_passes < 0 || p->build_passes > GRT_MAX_BUILD_PASSES)
+        return set_error(GRT_ERR_ARG, "build_passes = %d outside [0, %d]", p->build_passes, GRT_MAX_BUILD_PASSES);
     return GRT_OK;
 }
 

@@ -38,6 +38,17 @@ def test_bad_params_rejected_without_gpu():
     assert lib.grt_env_tables_bytes(0, 256) == 0
 
 
+def test_build_passes_checked_without_gpu():
+    lib = _lib.load()
+    s = _lib.Surfels(0, 3)
+    out = ctypes.c_void_p()
+    for bad in (-1, _lib.GRT_MAX_BUILD_PASSES + 1):
+        p = _lib.TraceParams(1 / 255, 0.99, 0.01, 3e38, 1e-4, 1e-6, 16, bad)
+        assert lib.grt_build_bvh(ctypes.byref(s), ctypes.byref(p), ctypes.byref(out), None) == _lib.GRT_ERR_ARG
+        assert b"build_passes" in lib.grt_last_error()
+        assert not out.value
+
+
 def test_saved_record_size_and_checks_without_gpu():
     lib = _lib.load()
     smp = _lib.Sampling(8, 4, 4, 1, 7)

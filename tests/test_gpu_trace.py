@@ -57,6 +57,35 @@ def test_results_do_not_depend_on_k(k):
         assert torch.equal(a, b)
 
 
+def test_results_do_not_depend_on_treelet_restructuring():
+    # the restructured trees hold the same surfels under another topology: hit lists and
+    # radiance are bit-identical, only the node visits change
+    sc = wl.scene_objects(30000, seed=7)
+    rng = np.random.default_rng(8)
+    o, d = random_rays(rng, 4096, -2.0, 2.0, 1.5)
+    to, td = t(o), t(d)
+    scenes = [scene_gpu(sc, build_passes=p) for p in (0, 1, 3)]
+    base = api.trace_forward(scenes[0], to, td, max_hits=64)
+    visits = []
+    for S in scenes:
+        got = api.trace_forward(S, to, td, max_hits=64)
+        for a, b in zip(base, got):
+            assert torch.equal(a, b)
+        visits.append(int(api.trace_count(S, to, td)[0]))
+        assert S.status() == 0
+    assert visits[1] < visits[0] and visits[2] <= visits[1]
+    # a rebuild after moving every surfel restructures again: same results as a fresh
+    # plain build of the moved scene
+    shift = torch.tensor([0.05, -0.02, 0.03], device="cuda")
+    for S in scenes:
+        S.mu.add_(shift)
+        S.rebuild()
+    moved = api.trace_forward(scenes[0], to, td, max_hits=64)
+    for S in scenes[1:]:
+        for a, b in zip(moved, api.trace_forward(S, to, td, max_hits=64)):
+            assert torch.equal(a, b)
+
+
 def test_deep_rays_need_several_rounds():
     # 40 stacked faint surfels: k=4 needs many rounds, result identical to the oracle.
     sc = hand_scene([dict(mu=(0, 0, 0.05 * i), scale=(0.5, 0.5), opacity=0.2, color=(i / 40, 1 - i / 40, 0.5))
