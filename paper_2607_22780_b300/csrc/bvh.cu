@@ -573,6 +573,13 @@ __device__ void restructure_treelet(int R, const float* __restrict__ leaf_box, i
     int ref = 0;
     float bx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int inner = R;
+    // a lane whose treelet leaf is a binary node holds that node's children (boxes, refs),
+    // loaded as soon as the leaf appears: an expansion then shuffles them from the lane
+    // instead of waiting for a dependent load
+    float nb[12];
+    int ncl = 0, ncr = 0;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) nb[c] = 0.f;
     {
         float cb[12];
         int cl, cr;
@@ -585,6 +592,7 @@ __device__ void restructure_treelet(int R, const float* __restrict__ leaf_box, i
             ref = lane == 0 ? cl : cr;
 #pragma unroll
             for (int c = 0; c < 6; ++c) bx[c] = lane == 0 ? cb[c] : cb[6 + c];
+            if (ref >= 0) load_node(ref, nb, &ncl, &ncr);
         }
     }
     int nt = 2;
@@ -596,8 +604,9 @@ __device__ void restructure_treelet(int R, const float* __restrict__ leaf_box, i
         if (key < 0.f) break;  // every treelet leaf is a surfel
         const int x = __shfl_sync(0xffffffffu, ref, best);
         float cb[12];
-        int cl, cr;
-        load_node(x, cb, &cl, &cr);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) cb[c] = __shfl_sync(0xffffffffu, nb[c], best);
+        const int cl = __shfl_sync(0xffffffffu, ncl, best), cr = __shfl_sync(0xffffffffu, ncr, best);
         if (bad(cl) || bad(cr)) {
             if (lane == 0) atomicOr(status, GRT_STATUS_BAD_TREE);
             return;
@@ -609,6 +618,7 @@ __device__ void restructure_treelet(int R, const float* __restrict__ leaf_box, i
             ref = side ? cr : cl;
 #pragma unroll
             for (int c = 0; c < 6; ++c) bx[c] = side ? cb[6 + c] : cb[c];
+            if (ref >= 0) load_node(ref, nb, &ncl, &ncr);
         }
         ++nt;
     }
