@@ -540,19 +540,6 @@ __constant__ unsigned char c_pair_b[36] = {1, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6
                                            6, 7, 8, 4, 5, 6, 7, 8, 5, 6, 7, 8, 6, 7, 8, 7, 8, 8};
 static_assert(kTreelet == 9, "the pair table enumerates the pairs of 9 treelet leaves");
 
-// Argmax (argmin with negated keys) of (key, index) over the warp; ties go to the lower index.
-__device__ __forceinline__ void warp_argmax(float& key, int& idx) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ok = __shfl_xor_sync(0xffffffffu, key, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (ok > key || (ok == key && oi < idx)) {
-            key = ok;
-            idx = oi;
-        }
-    }
-}
-
 // One treelet at root R, processed by the whole warp (R the same on every lane).  Lane k
 // holds treelet leaf k (its ref, box, leaf count) and, during the agglomeration, cluster
 // k; lane m records merge m; lane k holds the treelet's internal index inner[k].
@@ -598,10 +585,14 @@ __device__ void restructure_treelet(int R, const float* __restrict__ leaf_box, i
     int nt = 2;
     float cost_old = 0.f;
     for (int it = 0; it < kTreelet - 2; ++it) {
-        float key = (lane < nt && ref >= 0) ? half_area(bx) : -1.f;
-        int best = lane;
-        warp_argmax(key, best);
-        if (key < 0.f) break;  // every treelet leaf is a surfel
+        // the largest area among the treelet's binary-node leaves, ties to the lower lane:
+        // one max reduction over (area bits with the low 5 replaced by 31 - lane); 0 = none
+        const float area = half_area(bx);
+        const unsigned mine = (lane < nt && ref >= 0) ? ((__float_as_uint(fmaxf(area, 0.f)) & ~31u) | (31u - lane)) : 0u;
+        const unsigned top = __reduce_max_sync(0xffffffffu, mine);
+        if (top == 0u) break;  // every treelet leaf is a surfel
+        const int best = 31 - (int)(top & 31u);
+        const float key = __shfl_sync(0xffffffffu, area, best);
         const int x = __shfl_sync(0xffffffffu, ref, best);
         float cb[12];
 #pragma unroll
@@ -638,34 +629,30 @@ __device__ void restructure_treelet(int R, const float* __restrict__ leaf_box, i
     const int pa0 = c_pair_a[lane], pb0 = c_pair_b[lane];
     const int p1 = lane + 32 < 36 ? lane + 32 : 35;
     const int pa1 = c_pair_a[p1], pb1 = c_pair_b[p1];
-    for (int m = 0; m < nt - 1; ++m) {
-        float d0 = 3.4e38f, d1 = 3.4e38f;
-        {
-            float lo[3], hi[3];
+    // union area of a lane's pair from the two clusters' boxes (shuffled from their lanes);
+    // a pair keeps its value until one of its clusters changes
+    auto pair_area = [&](int pa_, int pb_) {
+        float lo[3], hi[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                lo[c] = fminf(__shfl_sync(0xffffffffu, bx[c], pa0), __shfl_sync(0xffffffffu, bx[c], pb0));
-                hi[c] = fmaxf(__shfl_sync(0xffffffffu, bx[3 + c], pa0), __shfl_sync(0xffffffffu, bx[3 + c], pb0));
-            }
-            if ((active >> pa0) & (active >> pb0) & 1u) {
-                const float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
-                d0 = dx * dy + dy * dz + dz * dx;
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                lo[c] = fminf(__shfl_sync(0xffffffffu, bx[c], pa1), __shfl_sync(0xffffffffu, bx[c], pb1));
-                hi[c] = fmaxf(__shfl_sync(0xffffffffu, bx[3 + c], pa1), __shfl_sync(0xffffffffu, bx[3 + c], pb1));
-            }
-            if (lane + 32 < 36 && ((active >> pa1) & (active >> pb1) & 1u)) {
-                const float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
-                d1 = dx * dy + dy * dz + dz * dx;
-            }
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fminf(__shfl_sync(0xffffffffu, bx[c], pa_), __shfl_sync(0xffffffffu, bx[c], pb_));
+            hi[c] = fmaxf(__shfl_sync(0xffffffffu, bx[3 + c], pa_), __shfl_sync(0xffffffffu, bx[3 + c], pb_));
         }
-        float key = -fminf(d0, d1);
-        int pidx = d0 <= d1 ? lane : lane + 32;
-        warp_argmax(key, pidx);
-        const float bd = -key;
+        const float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        return dx * dy + dy * dz + dz * dx;
+    };
+    float d0 = pair_area(pa0, pb0), d1 = pair_area(pa1, pb1);
+    for (int m = 0; m < nt - 1; ++m) {
+        // smallest union area over the live pairs, ties to the lower pair index: one min
+        // reduction over (area bits with the low 6 replaced by the pair index)
+        const bool live0 = (active >> pa0) & (active >> pb0) & 1u;
+        const bool live1 = lane + 32 < 36 && ((active >> pa1) & (active >> pb1) & 1u);
+        const unsigned k0 = live0 ? ((__float_as_uint(d0) & ~63u) | (unsigned)lane) : 0xFFFFFFFFu;
+        const unsigned k1 = live1 ? ((__float_as_uint(d1) & ~63u) | (unsigned)(lane + 32)) : 0xFFFFFFFFu;
+        const unsigned low = __reduce_min_sync(0xffffffffu, min(k0, k1));
+        const int pidx = (int)(low & 63u);
         const int pa = c_pair_a[pidx], pb = c_pair_b[pidx];
+        const float bd = __shfl_sync(0xffffffffu, pidx < 32 ? d0 : d1, pidx & 31);
         float ub[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -689,6 +676,26 @@ __device__ void restructure_treelet(int R, const float* __restrict__ leaf_box, i
         }
         active &= ~(1u << pb);
         if (m != nt - 2) cost_new += bd;
+        // the pairs with cluster pa: union of its new box (ub, on every lane) and the partner's
+        if (m + 1 < nt - 1) {
+            const int q0 = pa0 == pa ? pb0 : pa0, q1 = pa1 == pa ? pb1 : pa1;
+            float lo0[3], hi0[3], lo1[3], hi1[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lo0[c] = fminf(ub[c], __shfl_sync(0xffffffffu, bx[c], q0));
+                hi0[c] = fmaxf(ub[3 + c], __shfl_sync(0xffffffffu, bx[3 + c], q0));
+                lo1[c] = fminf(ub[c], __shfl_sync(0xffffffffu, bx[c], q1));
+                hi1[c] = fmaxf(ub[3 + c], __shfl_sync(0xffffffffu, bx[3 + c], q1));
+            }
+            if (pa0 == pa || pb0 == pa) {
+                const float dx = hi0[0] - lo0[0], dy = hi0[1] - lo0[1], dz = hi0[2] - lo0[2];
+                d0 = dx * dy + dy * dz + dz * dx;
+            }
+            if (pa1 == pa || pb1 == pa) {
+                const float dx = hi1[0] - lo1[0], dy = hi1[1] - lo1[1], dz = hi1[2] - lo1[2];
+                d1 = dx * dy + dy * dz + dz * dx;
+            }
+        }
     }
     if (!(cost_new < cost_old * 0.9999f)) return;
     // lane m < nt - 1 writes merge m's node
