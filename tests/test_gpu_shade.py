@@ -36,6 +36,39 @@ def test_gbuffer_matches_oracle_c1():
         assert np.all(err < gbuffer_tolerance(k, ref["depth"][v])), k
 
 
+def test_gbuffer_deep_stack_does_not_depend_on_k():
+    # 60 faint surfels stacked in front of the camera: a covered pixel composites all 60
+    # hits, 15 rounds at k = 4 and 2 at k = 32; the outputs are the same bit for bit, and the
+    # oracle's
+    from tests._handmade import scene as hand_scene
+    rng = np.random.default_rng(11)
+    sc = hand_scene([dict(mu=(0.02 * rng.standard_normal(), 0.02 * rng.standard_normal(), -0.6 + 0.02 * i),
+                          scale=(0.8, 0.8), opacity=0.12, color=(0.5, 0.5, 0.5),
+                          albedo=tuple(rng.uniform(0.1, 0.9, 3)), rough=float(rng.uniform(0.1, 0.9)),
+                          metal=float(i % 2)) for i in range(60)])
+    cam = wl.Camera(eye=(0.0, 0.0, 3.0), target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0), tan_half_fovy=0.3,
+                    width=40, height=32)
+    outs = {}
+    for k in (4, 8, 16, 32):
+        S = scene_gpu(sc, k=k)
+        g = api.gbuffer_primary(S, cam)
+        outs[k] = {f: getattr(g, f).cpu().numpy() for f in ("pos", "normal", "albedo", "rough", "metal", "alpha",
+                                                           "depth", "valid")}
+        assert S.status() == 0
+    assert outs[32]["valid"].sum() > 300
+    for k in (4, 8, 16):
+        for f, a in outs[k].items():
+            assert np.array_equal(a, outs[32][f]), (k, f)
+    ref = oracle.gbuffer(sc, cam)
+    m = unflagged(ref["flags"])
+    assert np.array_equal(outs[4]["valid"][m], ref["valid"][m])
+    v = m & (ref["valid"] == 1)
+    assert v.sum() > 300
+    for f in ("pos", "normal", "albedo", "rough", "metal", "alpha", "depth"):
+        err = np.abs(outs[4][f][v] - ref[f][v]).reshape(int(v.sum()), -1).max(1)
+        assert np.all(err < gbuffer_tolerance(f, ref["depth"][v])), f
+
+
 def test_shade_c1_cosine_lambert():
     # 64x64 G-buffer, 4 cosine rays per pixel, constant white map, Lambert.
     sc = wl.scene_sphere_plane(8000, seed=2607)
