@@ -86,6 +86,23 @@ def test_results_do_not_depend_on_treelet_restructuring():
             assert torch.equal(a, b)
 
 
+def test_restructuring_on_tiny_and_degenerate_trees():
+    # trees of 1 to 17 surfels, and 40 surfels sharing one centre and one box (every union
+    # area ties): four restructuring passes change no result and leave the tree sound
+    rng = np.random.default_rng(12)
+    o, d = random_rays(rng, 512, -1.5, 1.5, 0.5)
+    to, td = t(o), t(d)
+    scenes = [hand_scene([dict(mu=tuple(rng.uniform(-0.5, 0.5, 3)), scale=(0.3, 0.2), opacity=0.6,
+                               color=tuple(rng.uniform(0, 1, 3))) for _ in range(n)]) for n in (1, 2, 3, 4, 5, 9, 17)]
+    scenes.append(hand_scene([dict(mu=(0.0, 0.0, 0.0), scale=(0.3, 0.3), opacity=0.3,
+                                   color=(i / 40, 1 - i / 40, 0.5)) for i in range(40)]))
+    for sc in scenes:
+        S0, S4 = scene_gpu(sc, build_passes=0), scene_gpu(sc, build_passes=4)
+        for a, b in zip(api.trace_forward(S0, to, td, max_hits=64), api.trace_forward(S4, to, td, max_hits=64)):
+            assert torch.equal(a, b)
+        assert S0.status() == 0 and S4.status() == 0
+
+
 def test_deep_rays_need_several_rounds():
     # 40 stacked faint surfels: k=4 needs many rounds, result identical to the oracle.
     sc = hand_scene([dict(mu=(0, 0, 0.05 * i), scale=(0.5, 0.5), opacity=0.2, color=(i / 40, 1 - i / 40, 0.5))
