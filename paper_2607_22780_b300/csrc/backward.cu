@@ -295,10 +295,11 @@ struct AdjointTask {
     const JobTable<1>* T;
     const float4 *dirs, *res, *adj;
     GradPtrs g;
-    const long long* list;  // rays to walk (those the replay could not take), or all rays
+    const long long* list;  // record rows to walk (rays the replay could not take), or NULL: all rays
     const SavedHits* sv;    // with a list: their records, replayed before the walk resumes
     __device__ __forceinline__ bool begin(long long i, WalkState<K>& ts, Visitor& av, const DevBvh*& bvh) {
-        const long long r = list ? __ldg(list + i) : i;
+        const long long row = list ? __ldg(list + i) : i;
+        const long long r = (list && sv->order) ? (long long)__ldg(sv->order + row) : row;
         float4 a = __ldg(adj + r);
         if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f) return false;
         const ShadeJob& J = T->job[0];
@@ -315,7 +316,7 @@ struct AdjointTask {
         float Tb = 1.f, tau = 0.f;
         int id = 0;
         for (int k = 0; k < sv->L; ++k) {
-            const size_t j = (size_t)k * sv->R + r;
+            const size_t j = (size_t)k * sv->R + row;
             id = __ldg(sv->ids + j);
             tau = __ldg(sv->tau + j);
             const float alpha = __ldg(sv->alpha + j);
@@ -335,16 +336,15 @@ struct AdjointTask {
 // Replay of the saved hit records: one thread per ray walks its (id, tau, alpha) list in
 // compositing order, rebuilding T_k exactly as the forward compositor did.  The first
 // ov_cap threads take the rays that hold an overflow slot (more than L hits), so that the
-// longest lists start first and do not trail the launch; the other threads take every
-// ray with at most L hits.  Rays longer than the record and its overflow slot, and rays
-// that found no slot free, are listed for the traced adjoint walk.
-#ifndef GRT_REPLAY_ORDER
-#define GRT_REPLAY_ORDER 1
-#endif
-__device__ __forceinline__ void replay_hit(const SavedHits& sv, long long r, int slot, int k, int* id, float* tau,
+// longest lists start first and do not trail the launch; the other threads take the record
+// rows in order, i.e. the rays in the forward walk's coherent order, so that a warp reads
+// neighbouring words of the record and meets the same surfels.  Rays longer than the
+// record and its overflow slot, and rays that found no slot free, are listed (by row) for
+// the traced adjoint walk.
+__device__ __forceinline__ void replay_hit(const SavedHits& sv, long long row, int slot, int k, int* id, float* tau,
                                            float* alpha) {
     if (k < sv.L) {
-        const size_t i = (size_t)k * sv.R + r;
+        const size_t i = (size_t)k * sv.R + row;
         *id = __ldg(sv.ids + i);
         *tau = __ldg(sv.tau + i);
         *alpha = __ldg(sv.alpha + i);
@@ -364,22 +364,22 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_replay(const __grid_c
                                                                   unsigned long long* __restrict__ over_count,
                                                                   long long* __restrict__ over_list) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long r;
+    long long row;  // record row = walk position
     int slot = -1;
     if (t < sv.ov_cap) {
         const unsigned used = *sv.ov_count;
         if (t >= (long long)(used < (unsigned)sv.ov_cap ? used : (unsigned)sv.ov_cap)) return;
         slot = (int)t;
-        r = __ldg(sv.ov_ray + slot);
-        if ((unsigned long long)r >= (unsigned long long)T.total_rays) {
+        row = __ldg(sv.ov_ray + slot);
+        if ((unsigned long long)row >= (unsigned long long)T.total_rays) {
             atomicOr(T.job[0].bvh.status, GRT_STATUS_BAD_INDEX);
             return;
         }
     } else {
-        r = t - sv.ov_cap;
-        if (r >= T.total_rays) return;
-        if (GRT_REPLAY_ORDER && sv.order) r = __ldg(sv.order + r);  // the forward's coherent ray order
+        row = t - sv.ov_cap;
+        if (row >= T.total_rays) return;
     }
+    const long long r = sv.order ? (long long)__ldg(sv.order + row) : row;  // the ray's slot
     const int raw = __ldg(sv.nh + r);
     const int n = raw & (kNoSlot - 1);
     if (n == 0) return;
@@ -387,11 +387,11 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_replay(const __grid_c
     if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f) return;
     if (n > sv.L) {
         if (slot < 0) {  // a long ray: its slot thread takes it, or, without a slot, the walk
-            if (raw & kNoSlot) over_list[atomicAdd(over_count, 1ull)] = r;
+            if (raw & kNoSlot) over_list[atomicAdd(over_count, 1ull)] = row;
             return;
         }
         if (n > sv.L + kOverflowHits) {  // longer than record and slot: left to the walk
-            over_list[atomicAdd(over_count, 1ull)] = r;
+            over_list[atomicAdd(over_count, 1ull)] = row;
             return;
         }
     }
@@ -404,11 +404,11 @@ __global__ void __launch_bounds__(kShadeThreads) k_adjoint_replay(const __grid_c
     // the next hit's record is loaded while the current one is composited
     int id;
     float tau, alpha;
-    replay_hit(sv, r, slot, 0, &id, &tau, &alpha);
+    replay_hit(sv, row, slot, 0, &id, &tau, &alpha);
     for (int k = 0; k < n; ++k) {
         int idn = 0;
         float taun = 0.f, alphan = 0.f;
-        if (k + 1 < n) replay_hit(sv, r, slot, k + 1, &idn, &taun, &alphan);
+        if (k + 1 < n) replay_hit(sv, row, slot, k + 1, &idn, &taun, &alphan);
         if ((unsigned)id >= (unsigned)ns) {
             atomicOr(J.bvh.status, GRT_STATUS_BAD_INDEX);
             return;

@@ -13,6 +13,9 @@
 // whatever K and the tree shape are.
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include "grt_internal.cuh"
 
 namespace grt {
@@ -773,6 +776,12 @@ constexpr size_t walk_smem_bytes() {
     return (size_t)K * (sizeof(uint64_t) + sizeof(float)) * kPersistentThreads;
 }
 
+// A task with a `pos` member learns each ray's position in the walk order before begin().
+template <class T, class = void>
+struct wants_pos : std::false_type {};
+template <class T>
+struct wants_pos<T, std::void_t<decltype(std::declval<T&>().pos)>> : std::true_type {};
+
 template <int K, class Task>
 __device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& P, unsigned long long* next,
                                                  long long total, int* q, int qstride,
@@ -811,6 +820,7 @@ __device__ __forceinline__ void persistent_trace(Task& task, const TraceParams& 
                 long long r = (long long)base + __popc(idle & lt);
                 if (r < total) {
                     ray = order ? (long long)__ldg(order + r) : r;
+                    if constexpr (wants_pos<Task>::value) task.pos = r;
                     act = task.begin(ray, ts, vis, bvh);
                     nq = 0;
                 }

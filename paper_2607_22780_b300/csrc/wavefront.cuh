@@ -420,7 +420,7 @@ struct SavedHits {
     float* ov_alpha;
     unsigned* ov_count;
     int ov_cap;
-    unsigned* order;  // the forward walk's ray order (the replay takes rays in it), or NULL
+    unsigned* order;  // the forward walk's ray order: record row p is ray order[p] (NULL: row = ray)
 };
 
 // Overflow slots of a record over R rays: one ray in 256, at least 64 (0 without a record).
@@ -515,13 +515,17 @@ inline int saved_buffers(const void* saved, size_t saved_bytes, int32_t n_pixels
 
 // Radiance visitor that also writes the composited hits of its ray into the record: the
 // first L in place, the next kOverflowHits in an overflow slot taken at hit L.
+// The record's rows follow the walk order: hit k of the ray at walk position p sits at
+// k * R + p, so that the lanes of a warp, which walk neighbouring positions, write (and the
+// replay, taking positions in order, reads) neighbouring words.  Overflow slots name the
+// position too; the ray's slot is order[p].
 struct SavingVisitor : RadianceVisitor {
     const SavedHits* sv;
-    long long r;
-    int slot;  // overflow slot, -1 until hit L (and when none was left)
+    long long r;  // the ray's position in the walk order (its record row)
+    int slot;     // overflow slot, -1 until hit L (and when none was left)
     __device__ __forceinline__ SavingVisitor() {}
-    __device__ __forceinline__ SavingVisitor(const float* col, int cd, f3 dir, const SavedHits* s, long long ray)
-        : RadianceVisitor(col, cd, dir), sv(s), r(ray), slot(-1) {}
+    __device__ __forceinline__ SavingVisitor(const float* col, int cd, f3 dir, const SavedHits* s, long long pos)
+        : RadianceVisitor(col, cd, dir), sv(s), r(pos), slot(-1) {}
     __device__ __forceinline__ void composite(int k, int id, float tau, float alpha, float Tb) {
         RadianceVisitor::composite(k, id, tau, alpha, Tb);
         record(k, id, tau, alpha);
@@ -556,6 +560,7 @@ struct ShadeTraceSave {
     const float4* dirs;
     float4* res;
     const SavedHits* sv;
+    long long pos = 0;  // walk position of the ray begin() takes (set by the walk)
     __device__ __forceinline__ bool begin(long long r, WalkState<K>& ts, Visitor& cv, const DevBvh*& bvh) {
         float4 dw = __ldg(dirs + r);
         if (dw.w == 0.f) {
@@ -571,7 +576,7 @@ struct ShadeTraceSave {
         f3 d = mk3(dw.x, dw.y, dw.z);
         bvh = &J.bvh;
         trace_begin(J.bvh, ts, o, d, T->P);
-        cv = SavingVisitor(J.color, J.cdim, d, sv, r);
+        cv = SavingVisitor(J.color, J.cdim, d, sv, pos);
         return true;
     }
     __device__ __forceinline__ void end(long long r, const WalkState<K>& ts, Visitor& cv) {
