@@ -18,6 +18,7 @@ GRT_MAX_BATCH = 48
 GRT_NOALLOC_MAX_SURFELS = 524288
 GRT_MAX_SAVED_HITS = 64
 GRT_MAX_BUILD_PASSES = 4
+GRT_GBUFFER_SMALL_FRAME = 1 << 20
 GRT_DENOISE_MAX_RADIUS = 8
 STATUS_STACK_OVERFLOW = 1
 STATUS_NONFINITE = 2
@@ -34,7 +35,7 @@ class Surfels(C.Structure):
 
 class TraceParams(C.Structure):
     _fields_ = [(k, C.c_float) for k in ("alpha_min", "alpha_max", "t_min", "t_max", "T_min", "eps_nd")] + \
-        [("k", C.c_int32), ("build_passes", C.c_int32)]
+        [("k", C.c_int32), ("build_passes", C.c_int32), ("gbuffer_k", C.c_int32)]
 
 
 class BvhInfo(C.Structure):

@@ -14,14 +14,14 @@ import torch
 from . import _lib as L
 
 DEFAULT_PARAMS = dict(alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=0.01, t_max=3.0e38, T_min=1e-4,
-                      eps_nd=1e-6, k=16, build_passes=1)
+                      eps_nd=1e-6, k=16, build_passes=1, gbuffer_k=0)
 
 
 def trace_params(**kw) -> L.TraceParams:
     p = dict(DEFAULT_PARAMS)
     p.update({k: v for k, v in kw.items() if v is not None})
     return L.TraceParams(*[float(p[k]) for k in ("alpha_min", "alpha_max", "t_min", "t_max", "T_min", "eps_nd")],
-                         int(p["k"]), int(p["build_passes"]))
+                         int(p["k"]), int(p["build_passes"]), int(p["gbuffer_k"]))
 
 
 def _stream(stream=None) -> int:

@@ -20,6 +20,9 @@ inline int check_params(const grt_trace_params* p) {
         return set_error(GRT_ERR_UNSUPPORTED, "k = %d; built sizes are 4, 8, 16, 32", p->k);
     if (p->build_passes < 0 || p->build_passes > GRT_MAX_BUILD_PASSES)
         return set_error(GRT_ERR_ARG, "build_passes = %d outside [0, %d]", p->build_passes, GRT_MAX_BUILD_PASSES);
+    if (p->gbuffer_k != 0 && p->gbuffer_k != 4 && p->gbuffer_k != 8 && p->gbuffer_k != 16 && p->gbuffer_k != 32)
+        return set_error(GRT_ERR_UNSUPPORTED, "gbuffer_k = %d; 0 (by frame size) or a built size 4, 8, 16, 32",
+                         p->gbuffer_k);
     return GRT_OK;
 }
 

@@ -150,7 +150,9 @@ extern "C" int grt_gbuffer_primary(const grt_bvh* b, const grt_surfels* s, const
     unsigned long long* next = nullptr;
     GRT_CUDA(cudaMallocAsync((void**)&next, sizeof(unsigned long long), st));
     GRT_CUDA(cudaMemsetAsync(next, 0, sizeof(unsigned long long), st));
-    dispatch_k(p->k, [&](auto kc) {
+    // a frame too small to fill the device is bound by its slowest warps: fewer rounds
+    const int k = p->gbuffer_k ? p->gbuffer_k : ((long long)W * H <= GRT_GBUFFER_SMALL_FRAME ? 32 : p->k);
+    dispatch_k(k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
         constexpr size_t smem = walk_smem_bytes<K>();
         const long long grid = persistent_grid(k_gbuffer<K>, smem, gmax);

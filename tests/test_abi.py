@@ -49,6 +49,20 @@ def test_build_passes_checked_without_gpu():
         assert not out.value
 
 
+def test_gbuffer_k_checked_without_gpu():
+    # 0 (chosen by frame size) and the built k-buffer sizes pass; anything else is refused
+    # before a request is read
+    lib = _lib.load()
+    req = (_lib.ShadeRequest * 1)()
+    for bad in (-1, 2, 12, 64):
+        p = _lib.TraceParams(1 / 255, 0.99, 0.01, 3e38, 1e-4, 1e-6, 16, 1, bad)
+        assert lib.grt_shade_batch(req, 1, ctypes.byref(p), None, 0, None) == _lib.GRT_ERR_UNSUPPORTED
+        assert b"gbuffer_k" in lib.grt_last_error()
+    p = _lib.TraceParams(1 / 255, 0.99, 0.01, 3e38, 1e-4, 1e-6, 16, 1, 32)
+    rc = lib.grt_shade_batch(req, 1, ctypes.byref(p), ctypes.c_void_p((1 << 20) + 4), 1 << 20, None)
+    assert rc == _lib.GRT_ERR_ARG and b"aligned" in lib.grt_last_error()  # params accepted
+
+
 def test_saved_record_size_and_checks_without_gpu():
     lib = _lib.load()
     smp = _lib.Sampling(8, 4, 4, 1, 7)

@@ -38,7 +38,7 @@ def test_gbuffer_matches_oracle_c1():
 
 def test_gbuffer_deep_stack_does_not_depend_on_k():
     # 60 faint surfels stacked in front of the camera: a covered pixel composites all 60
-    # hits, 15 rounds at k = 4 and 2 at k = 32; the outputs are the same bit for bit, and the
+    # hits, 15 rounds at gbuffer_k = 4 and 2 at 32; the outputs are the same bit for bit, and the
     # oracle's
     from tests._handmade import scene as hand_scene
     rng = np.random.default_rng(11)
@@ -49,14 +49,14 @@ def test_gbuffer_deep_stack_does_not_depend_on_k():
     cam = wl.Camera(eye=(0.0, 0.0, 3.0), target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0), tan_half_fovy=0.3,
                     width=40, height=32)
     outs = {}
-    for k in (4, 8, 16, 32):
-        S = scene_gpu(sc, k=k)
+    for k in (4, 8, 16, 32, 0):   # gbuffer_k = 0: chosen by frame size
+        S = scene_gpu(sc, k=k or 16, gbuffer_k=k)
         g = api.gbuffer_primary(S, cam)
         outs[k] = {f: getattr(g, f).cpu().numpy() for f in ("pos", "normal", "albedo", "rough", "metal", "alpha",
                                                            "depth", "valid")}
         assert S.status() == 0
     assert outs[32]["valid"].sum() > 300
-    for k in (4, 8, 16):
+    for k in (4, 8, 16, 0):
         for f, a in outs[k].items():
             assert np.array_equal(a, outs[32][f]), (k, f)
     ref = oracle.gbuffer(sc, cam)
