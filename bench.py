@@ -86,13 +86,23 @@ def alg_bytes(cnt, R, alloc, extra_per_hit=0.0, extra_per_ray=0.0):
             (io + extra_per_ray) * R)
 
 
+def floor_bytes(cnt, R, alloc):
+    """The survey's BVH-independent floor of the same launch: a 48-byte record and the
+    colour of every composited hit plus the ray I/O, with no node or missed-record bytes.
+    The composited counts are the counting pass's, which equal the oracle's on every
+    unflagged ray (the hit lists are bit-exact)."""
+    nr = float(sum(alloc))
+    io = (48.0 + 28.0) / nr + 4.0 * alloc[2] / nr
+    return (ALG_REC_BYTES + SH_BYTES) * cnt[2] + io * R
+
+
 def layout_bytes(cnt, R, extra_per_hit=0.0, extra_per_ray=0.0):
     """Bytes the kernel's own node and record layout loads for the same traversal."""
     return (NODE_BYTES * cnt[0] + REC_BYTES * cnt[1] + (SH_BYTES + extra_per_hit) * cnt[2] +
             (RAY_IO_BYTES + extra_per_ray) * R)
 
 
-def roofline(kernel, nbytes, lbytes, t_ms, peak, peak_kind, **extra):
+def roofline(kernel, nbytes, lbytes, t_ms, peak, peak_kind, floor=None, rays=None, **extra):
     ach = nbytes / (t_ms * 1e-3) / 1e9
     lach = lbytes / (t_ms * 1e-3) / 1e9
     out = {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
@@ -100,6 +110,10 @@ def roofline(kernel, nbytes, lbytes, t_ms, peak, peak_kind, **extra):
            "bytes": "survey count: 64 per node visit + 48 per record test + 192 per SH hit + ray I/O",
            "layout": {"bytes_per_launch": lbytes, "achieved": lach, "frac": lach / peak,
                       "bytes": "kernel layout: 112 per 4-wide node visit + 64 per record + 192 per SH hit + 44 per ray"}}
+    if floor is not None:
+        out["floor"] = {"bytes_per_launch": floor, "bytes_per_ray": floor / rays, "survey_over_floor": nbytes / floor,
+                        "ms_at_peak": floor / (peak * 1e9) * 1e3,
+                        "bytes": "BVH-independent floor: (48 + 192) per composited hit + ray I/O"}
     out.update(extra)
     return out
 
@@ -449,6 +463,7 @@ def run_grt(args):
                "gpu_launches": launches_per_step * args.steps,
                "roofline": roofline(
                    "k_trace_rays_ww", alg_bytes(cnt, R, ALLOC), layout_bytes(cnt, R), trace_s * 1e3, peak, peak_kind,
+                   floor=floor_bytes(cnt, R, ALLOC), rays=R,
                    traffic=TRACE_DRAM_BYTES if (args.k == 16 and W_IMG == 800) else None,
                    l2=l2_summary(R, trace_s * 1e3) if args.k == 16 else None,
                    phase_ms={"sample": float(np.mean(ph[:, 0])), "trace": float(np.mean(ph[:, 1])),
@@ -869,7 +884,7 @@ def time_large(api, dev, args):
             "fwd_rays_per_s": R / (res["fwd"] * 1e-3), "fwd_bwd_rays_per_s": R / (res["fwd_bwd"] * 1e-3),
             "trace_kernel_ms": trace_ms, "per_ray": {"nodes": cnt[0] / R, "tests": cnt[1] / R, "composited": cnt[2] / R},
             "roofline_trace": roofline("k_trace_rays_ww", alg_bytes(cnt, R, LARGE_ALLOC), layout_bytes(cnt, R),
-                                       trace_ms, peak, peak_kind),
+                                       trace_ms, peak, peak_kind, floor=floor_bytes(cnt, R, LARGE_ALLOC), rays=R),
             "steps": n, "l2": "inputs larger than L2"}
 
 
