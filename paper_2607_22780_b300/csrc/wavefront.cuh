@@ -156,6 +156,9 @@ inline RayOrder ray_order_bufs(void* base, long long n, unsigned* order = nullpt
     return o;
 }
 
+#ifndef GRT_SAMPLE_REMAP
+#define GRT_SAMPLE_REMAP 1
+#endif
 // ray buffer entry: (direction, 1) for a traced sample, (0, 0, 0, 0) for none; with an
 // order (o.key != nullptr), also the slot's bucket and its rank among the bucket's slots
 template <int CAP>
@@ -163,11 +166,25 @@ __global__ void __launch_bounds__(kShadeThreads) k_sample_rays(const __grid_cons
                                                                float4* __restrict__ dirs,
                                                                RayOrder o = RayOrder{nullptr, nullptr, nullptr,
                                                                                      nullptr}) {
-    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= T.total_rays) return;
-    const int job = T.find_ray(r);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T.total_rays) return;
+    const int job = T.find_ray(t);
     const ShadeJob& J = T.job[job];
-    long long lr = r - J.ray_begin;
+    long long lr = t - J.ray_begin;
+#if GRT_SAMPLE_REMAP
+    // thread -> slot: a complete group of 4 pixels (4 Nr slots, Nr a multiple of 8) is drawn
+    // by warps of 4 pixels x 8 consecutive samples, so that a warp draws from one proposal
+    // when the allocations are multiples of 8 (a pixel's 32 samples in one warp went three
+    // ways: 17 of 32 lanes active); a slot's direction depends only on (pixel, j)
+    if ((J.Nr & 7) == 0) {
+        const long long g = lr / (4 * J.Nr);
+        if ((g + 1) * 4 <= J.n_pixels) {
+            const int u = (int)(lr - g * 4 * J.Nr);
+            lr = g * 4 * J.Nr + (long long)(u & 3) * J.Nr + (((u >> 5) << 3) | ((u & 31) >> 2));
+        }
+    }
+#endif
+    const long long r = J.ray_begin + lr;
     int li = (int)(lr / J.Nr), j = (int)(lr - (long long)li * J.Nr);
     int pix = pixel_of(J, li);
     float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
