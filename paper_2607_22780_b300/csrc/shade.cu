@@ -17,8 +17,14 @@ namespace {
 
 // Eq. 13: a warp unit shades 32/G pixels; lane sub of a pixel group takes samples
 // j = sub + m G in order, the group sums with a butterfly, so the result is fixed.
+// 8 blocks per SM (64 registers, a 24-byte spill): the kernel waits on its ray, G-buffer
+// and texel loads, and 72 registers had left it at 7 blocks (0.552 -> 0.515 ms for 10 M
+// rays on the 300k-surfel 800x800 frame)
+#ifndef GRT_ACC_MIN_BLOCKS
+#define GRT_ACC_MIN_BLOCKS 8
+#endif
 template <int CAP>
-__global__ void __launch_bounds__(kShadeThreads) k_accumulate(const __grid_constant__ JobTable<CAP> T,
+__global__ void __launch_bounds__(kShadeThreads, GRT_ACC_MIN_BLOCKS) k_accumulate(const __grid_constant__ JobTable<CAP> T,
                                                               const float4* __restrict__ dirs,
                                                               const float4* __restrict__ res) {
     long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
