@@ -9,6 +9,7 @@ import ctypes as C
 import dataclasses
 from typing import Optional
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -73,6 +74,24 @@ class Scene:
         self._lib = L.load()
         L.check(self._lib.grt_build_bvh(C.byref(self.surfels()), C.byref(self.params), C.byref(self._bvh),
                                         _stream(stream)))
+
+    FIELDS = ("mu", "quat", "scale", "opacity", "color", "albedo", "rough", "metal")
+
+    def save(self, path):
+        """Write the surfel parameters to a .npz file.  The tree is not stored: Scene.load
+        builds it again from the parameters."""
+        arrays = {f: getattr(self, f).detach().cpu().numpy() for f in self.FIELDS if getattr(self, f) is not None}
+        np.savez(path, **arrays)
+
+    @staticmethod
+    def load(path, device="cuda", params=None) -> "Scene":
+        """A resident scene from a .npz file written by Scene.save (its tree built anew)."""
+        with np.load(path) as z:
+            missing = [f for f in Scene.FIELDS[:5] if f not in z.files]
+            if missing:
+                raise ValueError(f"{path}: no {', '.join(missing)}")
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device)
+            return Scene(*[t(z[f]) if f in z.files else None for f in Scene.FIELDS], params=params)
 
     @staticmethod
     def from_workload(sc, device="cuda", params=None) -> "Scene":

@@ -141,6 +141,25 @@ def test_deterministic_repeat():
         assert torch.equal(x, y)
 
 
+def test_scene_save_and_load_round_trip(tmp_path):
+    # the parameters come back bit for bit, and the tree built anew traces the same hits
+    sc = wl.scene_objects(5000, seed=31)
+    S = scene_gpu(sc)
+    S.save(tmp_path / "scene.npz")
+    R = api.Scene.load(tmp_path / "scene.npz")
+    for f in api.Scene.FIELDS:
+        assert torch.equal(getattr(S, f), getattr(R, f)), f
+    o, d = random_rays(np.random.default_rng(5), 3000)
+    a = api.trace_forward(S, t(o), t(d), max_hits=64)
+    b = api.trace_forward(R, t(o), t(d), max_hits=64)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    assert R.status() == 0
+    np.savez(tmp_path / "partial.npz", mu=sc.mu, quat=sc.quat)
+    with pytest.raises(ValueError):
+        api.Scene.load(tmp_path / "partial.npz")
+
+
 def test_refit_after_moving_surfels():
     sc = wl.scene_sphere_plane(8000, seed=9)
     S = scene_gpu(sc)
