@@ -23,31 +23,51 @@ __device__ __forceinline__ float lum_d(const float* t) {
     return l;
 }
 
+// One warp per row.  The row's luminances arrive 32 at a time (one coalesced load per lane)
+// and are added to the running sum in column order, one explicitly rounded add per column
+// exactly as in the sequential definition: every lane forms the same chain of sums from the
+// shuffled values, and lane k keeps the sum through column k of the chunk.  (A thread per
+// row waited on one dependent texel load per column: 0.31 ms for a 512x256 map.)
 __global__ void k_env_rows(const float* __restrict__ rgb, int W, int H, float* __restrict__ marg,
                            float* __restrict__ cond) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= H) return;
+    const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (r >= H) return;  // whole warps
     float* cr = cond + (size_t)r * (W + 1);
+    if (lane == 0) cr[0] = 0.f;
     float acc = 0.f;
-    cr[0] = 0.f;
-    for (int c = 0; c < W; ++c) {
-        acc = add_d(acc, lum_d(rgb + ((size_t)r * W + c) * 3));
-        cr[c + 1] = acc;
+    for (int c0 = 0; c0 < W; c0 += 32) {
+        const int c = c0 + lane, n = min(32, W - c0);
+        const float l = c < W ? lum_d(rgb + ((size_t)r * W + c) * 3) : 0.f;
+        float mine = 0.f;
+        for (int k = 0; k < n; ++k) {
+            acc = add_d(acc, __shfl_sync(0xffffffffu, l, k));
+            if (lane == k) mine = acc;
+        }
+        if (c < W) cr[c + 1] = mine;
     }
-    for (int c = 1; c <= W; ++c) cr[c] = acc > 0.f ? div_d(cr[c], acc) : div_d((float)c, (float)W);
-    marg[r + 1] = acc;
+    // each lane normalises the entries it wrote
+    for (int c = 1 + lane; c <= W; c += 32) cr[c] = acc > 0.f ? div_d(cr[c], acc) : div_d((float)c, (float)W);
+    if (lane == 0) marg[r + 1] = acc;
 }
 
+// The marginal CDF in row order, by one warp in the same way.
 __global__ void k_env_marg(float* __restrict__ marg, int H) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+    if (lane == 0) marg[0] = 0.f;
     float tot = 0.f;
-    marg[0] = 0.f;
-    for (int r = 1; r <= H; ++r) {
-        tot = add_d(tot, marg[r]);
-        marg[r] = tot;
+    for (int r0 = 1; r0 <= H; r0 += 32) {
+        const int r = r0 + lane, n = min(32, H - r0 + 1);
+        const float v = r <= H ? marg[r] : 0.f;
+        float mine = 0.f;
+        for (int k = 0; k < n; ++k) {
+            tot = add_d(tot, __shfl_sync(0xffffffffu, v, k));
+            if (lane == k) mine = tot;
+        }
+        if (r <= H) marg[r] = mine;
     }
-    for (int r = 1; r <= H; ++r) marg[r] = div_d(marg[r], tot);
-    marg[H + 1] = tot;  // scratch slot past the CDF: total luminance
+    for (int r = 1 + lane; r <= H; r += 32) marg[r] = div_d(marg[r], tot);
+    if (lane == 0) marg[H + 1] = tot;  // scratch slot past the CDF: total luminance
 }
 
 __global__ void k_env_texels(const float* __restrict__ rgb, int W, int H, const float* __restrict__ marg,
@@ -80,7 +100,7 @@ extern "C" int grt_env_prepare(const float* rgb, int32_t W, int32_t H, void* tab
     float* marg = (float*)(base + l.marg);
     float* cond = (float*)(base + l.cond);
     cudaStream_t st = (cudaStream_t)stream;
-    k_env_rows<<<(H + 63) / 64, 64, 0, st>>>(rgb, W, H, marg, cond);
+    k_env_rows<<<(H + 3) / 4, 128, 0, st>>>(rgb, W, H, marg, cond);  // a warp per row
     k_env_marg<<<1, 32, 0, st>>>(marg, H);
     k_env_texels<<<(W * H + 255) / 256, 256, 0, st>>>(rgb, W, H, marg, texel);
     return launch_error("grt_env_prepare");
