@@ -147,7 +147,11 @@ class RelightServer:
     """Resident scenes + continuous batching of relight requests on one GPU."""
 
     def __init__(self, scenes: Dict[str, api.Scene], device="cuda", hbm_budget: int = 8 << 30,
-                 ray_budget: int = 8 << 20, max_batch: int = 16, inflight: int = 4, streams: int = 2):
+                 ray_budget: int = 8 << 20, max_batch: int = 16, inflight: int = 2, streams: int = 2,
+                 order: str = "fifo"):
+        if order not in ("fifo", "srpt"):
+            raise ValueError(f"order must be 'fifo' or 'srpt', got {order!r}")
+        self.order = order    # slices oldest request first, or least remaining work first
         self.scenes = scenes
         self.device = torch.device(device)
         self.hbm_budget = int(hbm_budget)
@@ -173,7 +177,13 @@ class RelightServer:
 
         Launches alternate over `streams` compute streams, so that one launch's kernels start
         while the previous one's persistent walk drains its last rays; a request is complete
-        when every launch holding one of its slices has ended."""
+        when every launch holding one of its slices has ended.  At most `inflight` launches
+        wait on the GPU: a deeper queue delays a new request's first slice behind it.
+
+        Slices go to the oldest request first (order "fifo"), or to the request with the
+        fewest rays left ("srpt"), which lowers the median latency and raises the tail.  The
+        rays/s statistic counts from the end of the warm-up requests, so it holds for "fifo",
+        under which they finish first."""
         dev = self.device
         compute = [torch.cuda.Stream(dev) for _ in range(self.streams)]
         prep = torch.cuda.Stream(dev)
@@ -228,9 +238,11 @@ class RelightServer:
             if len(inflight) >= self.inflight:
                 inflight[0].synchronize()
                 continue
-            # next iteration: FIFO slices up to the ray budget
+            # next iteration: slices up to the ray budget, oldest request first or (srpt) the
+            # request with the fewest rays left first
             batch, budget = [], self.ray_budget
-            for st in active:
+            cand = active if self.order == "fifo" else sorted(active, key=lambda q: (q.P - q.next) * q.req.rays)
+            for st in cand:
                 if len(batch) >= self.max_batch or budget <= 0:
                     break
                 left = st.P - st.next

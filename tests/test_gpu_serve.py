@@ -24,8 +24,11 @@ def _alone(st):
     return api.shade_pixels(st.scene, st.gb, st.env, a[0], a[1], a[2], st.req.seed, brdf=1)
 
 
-def test_batched_equals_alone_with_sliced_mixed_launches():
-    srv = serve.RelightServer(_scenes(), ray_budget=3000, max_batch=4)
+@pytest.mark.parametrize("order", ["fifo", "srpt"])
+def test_batched_equals_alone_with_sliced_mixed_launches(order):
+    # either slice order (oldest request first, or fewest rays left first) only schedules:
+    # every request's image is its run-alone image
+    srv = serve.RelightServer(_scenes(), ray_budget=3000, max_batch=4, order=order)
     trace = _trace()
     out = srv.run_batched(trace, realtime=False)
     assert out["requests"] == len(trace)
