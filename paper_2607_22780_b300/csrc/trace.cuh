@@ -729,7 +729,7 @@ struct ColourVisitor {
 // Generic persistent two-phase walk over a flat list of `total` rays.  Warps stay resident;
 // once kRefill lanes are idle they claim that many rays from *next (a global counter);
 // then the warp alternates (A) internal-node visits with hit leaves queued in shared memory,
-// until every active lane has a leaf queued or has finished its walk, (B) the queued surfel
+// until every active lane has kLeafBatch leaves queued or has finished its walk, (B) the queued surfel
 // tests of all lanes, (C) compositing of finished walks, once kCompositeBatch of them (or
 // all active lanes) are waiting.  Task supplies
 //   bool begin(long long ray, WalkState<K>&, Visitor&, const DevBvh*&)  -- false: no ray
@@ -742,10 +742,10 @@ struct ColourVisitor {
 #define GRT_QUEUE 12
 #endif
 #ifndef GRT_LEAF_BATCH
-#define GRT_LEAF_BATCH 1
+#define GRT_LEAF_BATCH 2
 #endif
 #ifndef GRT_COMPOSITE_BATCH
-#define GRT_COMPOSITE_BATCH 8
+#define GRT_COMPOSITE_BATCH 12
 #endif
 // Scheduling of the walk, measured on the 300k-surfel 800x800 workload (M rays/s):
 // queue 8 / 12 / 16 / 24 leaves: 339 / 364 / 351 / 333; leaf batch 1 / 2 / 4: 339 / 328 /
@@ -754,7 +754,11 @@ struct ColourVisitor {
 // refill at 4 / 8 / 12 idle lanes: 397 / 394 / 385.  With rays in bucket order (coherent
 // warps): queue 12 / 16 / 20 / 24: 424 / 430 / 429 / 427; refill 2 / 4 / 8: 424 / 424 / 421;
 // composite batch 4 / 8 / 12: 417 / 424 / 425; shared stack 8 / 16 / 24 entries: 418 / 424 /
-// 424; at least 3 / 4 / 5 blocks per SM: 377 / 424 / 333.
+// 424; at least 3 / 4 / 5 blocks per SM: 377 / 424 / 333.  On the current walk (k-buffer in
+// shared memory, near cull, restructured tree, 32-byte loads), walk ms with composite batch
+// 4 / 8 / 12 / 16: 12.01 / 11.78 / 11.64 / 11.72; leaf batch 1 / 2 / 3: 11.78 / 11.72 / 11.76;
+// refill at 2 / 4 / 8: 11.78 / 11.78 / 11.82; composite batch 12 with leaf batch 2: 11.57
+// (G-buffer 1.25 -> 1.24 ms, 2M-surfel forward unchanged at 66.7 ms).
 constexpr int kRefill = GRT_REFILL;         // idle lanes that trigger a refill
 constexpr int kQueue = GRT_QUEUE;           // queued leaves per lane
 constexpr int kLeafBatch = GRT_LEAF_BATCH;  // leaves every walking lane queues before the tests
