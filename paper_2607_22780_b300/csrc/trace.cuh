@@ -758,7 +758,9 @@ struct ColourVisitor {
 // shared memory, near cull, restructured tree, 32-byte loads), walk ms with composite batch
 // 4 / 8 / 12 / 16: 12.01 / 11.78 / 11.64 / 11.72; leaf batch 1 / 2 / 3: 11.78 / 11.72 / 11.76;
 // refill at 2 / 4 / 8: 11.78 / 11.78 / 11.82; composite batch 12 with leaf batch 2: 11.57
-// (G-buffer 1.25 -> 1.24 ms, 2M-surfel forward unchanged at 66.7 ms).
+// (G-buffer 1.25 -> 1.24 ms, 2M-surfel forward unchanged at 66.7 ms).  With those: queue
+// 10 / 12 / 14 leaves: 11.81 / 11.53 / 11.92; shared stack 6 / 8 / 12 entries: 11.78 / 11.53 /
+// 11.88; leaf batch 3: 11.59 (2M forward 66.5 ms at the defaults, 67.3-70.1 otherwise).
 constexpr int kRefill = GRT_REFILL;         // idle lanes that trigger a refill
 constexpr int kQueue = GRT_QUEUE;           // queued leaves per lane
 constexpr int kLeafBatch = GRT_LEAF_BATCH;  // leaves every walking lane queues before the tests
