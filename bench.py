@@ -62,7 +62,7 @@ SURFEL_BYTES = 232  # mu 12 + quat 16 + scale 8 + opacity 4 + SH 192, read per r
 GRAD_RMW_BYTES = 464  # the same 232 B of gradients read and written (atomics) per replayed hit
 REPLAY_RAY_BYTES = 64  # per traced ray in the replay: hit count 4, direction 16, origin 12, (c_rt, T) 16, adjoint 16
 RAY_IO_BYTES = 44   # direction 16 + origin 12 read, (c_rt, T) 16 written
-COLLAPSE_LAUNCHES = 1  # the 4-wide collapse is one launch (a thread per binary node)
+COLLAPSE_LAUNCHES = 2  # the collapse's cost pass (bottom-up) and the 4-wide collapse (a thread per binary node)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace_rays_ww launch of the default
 # workload (k = 16, 800x800) from one ncu capture of the current kernel; None until taken
 TRACE_DRAM_BYTES = 1_199_826_688  # 859.3 MB read + 340.5 MB written

@@ -801,9 +801,85 @@ __device__ __forceinline__ void write_slot(float4* W, int s, const float* box, i
 // records, larger ones the wide node of the same index.  Only the nodes reachable from
 // the root (wide node 0 = binary node 0) are ever traversed; the others are built too,
 // since whether a binary node heads a wide node depends on its ancestors' choices.
+// SAH-optimal choice of the 4-wide nodes' children (after the dynamic programme of Ylitie,
+// Karras and Laine 2017 for wide BVHs, with wide node b kept at binary node b).  F(x, j) is the
+// least expected cost of covering binary subtree x with at most j child slots of a wide node:
+// x itself as one slot costs W(x) = A(x) C_node + F*(x), where F*(x) = min over j1 + j2 = 4 of
+// F(l, j1) + F(r, j2) is x's own wide node opening it into up to four slots; a surfel leaf as a
+// slot costs A(leaf) C_test; and F(x, j >= 2) = min(W(x), min over j1 + j2 = j of F(l, j1) +
+// F(r, j2)).  A (the half surface area) is the probability of a ray entering the box.  The
+// costs fill bottom-up with the refit's arrival counters; the collapse then takes wide node
+// b's slots from b's optimal split instead of opening its largest children greedily.
+#ifndef GRT_DP_COLLAPSE
+#define GRT_DP_COLLAPSE 1
+#endif
+#ifndef GRT_DP_CNODE
+#define GRT_DP_CNODE 1.0f
+#endif
+#ifndef GRT_DP_CTEST
+#define GRT_DP_CTEST 1.0f
+#endif
+constexpr float kDpNode = GRT_DP_CNODE, kDpTest = GRT_DP_CTEST;
+
+// F(y, 1), F(y, 2), F(y, 3) of a child ref: a surfel leaf costs its test in any number of slots
+__device__ __forceinline__ void dp_child(int ref, const float* leaf_box, const float4* dpc, float F[3]) {
+    if (ref < 0) {
+        const float a = kDpTest * half_area(leaf_box + 6 * (size_t)(~ref));
+        F[0] = F[1] = F[2] = a;
+    } else {
+        const float* c = reinterpret_cast<const float*>(dpc + ref);
+        F[0] = __ldcg(c);
+        F[1] = __ldcg(c + 1);
+        F[2] = __ldcg(c + 2);
+    }
+}
+
+// Decisions of node x, packed: bits 0-1 the split of F(x, 2), 2-3 of F(x, 3), 4-5 of
+// F(x, 4) (0: x itself, else the left child's slot count j1), 6-7 the split of F*(x).
+__global__ void k_collapse_cost(const float4* __restrict__ bnodes, const float* __restrict__ bin_box,
+                                const float* __restrict__ leaf_box, const int* __restrict__ parent, int n,
+                                int* __restrict__ flags, float4* __restrict__ dpc, unsigned* __restrict__ dpd,
+                                int* status) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int p = parent[j];
+    for (int level = 0; p >= 0; ++level) {
+        if (level > 255 || (p >> 1) >= n - 1) {
+            atomicOr(status, GRT_STATUS_BAD_TREE);
+            return;
+        }
+        const int node = p >> 1;
+        const int up = parent[n + node];
+        // release: this child's costs are visible to the sibling's thread once it sees the
+        // count; acquire: the sibling's costs are visible here once this thread sees it
+        if (atomic_add_acq_rel(flags + node, 1) == 0) return;
+        const float* f = reinterpret_cast<const float*>(bnodes + 4 * (size_t)node);
+        const int l = __float_as_int(__ldcg(f + 12)), r = __float_as_int(__ldcg(f + 13));
+        float L[3], Rr[3];
+        dp_child(l, leaf_box, dpc, L);
+        dp_child(r, leaf_box, dpc, Rr);
+        // F*: four slots inside x's own wide node
+        float fs = L[0] + Rr[2];
+        unsigned ss = 1;
+        if (L[1] + Rr[1] < fs) { fs = L[1] + Rr[1]; ss = 2; }
+        if (L[2] + Rr[0] < fs) { fs = L[2] + Rr[0]; ss = 3; }
+        const float W = kDpNode * half_area(bin_box + 6 * (size_t)node) + fs;
+        // F(x, 2), F(x, 3), F(x, 4): x itself, or x opened into j1 + j2 slots
+        float f2 = W, f3 = W, f4 = W;
+        unsigned d2 = 0, d3 = 0, d4 = 0;
+        if (L[0] + Rr[0] < f2) { f2 = L[0] + Rr[0]; d2 = 1; }
+        if (L[0] + Rr[1] < f3) { f3 = L[0] + Rr[1]; d3 = 1; }
+        if (L[1] + Rr[0] < f3) { f3 = L[1] + Rr[0]; d3 = 2; }
+        if (fs < f4) { f4 = fs; d4 = ss; }
+        __stcg(reinterpret_cast<float4*>(dpc + node), make_float4(W, f2, f3, f4));
+        __stcg(dpd + node, d2 | (d3 << 2) | (d4 << 4) | (ss << 6));
+        p = up;
+    }
+}
+
 __global__ void k_collapse(const float4* __restrict__ bnodes, const float* __restrict__ bin_box,
                            const float* __restrict__ leaf_box, int n_int, float4* __restrict__ wnodes,
-                           int* status) {
+                           int* status, const unsigned* __restrict__ dpd) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_int) return;
     const float* fb = reinterpret_cast<const float*>(bnodes + 4 * (size_t)b);
@@ -817,6 +893,34 @@ __global__ void k_collapse(const float4* __restrict__ bnodes, const float* __res
         atomicOr(status, GRT_STATUS_BAD_TREE);
         nc = 0;
     }
+#if GRT_DP_COLLAPSE
+    if (kLeafMax == 1 && dpd && nc == 2) {
+        // the optimal split of F*(b), each part expanded by its own decisions
+        int st_ref[kWide], st_j[kWide], ns = 0;
+        const unsigned sb = (dpd[b] >> 6) & 3u;
+        st_ref[ns] = cand[1]; st_j[ns++] = kWide - (int)sb;
+        st_ref[ns] = cand[0]; st_j[ns++] = (int)sb;
+        nc = 0;
+        while (ns > 0 && nc < kWide) {
+            --ns;
+            const int y = st_ref[ns], jy = st_j[ns];
+            const unsigned d = (y < 0 || jy <= 1) ? 0u : (dpd[y] >> (2 * (jy - 2))) & 3u;
+            if (d == 0u || jy - (int)d < 1) {
+                cand[nc++] = y;
+                continue;
+            }
+            const float* fy = reinterpret_cast<const float*>(bnodes + 4 * (size_t)y);
+            const int yl = __float_as_int(fy[12]), yr = __float_as_int(fy[13]);
+            if (bad(yl) || bad(yr) || ns + 2 > kWide) {
+                atomicOr(status, GRT_STATUS_BAD_TREE);
+                cand[nc++] = y;
+                continue;
+            }
+            st_ref[ns] = yr; st_j[ns++] = jy - (int)d;
+            st_ref[ns] = yl; st_j[ns++] = (int)d;
+        }
+    } else
+#endif
     for (int rep = 2; rep < kWide && nc > 0; ++rep) {
         int best = -1;
         float ba = -1.f;
@@ -928,8 +1032,17 @@ static int finish_build(grt_bvh* b, const In& in, bool collapse, int passes, cud
                                                       b->bin_box);
             }
         }
+        const unsigned* dpd = nullptr;
+#if GRT_DP_COLLAPSE
+        if (collapse && kLeafMax == 1) {
+            GRT_CUDA(cudaMemsetAsync(b->refit_flags, 0, sizeof(int) * (size_t)b->n_int, st));
+            k_collapse_cost<<<g, kThreads, 0, st>>>(b->nodes, b->bin_box, b->leaf_box, b->parent, n, b->refit_flags,
+                                                    b->dp_cost, b->dp_dec, b->status);
+            dpd = b->dp_dec;
+        }
+#endif
         if (collapse)
-            k_collapse<<<cg, 128, 0, st>>>(b->nodes, b->bin_box, b->leaf_box, b->n_int, b->wnodes, b->status);
+            k_collapse<<<cg, 128, 0, st>>>(b->nodes, b->bin_box, b->leaf_box, b->n_int, b->wnodes, b->status, dpd);
         else
             k_wide_refit<<<std::min(cg, 1184), 128, 0, st>>>(b->wnodes, b->n_int, b->bin_box, b->leaf_box);
     }
@@ -1098,7 +1211,8 @@ static grt_bvh* alloc_bvh(int nleaf, cudaStream_t st, int* rc_out) {
     size_t n = (size_t)nleaf, ni = (size_t)b->n_int;
     size_t bytes = sizeof(float4) * 4 * (ni + n) + sizeof(float4) * n + sizeof(int) * (n + ni + 1) + sizeof(int) * (ni + 1) +
                    sizeof(float) * 6 * n + sizeof(int) * n + 64 + 64 +
-                   sizeof(float) * 6 * ni + sizeof(float4) * 8 * ni + 256 * 4;
+                   sizeof(float) * 6 * ni + sizeof(float4) * 8 * ni + sizeof(float4) * ni + sizeof(unsigned) * ni +
+                   256 * 5;
     char* base = nullptr;
     cudaError_t e = cudaMalloc((void**)&base, bytes);
     if (e != cudaSuccess) {
@@ -1121,6 +1235,9 @@ static grt_bvh* alloc_bvh(int nleaf, cudaStream_t st, int* rc_out) {
     p = (char*)(((uintptr_t)p + 127) & ~(uintptr_t)127);
     b->wnodes = (float4*)p; p += sizeof(float4) * 8 * ni;
     b->bin_box = (float*)p; p += sizeof(float) * 6 * ni;
+    p = (char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    b->dp_cost = (float4*)p; p += sizeof(float4) * ni;
+    b->dp_dec = (unsigned*)p; p += sizeof(unsigned) * ni;
     b->bytes = bytes;
     e = cudaMemsetAsync(b->status, 0, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->bounds, 0, 32, st);

@@ -299,6 +299,8 @@ struct grt_bvh {
     int* sorted_ids;   // [n]
     float4* wnodes;    // [n_int * 8] 4-wide nodes
     float* bin_box;    // [n_int * 6] box of each binary node
+    float4* dp_cost;   // [n_int] collapse costs of each binary node's subtree in 1..4 slots
+    unsigned* dp_dec;  // [n_int] the splits those costs take
     int* status;       // device status word
     float* bounds;     // [6] scene bounds (device)
     size_t bytes;
