@@ -74,17 +74,17 @@ typedef struct {
  * do not depend on k, only speed does.  build_passes (0 to GRT_MAX_BUILD_PASSES) is read
  * by the tree builds only: the number of treelet-restructuring passes applied to the
  * radix tree before its 4-wide collapse (0 = the plain LBVH; each pass costs about
- * 0.5 ms per 300k surfels and lowers the traversal's node visits: 33.2 -> 26.6 -> 26.0
+ * 0.5 ms per 300k surfels and lowers the traversal's node visits: 32.4 -> 25.7 -> 25.3
  * per secondary ray on a 300k-surfel scene); like k, it changes speed, not results.
  * gbuffer_k is the k-buffer size of grt_gbuffer_primary's walk: 4, 8, 16 or 32, or 0 to
  * choose by frame size -- 32 for frames of at most GRT_GBUFFER_SMALL_FRAME pixels, k for
  * larger ones.  Most of a small frame's time is the tail of its slowest warps, which
- * fewer k-buffer rounds shorten (300k surfels, 200x200: 0.82 ms at k = 16, 0.63 ms at
- * 32; 800x800: 1.35 and 1.26 ms), while a large frame is bound by throughput, which
- * k = 16's five blocks per SM serve better (1600x1600: 3.20 against 3.71 ms).  Results
- * do not depend on it.  Typical: 1/255, 0.99, 0.01, 3e38, 1e-4, 1e-6, 16, 1, 0. */
+ * fewer k-buffer rounds shorten (300k surfels, 200x200: 0.71 ms at k = 16, 0.57 ms at
+ * 32; 800x800: 1.16 and 1.13 ms), while a large frame is bound by throughput, which
+ * k = 16's five blocks per SM serve better (1024x1024: 1.52 against 1.61 ms; 1600x1600:
+ * 2.99 against 3.46 ms).  Results do not depend on it.  Typical: 1/255, 0.99, 0.01, 3e38, 1e-4, 1e-6, 16, 1, 0. */
 #define GRT_MAX_BUILD_PASSES 4
-#define GRT_GBUFFER_SMALL_FRAME (1 << 20)
+#define GRT_GBUFFER_SMALL_FRAME (3 << 18)
 typedef struct {
     float alpha_min, alpha_max, t_min, t_max, T_min, eps_nd;
     int32_t k;

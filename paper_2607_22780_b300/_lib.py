@@ -18,7 +18,7 @@ GRT_MAX_BATCH = 48
 GRT_NOALLOC_MAX_SURFELS = 524288
 GRT_MAX_SAVED_HITS = 64
 GRT_MAX_BUILD_PASSES = 4
-GRT_GBUFFER_SMALL_FRAME = 1 << 20
+GRT_GBUFFER_SMALL_FRAME = 3 << 18
 GRT_DENOISE_MAX_RADIUS = 8
 STATUS_STACK_OVERFLOW = 1
 STATUS_NONFINITE = 2
