@@ -124,3 +124,24 @@ def test_workspace_sizes_and_checks_without_gpu():
     req = (_lib.ShadeRequest * 1)()
     rc = lib.grt_shade_batch(req, 1, ctypes.byref(p), ctypes.c_void_p((1 << 20) + 4), 1 << 20, None)
     assert rc == _lib.GRT_ERR_ARG and b"aligned" in lib.grt_last_error()
+
+
+def test_python_constants_match_the_header():
+    # every integer #define of include/grt.h that the binding mirrors has the header's value
+    import re
+    from pathlib import Path
+    hdr = (Path(__file__).resolve().parents[1] / "include" / "grt.h").read_text()
+    defines = {}
+    for name, expr in re.findall(r"^#define (GRT_\w+)\s+([^/\n]+)", hdr, flags=re.M):
+        expr = expr.strip()
+        if re.fullmatch(r"[0-9()<>\s]+", expr):
+            defines[name] = eval(expr)  # digits, shifts and parentheses only
+    assert {"GRT_OK", "GRT_MAX_BATCH", "GRT_GBUFFER_SMALL_FRAME", "GRT_STATUS_BAD_TREE"} <= set(defines)
+    mirrored = 0
+    for name, value in defines.items():
+        for py in (name, name.replace("GRT_", "", 1)):
+            if hasattr(_lib, py):
+                assert getattr(_lib, py) == value, (name, getattr(_lib, py), value)
+                mirrored += 1
+                break
+    assert mirrored >= 12
