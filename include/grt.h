@@ -102,10 +102,12 @@ typedef struct {
 } grt_bvh_info_t;
 
 /* Build a linear BVH (Morton codes of the cut-off-ellipse AABB centres, LSD radix
- * sort, hierarchy from the sorted codes, bottom-up box refit) over the surfels.  Each
- * surfel is bounded by the exact box of its alpha_min ellipse u^2+v^2 <= 2 ln(o/alpha_min)
- * (the same region the icosahedron proxy of Eq. 6 encloses), padded for FP32.  Only
- * params->alpha_min is read.  Allocates device memory; asynchronous on `stream`.
+ * sort, hierarchy from the sorted codes, bottom-up box refit, params->build_passes passes
+ * of treelet restructuring, and the collapse to 4-wide nodes by the surface-area-optimal
+ * cut) over the surfels.  Each surfel is bounded by the exact box of its alpha_min ellipse
+ * u^2+v^2 <= 2 ln(o/alpha_min) (the same region the icosahedron proxy of Eq. 6 encloses),
+ * padded for FP32.  Only params->alpha_min and params->build_passes are read.  Allocates
+ * device memory; asynchronous on `stream`.
  * *out stays valid until grt_bvh_destroy().  n == 0 is allowed (every ray misses). */
 int grt_build_bvh(const grt_surfels* surfels, const grt_trace_params* params, grt_bvh** out,
                   void* stream);
@@ -115,8 +117,9 @@ int grt_build_bvh(const grt_surfels* surfels, const grt_trace_params* params, gr
 int grt_refit_bvh(grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
                   void* stream);
 
-/* Full rebuild (Morton codes, sort, hierarchy, refit) into the existing BVH after the
- * surfels moved; same n.  Sort scratch comes from the stream-ordered pool. */
+/* Full rebuild (Morton codes, sort, hierarchy, refit, restructuring passes, collapse, as
+ * grt_build_bvh) into the existing BVH after the surfels moved; same n.  Sort scratch
+ * comes from the stream-ordered pool. */
 int grt_rebuild_bvh(grt_bvh* bvh, const grt_surfels* surfels, const grt_trace_params* params,
                     void* stream);
 
