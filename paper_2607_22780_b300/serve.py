@@ -148,10 +148,11 @@ class RelightServer:
 
     def __init__(self, scenes: Dict[str, api.Scene], device="cuda", hbm_budget: int = 8 << 30,
                  ray_budget: int = 8 << 20, max_batch: int = 16, inflight: int = 2, streams: int = 2,
-                 order: str = "fifo"):
+                 order: str = "fifo", whole_when_alone: bool = True):
         if order not in ("fifo", "srpt"):
             raise ValueError(f"order must be 'fifo' or 'srpt', got {order!r}")
         self.order = order    # slices oldest request first, or least remaining work first
+        self.whole_when_alone = bool(whole_when_alone)
         self.scenes = scenes
         self.device = torch.device(device)
         self.hbm_budget = int(hbm_budget)
@@ -181,7 +182,9 @@ class RelightServer:
         wait on the GPU: a deeper queue delays a new request's first slice behind it.
 
         Slices go to the oldest request first (order "fifo"), or to the request with the
-        fewest rays left ("srpt"), which lowers the median latency and raises the tail.  The
+        fewest rays left ("srpt"), which lowers the median latency and raises the tail.  A
+        request alone in the server with no arrival waiting runs its remaining rays as one
+        launch (whole_when_alone), as the one-at-a-time arm does.  The
         rays/s statistic counts from the end of the warm-up requests, so it holds for "fifo",
         under which they finish first."""
         dev = self.device
@@ -241,6 +244,11 @@ class RelightServer:
             # next iteration: slices up to the ray budget, oldest request first or (srpt) the
             # request with the fewest rays left first
             batch, budget = [], self.ray_budget
+            live = [st for st in active if st.next < st.P]
+            if self.whole_when_alone and len(live) == 1 and not (pending and pending[0].arrival <= now):
+                # a request alone in the server runs its remaining rays as one launch, as the
+                # one-at-a-time arm does: slicing only pays when requests share the GPU
+                budget = max(budget, (live[0].P - live[0].next) * live[0].req.rays)
             cand = active if self.order == "fifo" else sorted(active, key=lambda q: (q.P - q.next) * q.req.rays)
             for st in cand:
                 if len(batch) >= self.max_batch or budget <= 0:
