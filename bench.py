@@ -310,9 +310,9 @@ def run_grt(args):
     n_valid = int(G.valid.sum().item())
     R = n_valid * sum(ALLOC)
     # kernel launches per step: prep + Morton, 4 x (histogram, scan, scatter), hierarchy + records + refit, one per
-    # treelet-restructuring pass, collapse, G-buffer, then sample + bucket scan + ray scatter
-    # + trace + accumulate
-    launches_per_step = 2 + 12 + 3 + int(S.params.build_passes) + COLLAPSE_LAUNCHES + 1 + 5
+    # treelet-restructuring pass, collapse (cost pass + collapse), G-buffer, then sample + bucket scan (tile
+    # sums, their scan, tile scans) + ray scatter + trace + accumulate
+    launches_per_step = 2 + 12 + 3 + int(S.params.build_passes) + COLLAPSE_LAUNCHES + 1 + 7
 
     for _ in range(args.warmup):
         step()

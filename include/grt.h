@@ -246,7 +246,7 @@ typedef struct {
 /* Bytes of workspace of grt_shade_pixels and grt_shade_batch over n_rays ray slots (the
  * sum of n_pixels x N_r over the requests): direction and traced (c_rt, T) per slot (32
  * bytes), a ray counter, and the order in which the walk takes the rays (12 bytes per slot
- * and 266 KB of bucket counters).  grt_shade_pixels_save keeps directions and totals in its
+ * and 4.2 MB of bucket counters).  grt_shade_pixels_save keeps directions and totals in its
  * `saved` buffer, so this size bounds its workspace too.  0 (with the error text) for
  * n_rays < 0. */
 size_t grt_shade_workspace_size(int64_t n_rays);

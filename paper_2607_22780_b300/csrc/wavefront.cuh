@@ -77,7 +77,10 @@ __device__ __forceinline__ int pixel_of(const ShadeJob& J, int li) {
 // per ray slot.  Measured on the 300k-surfel 800x800 workload (M rays/s, whole step): slot
 // order 395; buckets of 32x32 tiles x 8x8 direction cells 416.6, 64x64 x 4x4 416.1,
 // 16x16 x 16x16 415.8, 32x32 x 16x16 416.5, 64x64 x 8x8 416.0; direction-major keys
-// 401 (the same buckets in another order); the walk itself 20.8 -> 18.85 ms.
+// 401 (the same buckets in another order); the walk itself 20.8 -> 18.85 ms.  On the current
+// walk, with the tiled bucket scan: 32x32 tiles x 8x8 / 16x16 / 32x32 direction cells: walk
+// 11.31 / 11.18 / 11.06 ms, sampling phase 0.52 / 0.53 / 0.55 ms, step 14.27 / 14.14 / 14.07
+// ms; 16x16 tiles x 32x32 cells: 14.17 ms (2^20 buckets: 4 MB of counters per call).
 #ifndef GRT_RAY_ORDER
 #define GRT_RAY_ORDER 1
 #endif
@@ -85,7 +88,7 @@ __device__ __forceinline__ int pixel_of(const ShadeJob& J, int li) {
 #define GRT_ORDER_TILE_BITS 5
 #endif
 #ifndef GRT_ORDER_DIR_BITS
-#define GRT_ORDER_DIR_BITS 3
+#define GRT_ORDER_DIR_BITS 5
 #endif
 constexpr int kTileBits = GRT_ORDER_TILE_BITS, kDirBits = GRT_ORDER_DIR_BITS;
 // Launches with fewer ray slots keep the slot order: their walk is bound by the latency of
@@ -140,17 +143,25 @@ constexpr int kJobTileBits = 3, kJobDirBits = 2;
 constexpr unsigned kJobBuckets = 1u << (2 * (kJobTileBits + kJobDirBits));
 static_assert(kJobBuckets * 64 <= kRayBuckets, "request-major buckets of up to 64 requests");
 
+// The bucket scan works in tiles of kScanTile counters: tile sums, their scan, then each
+// tile's scan from its offset.
+constexpr int kScanTile = 4096;
+constexpr unsigned kScanTiles = (kAllBuckets + kScanTile - 1) / kScanTile;
+constexpr unsigned kScanTilesPad = (kScanTiles + 3) & ~3u;
+static_assert(kScanTiles <= 1024, "the tile sums are scanned by one block of 1024 threads");
+
 // Buffers of the ray order over n slots (order_scratch_bytes(n) bytes from `base`):
-// hist[kAllBuckets] bucket counts, then exclusive offsets; per slot its bucket, its rank in
-// the bucket, and order[] = the slots bucket by bucket.
+// hist[kAllBuckets] bucket counts, then exclusive offsets; the scan's tile sums; per slot
+// its bucket, its rank in the bucket, and order[] = the slots bucket by bucket.
 struct RayOrder {
-    unsigned *hist, *key, *rank, *order;
+    unsigned *hist, *tsum, *key, *rank, *order;
 };
-inline size_t order_scratch_bytes(long long n) { return 4 * (3 * (size_t)n + kAllBuckets); }
+inline size_t order_scratch_bytes(long long n) { return 4 * (3 * (size_t)n + kAllBuckets + kScanTilesPad); }
 inline RayOrder ray_order_bufs(void* base, long long n, unsigned* order = nullptr) {
     RayOrder o;
     o.hist = static_cast<unsigned*>(base);
-    o.key = o.hist + kAllBuckets;
+    o.tsum = o.hist + kAllBuckets;
+    o.key = o.tsum + kScanTilesPad;
     o.rank = o.key + n;
     o.order = order ? order : o.rank + n;
     return o;
@@ -209,29 +220,71 @@ __global__ void __launch_bounds__(kShadeThreads) k_sample_rays(const __grid_cons
     }
 }
 
-// Exclusive scan of n counters in place, one block of 1024 threads.
-__global__ void k_bucket_scan(unsigned* __restrict__ hist, int n) {
-    __shared__ unsigned part[1024];
-    const int per = (n + 1023) / 1024, b = threadIdx.x * per;
+// Exclusive scan of the n bucket counters in place, in three launches: the sum of each tile of
+// kScanTile counters (coalesced loads), the exclusive scan of the tile sums (one block), and
+// each tile's own scan from its offset.  The offsets are exact integer prefix sums, so the ray
+// order is the same as a serial scan's.  (One block of 1,024 threads over all counters, each
+// thread walking its own run, took 54 us for 2^16 buckets and 0.2 ms for 2^18.)
+__global__ void __launch_bounds__(256) k_bucket_tile_sums(const unsigned* __restrict__ hist, int n,
+                                                          unsigned* __restrict__ tsum) {
+    __shared__ unsigned ws[8];
+    const int base = blockIdx.x * kScanTile;
     unsigned s = 0;
-    for (int k = 0; k < per; ++k)
-        if (b + k < n) s += hist[b + k];
-    part[threadIdx.x] = s;
+    for (int i = threadIdx.x; i < kScanTile; i += 256) {
+        const int k = base + i;
+        if (k < n) s += hist[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < 8; ++w) t += ws[w];
+        tsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_bucket_tile_scan(unsigned* __restrict__ tsum, int tiles) {
+    __shared__ unsigned sh[1024];
+    const unsigned v = (int)threadIdx.x < tiles ? tsum[threadIdx.x] : 0u;
+    sh[threadIdx.x] = v;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
-        const unsigned v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        const unsigned a = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : 0u;
         __syncthreads();
-        part[threadIdx.x] += v;
+        sh[threadIdx.x] += a;
         __syncthreads();
     }
-    unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-    for (int k = 0; k < per; ++k) {
-        if (b + k < n) {
-            const unsigned c = hist[b + k];
-            hist[b + k] = run;
-            run += c;
-        }
+    if ((int)threadIdx.x < tiles) tsum[threadIdx.x] = sh[threadIdx.x] - v;
+}
+
+__global__ void __launch_bounds__(256) k_bucket_tile_apply(unsigned* __restrict__ hist, int n,
+                                                           const unsigned* __restrict__ tsum) {
+    constexpr int kPer = kScanTile / 256;
+    __shared__ unsigned ws[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kPer;
+    unsigned v[kPer];
+    unsigned tot = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const unsigned c = base + k < n ? hist[base + k] : 0u;
+        v[k] = tot;
+        tot += c;
     }
+    unsigned x = tot;  // inclusive scan of the thread totals over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    unsigned off = tsum[blockIdx.x] + x - tot;
+    for (int w = 0; w < warp; ++w) off += ws[w];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+        if (base + k < n) hist[base + k] = off + v[k];
 }
 
 // order[offset of the slot's bucket + its rank] = slot (hist holds the exclusive offsets).
@@ -243,7 +296,9 @@ __global__ void k_ray_scatter(long long n, RayOrder o) {
 
 // Bucket offsets and the order, after k_sample_rays has filled hist, key and rank.
 inline void launch_ray_order(const RayOrder& o, long long n, cudaStream_t st) {
-    k_bucket_scan<<<1, 1024, 0, st>>>(o.hist, (int)kAllBuckets);
+    k_bucket_tile_sums<<<kScanTiles, 256, 0, st>>>(o.hist, (int)kAllBuckets, o.tsum);
+    k_bucket_tile_scan<<<1, 1024, 0, st>>>(o.tsum, (int)kScanTiles);
+    k_bucket_tile_apply<<<kScanTiles, 256, 0, st>>>(o.hist, (int)kAllBuckets, o.tsum);
     k_ray_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, o);
 }
 
