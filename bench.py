@@ -154,28 +154,118 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+class _Nvml:
+    """Read-only NVML queries (SM clock, its maximum, power, clock-event reasons) through the
+    driver's libnvidia-ml by ctypes, on the device whose UUID torch reports for `dev`."""
 
+    def __init__(self, dev: int):
+        import ctypes
+        import torch
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        self._ok(self.lib.nvmlInit_v2())
+        uuid = ("GPU-" + str(torch.cuda.get_device_properties(dev).uuid)).encode()
+        self.h = ctypes.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(uuid), ctypes.byref(self.h)))
+        self.reasons_fn = (getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+                           or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons)
+
+    @staticmethod
+    def _ok(rc):
+        if rc != 0:
+            raise RuntimeError(f"NVML error {rc}")
+
+    def _uint(self, fn, *args):
+        v = self.c.c_uint()
+        self._ok(fn(self.h, *args, self.c.byref(v)))
+        return v.value
+
+    def sm_mhz(self):
+        return float(self._uint(self.lib.nvmlDeviceGetClockInfo, 1))   # NVML_CLOCK_SM
+
+    def max_sm_mhz(self):
+        return float(self._uint(self.lib.nvmlDeviceGetMaxClockInfo, 1))
+
+    def power_w(self):
+        return self._uint(self.lib.nvmlDeviceGetPowerUsage) / 1000.0   # milliwatts
+
+    def reasons(self):
+        v = self.c.c_ulonglong()
+        self._ok(self.reasons_fn(self.h, self.c.byref(v)))
+        return int(v.value)
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
+class ClockSampler:
+    """SM clock, power and throttle reasons sampled during the timed region.
+
+    NVML is read from a thread every 10 ms, so a region of a few hundred milliseconds still
+    gets tens of samples; start() returns once the first sample is in.  Without NVML it falls
+    back to `nvidia-smi -lms 100`, which starts slowly and samples a short region once or
+    twice."""
+
+    # clock-event reason bits of NVML
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, dev: int, reader=None):
+        self.dev = dev
+        self.reader = reader
         self.proc = None
+        self.thread = None
+        self.samples = []
         self.path = os.path.join("/tmp", f"grt_clocks_{os.getpid()}.csv")
 
+    def _poll(self, nv, mx):
+        while not self.done.is_set():
+            try:
+                self.samples.append((nv.sm_mhz(), mx, nv.power_w(), nv.reasons()))
+            except Exception:
+                pass
+            self.first.set()
+            self.done.wait(0.01)
+
     def start(self):
+        import threading
+        try:
+            nv = self.reader if self.reader is not None else _Nvml(self.dev)
+            self.reader = nv
+            mx = nv.max_sm_mhz()
+            nv.sm_mhz(), nv.reasons(), nv.power_w()   # a failing query falls back to nvidia-smi here
+            self.done, self.first = threading.Event(), threading.Event()
+            self.thread = threading.Thread(target=self._poll, args=(nv, mx), daemon=True)
+            self.thread.start()
+            self.first.wait(2.0)
+            return
+        except Exception:
+            self.thread = None
         try:
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.done.set()
+            self.thread.join(timeout=5)
+            try:
+                self.reader.close()
+            except Exception:
+                pass
+            sm = [x[0] for x in self.samples]
+            mx = [x[1] for x in self.samples]
+            reasons = {nm for nm, bit in self.REASONS for x in self.samples if x[3] & bit}
+            return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                    "reasons": sorted(reasons), "samples": len(sm), "source": "nvml, 10 ms",
+                    "power_w_median": float(np.median([x[2] for x in self.samples])) if sm else None}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -185,7 +275,6 @@ class ClockSampler:
             self.proc.kill()
         self.f.close()
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 8:
@@ -195,12 +284,12 @@ class ClockSampler:
                 mx.append(float(parts[1]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
+            for (nm, _), v in zip(self.REASONS, parts[4:8]):
                 if v.lower() == "active":
                     reasons.add(nm)
         os.unlink(self.path)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 100 ms"}
 
 
 # ----------------------------------------------------------------------------- workload

@@ -32,3 +32,28 @@ def test_floor_is_below_the_survey_count_and_reported_beside_it():
     assert r["floor"]["survey_over_floor"] == pytest.approx(a / f)
     assert r["floor"]["ms_at_peak"] == pytest.approx(f / 6000e9 * 1e3)
     assert "floor" not in bench.roofline("k", a, a, 2.0, 6000.0, "measured")
+
+
+def test_clock_sampler_decodes_nvml_samples():
+    """The sampler's host logic on a fake NVML reader: reasons decoded from the clock-event
+    bits, the clock the median of the samples, the reader closed at the end."""
+    import time
+    import types
+
+    seq = iter([(1980.0, 0x0), (2032.0, 0x4), (2032.0, 0x4 | 0x40)] + [(2032.0, 0x0)] * 1000)
+    cur = {}
+
+    def sm():
+        cur["s"] = next(seq)
+        return cur["s"][0]
+
+    closed = []
+    fake = types.SimpleNamespace(sm_mhz=sm, max_sm_mhz=lambda: 2032.0, power_w=lambda: 900.0,
+                                 reasons=lambda: cur["s"][1], close=lambda: closed.append(1))
+    c = bench.ClockSampler(0, reader=fake)
+    c.start()
+    time.sleep(0.08)
+    r = c.stop()
+    assert r["samples"] >= 3 and r["source"].startswith("nvml") and closed == [1]
+    assert r["sm_mhz"] == 2032.0 and r["sm_max_mhz"] == 2032.0 and r["power_w_median"] == 900.0
+    assert r["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
