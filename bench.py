@@ -65,12 +65,12 @@ RAY_IO_BYTES = 44   # direction 16 + origin 12 read, (c_rt, T) 16 written
 COLLAPSE_LAUNCHES = 2  # the collapse's cost pass (bottom-up) and the 4-wide collapse (a thread per binary node)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace_rays_ww launch of the default
 # workload (k = 16, 800x800) from one ncu capture of the current kernel; None until taken
-TRACE_DRAM_BYTES = 1_187_889_152  # 848.0 MB read + 339.9 MB written
+TRACE_DRAM_BYTES = 1_187_873_280  # 847.4 MB read + 340.5 MB written
 # L2 traffic of the same kernel (lts__t_bytes.sum) per ray and the L2 throughput fraction,
-# from one ncu capture of the 256x256 case of the same step (1,031,680 rays: 4.41 GB in one
+# from one ncu capture of the 256x256 case of the same step (1,031,680 rays: 4.23 GB in one
 # launch); None until taken for the current kernel
-TRACE_L2 = {"lts_bytes_per_ray": 4_242_648_864 / 1_031_680, "lts_throughput_pct_of_peak": 16.88,
-            "lts_sector_hit_pct": 93.42, "case": "256x256, 300k surfels, 32 rays/pixel (one ncu capture)"}
+TRACE_L2 = {"lts_bytes_per_ray": 4_228_348_672 / 1_031_680, "lts_throughput_pct_of_peak": 16.22,
+            "lts_sector_hit_pct": 93.51, "case": "256x256, 300k surfels, 32 rays/pixel (one ncu capture)"}
 LARGE_N = 2_000_000          # unbounded scene: ground plane, 50 primitives, r = 50 shell
 LARGE_W, LARGE_H = 1920, 1080
 LARGE_ALLOC = (8, 4, 4)

@@ -113,14 +113,18 @@ __device__ __forceinline__ bool intersect(const float4* __restrict__ records, in
     f3 n = mk3(r1.x, r1.y, r1.z);
     f3 w = mk3(sub_d(r0.x, r.o.x), sub_d(r0.y, r.o.y), sub_d(r0.z, r.o.z));
     float num = dot_d(n, w), den = dot_d(n, r.d);
-    if (!(fabsf(den) >= P.eps_nd)) return false;
+    // every test runs the whole of Eq. 7 and decides once at the end: a hit computes the same
+    // values, a miss may divide by a tiny |n.d| (inf or NaN, which fail the checks).  Exiting
+    // at the plane and depth checks split the lanes of a warp three ways: walk 11.07 -> 10.74
+    // ms on 300k surfels at 800x800, G-buffer 1.12 -> 1.05 ms, 2M-surfel 1080p forward 65.1 ->
+    // 63.2 ms.
     float t = div_d(num, den);
-    if (!(t > P.t_min && t < P.t_max)) return false;
     f3 dp = mk3(fmaf(t, r.d.x, -w.x), fmaf(t, r.d.y, -w.y), fmaf(t, r.d.z, -w.z));
     float u = fmaf(r2.x, dp.x, fmaf(r2.y, dp.y, r2.z * dp.z));
     float v = fmaf(r3.x, dp.x, fmaf(r3.y, dp.y, r3.z * dp.z));
     float q = fmaf(u, u, v * v);
-    if (!(q <= r2.w)) return false;
+    const bool ok = (fabsf(den) >= P.eps_nd) & (t > P.t_min) & (t < P.t_max) & (q <= r2.w);
+    if (!ok) return false;
     *alpha = fminf(r0.w * __expf(-0.5f * q), P.alpha_max);
     *tau = t;
     *id = __float_as_int(r1.w);
