@@ -185,3 +185,27 @@ def test_counters_are_consistent():
     _, _, _, nh = api.trace_forward(S, t(o), t(d), max_hits=1)
     assert c[2] == int(nh.sum())          # composited hits
     assert c[1] >= c[2] and c[0] > 0
+
+
+def test_parallel_and_boundary_rays():
+    """Rays in a surfel's plane (n.d = 0 exactly, so tau is 0/0 or +-inf), before t_min and
+    behind the origin: each record test must reject them, on the walk and against the oracle.
+    Closed-form hit counts: the x ray at z = 0 meets only the x-facing surfel; the one at
+    z = 0.5 lies in the second surfel's plane and misses the x-facing one by 5 sigma; the
+    z ray from just below the first surfel starts inside t_min; the last lies in the x-facing
+    surfel's plane and passes 6 sigma from the first."""
+    from tests._handmade import Q_NX
+    sc = hand_scene([dict(mu=(0, 0, 0), opacity=0.9), dict(mu=(0, 0, 0.5), opacity=0.8),
+                     dict(mu=(0.6, 0, 0), quat=Q_NX, opacity=0.7)])
+    o = np.array([(-1, 0, 0), (-1, 0, 0.5), (0, 0, -0.005), (0, 0, -1), (0, 0, -1), (0.6, 0, -1)], np.float64)
+    d = np.array([(1, 0, 0), (1, 0, 0), (0, 0, 1), (0, 0, -1), (0, 0, 1), (0, 0, 1)], np.float64)
+    S = scene_gpu(sc, k=16)
+    rgb, op, hits, nh = api.trace_forward(S, t(o), t(d), max_hits=8)
+    ref = oracle.trace_rays(sc, o, d, max_hits=8)
+    assert ref["nhits"].tolist() == [1, 0, 1, 0, 2, 0]
+    assert nh.cpu().numpy().tolist() == [1, 0, 1, 0, 2, 0]
+    h = hits.cpu().numpy()
+    assert h[0, 0] == 2 and h[2, 0] == 1 and h[4, :2].tolist() == [0, 1]
+    assert np.abs(op.cpu().numpy() - ref["opacity"]).max() < TOL
+    assert np.abs(rgb.cpu().numpy() - ref["rgb"]).max() < TOL
+    assert S.status() == 0
